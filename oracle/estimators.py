@@ -1,0 +1,239 @@
+"""FFT series estimators of P_ell(k) and xi_ell(r) (O3), FP64, complex basis.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Every estimator follows the paper's boxed equation literally, with full complex
+``fftn`` transforms and complex spherical harmonics:
+
+  yamamoto  P: eq. Yamamoto-estimator      xi: eq. 2pcf-yama
+  midpoint  P: eq. FFT-midpoint, g from eq. g-JM-form
+            xi: eq. xi-parity-all-estimator (same g functions)
+  bisector  P: eq. bisector-pk-fft (boxed form)
+            xi: Sec. 6 boxed estimator, h summed over the B coefficients
+                before the inverse transform as Sec. 6 suggests
+  fixed     P: eq. after Sec. 2.1 (|delta(k)|^2 L_ell(k.n)); xi: eq.
+            2pcf-plane-parallel -- used only for the distant-observer pins.
+
+Discrete normalisation (the reading of Sec. 2 used throughout):
+  P_ell(k_b)  = 4 pi / A * mean_{k in b} Re[ sum_m Y_ell^m*(k) X_ell^m(k) ]
+  xi_ell(r_b) = 4 pi / (A V_cell) * mean_{Delta in b} Re[ sum_m Y_ell^m*(Delta) Z_ell^m(Delta) ]
+with A the FKP normalisation (``norm=1``) or 1 and V_cell = 1 (``norm=0``).
+The order K is the highest power of theta kept: midpoint alpha <= K, bisector
+beta <= floor(K/2).
+
+Parity pins (tests/test_oracle_estimators.py): each estimator equals the pair
+by pair evaluation of its truncated series (``oracle.pairs``) to rounding;
+midpoint K=0 equals Yamamoto; ell=0 equals across LOS; the exact pair sums are
+approached as K rises; distant-observer limit; particle pair sum (O1) equals
+the mesh pair sum (O2) on node-snapped catalogs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import mesh
+from .coeffs import B_table, f_table, phi_table
+from .special import FOUR_PI, legendre_L, ylm
+
+
+class Grid:
+    """Node, lag and Fourier grids of one mesh."""
+
+    def __init__(self, N, box_lo, box_len):
+        self.N = int(N)
+        self.box_lo = np.asarray(box_lo, dtype=np.float64)
+        self.box_len = float(box_len)
+        self.h = self.box_len / self.N
+        self.v_cell = self.h ** 3
+        self.x = mesh.node_positions(self.N, self.box_lo, self.box_len)
+        self.r = np.linalg.norm(self.x, axis=-1)
+        self.lag = mesh.lag_vectors(self.N, self.box_len)
+        self.lag_mag = mesh.lag_magnitude(self.N, self.box_len)
+        self.k = mesh.k_vectors(self.N, self.box_len)
+        self.k_mag = mesh.k_magnitude(self.N, self.box_len)
+
+
+def _flip_k(a: np.ndarray) -> np.ndarray:
+    """a(-k): the value at index (-n mod N) along every axis."""
+    return np.roll(a[::-1, ::-1, ::-1], 1, axis=(0, 1, 2))
+
+
+def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate):
+    g = Grid(N, box_lo, box_len)
+    delta, _ = mesh.density_mesh(gal, ran, g.N, g.box_lo, g.box_len, assign)
+    if norm:
+        _, A = mesh.norm_factors(gal, ran, ran_nbar)
+        if A is None:
+            raise ValueError("norm=1 needs randoms with nbar")
+        v_cell = g.v_cell
+    else:
+        A, v_cell = 1.0, 1.0
+    inv_w = 1.0 / mesh.compensation(g.N, assign) if compensate else None
+    return g, delta, A, v_cell, inv_w
+
+
+def _fwd(field, inv_w):
+    """Forward transform of a painted-derived field, with the optional 1/W(k)."""
+    F = mesh.fftn(field)
+    return F * inv_w if inv_w is not None else F
+
+
+def _ells(ell_max):
+    if ell_max < 0 or ell_max % 2:
+        raise ValueError("only even ell_max is supported (the paper assumes even ell)")
+    return list(range(0, ell_max + 1, 2))
+
+
+def _pk_out(g, ells, T, A, kedges):
+    pk, kmean, cnt = [], None, None
+    for ell in ells:
+        mean, kmean, cnt = mesh.shell_mean(T[ell], g.k_mag, kedges, g.k_mag == 0.0)
+        pk.append(FOUR_PI / A * mean)
+    return {"ells": ells, "pk": np.array(pk), "k_mean": kmean, "n_modes": cnt}
+
+
+def _xi_out(g, ells, Z, A, v_cell, redges):
+    xi, rmean, cnt = [], None, None
+    for ell in ells:
+        mean, rmean, cnt = mesh.shell_mean(Z[ell], g.lag_mag, redges, g.lag_mag == 0.0)
+        xi.append(FOUR_PI / (A * v_cell) * mean)
+    return {"ells": ells, "xi": np.array(xi), "r_mean": rmean, "n_cells": cnt}
+
+
+# --------------------------------------------------------------------------
+# midpoint convolution fields g^alpha_JM (eq. g-JM-form)
+# --------------------------------------------------------------------------
+def g_fields(g: Grid, delta, D, K, ell_max, inv_w):
+    """g^alpha_JM(Delta) = (-1)^J IFFT[ delta*(k) F[(2r)^-alpha Y_J^M delta](k) ](Delta)
+    for alpha <= K and J = alpha, alpha-2, ... <= ell_max + alpha (the J with
+    non-zero phi / f for even ell).  Cells with delta = 0 carry no field; a
+    non-empty cell at the observer has no expansion and is rejected."""
+    if np.any((g.r == 0.0) & (delta != 0.0)):
+        raise ValueError("a non-empty mesh node sits on the observer")
+    Dc = np.conj(D)
+    safe_r = np.where(g.r == 0.0, 1.0, g.r)
+    out = {}
+    for alpha in range(K + 1):
+        radial = np.where(delta != 0.0, (2.0 * safe_r) ** (-alpha), 0.0) * delta
+        for J in range(alpha % 2, ell_max + alpha + 1, 2):
+            for M in range(-J, J + 1):
+                F = _fwd(radial * ylm(J, M, g.x), inv_w)
+                out[(alpha, J, M)] = (-1) ** J * mesh.ifftn(Dc * F)
+    return out
+
+
+# --------------------------------------------------------------------------
+# public entry points (mirror the library's pk_multipoles / xi_multipoles)
+# --------------------------------------------------------------------------
+def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
+                  order, kedges, compensate=False, norm=1):
+    """P_ell(k) for ell = 0, 2, .., ell_max with LOS in
+    {'yamamoto', 'midpoint', 'bisector', 'fixed'}."""
+    g, delta, A, _, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
+                                     assign, norm, compensate)
+    ells = _ells(ell_max)
+    D = _fwd(delta, inv_w)
+    T = {}
+    if los == "yamamoto":
+        # eq. Yamamoto-estimator: sum_m Y*(k) F[Y delta](k) delta*(k)
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for m in range(-ell, ell + 1):
+                F = _fwd(ylm(ell, m, g.x) * delta, inv_w)
+                acc += np.conj(ylm(ell, m, g.k)) * F * np.conj(D)
+            T[ell] = acc.real
+    elif los == "midpoint":
+        # eq. FFT-midpoint: sum_m Y*(k) sum phi F[ Y_J1^M(Delta) Delta^alpha g^alpha_{J2 (m-M)}(Delta) ](k)
+        gf = g_fields(g, delta, D, order, ell_max, inv_w)
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for m in range(-ell, ell + 1):
+                H = np.zeros(D.shape, dtype=np.complex128)
+                for alpha in range(order + 1):
+                    dpow = g.lag_mag ** alpha
+                    for (J1, J2, M), c in phi_table(alpha, ell, m).items():
+                        H += c * ylm(J1, M, g.lag) * dpow * gf[(alpha, J2, m - M)]
+                acc += np.conj(ylm(ell, m, g.k)) * mesh.fftn(H)
+            T[ell] = acc.real
+    elif los == "bisector":
+        # eq. bisector-pk-fft: sum_m Y*(k) sum B F[Y_J1^M delta](-k) F[Y_J2^{m-M} delta](k)
+        bmax = order // 2
+        Jmax = ell_max + bmax
+        F = {(J, M): _fwd(ylm(J, M, g.x) * delta, inv_w)
+             for J in range(Jmax + 1) for M in range(-J, J + 1)}
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for m in range(-ell, ell + 1):
+                X = np.zeros(D.shape, dtype=np.complex128)
+                for beta in range(bmax + 1):
+                    for (J1, J2, M), c in B_table(beta, ell, m).items():
+                        X += c * _flip_k(F[(J1, M)]) * F[(J2, m - M)]
+                acc += np.conj(ylm(ell, m, g.k)) * X
+            T[ell] = acc.real
+    elif los == "fixed":
+        # |delta(k)|^2 L_ell(k . n) with n = the direction of the box centre
+        n = g.box_lo + 0.5 * g.box_len
+        n = n / np.linalg.norm(n)
+        mu = np.where(g.k_mag > 0, (g.k @ n) / np.where(g.k_mag > 0, g.k_mag, 1.0), 0.0)
+        for ell in ells:
+            T[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * np.abs(D) ** 2
+    else:
+        raise ValueError(f"unknown los {los!r}")
+    return _pk_out(g, ells, T, A, kedges)
+
+
+def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
+                  order, redges, compensate=False, norm=1):
+    """xi_ell(r) for ell = 0, 2, .., ell_max with LOS in
+    {'yamamoto', 'midpoint', 'bisector', 'fixed'}."""
+    g, delta, A, v_cell, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
+                                          assign, norm, compensate)
+    ells = _ells(ell_max)
+    D = _fwd(delta, inv_w)
+    Z = {}
+    if los == "yamamoto":
+        # eq. 2pcf-yama: sum_m Y*(Delta) IFFT[delta*(k) F[Y delta](k)](Delta)
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for m in range(-ell, ell + 1):
+                F = _fwd(ylm(ell, m, g.x) * delta, inv_w)
+                acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(np.conj(D) * F)
+            Z[ell] = acc.real
+    elif los == "midpoint":
+        # eq. xi-parity-all-estimator: sum f Y_J^M*(Delta) Delta^alpha g^alpha_JM(Delta)
+        gf = g_fields(g, delta, D, order, ell_max, inv_w)
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for alpha in range(order + 1):
+                dpow = g.lag_mag ** alpha
+                for J, c in f_table(alpha, ell).items():
+                    for M in range(-J, J + 1):
+                        acc += c * np.conj(ylm(J, M, g.lag)) * dpow * gf[(alpha, J, M)]
+            Z[ell] = acc.real
+    elif los == "bisector":
+        # Sec. 6: sum_m Y*(Delta) IFFT[ sum B F[Y_J1^M delta](-k) F[Y_J2^{m-M} delta](k) ](Delta)
+        bmax = order // 2
+        Jmax = ell_max + bmax
+        F = {(J, M): _fwd(ylm(J, M, g.x) * delta, inv_w)
+             for J in range(Jmax + 1) for M in range(-J, J + 1)}
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for m in range(-ell, ell + 1):
+                X = np.zeros(D.shape, dtype=np.complex128)
+                for beta in range(bmax + 1):
+                    for (J1, J2, M), c in B_table(beta, ell, m).items():
+                        X += c * _flip_k(F[(J1, M)]) * F[(J2, m - M)]
+                acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(X)
+            Z[ell] = acc.real
+    elif los == "fixed":
+        n = g.box_lo + 0.5 * g.box_len
+        n = n / np.linalg.norm(n)
+        mu = np.where(g.lag_mag > 0, (g.lag @ n) / np.where(g.lag_mag > 0, g.lag_mag, 1.0), 0.0)
+        c = mesh.ifftn(np.abs(D) ** 2).real
+        for ell in ells:
+            Z[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * c
+    else:
+        raise ValueError(f"unknown los {los!r}")
+    return _xi_out(g, ells, Z, A, v_cell, redges)

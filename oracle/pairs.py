@@ -1,0 +1,201 @@
+"""Brute-force pair sums: the exact pairwise-LOS estimators (no series).
+
+Test infrastructure only (see ``oracle/__init__``).
+
+* O2, ``mesh_pk`` / ``mesh_xi``: every ordered pair of occupied mesh nodes
+  (a, b) with lag Delta = minimal-image(x_b - x_a) and the exact line of sight
+  of Sec. 2 (eq. P-ell-midpoint-init, eq. 2pcf-pair):
+      yamamoto  n = hat x_b                         (eq. Yamamoto-estimator)
+      midpoint  n = hat(x_a + x_b)
+      bisector  n = hat(hat x_a + hat x_b)
+  P_ell(k) = 4 pi / A mean_shell Re sum_m Y_ell^m*(k) DFT[G_ell^m](k) with
+  G_ell^m(Delta) = sum_{pairs at Delta} delta_a delta_b Y_ell^m(n)  (addition
+  theorem, eq. addition-theorem); xi_ell(r_b) = (2 ell + 1) / (A V_cell N_b)
+  sum_{pairs, |Delta| in b, Delta != 0} delta_a delta_b L_ell(hat Delta . n).
+  With ``series=K`` the exact Y_ell^m(n) / L_ell(hat Delta . n) is replaced by
+  its truncated expansion taken pair by pair (midpoint: eq. Ylm-shift-theorem
+  around A = 2 x_b, a = -Delta, and eq. Legendre-shift-theorem-all-parity;
+  bisector: eq. bisector-ylm-expan and eq. bisector-leg-expan).
+* O1, ``particle_xi``: the same xi_ell sum over distinct particle pairs
+  (weights w and -alpha_r w), no mesh, no periodic wrap; binned with the mesh
+  lag-cell counts N_b so that node-snapped catalogs give O2 exactly.
+
+Pins: tests/test_oracle_estimators.py (O1 == O2 on node-snapped CIC
+catalogs; O2 with the truncated series == the FFT estimators to rounding).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mesh
+from .coeffs import B_table, f_table, phi_table
+from .special import FOUR_PI, legendre_L, ylm
+
+
+def _occupied(delta, N, box_lo, box_len):
+    idx = np.argwhere(delta != 0.0)
+    h = box_len / N
+    x = np.asarray(box_lo, dtype=np.float64)[None, :] + idx * h
+    return idx, x, delta[delta != 0.0]
+
+
+def _pairs(idx, x, d, N, box_len):
+    n = len(d)
+    ia = np.repeat(np.arange(n), n)
+    ib = np.tile(np.arange(n), n)
+    j = (idx[ib] - idx[ia] + N // 2) % N - N // 2          # minimal-image lag labels
+    lag = j * (box_len / N)
+    flat = np.ravel_multi_index(tuple((j % N).T), (N, N, N))
+    return ia, ib, lag, flat, d[ia] * d[ib]
+
+
+def _unit(v):
+    n = np.linalg.norm(v, axis=-1, keepdims=True)
+    return v / np.where(n == 0.0, 1.0, n)
+
+
+def _los(los, xa, xb):
+    if los == "yamamoto":
+        return xb
+    if los == "midpoint":
+        return xa + xb
+    if los == "bisector":
+        return _unit(xa) + _unit(xb)
+    raise ValueError(los)
+
+
+def _ylm_pair(los, ell, m, xa, xb, lag, series):
+    """Y_ell^m of the pair's line of sight, exact or its truncated series."""
+    if series is None or los == "yamamoto":
+        return ylm(ell, m, _los(los, xa, xb))
+    if los == "midpoint":
+        # R = x_a + x_b = 2 x_b - Delta: a = -Delta, A = 2 x_b (eq. Ylm-shift-theorem)
+        eps = np.linalg.norm(lag, axis=-1) / (2.0 * np.linalg.norm(xb, axis=-1))
+        out = np.zeros(len(xb), dtype=np.complex128)
+        for alpha in range(series + 1):
+            for (J1, J2, M), c in phi_table(alpha, ell, m).items():
+                out += c * eps ** alpha * ylm(J1, M, -lag) * ylm(J2, m - M, xb)
+        return out
+    if los == "bisector":
+        out = np.zeros(len(xb), dtype=np.complex128)
+        for beta in range(series // 2 + 1):
+            for (J1, J2, M), c in B_table(beta, ell, m).items():
+                out += c * ylm(J1, M, xa) * ylm(J2, m - M, xb)
+        return out
+    raise ValueError(los)
+
+
+def _legendre_pair(los, ell, xa, xb, lag, series):
+    """L_ell(hat Delta . n) of the pair, exact or its truncated series."""
+    if series is None or los == "yamamoto":
+        n = _unit(_los(los, xa, xb))
+        mu = np.sum(_unit(lag) * n, axis=-1)
+        return legendre_L(ell, mu)
+    if los == "midpoint":
+        # L_ell(hat Delta . hat R) = L_ell(hat a . hat(a + A)), a = -Delta, A = 2 x_b (even ell)
+        eps = np.linalg.norm(lag, axis=-1) / (2.0 * np.linalg.norm(xb, axis=-1))
+        mu = np.sum(_unit(-lag) * _unit(xb), axis=-1)
+        out = np.zeros(len(xb))
+        for alpha in range(series + 1):
+            for J, c in f_table(alpha, ell).items():
+                out += (2 * J + 1) / (2 * ell + 1) * c * eps ** alpha * legendre_L(J, mu)
+        return out
+    if los == "bisector":
+        # eq. bisector-leg-expan
+        out = np.zeros(len(xb), dtype=np.complex128)
+        for m in range(-ell, ell + 1):
+            out += np.conj(ylm(ell, m, lag)) * _ylm_pair(los, ell, m, xa, xb, lag, series)
+        return (FOUR_PI / (2 * ell + 1) * out).real
+    raise ValueError(los)
+
+
+def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, kedges,
+            norm=1, series=None):
+    """O2 power-spectrum multipoles from explicit pairs of occupied nodes."""
+    delta, _ = mesh.density_mesh(gal, ran, N, box_lo, box_len, assign)
+    A = mesh.norm_factors(gal, ran, ran_nbar)[1] if norm else 1.0
+    idx, x, d = _occupied(delta, N, box_lo, box_len)
+    ia, ib, lag, flat, w = _pairs(idx, x, d, N, box_len)
+    xa, xb = x[ia], x[ib]
+    kv = mesh.k_vectors(N, box_len)
+    kmag = mesh.k_magnitude(N, box_len)
+    ells = list(range(0, ell_max + 1, 2))
+    pk, kmean, cnt = [], None, None
+    for ell in ells:
+        acc = np.zeros((N, N, N), dtype=np.complex128)
+        for m in range(-ell, ell + 1):
+            G = np.zeros(N * N * N, dtype=np.complex128)
+            np.add.at(G, flat, w * _ylm_pair(los, ell, m, xa, xb, lag, series))
+            acc += np.conj(ylm(ell, m, kv)) * mesh.fftn(G.reshape(N, N, N))
+        mean, kmean, cnt = mesh.shell_mean(acc.real, kmag, kedges, kmag == 0.0)
+        pk.append(FOUR_PI / A * mean)
+    return {"ells": ells, "pk": np.array(pk), "k_mean": kmean, "n_modes": cnt}
+
+
+def mesh_xi(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, redges,
+            norm=1, series=None):
+    """O2 correlation-function multipoles from explicit pairs of occupied nodes."""
+    delta, _ = mesh.density_mesh(gal, ran, N, box_lo, box_len, assign)
+    if norm:
+        A = mesh.norm_factors(gal, ran, ran_nbar)[1]
+        v_cell = (box_len / N) ** 3
+    else:
+        A, v_cell = 1.0, 1.0
+    idx, x, d = _occupied(delta, N, box_lo, box_len)
+    ia, ib, lag, flat, w = _pairs(idx, x, d, N, box_len)
+    lmag = np.linalg.norm(lag, axis=-1)
+    redges = np.asarray(redges, dtype=np.float64)
+    b = mesh.shell_index(lmag, redges)
+    b[lmag == 0.0] = -1
+    sel = b >= 0
+    lagmag_grid = mesh.lag_magnitude(N, box_len)
+    _, rmean, ncell = mesh.shell_mean(np.zeros_like(lagmag_grid), lagmag_grid, redges,
+                                      lagmag_grid == 0.0)
+    ells = list(range(0, ell_max + 1, 2))
+    nb = len(redges) - 1
+    xi = []
+    for ell in ells:
+        L = _legendre_pair(los, ell, x[ia][sel], x[ib][sel], lag[sel], series)
+        s = np.bincount(b[sel], weights=w[sel] * L, minlength=nb)
+        xi.append(np.where(ncell > 0, (2 * ell + 1) * s / (A * v_cell * np.maximum(ncell, 1)), 0.0))
+    return {"ells": ells, "xi": np.array(xi), "r_mean": rmean, "n_cells": ncell}
+
+
+def particle_xi(gal, ran, ran_nbar, *, N, box_lo, box_len, ell_max, los, redges, norm=1):
+    """O1: xi_ell from distinct particle pairs (eq. 2pcf-pair with the bin
+    replacement of Sec. 2.2, bin volume v_b = N_b V_cell from the mesh)."""
+    alpha, A = mesh.norm_factors(gal, ran, ran_nbar)
+    parts = [np.asarray(gal, dtype=np.float64)]
+    wts = [parts[0][:, 3]]
+    if ran is not None and len(ran):
+        r = np.asarray(ran, dtype=np.float64)
+        parts.append(r)
+        wts.append(-alpha * r[:, 3])
+    p = np.concatenate(parts)[:, :3]
+    w = np.concatenate(wts)
+    if not norm:
+        A, v_cell = 1.0, 1.0
+    else:
+        v_cell = (box_len / N) ** 3
+    n = len(w)
+    ia = np.repeat(np.arange(n), n)
+    ib = np.tile(np.arange(n), n)
+    keep = ia != ib
+    ia, ib = ia[keep], ib[keep]
+    lag = p[ib] - p[ia]
+    lmag = np.linalg.norm(lag, axis=-1)
+    redges = np.asarray(redges, dtype=np.float64)
+    b = mesh.shell_index(lmag, redges)
+    b[lmag == 0.0] = -1
+    sel = b >= 0
+    lagmag_grid = mesh.lag_magnitude(N, box_len)
+    _, _, ncell = mesh.shell_mean(np.zeros_like(lagmag_grid), lagmag_grid, redges,
+                                  lagmag_grid == 0.0)
+    ells = list(range(0, ell_max + 1, 2))
+    nb = len(redges) - 1
+    xi = []
+    for ell in ells:
+        L = _legendre_pair(los, ell, p[ia][sel], p[ib][sel], lag[sel], None)
+        s = np.bincount(b[sel], weights=(w[ia] * w[ib])[sel] * L, minlength=nb)
+        xi.append(np.where(ncell > 0, (2 * ell + 1) * s / (A * v_cell * np.maximum(ncell, 1)), 0.0))
+    return {"ells": ells, "xi": np.array(xi), "n_cells": ncell}
