@@ -1,0 +1,142 @@
+/*
+ * bym.h -- C ABI of the GB300 (sm_103a) pairwise line-of-sight multipole library.
+ *
+ * Power-spectrum multipoles P_ell(k) and correlation-function multipoles
+ * xi_ell(r) of a galaxy catalog with random catalog, for the line-of-sight
+ * choices of Philcox & Slepian, "Beyond Yamamoto" (arXiv:2102.08384):
+ *
+ *   BYM_LOS_YAMAMOTO  n = hat r_2                 Sec. 2, eq. Yamamoto-estimator / eq. 2pcf-yama
+ *   BYM_LOS_MIDPOINT  n = hat(r_1 + r_2)          Secs. 3-4, eq. FFT-midpoint / eq. xi-parity-all-estimator
+ *   BYM_LOS_BISECTOR  n = hat(hat r_1 + hat r_2)  Secs. 5-6, eq. bisector-pk-fft / Sec. 6 boxed estimator
+ *
+ * expanded to order K in the pair opening angle theta ("order"): the midpoint
+ * series keeps alpha <= K (eq. Ylm-shift-theorem, eq. Legendre-shift-theorem-
+ * all-parity), the bisector series keeps beta <= floor(K/2) (eq.
+ * bisector-ylm-expan, beta <-> theta^(2 beta)).  Only even ell are returned
+ * (ell = 0, 2, .., ell_max), as the paper assumes (Sec. 3.2).
+ *
+ * Conventions shared by every entry point:
+ *   - The observer sits at the origin.  Mesh node i (per axis) is at
+ *     box_lo + i * box_len / n_mesh; the mesh is periodic.
+ *   - delta = paint(galaxies, w) - alpha_r paint(randoms, w), alpha_r =
+ *     sum w_g / sum w_r (Sec. 2.1); CIC (assign = 2) or TSC (assign = 3).
+ *   - Forward transforms use e^{-i k.x} (Sec. 2, first equation).
+ *   - |k| = (2 pi / box_len) sqrt(n.n), |Delta| = (box_len / n_mesh) sqrt(j.j)
+ *     with integer labels n, j in [-n_mesh/2, n_mesh/2); a bin b collects
+ *     magnitudes in [edges[b], edges[b+1]); k = 0 and Delta = 0 never enter.
+ *   - Normalisation (norm = 1): P_ell = 4 pi / A * (bin mean), xi_ell =
+ *     4 pi / (A V_cell) * (bin mean), A = alpha_r sum_r nbar_r w_r^2 (FKP);
+ *     norm = 0 sets A = V_cell = 1.
+ *   - Outputs are host arrays owned by the caller, laid out [ell/2][bin].
+ *   - Calls are synchronous on the given CUDA stream (NULL: the context's
+ *     stream) unless submitted through bym_submit.
+ *
+ * Every function returns BYM_OK (0) or a negative BYM_E_* code; the message
+ * of the last failure on a context is available from bym_last_error.  A
+ * context is not thread-safe except for bym_submit / bym_poll / bym_wait.
+ */
+#ifndef BYM_H
+#define BYM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BYM_OK = 0,
+  BYM_E_INVAL = -1,        /* bad argument (null pointer, bad size, unsorted edges, ...) */
+  BYM_E_OUT_OF_BOX = -2,   /* a particle lies outside [box_lo, box_lo + box_len) or is not finite */
+  BYM_E_NOMEM = -3,        /* device allocation failed or the request exceeds the HBM budget */
+  BYM_E_CUDA = -4,         /* CUDA runtime / cuFFT / NVRTC failure */
+  BYM_E_TIMEOUT = -5,      /* bym_wait deadline passed (the request keeps running) */
+  BYM_E_UNSUPPORTED = -6,  /* odd ell_max, order > 12, ell_max > 8, n_mesh out of range */
+  BYM_E_BUSY = -7          /* no free serving slot */
+};
+
+typedef enum { BYM_LOS_YAMAMOTO = 0, BYM_LOS_MIDPOINT = 1, BYM_LOS_BISECTOR = 2 } bym_los;
+
+typedef struct bym_ctx bym_ctx;
+
+/* A catalog: n objects as (x, y, z, w) float quadruples, row major, and an
+ * optional per-object nbar (needed for the randoms when norm = 1).
+ * on_device = 1: the pointers are device pointers of the context's GPU.
+ * The caller owns the memory; it is only read during the call. */
+typedef struct {
+  const float *xyzw;
+  const float *nbar;
+  int64_t n;
+  int on_device;
+} bym_catalog;
+
+typedef struct {
+  double box_lo[3];   /* position of mesh node (0,0,0) */
+  double box_len;     /* cubic box side */
+  int n_mesh;         /* N, even, 8 <= N <= 1024 */
+  int assign;         /* 2 = CIC, 3 = TSC */
+  int ell_max;        /* even, 0..8 */
+  int los;            /* bym_los */
+  int order;          /* K = highest power of theta kept, 0..12 */
+  int compensate;     /* 1: divide each painted-field transform by the assignment window W(k) */
+  int precision;      /* 32: FP32 fields and FFTs; 64: FP64 throughout. Shell sums are FP64 either way */
+  int norm;           /* 1: FKP normalisation A; 0: raw (A = V_cell = 1) */
+} bym_params;
+
+typedef struct {
+  const double *edges;   /* nbins + 1 increasing edges, host memory */
+  int nbins;             /* 1..4096 */
+} bym_bins;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the context may hold for requests (0: all free memory).
+ * *out receives the context (NULL on failure). */
+int bym_create(bym_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context: waits for its work, frees its memory, plans and kernels. */
+void bym_destroy(bym_ctx *ctx);
+
+/* Message of the last failure on ctx (owned by ctx, valid until the next call). */
+const char *bym_last_error(const bym_ctx *ctx);
+
+/* Library version string (static storage). */
+const char *bym_version(void);
+
+/* Projected device bytes one request with these parameters and catalog
+ * sizes holds at its peak (the admission test of the serving loop). */
+int bym_footprint(const bym_params *p, int64_t n_gal, int64_t n_ran, int want_pk, int want_xi,
+                  size_t *bytes);
+
+/* Power-spectrum multipoles, Sec. 2 eq. Pk-def with the LOS of p->los:
+ *   pk[(ell/2) * nbins + b]  P_ell in bin b
+ *   k_mean[b]                mean |k| of the modes in bin b (may be NULL)
+ *   n_modes[b]               number of modes in bin b, full grid (may be NULL)
+ * ran may be NULL (no randoms, alpha_r = 0; requires norm = 0). */
+int bym_pk_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran,
+                      const bym_params *p, const bym_bins *kbins, double *pk,
+                      double *k_mean, int64_t *n_modes, void *cuda_stream);
+
+/* Correlation-function multipoles, Sec. 2.2 eq. general-2pcf-form with the bin
+ * replacement Theta^a / v^a, v^a = n_cells * V_cell:
+ *   xi[(ell/2) * nbins + b], r_mean[b], n_cells[b] (last two may be NULL). */
+int bym_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran,
+                      const bym_params *p, const bym_bins *rbins, double *xi,
+                      double *r_mean, int64_t *n_cells, void *cuda_stream);
+
+/* Both at once from one painting and one set of fields (the midpoint g
+ * functions of eq. g-JM-form and the bisector transforms F[Y_J^M delta] serve
+ * P and xi alike).  Same output conventions as the two calls above. */
+int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran,
+                         const bym_params *p, const bym_bins *kbins, const bym_bins *rbins,
+                         double *pk, double *k_mean, int64_t *n_modes,
+                         double *xi, double *r_mean, int64_t *n_cells, void *cuda_stream);
+
+/* Compile (without running) the runtime-specialised kernels for these
+ * parameters; works without a GPU.  Used by build checks. */
+int bym_jit_check(const bym_params *p, char *log, size_t log_len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BYM_H */

@@ -1,0 +1,234 @@
+"""Pairwise line-of-sight power-spectrum and correlation-function multipoles on GB300.
+
+Thin ctypes binding of the C ABI in ``include/bym.h`` (library ``libbym.so``,
+built in-tree by ``paper_2102_08384_gb300.build``).  This module only
+marshals arguments: every step of the estimators runs in the library's CUDA
+kernels.  Catalogs are (n, 4) float32 arrays of x, y, z, w -- numpy arrays
+(host memory) or CUDA torch tensors (device memory) -- with optional float32
+nbar arrays.
+
+Estimators (Philcox & Slepian, arXiv:2102.08384):
+  los="yamamoto"  Sec. 2, eq. Yamamoto-estimator / eq. 2pcf-yama
+  los="midpoint"  Secs. 3-4, eq. FFT-midpoint / eq. xi-parity-all-estimator
+  los="bisector"  Secs. 5-6, eq. bisector-pk-fft / the Sec. 6 estimator
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbym.so")
+
+LOS = {"yamamoto": 0, "midpoint": 1, "bisector": 2}
+
+BYM_OK = 0
+ERRORS = {-1: "INVAL", -2: "OUT_OF_BOX", -3: "NOMEM", -4: "CUDA", -5: "TIMEOUT", -6: "UNSUPPORTED",
+          -7: "BUSY"}
+
+
+class BymError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bym error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Catalog(ctypes.Structure):
+    _fields_ = [("xyzw", ctypes.c_void_p), ("nbar", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("on_device", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("box_lo", ctypes.c_double * 3), ("box_len", ctypes.c_double), ("n_mesh", ctypes.c_int),
+                ("assign", ctypes.c_int), ("ell_max", ctypes.c_int), ("los", ctypes.c_int),
+                ("order", ctypes.c_int), ("compensate", ctypes.c_int), ("precision", ctypes.c_int),
+                ("norm", ctypes.c_int)]
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("edges", ctypes.c_void_p), ("nbins", ctypes.c_int)]
+
+
+_lib_handle = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+        L.bym_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t]
+        L.bym_destroy.argtypes = [vp]
+        L.bym_destroy.restype = None
+        L.bym_last_error.argtypes = [vp]
+        L.bym_last_error.restype = ctypes.c_char_p
+        L.bym_version.restype = ctypes.c_char_p
+        L.bym_footprint.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+        cat_p, par_p, bins_p = ctypes.POINTER(Catalog), ctypes.POINTER(Params), ctypes.POINTER(Bins)
+        L.bym_pk_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, dp, dp, i64p, vp]
+        L.bym_xi_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, dp, dp, i64p, vp]
+        L.bym_pk_xi_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, dp, dp, i64p, dp, dp, i64p,
+                                           vp]
+        L.bym_jit_check.argtypes = [par_p, ctypes.c_char_p, ctypes.c_size_t]
+        _lib_handle = L
+    return _lib_handle
+
+
+def make_params(*, box_lo, box_len, n_mesh, assign=2, ell_max=4, los="yamamoto", order=0,
+                compensate=False, precision=32, norm=1) -> Params:
+    p = Params()
+    p.box_lo[:] = [float(v) for v in box_lo]
+    p.box_len = float(box_len)
+    p.n_mesh = int(n_mesh)
+    p.assign = int(assign)
+    p.ell_max = int(ell_max)
+    p.los = LOS[los] if isinstance(los, str) else int(los)
+    p.order = int(order)
+    p.compensate = int(bool(compensate))
+    p.precision = int(precision)
+    p.norm = int(norm)
+    return p
+
+
+def _catalog(xyzw, nbar, keep):
+    """Catalog struct for a numpy (host) or CUDA torch (device) array."""
+    c = Catalog()
+    if xyzw is None:
+        return None
+    if hasattr(xyzw, "is_cuda") and xyzw.is_cuda:
+        import torch
+        assert xyzw.dtype == torch.float32 and xyzw.dim() == 2 and xyzw.shape[1] == 4
+        xyzw = xyzw.contiguous()
+        keep.append(xyzw)
+        c.xyzw, c.n, c.on_device = xyzw.data_ptr(), xyzw.shape[0], 1
+        if nbar is not None:
+            nbar = nbar.contiguous().to(torch.float32)
+            keep.append(nbar)
+            c.nbar = nbar.data_ptr()
+        return c
+    a = np.ascontiguousarray(xyzw, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 4:
+        raise ValueError("catalog must be (n, 4) float32")
+    keep.append(a)
+    c.xyzw, c.n, c.on_device = a.ctypes.data, a.shape[0], 0
+    if nbar is not None:
+        nb = np.ascontiguousarray(nbar, dtype=np.float32)
+        keep.append(nb)
+        c.nbar = nb.ctypes.data
+    return c
+
+
+def _bins(edges, keep):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    keep.append(e)
+    b = Bins()
+    b.edges, b.nbins = e.ctypes.data, len(e) - 1
+    return b
+
+
+def _ptr(obj):
+    return ctypes.byref(obj) if obj is not None else None
+
+
+class Context:
+    """One library context on a CUDA device (plans, tables and kernels cached)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._L = lib()
+        h = ctypes.c_void_p()
+        rc = self._L.bym_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if rc != BYM_OK:
+            raise BymError(rc, "bym_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.bym_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != BYM_OK:
+            raise BymError(rc, self._L.bym_last_error(self._h).decode())
+
+    def _run(self, which, gal, ran, params, kedges, redges, gal_nbar, ran_nbar, stream):
+        keep = []
+        g = _catalog(gal, gal_nbar, keep)
+        r = _catalog(ran, ran_nbar, keep)
+        nl = params.ell_max // 2 + 1
+        out = {}
+        st = ctypes.c_void_p(stream) if stream else None
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        if kedges is not None:
+            kb = _bins(kedges, keep)
+            nbk = kb.nbins
+            out["pk"] = np.zeros((nl, nbk))
+            out["k_mean"] = np.zeros(nbk)
+            out["n_modes"] = np.zeros(nbk, dtype=np.int64)
+        if redges is not None:
+            rb = _bins(redges, keep)
+            nbr = rb.nbins
+            out["xi"] = np.zeros((nl, nbr))
+            out["r_mean"] = np.zeros(nbr)
+            out["n_cells"] = np.zeros(nbr, dtype=np.int64)
+        if which == "pk":
+            rc = self._L.bym_pk_multipoles(self._h, _ptr(g), _ptr(r), ctypes.byref(params), ctypes.byref(kb),
+                                           out["pk"].ctypes.data_as(dp), out["k_mean"].ctypes.data_as(dp),
+                                           out["n_modes"].ctypes.data_as(i64p), st)
+        elif which == "xi":
+            rc = self._L.bym_xi_multipoles(self._h, _ptr(g), _ptr(r), ctypes.byref(params), ctypes.byref(rb),
+                                           out["xi"].ctypes.data_as(dp), out["r_mean"].ctypes.data_as(dp),
+                                           out["n_cells"].ctypes.data_as(i64p), st)
+        else:
+            rc = self._L.bym_pk_xi_multipoles(self._h, _ptr(g), _ptr(r), ctypes.byref(params), ctypes.byref(kb),
+                                              ctypes.byref(rb), out["pk"].ctypes.data_as(dp),
+                                              out["k_mean"].ctypes.data_as(dp),
+                                              out["n_modes"].ctypes.data_as(i64p), out["xi"].ctypes.data_as(dp),
+                                              out["r_mean"].ctypes.data_as(dp),
+                                              out["n_cells"].ctypes.data_as(i64p), st)
+        self._check(rc)
+        out["ells"] = list(range(0, params.ell_max + 1, 2))
+        return out
+
+    def pk_multipoles(self, gal, ran, params, kedges, gal_nbar=None, ran_nbar=None, stream=None):
+        return self._run("pk", gal, ran, params, kedges, None, gal_nbar, ran_nbar, stream)
+
+    def xi_multipoles(self, gal, ran, params, redges, gal_nbar=None, ran_nbar=None, stream=None):
+        return self._run("xi", gal, ran, params, None, redges, gal_nbar, ran_nbar, stream)
+
+    def pk_xi_multipoles(self, gal, ran, params, kedges, redges, gal_nbar=None, ran_nbar=None, stream=None):
+        return self._run("both", gal, ran, params, kedges, redges, gal_nbar, ran_nbar, stream)
+
+
+def footprint(params: Params, n_gal: int, n_ran: int, want_pk=True, want_xi=True) -> int:
+    n = ctypes.c_size_t()
+    rc = lib().bym_footprint(ctypes.byref(params), int(n_gal), int(n_ran), int(want_pk), int(want_xi),
+                             ctypes.byref(n))
+    if rc != BYM_OK:
+        raise BymError(rc, "bym_footprint failed")
+    return n.value
+
+
+def jit_check(params: Params) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = lib().bym_jit_check(ctypes.byref(params), buf, len(buf))
+    if rc != BYM_OK:
+        raise BymError(rc, buf.value.decode(errors="replace"))
+    return buf.value.decode(errors="replace")
+
+
+def version() -> str:
+    return lib().bym_version().decode()

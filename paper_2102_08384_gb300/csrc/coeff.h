@@ -1,0 +1,45 @@
+// Host-side (FP64) series coefficients of arXiv:2102.08384 and their
+// real-spherical-harmonic form, as sparse term lists for the kernel generator.
+#pragma once
+#include <vector>
+
+namespace bym {
+
+// ---- complex-basis coefficients, taken term by term from the paper --------
+double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
+double gaunt(int l1, int l2, int l3, int m1, int m2, int m3);      // eq. Gaunt-3j-def
+double solid_coupling(int ell, int m, int lam, int mu);              // A_{ell m}^{lam mu}, eq. solid-harm-application
+double legendre_inverse(int L, int n);                               // c~^L_n, eq. Leg-polynomial-inv-def
+double gegenbauer_term(int two_a, int N, int k);                     // C_{Nk}^{a}, a = two_a / 2, eq. gegenbauer-explicit
+double shift_phi(int alpha, int ell, int m, int J1, int J2, int M);  // eq. shift-coeff-def
+double legendre_shift_f(int alpha, int ell, int J);                  // eq. f-alpha-def
+double bisector_B(int beta, int ell, int m, int J1, int J2, int M);  // eq. B-def
+
+// ---- real-basis indexing ---------------------------------------------------
+// Real spherical harmonics (orthonormal, no Condon-Shortley phase):
+//   Y_{l,0} = Y_l^0;  Y_{l,+m} = sqrt2 (-1)^m Re Y_l^m;  Y_{l,-m} = sqrt2 (-1)^m Im Y_l^m.
+inline int ylm_index(int l, int nu) { return l * l + l + nu; }          // all l
+inline int even_lm_index(int l, int mu) { return l * (l + 1) / 2 + mu; } // even l only
+inline int n_even_lm(int ell_max) { return (ell_max + 1) * (ell_max + 2) / 2; }
+
+// Midpoint convolution fields g^alpha_{J nu}: alpha = 0..K, J = alpha mod 2,
+// alpha mod 2 + 2, .., <= ell_max + alpha, nu = -J..J.
+struct GField { int alpha, J, nu; };
+std::vector<GField> midpoint_gfields(int ell_max, int K);
+int midpoint_gfield_index(int ell_max, int alpha, int J, int nu);
+
+// Bisector P / X: X_{lm}(k) = sum c * Re(conj F_i(k) F_j(k)), i <= j (field i = ylm_index),
+// summed over beta <= floor(K/2); c already symmetrised over (i, j) <-> (j, i).
+struct BisTerm { int lm, i, j; double c; };
+std::vector<BisTerm> bisector_terms(int ell_max, int K);
+
+// Midpoint P: H_{lm}(Delta) = sum c t^alpha Y_{y}(hat Delta) g_{g}(Delta)
+// (t = |Delta| / r0, fields carry (2r/r0)^-alpha), y = ylm_index(J1, nu1).
+struct MidTerm { int lm, alpha, y, g; double c; };
+std::vector<MidTerm> midpoint_terms(int ell_max, int K);
+
+// Midpoint xi: T_l(Delta) = sum f t^alpha sum_nu Y_{J nu}(hat Delta) g^alpha_{J nu}(Delta).
+struct XiTerm { int l, alpha, J; double f; };
+std::vector<XiTerm> midpoint_xi_terms(int ell_max, int K);
+
+}  // namespace bym

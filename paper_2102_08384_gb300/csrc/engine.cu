@@ -1,0 +1,660 @@
+// Request engine and C ABI: validation, device buffers, cuFFT plans, shell
+// geometry caches and the launch sequence of each estimator (include/bym.h).
+//
+// Launch sequence of one request (all on the caller's stream):
+//   norm_reduce (gal, ran) -> paint (gal, ran) -> gen_fields -> batched R2C
+//   Yamamoto : kcontract                      | spec_mul -> C2R -> xi_lag
+//   midpoint : spec_mul -> C2R -> [xi_lag] -> [mid_combine -> R2C(H) -> kcontract]
+//   bisector : kcontract (or kcontract_x -> C2R(X) -> xi_lag)
+// then one device-to-host copy of the FP64 shell sums.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bym.h"
+#include "coeff.h"
+#include "engine.h"
+#include "jit.h"
+#include "kernels.cuh"
+
+using namespace bym;
+
+namespace {
+
+constexpr int kFftBatch = 8;
+
+int fail(bym_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+// Device allocations of one request, released in stream order.
+struct DevBufs {
+  cudaStream_t st;
+  std::vector<void *> ptrs;
+  explicit DevBufs(cudaStream_t s) : st(s) {}
+  ~DevBufs() {
+    for (void *p : ptrs) cudaFreeAsync(p, st);
+  }
+  cudaError_t alloc(void **p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+};
+
+template <class... A>
+cudaError_t launch(cudaKernel_t k, unsigned grid, unsigned block, size_t smem, cudaStream_t st, A... args) {
+  void *argv[] = {(void *)&args...};
+  return cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), argv, smem, st);
+}
+
+unsigned grid_of(long long work, int nsm, int per_sm) {
+  long long g = (work + 255) / 256;
+  const long long cap = (long long)nsm * per_sm;
+  return (unsigned)std::max(1LL, std::min(g, cap));
+}
+
+int lab(int i, int N) { return i < N / 2 ? i : i - N; }
+
+bool finite_all(const double *v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// validation and sizes
+// ---------------------------------------------------------------------------
+int bym::validate_params(bym_ctx *c, const bym_params *p) {
+  if (!p) return fail(c, BYM_E_INVAL, "params is NULL");
+  if (p->ell_max < 0 || p->ell_max % 2 || p->ell_max > 8)
+    return fail(c, BYM_E_UNSUPPORTED, "ell_max must be even and at most 8");
+  if (p->order < 0 || p->order > 12) return fail(c, BYM_E_UNSUPPORTED, "order must be in 0..12");
+  if (p->n_mesh < 8 || p->n_mesh > 1024 || p->n_mesh % 2)
+    return fail(c, BYM_E_UNSUPPORTED, "n_mesh must be even and in 8..1024");
+  if (p->assign != 2 && p->assign != 3) return fail(c, BYM_E_INVAL, "assign must be 2 (CIC) or 3 (TSC)");
+  if (p->los < 0 || p->los > 2) return fail(c, BYM_E_INVAL, "los must be 0, 1 or 2");
+  if (p->precision != 32 && p->precision != 64) return fail(c, BYM_E_INVAL, "precision must be 32 or 64");
+  if (p->norm != 0 && p->norm != 1) return fail(c, BYM_E_INVAL, "norm must be 0 or 1");
+  if (p->compensate != 0 && p->compensate != 1) return fail(c, BYM_E_INVAL, "compensate must be 0 or 1");
+  if (!(p->box_len > 0.0) || !std::isfinite(p->box_len) || !finite_all(p->box_lo, 3))
+    return fail(c, BYM_E_INVAL, "box must be finite with box_len > 0");
+  return BYM_OK;
+}
+
+int bym::validate(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                  const bym_bins *kb, const bym_bins *rb) {
+  int rc = validate_params(c, p);
+  if (rc) return rc;
+  if (!gal || gal->n < 0 || (gal->n > 0 && !gal->xyzw)) return fail(c, BYM_E_INVAL, "bad galaxy catalog");
+  if (ran && (ran->n < 0 || (ran->n > 0 && !ran->xyzw))) return fail(c, BYM_E_INVAL, "bad random catalog");
+  const bool have_ran = ran && ran->n > 0;
+  if (p->norm == 1 && (!have_ran || !ran->nbar))
+    return fail(c, BYM_E_INVAL, "norm = 1 needs randoms with nbar");
+  for (const bym_catalog *cat : {gal, ran}) {
+    if (cat && cat->n > 0 && cat->on_device && ((uintptr_t)cat->xyzw % 16))
+      return fail(c, BYM_E_INVAL, "device xyzw must be 16-byte aligned");
+  }
+  for (const bym_bins *b : {kb, rb}) {
+    if (!b) continue;
+    if (!b->edges || b->nbins < 1 || b->nbins > 1024) return fail(c, BYM_E_INVAL, "bins: need 1..1024 bins");
+    if (!finite_all(b->edges, b->nbins + 1) || b->edges[0] < 0.0)
+      return fail(c, BYM_E_INVAL, "bins: edges must be finite and non-negative");
+    for (int i = 0; i < b->nbins; ++i)
+      if (!(b->edges[i + 1] > b->edges[i])) return fail(c, BYM_E_INVAL, "bins: edges must increase");
+  }
+  return BYM_OK;
+}
+
+static int order_key(const bym_params *p) { return p->los == BYM_LOS_YAMAMOTO ? 0 : p->order; }
+
+static int n_fields(const bym_params *p) {
+  if (p->los == BYM_LOS_YAMAMOTO) return n_even_lm(p->ell_max);
+  if (p->los == BYM_LOS_BISECTOR) {
+    const int J = p->ell_max + p->order / 2;
+    return (J + 1) * (J + 1);
+  }
+  return (int)midpoint_gfields(p->ell_max, p->order).size();
+}
+
+static int n_extra_slots(const bym_params *p, bool want_pk, bool want_xi) {
+  if (p->los == BYM_LOS_MIDPOINT && want_pk) return n_even_lm(p->ell_max);
+  if (p->los == BYM_LOS_BISECTOR && want_xi) return n_even_lm(p->ell_max);
+  return 0;
+}
+
+size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
+                            bool cats_on_device) {
+  const size_t N = (size_t)p->n_mesh;
+  const size_t esz = p->precision == 64 ? 8 : 4;
+  const size_t slot = N * N * (N + 2) * esz;
+  const size_t slots = 1 + (size_t)n_fields(p) + (size_t)n_extra_slots(p, want_pk, want_xi);
+  size_t cats = 0;
+  if (!cats_on_device) cats = (size_t)(std::max<int64_t>(n_gal, 0) + std::max<int64_t>(n_ran, 0)) * 20;
+  return slots * slot + cats + (1 << 20);
+}
+
+// ---------------------------------------------------------------------------
+// cuFFT plans (in place, padded real layout), shared work area
+// ---------------------------------------------------------------------------
+static int get_plan(bym_ctx *c, int N, int prec, int inverse, int batch, cufftHandle *out) {
+  auto key = std::make_tuple(N, prec, inverse, batch);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    *out = it->second;
+    return BYM_OK;
+  }
+  cufftHandle h;
+  if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftCreate failed");
+  cufftSetAutoAllocation(h, 0);
+  long long n[3] = {N, N, N};
+  long long real_emb[3] = {N, N, 2 * (N / 2 + 1)};
+  long long cplx_emb[3] = {N, N, N / 2 + 1};
+  const long long rdist = (long long)N * N * 2 * (N / 2 + 1);
+  const long long cdist = (long long)N * N * (N / 2 + 1);
+  cufftType type = prec == 64 ? (inverse ? CUFFT_Z2D : CUFFT_D2Z) : (inverse ? CUFFT_C2R : CUFFT_R2C);
+  size_t work = 0;
+  cufftResult r;
+  if (!inverse)
+    r = cufftMakePlanMany64(h, 3, n, real_emb, 1, rdist, cplx_emb, 1, cdist, type, batch, &work);
+  else
+    r = cufftMakePlanMany64(h, 3, n, cplx_emb, 1, cdist, real_emb, 1, rdist, type, batch, &work);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(h);
+    return fail(c, BYM_E_CUDA, "cufftMakePlanMany failed (" + std::to_string((int)r) + ")");
+  }
+  if (work > c->fft_work_size) {
+    cudaDeviceSynchronize();
+    if (c->fft_work) cudaFree(c->fft_work);
+    c->fft_work = nullptr;
+    c->fft_work_size = 0;
+    if (cudaMalloc(&c->fft_work, work) != cudaSuccess) {
+      cudaGetLastError();
+      cufftDestroy(h);
+      return fail(c, BYM_E_NOMEM, "cuFFT work area allocation failed");
+    }
+    c->fft_work_size = work;
+  }
+  c->plans[key] = h;
+  *out = h;
+  return BYM_OK;
+}
+
+static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
+                     int first, int count) {
+  for (int done = 0; done < count;) {
+    const int b = std::min(kFftBatch, count - done);
+    cufftHandle h;
+    int rc = get_plan(c, N, prec, inverse, b, &h);
+    if (rc) return rc;
+    cufftSetStream(h, st);
+    cufftSetWorkArea(h, c->fft_work);
+    char *ptr = (char *)base + (size_t)(first + done) * slot_bytes;
+    cufftResult r;
+    if (prec == 64)
+      r = inverse ? cufftExecZ2D(h, (cufftDoubleComplex *)ptr, (cufftDoubleReal *)ptr)
+                  : cufftExecD2Z(h, (cufftDoubleReal *)ptr, (cufftDoubleComplex *)ptr);
+    else
+      r = inverse ? cufftExecC2R(h, (cufftComplex *)ptr, (cufftReal *)ptr)
+                  : cufftExecR2C(h, (cufftReal *)ptr, (cufftComplex *)ptr);
+    if (r != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftExec failed (" + std::to_string((int)r) + ")");
+    done += b;
+  }
+  return BYM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// shell geometry: bin look-up tables over |n|^2 and per-bin counts / means
+// ---------------------------------------------------------------------------
+static std::string geom_key(int N, double L, const bym_bins *b, char kind) {
+  std::ostringstream o;
+  o << kind << N << ':';
+  o.write((const char *)&L, sizeof L);
+  o.write((const char *)b->edges, sizeof(double) * (b->nbins + 1));
+  return o.str();
+}
+
+static std::vector<int> bin_lut(int N, double unit, const bym_bins *b) {
+  const int h = N / 2;
+  const long long n2max = 3LL * h * h;
+  std::vector<int> lut((size_t)n2max + 1, -1);
+  const double *e = b->edges;
+  for (long long n2 = 1; n2 <= n2max; ++n2) {
+    const double mag = unit * std::sqrt((double)n2);
+    const double *u = std::upper_bound(e, e + b->nbins + 1, mag);
+    const long long bin = (long long)(u - e) - 1;
+    if (bin >= 0 && bin < b->nbins) lut[(size_t)n2] = (int)bin;
+  }
+  return lut;
+}
+
+static int get_geom(bym_ctx *c, const KernelSet &ks, int N, double L, const bym_bins *b, char kind,
+                    cudaStream_t st, Geom **out) {
+  auto &cache = kind == 'k' ? c->kgeo : c->rgeo;
+  const std::string key = geom_key(N, L, b, kind);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = &it->second;
+    return BYM_OK;
+  }
+  Geom g;
+  g.nbins = b->nbins;
+  const double h = L / N;
+  const double unit = kind == 'k' ? 2.0 * M_PI / L : h;
+  std::vector<int> lut = bin_lut(N, unit, b);
+  if (cudaMalloc(&g.lut, lut.size() * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "bin table allocation failed");
+  }
+  cudaMemcpy(g.lut, lut.data(), lut.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (kind == 'r') {
+    int jm = (int)std::floor(b->edges[b->nbins] / h) + 1;
+    g.full = (2 * jm + 1 > N) ? 1 : 0;
+    g.jm = g.full ? N / 2 : jm;
+  }
+  double *sums = nullptr;
+  if (cudaMalloc(&sums, sizeof(double) * 2 * b->nbins) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "geometry allocation failed");
+  }
+  cudaMemsetAsync(sums, 0, sizeof(double) * 2 * b->nbins, st);
+  cudaError_t e;
+  const size_t smem = sizeof(double) * 2 * b->nbins;
+  if (kind == 'k') {
+    const long long work = (long long)N * N * (N / 2 + 1);
+    e = launch(ks.kgeom, grid_of(work, c->nsm, 4), 256, smem, st, N, (const int *)g.lut, b->nbins, unit, sums);
+  } else {
+    const int Lc = g.full ? N : 2 * g.jm + 1;
+    const long long work = (long long)Lc * Lc * Lc;
+    e = launch(ks.rgeom, grid_of(work, c->nsm, 4), 256, smem, st, N, g.jm, g.full, (const int *)g.lut, b->nbins, h,
+               sums);
+  }
+  std::vector<double> hs(2 * b->nbins);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), sums, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(sums);
+  if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("geometry kernel: ") + cudaGetErrorString(e));
+  g.count.resize(b->nbins);
+  g.mean.resize(b->nbins);
+  for (int i = 0; i < b->nbins; ++i) {
+    g.count[i] = (int64_t)std::llround(hs[2 * i]);
+    g.mean[i] = g.count[i] > 0 ? hs[2 * i + 1] / hs[2 * i] : 0.0;
+  }
+  auto res = cache.emplace(key, std::move(g));
+  *out = &res.first->second;
+  return BYM_OK;
+}
+
+// A table of -1 (no k bin) for requests that need X(k) but no P.
+static int get_null_kgeom(bym_ctx *c, int N, Geom **out) {
+  const std::string key = "null" + std::to_string(N);
+  auto it = c->kgeo.find(key);
+  if (it != c->kgeo.end()) {
+    *out = &it->second;
+    return BYM_OK;
+  }
+  Geom g;
+  g.nbins = 1;
+  const size_t n = 3 * (size_t)(N / 2) * (N / 2) + 1;
+  std::vector<int> lut(n, -1);
+  if (cudaMalloc(&g.lut, n * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "bin table allocation failed");
+  }
+  cudaMemcpy(g.lut, lut.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+  auto res = c->kgeo.emplace(key, std::move(g));
+  *out = &res.first->second;
+  return BYM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one request
+// ---------------------------------------------------------------------------
+template <typename T, typename T2>
+static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
+  const bym_params *p = rq.p;
+  const int N = p->n_mesh;
+  const bool want_pk = rq.kb != nullptr, want_xi = rq.rb != nullptr;
+  std::string jerr;
+  auto ks = get_kernels(JitKey{p->los, p->ell_max, order_key(p), p->precision}, jerr);
+  if (!ks) return fail(c, BYM_E_CUDA, jerr);
+  const KernelSet &K = *ks;
+  const int nf = (int)K.fields.size();
+  const int nlm = K.n_lm, NL = K.n_ell;
+  const int nextra = n_extra_slots(p, want_pk, want_xi);
+  const long long slot_reals = (long long)N * N * (N + 2);
+  const long long cslot = slot_reals / 2;
+  const size_t slot_bytes = (size_t)slot_reals * sizeof(T);
+  const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
+
+  if (c->budget) {
+    const size_t need = footprint_bytes(p, rq.gal->n, rq.ran ? rq.ran->n : 0, want_pk, want_xi,
+                                        rq.gal->on_device && (!rq.ran || rq.ran->on_device));
+    if (need > c->budget) return fail(c, BYM_E_NOMEM, "request exceeds the context's HBM budget");
+  }
+
+  Geom *kg = nullptr, *rg = nullptr;
+  int rc;
+  if (want_pk && (rc = get_geom(c, K, N, p->box_len, rq.kb, 'k', st, &kg))) return rc;
+  if (want_xi && (rc = get_geom(c, K, N, p->box_len, rq.rb, 'r', st, &rg))) return rc;
+  if (!kg && p->los == BYM_LOS_BISECTOR && (rc = get_null_kgeom(c, N, &kg))) return rc;
+
+  DevBufs buf(st);
+  auto alloc = [&](void **ptr, size_t bytes) -> int {
+    if (buf.alloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, BYM_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return BYM_OK;
+  };
+#define TRY(x)                  \
+  do {                          \
+    int rc_ = (x);              \
+    if (rc_) return rc_;        \
+  } while (0)
+#define CUDA_TRY(x)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess) return fail(c, BYM_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+  // catalogs
+  const float4 *cat4[2] = {nullptr, nullptr};
+  const float *catnb[2] = {nullptr, nullptr};
+  long long catn[2] = {rq.gal->n, rq.ran ? rq.ran->n : 0};
+  const bym_catalog *cats[2] = {rq.gal, rq.ran};
+  for (int w = 0; w < 2; ++w) {
+    const bym_catalog *cat = cats[w];
+    if (!cat || cat->n <= 0) continue;
+    if (cat->on_device) {
+      cat4[w] = (const float4 *)cat->xyzw;
+      catnb[w] = cat->nbar;
+    } else {
+      void *d4 = nullptr;
+      TRY(alloc(&d4, (size_t)cat->n * 16));
+      CUDA_TRY(cudaMemcpyAsync(d4, cat->xyzw, (size_t)cat->n * 16, cudaMemcpyHostToDevice, st));
+      cat4[w] = (const float4 *)d4;
+      if (cat->nbar) {
+        void *dn = nullptr;
+        TRY(alloc(&dn, (size_t)cat->n * 4));
+        CUDA_TRY(cudaMemcpyAsync(dn, cat->nbar, (size_t)cat->n * 4, cudaMemcpyHostToDevice, st));
+        catnb[w] = (const float *)dn;
+      }
+    }
+  }
+
+  double *stats = nullptr, *ksum = nullptr, *rsum = nullptr, *scale = nullptr;
+  T *invw = nullptr;
+  TRY(alloc((void **)&stats, 8 * sizeof(double)));
+  CUDA_TRY(cudaMemsetAsync(stats, 0, 8 * sizeof(double), st));
+  const int nbk = want_pk ? rq.kb->nbins : 1, nbr = want_xi ? rq.rb->nbins : 1;
+  TRY(alloc((void **)&ksum, sizeof(double) * NL * nbk));
+  TRY(alloc((void **)&rsum, sizeof(double) * NL * nbr));
+  CUDA_TRY(cudaMemsetAsync(ksum, 0, sizeof(double) * NL * nbk, st));
+  CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * NL * nbr, st));
+  if (p->compensate) {
+    std::vector<T> w(N);
+    for (int i = 0; i < N; ++i) {
+      const double x = M_PI * lab(i, N) / N;
+      const double s = x == 0.0 ? 1.0 : std::sin(x) / x;
+      w[i] = (T)(1.0 / std::pow(s, p->assign));
+    }
+    TRY(alloc((void **)&invw, sizeof(T) * N));
+    CUDA_TRY(cudaMemcpyAsync(invw, w.data(), sizeof(T) * N, cudaMemcpyHostToDevice, st));
+  }
+  {
+    std::vector<double> sc(nf);
+    const double inv_n3 = 1.0 / ((double)N * N * N);
+    for (int i = 0; i < nf; ++i) {
+      const double sign = (p->los == BYM_LOS_MIDPOINT && (K.fields[i].J % 2)) ? -1.0 : 1.0;
+      sc[i] = sign * inv_n3;
+    }
+    TRY(alloc((void **)&scale, sizeof(double) * std::max(nf, 1)));
+    CUDA_TRY(cudaMemcpyAsync(scale, sc.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
+  }
+
+  // mesh slots: [0] delta, [1, 1+nf) fields, [1+nf, 1+nf+nextra) H or X
+  const int nslots = 1 + nf + nextra;
+  T *slots = nullptr;
+  TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
+  auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
+  auto slot_c = [&](int i) { return (T2 *)(slots + (long long)i * slot_reals); };
+  CUDA_TRY(cudaMemsetAsync(slots, 0, slot_bytes, st));
+
+  // norms and painting
+  for (int w = 0; w < 2; ++w)
+    if (cat4[w]) launch_norm_reduce(cat4[w], catnb[w], catn[w], w, p->box_lo, inv_h, N, stats, c->nsm, st);
+  for (int w = 0; w < 2; ++w)
+    if (cat4[w]) launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(0), N, p->box_lo, inv_h, p->assign, c->nsm, st);
+  CUDA_TRY(cudaGetLastError());
+
+  // field generation
+  {
+    const long long ncell = (long long)N * N * N;
+    CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, 16), 256, 0, st, (const T *)slot_r(0), slot_r(1),
+                    slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+  }
+
+  const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, 4);
+  const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
+  const double tscale = h * inv_r0;
+
+  if (p->los == BYM_LOS_YAMAMOTO) {
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
+    if (want_pk)
+      CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
+                      (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
+    if (want_xi) {
+      launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
+      const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
+                      slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
+    }
+  } else if (p->los == BYM_LOS_MIDPOINT) {
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
+    launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+    TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
+    if (want_xi) {
+      const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
+                      slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
+    }
+    if (want_pk) {
+      CUDA_TRY(launch(K.mid_combine, grid_of((long long)N * N * N, c->nsm, 16), 256, 0, st, (const T *)slot_r(1),
+                      slot_reals, slot_r(1 + nf), N, tscale));
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm));
+      CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
+                      (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
+    }
+  } else {
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf));
+    if (want_xi) {
+      CUDA_TRY(launch(K.kcontract_x, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
+                      (const int *)kg->lut, nbk, ksum, slot_c(1 + nf), cslot, (const T *)invw));
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1 + nf, nlm));
+      const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
+                      (const T *)slot_r(1 + nf), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
+                      1.0 / ((double)N * N * N), tscale));
+    } else {
+      CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
+                      (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+
+  // results
+  std::vector<double> hstats(8), hk((size_t)NL * nbk), hr((size_t)NL * nbr);
+  CUDA_TRY(cudaMemcpyAsync(hstats.data(), stats, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hk.data(), ksum, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hr.data(), rsum, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (hstats[3] > 0.0)
+    return fail(c, BYM_E_OUT_OF_BOX,
+                std::to_string((long long)hstats[3]) + " objects lie outside the box or are not finite");
+  double A = 1.0, vcell = 1.0;
+  if (p->norm == 1) {
+    const double alpha = hstats[0] / hstats[1];
+    A = alpha * hstats[2];
+    vcell = h * h * h;
+    if (!(A > 0.0) || !std::isfinite(A)) return fail(c, BYM_E_INVAL, "FKP normalisation A is not positive");
+  }
+  const double four_pi = 4.0 * M_PI;
+  if (want_pk) {
+    for (int l = 0; l < NL; ++l)
+      for (int b = 0; b < nbk; ++b)
+        rq.pk[l * nbk + b] = kg->count[b] > 0 ? four_pi / A * hk[(size_t)b * NL + l] / (double)kg->count[b] : 0.0;
+    if (rq.kmean) std::copy(kg->mean.begin(), kg->mean.end(), rq.kmean);
+    if (rq.nmodes) std::copy(kg->count.begin(), kg->count.end(), rq.nmodes);
+  }
+  if (want_xi) {
+    for (int l = 0; l < NL; ++l)
+      for (int b = 0; b < nbr; ++b)
+        rq.xi[l * nbr + b] =
+            rg->count[b] > 0 ? four_pi / (A * vcell) * hr[(size_t)b * NL + l] / (double)rg->count[b] : 0.0;
+    if (rq.rmean) std::copy(rg->mean.begin(), rg->mean.end(), rq.rmean);
+    if (rq.ncells) std::copy(rg->count.begin(), rg->count.end(), rq.ncells);
+  }
+  return BYM_OK;
+#undef TRY
+#undef CUDA_TRY
+}
+
+int bym::run_request(bym_ctx *c, const Request &rq, cudaStream_t st) {
+  if (!c) return BYM_E_INVAL;
+  int rc = validate(c, rq.gal, rq.ran, rq.p, rq.kb, rq.rb);
+  if (rc) return rc;
+  if ((rq.kb && !rq.pk) || (rq.rb && !rq.xi) || (!rq.kb && !rq.rb))
+    return fail(c, BYM_E_INVAL, "missing output array");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  if (!st) st = c->stream;
+  try {
+    if (rq.p->precision == 64) return run_typed<double, double2>(c, rq, st);
+    return run_typed<float, float2>(c, rq, st);
+  } catch (const std::exception &e) {
+    return fail(c, BYM_E_CUDA, std::string("internal error: ") + e.what());
+  }
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *bym_version(void) { return "bym 0.1 (sm_103a)"; }
+
+int bym_create(bym_ctx **out, int device, size_t hbm_budget_bytes) {
+  if (!out) return BYM_E_INVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BYM_E_CUDA;
+  }
+  auto *c = new bym_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return BYM_E_CUDA;
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  *out = c;
+  return BYM_OK;
+}
+
+void bym_destroy(bym_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  shutdown_serving(c);
+  for (auto &kv : c->plans) cufftDestroy(kv.second);
+  if (c->fft_work) cudaFree(c->fft_work);
+  for (auto *m : {&c->kgeo, &c->rgeo})
+    for (auto &kv : *m)
+      if (kv.second.lut) cudaFree(kv.second.lut);
+  cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char *bym_last_error(const bym_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+int bym_footprint(const bym_params *p, int64_t n_gal, int64_t n_ran, int want_pk, int want_xi, size_t *bytes) {
+  if (!p || !bytes) return BYM_E_INVAL;
+  int rc = validate_params(nullptr, p);
+  if (rc) return rc;
+  *bytes = footprint_bytes(p, n_gal, n_ran, want_pk != 0, want_xi != 0, false);
+  return BYM_OK;
+}
+
+int bym_pk_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                      const bym_bins *kbins, double *pk, double *k_mean, int64_t *n_modes, void *stream) {
+  if (!c) return BYM_E_INVAL;
+  if (!kbins) return fail(c, BYM_E_INVAL, "kbins is NULL");
+  std::lock_guard<std::mutex> lock(c->mu);
+  Request rq{gal, ran, p, kbins, nullptr, pk, k_mean, n_modes, nullptr, nullptr, nullptr};
+  return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                      const bym_bins *rbins, double *xi, double *r_mean, int64_t *n_cells, void *stream) {
+  if (!c) return BYM_E_INVAL;
+  if (!rbins) return fail(c, BYM_E_INVAL, "rbins is NULL");
+  std::lock_guard<std::mutex> lock(c->mu);
+  Request rq{gal, ran, p, nullptr, rbins, nullptr, nullptr, nullptr, xi, r_mean, n_cells};
+  return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_pk_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                         const bym_bins *kbins, const bym_bins *rbins, double *pk, double *k_mean, int64_t *n_modes,
+                         double *xi, double *r_mean, int64_t *n_cells, void *stream) {
+  if (!c) return BYM_E_INVAL;
+  if (!kbins || !rbins) return fail(c, BYM_E_INVAL, "kbins and rbins are required");
+  std::lock_guard<std::mutex> lock(c->mu);
+  Request rq{gal, ran, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
+  return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_jit_check(const bym_params *p, char *log, size_t log_len) {
+  if (!p) return BYM_E_INVAL;
+  int rc = validate_params(nullptr, p);
+  if (rc) return rc;
+  std::string src, lg;
+  try {
+    src = generate_source(JitKey{p->los, p->ell_max, order_key(p), p->precision}, nullptr);
+  } catch (const std::exception &e) {
+    lg = e.what();
+  }
+  std::vector<char> cubin;
+  const bool ok = !src.empty() && compile_cubin(src, cubin, lg);
+  if (log && log_len) {
+    const size_t n = std::min(log_len - 1, lg.size());
+    memcpy(log, lg.data(), n);
+    log[n] = '\0';
+  }
+  return ok ? BYM_OK : BYM_E_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Internal interfaces of the request engine shared by engine.cu and serve.cpp.
+#pragma once
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bym.h"
+
+namespace bym {
+
+struct Geom {
+  int *lut = nullptr;           // device: bin of each |n|^2 (or -1)
+  int nbins = 0;
+  int jm = 0, full = 0;         // lag cube half-width (r bins only)
+  std::vector<int64_t> count;   // modes / lag cells per bin (full grid)
+  std::vector<double> mean;     // mean |k| or |Delta| per bin
+};
+
+struct Request {
+  const bym_catalog *gal, *ran;
+  const bym_params *p;
+  const bym_bins *kb, *rb;      // NULL: that statistic is not requested
+  double *pk, *kmean;
+  int64_t *nmodes;
+  double *xi, *rmean;
+  int64_t *ncells;
+};
+
+struct Server;  // serving loop state (serve.cpp)
+
+}  // namespace bym
+
+struct bym_ctx {
+  int device = 0;
+  size_t budget = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::mutex mu;                                               // one request at a time per context
+  std::map<std::tuple<int, int, int, int>, cufftHandle> plans;  // (N, precision, inverse, batch)
+  void *fft_work = nullptr;
+  size_t fft_work_size = 0;
+  std::map<std::string, bym::Geom> kgeo, rgeo;
+  bym::Server *server = nullptr;
+};
+
+namespace bym {
+
+int validate_params(bym_ctx *c, const bym_params *p);
+int validate(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p, const bym_bins *kb,
+             const bym_bins *rb);
+size_t footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
+                       bool cats_on_device);
+int run_request(bym_ctx *c, const Request &rq, cudaStream_t st);
+void shutdown_serving(bym_ctx *c);
+
+}  // namespace bym

@@ -1,0 +1,497 @@
+// Kernel generator for the field-dependent steps of the estimators.
+//
+// For one (LOS, ell_max, order K, precision) it writes a CUDA C++ module with
+//   gen_fields   field generation: Y_{J nu}(hat x) (2r/r0)^-alpha delta(x) for every
+//                field the series needs, one pass over the mesh (FP64 recurrence);
+//   kgeom/rgeom  mode / lag-cell counts and mean |k| / |Delta| per shell;
+//   kcontract    k-space contraction with Y_{l mu}(hat k) and FP64 shell sums
+//                (Yamamoto: Re F conj(delta); midpoint: Re F[H]; bisector: the
+//                bilinear form sum B Re(conj F_i F_j));
+//   kcontract_x  bisector variant that also writes X_{l mu}(k) for the xi path;
+//   mid_combine  midpoint Delta-space combine H_{l mu} = sum phi Y (|Delta|/r0)^alpha g;
+//   xi_lag       configuration-space contraction over the lag cube r < r_max.
+// The couplings (phi, B, f) enter as floating-point immediates and every
+// field value lives in a register, so the sparse sums compile to plain FMA
+// streams.  Real spherical harmonics are produced by an unrolled
+// associated-Legendre recurrence (orthonormal, no Condon-Shortley phase).
+#include "jit.h"
+
+#include <nvrtc.h>
+
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <set>
+#include <sstream>
+
+#include "coeff.h"
+
+namespace bym {
+namespace {
+
+std::string lit(double v, bool f32) {
+  char buf[64];
+  if (f32)
+    snprintf(buf, sizeof buf, "(%.9ef)", v);
+  else
+    snprintf(buf, sizeof buf, "(%.17e)", v);
+  return buf;
+}
+
+// Declares variables P<l*l+l+nu> = Y_{l nu}(u) for l <= L from the unit vector
+// (ux, uy, uz); zm (0 or 1) zeroes every l > 0 term (the zero vector carries
+// Y = delta_{l0} / sqrt(4 pi)).
+void emit_ylm(std::ostream &o, int L, bool f32, const std::string &P, const std::string &ux,
+              const std::string &uy, const std::string &uz, const std::string &zm) {
+  const char *TY = f32 ? "float" : "double";
+  o << "  " << TY << " " << P << "c0 = 1, " << P << "s0 = 0;\n";
+  for (int m = 1; m <= L; ++m)
+    o << "  " << TY << " " << P << "c" << m << " = " << P << "c" << m - 1 << " * " << ux << " - " << P << "s"
+      << m - 1 << " * " << uy << ", " << P << "s" << m << " = " << P << "s" << m - 1 << " * " << ux << " + " << P
+      << "c" << m - 1 << " * " << uy << ";\n";
+  for (int m = 0; m <= L; ++m) {
+    if (m == 0)
+      o << "  " << TY << " " << P << "p0_0 = " << lit(1.0 / std::sqrt(4.0 * M_PI), f32) << ";\n";
+    else
+      o << "  " << TY << " " << P << "p" << m << "_" << m << " = " << P << "p" << m - 1 << "_" << m - 1 << " * "
+        << lit(std::sqrt((2.0 * m + 1) / (2.0 * m)), f32) << ";\n";
+    if (m + 1 <= L)
+      o << "  " << TY << " " << P << "p" << m + 1 << "_" << m << " = " << lit(std::sqrt(2.0 * m + 3), f32) << " * "
+        << uz << " * " << P << "p" << m << "_" << m << ";\n";
+    for (int l = m + 2; l <= L; ++l) {
+      const double a = std::sqrt((4.0 * l * l - 1) / ((double)l * l - (double)m * m));
+      const double b = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1));
+      o << "  " << TY << " " << P << "p" << l << "_" << m << " = " << lit(a, f32) << " * (" << uz << " * " << P
+        << "p" << l - 1 << "_" << m << " - " << lit(b, f32) << " * " << P << "p" << l - 2 << "_" << m << ");\n";
+    }
+    for (int l = m; l <= L; ++l) {
+      if (m == 0) {
+        o << "  " << TY << " " << P << l * l + l << " = " << P << "p" << l << "_0";
+        if (l > 0) o << " * " << zm;
+        o << ";\n";
+      } else {
+        o << "  " << TY << " " << P << l * l + l + m << " = " << lit(std::sqrt(2.0), f32) << " * " << P << "p" << l
+          << "_" << m << " * " << P << "c" << m << ";\n";
+        o << "  " << TY << " " << P << l * l + l - m << " = " << lit(std::sqrt(2.0), f32) << " * " << P << "p" << l
+          << "_" << m << " * " << P << "s" << m << ";\n";
+      }
+    }
+  }
+}
+
+const char *kPrelude = R"(
+#define BYM_FULL 0xffffffffu
+__device__ __forceinline__ double bym_wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(BYM_FULL, v, o);
+  return v;
+}
+// Per-block FP64 shell sums: every lane holds (bin, v[NL]); lanes that share a
+// bin are reduced with shuffles and the group leader adds to shared memory.
+template <int NL>
+__device__ __forceinline__ void bym_bin_flush(int bin, const double (&v)[NL], double *s) {
+  unsigned pending = __ballot_sync(BYM_FULL, bin >= 0);
+  const int lane = threadIdx.x & 31;
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int bl = __shfl_sync(BYM_FULL, bin, leader);
+    const bool mine = (bin == bl);
+    const unsigned grp = __ballot_sync(BYM_FULL, mine);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const double x = bym_wsum(mine ? v[l] : 0.0);
+      if (lane == leader) atomicAdd(s + bl * NL + l, x);
+    }
+    pending &= ~grp;
+  }
+}
+__device__ __forceinline__ void bym_bins_init(double *s, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = 0.0;
+  __syncthreads();
+}
+__device__ __forceinline__ void bym_bins_out(const double *s, double *g, int n) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = s[i];
+    if (x != 0.0) atomicAdd(g + i, x);
+  }
+}
+__device__ __forceinline__ int bym_lab(int i, int N) { return i < N / 2 ? i : i - N; }
+__device__ __forceinline__ float bym_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double bym_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float bym_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double bym_sqrt(double x) { return sqrt(x); }
+)";
+
+struct Fields {
+  std::vector<FieldInfo> list;
+};
+
+Fields field_set(const JitKey &k) {
+  Fields f;
+  if (k.los == 0) {  // Yamamoto: Y_{l mu} delta, even l
+    for (int l = 0; l <= k.ell_max; l += 2)
+      for (int nu = -l; nu <= l; ++nu) f.list.push_back({0, l, nu});
+  } else if (k.los == 2) {  // bisector: Y_{J nu} delta, J <= ell_max + floor(K/2)
+    const int Jmax = k.ell_max + k.K / 2;
+    for (int J = 0; J <= Jmax; ++J)
+      for (int nu = -J; nu <= J; ++nu) f.list.push_back({0, J, nu});
+  } else {  // midpoint: g^alpha_{J nu}
+    for (auto &g : midpoint_gfields(k.ell_max, k.K)) f.list.push_back({g.alpha, g.J, g.nu});
+  }
+  return f;
+}
+
+void emit_bin_loop_head(std::ostream &o, const std::string &count_expr) {
+  o << "  const int lane = threadIdx.x & 31;\n";
+  o << "  const long long total = " << count_expr << ";\n";
+  o << "  for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < total;"
+       " base += (long long)gridDim.x * blockDim.x) {\n";
+  o << "    const long long m = base + lane;\n";
+}
+
+}  // namespace
+
+std::string generate_source(const JitKey &key, KernelSet *meta) {
+  const bool f32 = key.prec == 32;
+  const char *real = f32 ? "float" : "double";
+  const int L = key.ell_max;
+  const int n_lm = n_even_lm(L);
+  const int NL = L / 2 + 1;
+  const Fields F = field_set(key);
+  const int nf = (int)F.list.size();
+  std::ostringstream o;
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << kPrelude;
+
+  // ------------------------------------------------------------------ gen_fields
+  {
+    int Jmax = 0, amax = 0;
+    for (auto &fi : F.list) {
+      Jmax = std::max(Jmax, fi.J);
+      amax = std::max(amax, fi.alpha);
+    }
+    o << "extern \"C\" __global__ void __launch_bounds__(256) gen_fields(const real* __restrict__ delta,"
+         " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
+         " double inv_r0) {\n";
+    o << "  const long long ncell = (long long)N * N * N;\n";
+    o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
+         " c += (long long)gridDim.x * blockDim.x) {\n";
+    o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
+    o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
+    o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+    o << "    const real d = delta[off];\n";
+    o << "    if (d == (real)0) {\n";
+    for (int i = 0; i < nf; ++i) o << "      out[" << i << "LL * slot + off] = (real)0;\n";
+    o << "      continue;\n    }\n";
+    o << "    const double x = lo0 + ix * h, y = lo1 + iy * h, z = lo2 + iz * h;\n";
+    o << "    const double r2 = x * x + y * y + z * z;\n";
+    o << "    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;\n";
+    o << "    const double ux = x * ir, uy = y * ir, uz = z * ir, zm = r2 > 0.0 ? 1.0 : 0.0;\n";
+    o << "    const double rad0 = (double)d;\n";
+    if (amax > 0) o << "    const double q = r2 > 0.0 ? 1.0 / (2.0 * sqrt(r2) * inv_r0) : 0.0;\n";
+    for (int a = 1; a <= amax; ++a) o << "    const double rad" << a << " = rad" << a - 1 << " * q;\n";
+    emit_ylm(o, Jmax, false, "y", "ux", "uy", "uz", "zm");
+    for (int i = 0; i < nf; ++i)
+      o << "    out[" << i << "LL * slot + off] = (real)(y" << ylm_index(F.list[i].J, F.list[i].nu) << " * rad"
+        << F.list[i].alpha << ");\n";
+    o << "  }\n}\n";
+  }
+
+  // ------------------------------------------------------------------ geometry
+  o << "extern \"C\" __global__ void __launch_bounds__(256) kgeom(int N, const int* __restrict__ lut, int nbins,"
+       " double kf, double* __restrict__ gsum) {\n";
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * 2);\n  const int H = N / 2 + 1;\n";
+  emit_bin_loop_head(o, "(long long)N * N * H");
+  o << "    int bin = -1; double v[2] = {0.0, 0.0};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+  o << "      const int nx = bym_lab((int)(row / N), N), ny = bym_lab((int)(row % N), N);\n";
+  o << "      const int nz = (iz == N / 2) ? -N / 2 : iz;\n";
+  o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
+  o << "      bin = lut[n2];\n";
+  o << "      if (bin >= 0) { const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;"
+       " v[0] = w; v[1] = w * kf * sqrt((double)n2); }\n";
+  o << "    }\n    bym_bin_flush<2>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
+
+  o << "extern \"C\" __global__ void __launch_bounds__(256) rgeom(int N, int jm, int full,"
+       " const int* __restrict__ lut, int nbins, double h, double* __restrict__ gsum) {\n";
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * 2);\n";
+  o << "  const int Lc = full ? N : 2 * jm + 1;\n";
+  emit_bin_loop_head(o, "(long long)Lc * Lc * Lc");
+  o << "    int bin = -1; double v[2] = {0.0, 0.0};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int a = (int)(m % Lc); const long long t = m / Lc;\n";
+  o << "      const int b = (int)(t % Lc); const int c = (int)(t / Lc);\n";
+  o << "      const int jx = full ? bym_lab(c, N) : c - jm, jy = full ? bym_lab(b, N) : b - jm,"
+       " jz = full ? bym_lab(a, N) : a - jm;\n";
+  o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
+  o << "      bin = lut[j2];\n";
+  o << "      if (bin >= 0) { v[0] = 1.0; v[1] = h * sqrt((double)j2); }\n";
+  o << "    }\n    bym_bin_flush<2>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
+
+  // ------------------------------------------------------------------ k-space contraction
+  auto emit_kcontract = [&](const char *name, bool with_x) {
+    o << "extern \"C\" __global__ void __launch_bounds__(256) " << name
+      << "(const real2* __restrict__ F, long long cslot, const real2* __restrict__ D, int N,"
+         " const int* __restrict__ lut, int nbins, double* __restrict__ gsum, real2* __restrict__ xout,"
+         " long long xslot, const real* __restrict__ invw) {\n";
+    o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n  const int H = N / 2 + 1;\n";
+    emit_bin_loop_head(o, "(long long)N * N * H");
+    o << "    int bin = -1; double v[" << NL << "] = {";
+    for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
+    o << "};\n";
+    o << "    if (m < total) {\n";
+    o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+    o << "      const int ix = (int)(row / N), iy = (int)(row % N);\n";
+    o << "      const int nx = bym_lab(ix, N), ny = bym_lab(iy, N), nz = (iz == N / 2) ? -N / 2 : iz;\n";
+    o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
+    o << "      bin = lut[n2];\n";
+    o << "      if (" << (with_x ? "true" : "bin >= 0") << ") {\n";
+    o << "        real cc = (real)1;\n";
+    if (key.los != 1)
+      o << "        if (invw) { cc = invw[ix] * invw[iy] * invw[iz]; cc = cc * cc; }\n";
+    // X_{lm}
+    for (int i = 0; i < n_lm; ++i) o << "        real X" << i << " = (real)0;\n";
+    if (key.los == 0) {
+      o << "        const real2 d = D[m];\n";
+      for (int i = 0; i < n_lm; ++i)
+        o << "        { const real2 f = F[" << i << "LL * cslot + m]; X" << i << " = (f.x * d.x + f.y * d.y) * cc; }\n";
+    } else if (key.los == 1) {
+      for (int i = 0; i < n_lm; ++i) o << "        X" << i << " = F[" << i << "LL * cslot + m].x;\n";
+    } else {
+      for (int i = 0; i < nf; ++i) o << "        const real2 f" << i << " = F[" << i << "LL * cslot + m];\n";
+      auto terms = bisector_terms(key.ell_max, key.K);
+      std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> by_pair;
+      for (auto &t : terms) by_pair[{t.i, t.j}].push_back({t.lm, t.c});
+      for (auto &kv : by_pair) {
+        const int i = kv.first.first, j = kv.first.second;
+        o << "        { const real q = f" << i << ".x * f" << j << ".x + f" << i << ".y * f" << j << ".y;";
+        for (auto &lc : kv.second) o << " X" << lc.first << " += " << lit(lc.second, f32) << " * q;";
+        o << " }\n";
+      }
+      for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
+      if (with_x)
+        for (int i = 0; i < n_lm; ++i) {
+          o << "        { real2 xv; xv.x = X" << i << "; xv.y = (real)0; xout[" << i << "LL * xslot + m] = xv; }\n";
+        }
+    }
+    o << "        if (bin >= 0) {\n";
+    o << "          const real w = (iz == 0 || iz == N / 2) ? (real)1 : (real)2;\n";
+    o << "          const real r2 = (real)n2; const real ir = bym_rsqrt(r2);\n";
+    o << "          const real ux = nx * ir, uy = ny * ir, uz = nz * ir; const real zm = (real)1;\n";
+    {
+      std::ostringstream yy;
+      emit_ylm(yy, L, f32, "yk", "ux", "uy", "uz", "zm");
+      std::string s = yy.str();
+      std::istringstream is(s);
+      std::string line;
+      while (std::getline(is, line)) o << "        " << line << "\n";
+    }
+    for (int l = 0; l <= L; l += 2) {
+      o << "          { real T = (real)0;";
+      for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << even_lm_index(l, mu) << ";";
+      o << " v[" << l / 2 << "] = (double)(w * T); }\n";
+    }
+    o << "        }\n      }\n    }\n";
+    o << "    bym_bin_flush<" << NL << ">(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  };
+  emit_kcontract("kcontract", false);
+  if (key.los == 2) emit_kcontract("kcontract_x", true);
+
+  // ------------------------------------------------------------------ midpoint combine
+  if (key.los == 1) {
+    auto terms = midpoint_terms(key.ell_max, key.K);
+    o << "extern \"C\" __global__ void __launch_bounds__(256) mid_combine(const real* __restrict__ G,"
+         " long long slot, real* __restrict__ Hout, int N, double tscale) {\n";
+    o << "  const long long ncell = (long long)N * N * N;\n";
+    o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
+         " c += (long long)gridDim.x * blockDim.x) {\n";
+    o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
+    o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
+    o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+    o << "    const int jx = bym_lab(ix, N), jy = bym_lab(iy, N), jz = bym_lab(iz, N);\n";
+    o << "    const int j2 = jx * jx + jy * jy + jz * jz;\n";
+    o << "    const real rr = bym_sqrt((real)j2);\n";
+    o << "    const real ir = j2 > 0 ? (real)1 / rr : (real)0;\n";
+    o << "    const real ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = j2 > 0 ? (real)1 : (real)0;\n";
+    o << "    const real t1 = (real)(rr * tscale);\n";
+    for (int a = 2; a <= key.K; ++a) o << "    const real t" << a << " = t" << a - 1 << " * t1;\n";
+    {
+      std::ostringstream yy;
+      emit_ylm(yy, key.K, f32, "yd", "ux", "uy", "uz", "zm");
+      std::istringstream is(yy.str());
+      std::string line;
+      while (std::getline(is, line)) o << "  " << line << "\n";
+    }
+    for (int i = 0; i < n_lm; ++i) o << "    real H" << i << " = (real)0;\n";
+    for (int a = 0; a <= key.K; ++a) {
+      std::set<int> gs;
+      std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> groups;  // (lm, y) -> (g, c)
+      for (auto &tm : terms)
+        if (tm.alpha == a) {
+          gs.insert(tm.g);
+          groups[{tm.lm, tm.y}].push_back({tm.g, tm.c});
+        }
+      if (groups.empty()) continue;
+      o << "    {\n";
+      for (int g : gs) o << "      const real g" << g << " = G[" << g << "LL * slot + off];\n";
+      for (auto &kv : groups) {
+        o << "      { real S = (real)0;";
+        for (auto &gc : kv.second) o << " S += " << lit(gc.second, f32) << " * g" << gc.first << ";";
+        o << " H" << kv.first.first << " += yd" << kv.first.second;
+        if (a > 0) o << " * t" << a;
+        o << " * S; }\n";
+      }
+      o << "    }\n";
+    }
+    for (int i = 0; i < n_lm; ++i) o << "    Hout[" << i << "LL * slot + off] = H" << i << ";\n";
+    o << "  }\n}\n";
+  }
+
+  // ------------------------------------------------------------------ xi on the lag cube
+  int jlag = L;
+  std::vector<XiTerm> xterms;
+  if (key.los == 1) {
+    xterms = midpoint_xi_terms(key.ell_max, key.K);
+    for (auto &x : xterms) jlag = std::max(jlag, x.J);
+  }
+  o << "extern \"C\" __global__ void __launch_bounds__(256) xi_lag(const real* __restrict__ Z, long long slot,"
+       " int N, int jm, int full, const int* __restrict__ lut, int nbins, double* __restrict__ gsum,"
+       " double zscale, double tscale) {\n";
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n";
+  o << "  const int Lc = full ? N : 2 * jm + 1;\n";
+  emit_bin_loop_head(o, "(long long)Lc * Lc * Lc");
+  o << "    int bin = -1; double v[" << NL << "] = {";
+  for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
+  o << "};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int a = (int)(m % Lc); const long long t = m / Lc;\n";
+  o << "      const int b = (int)(t % Lc); const int c = (int)(t / Lc);\n";
+  o << "      const int jx = full ? bym_lab(c, N) : c - jm, jy = full ? bym_lab(b, N) : b - jm,"
+       " jz = full ? bym_lab(a, N) : a - jm;\n";
+  o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
+  o << "      bin = lut[j2];\n";
+  o << "      if (bin >= 0) {\n";
+  o << "        const int ix = jx < 0 ? jx + N : jx, iy = jy < 0 ? jy + N : jy, iz = jz < 0 ? jz + N : jz;\n";
+  o << "        const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "        const double rr = sqrt((double)j2); const double ir = 1.0 / rr;\n";
+  o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
+  {
+    std::ostringstream yy;
+    emit_ylm(yy, jlag, false, "yl", "ux", "uy", "uz", "zm");
+    std::istringstream is(yy.str());
+    std::string line;
+    while (std::getline(is, line)) o << "      " << line << "\n";
+  }
+  if (key.los == 1) {
+    int amax = 0;
+    for (auto &x : xterms) amax = std::max(amax, x.alpha);
+    o << "        const double t1 = rr * tscale;\n";
+    for (int a2 = 2; a2 <= amax; ++a2) o << "        const double t" << a2 << " = t" << a2 - 1 << " * t1;\n";
+    for (int l = 0; l <= L; l += 2) {
+      o << "        { double T = 0.0;\n";
+      for (auto &x : xterms) {
+        if (x.l != l) continue;
+        o << "          { double S = 0.0;";
+        for (int nu = -x.J; nu <= x.J; ++nu)
+          o << " S += yl" << ylm_index(x.J, nu) << " * (double)Z["
+            << midpoint_gfield_index(key.ell_max, x.alpha, x.J, nu) << "LL * slot + off];";
+        o << " T += " << lit(x.f, false);
+        if (x.alpha > 0) o << " * t" << x.alpha;
+        o << " * S; }\n";
+      }
+      o << "          v[" << l / 2 << "] = T * zscale; }\n";
+    }
+  } else {
+    for (int l = 0; l <= L; l += 2) {
+      o << "        { double T = 0.0;";
+      for (int mu = -l; mu <= l; ++mu)
+        o << " T += yl" << ylm_index(l, mu) << " * (double)Z[" << even_lm_index(l, mu) << "LL * slot + off];";
+      o << " v[" << l / 2 << "] = T * zscale; }\n";
+    }
+  }
+  o << "      }\n    }\n";
+  o << "    bym_bin_flush<" << NL << ">(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+
+  if (meta) {
+    meta->key = key;
+    meta->fields = F.list;
+    meta->n_lm = n_lm;
+    meta->n_ell = NL;
+    meta->jmax_lag = jlag;
+  }
+  return o.str();
+}
+
+bool compile_cubin(const std::string &src, std::vector<char> &cubin, std::string &log) {
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "bym_generated.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    log = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "-lineinfo",
+                        "-diag-suppress=177,550"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 5, opts);
+  size_t n = 0;
+  nvrtcGetProgramLogSize(prog, &n);
+  log.assign(n, '\0');
+  if (n) nvrtcGetProgramLog(prog, &log[0]);
+  if (rc != NVRTC_SUCCESS) {
+    nvrtcDestroyProgram(&prog);
+    return false;
+  }
+  size_t cn = 0;
+  nvrtcGetCUBINSize(prog, &cn);
+  cubin.resize(cn);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  return true;
+}
+
+std::shared_ptr<KernelSet> get_kernels(const JitKey &key, std::string &err) {
+  static std::mutex mu;
+  static std::map<JitKey, std::shared_ptr<KernelSet>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  auto ks = std::make_shared<KernelSet>();
+  std::string src;
+  try {
+    src = generate_source(key, ks.get());
+  } catch (const std::exception &e) {
+    err = std::string("kernel generation failed: ") + e.what();
+    return nullptr;
+  }
+  std::vector<char> cubin;
+  std::string log;
+  if (!compile_cubin(src, cubin, log)) {
+    err = "NVRTC compile failed: " + log.substr(0, 2000);
+    return nullptr;
+  }
+  if (cudaLibraryLoadData(&ks->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+    err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(cudaGetLastError());
+    return nullptr;
+  }
+  auto get = [&](const char *name, cudaKernel_t *k) {
+    if (cudaLibraryGetKernel(k, ks->lib, name) != cudaSuccess) {
+      cudaGetLastError();
+      *k = nullptr;
+    }
+  };
+  get("gen_fields", &ks->gen_fields);
+  get("kgeom", &ks->kgeom);
+  get("rgeom", &ks->rgeom);
+  get("kcontract", &ks->kcontract);
+  get("kcontract_x", &ks->kcontract_x);
+  get("mid_combine", &ks->mid_combine);
+  get("xi_lag", &ks->xi_lag);
+  if (!ks->gen_fields || !ks->kgeom || !ks->rgeom || !ks->kcontract || !ks->xi_lag) {
+    err = "generated module is missing a kernel";
+    return nullptr;
+  }
+  cache[key] = ks;
+  return ks;
+}
+
+}  // namespace bym

@@ -1,0 +1,45 @@
+// Runtime-specialised kernels: for each (LOS, ell_max, order, precision) the
+// generator writes straight-line CUDA C++ (unrolled real-harmonic recurrences,
+// sparse couplings as immediates) and compiles it with NVRTC for sm_103a.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+namespace bym {
+
+struct JitKey {
+  int los, ell_max, K, prec;
+  bool operator<(const JitKey &o) const {
+    if (los != o.los) return los < o.los;
+    if (ell_max != o.ell_max) return ell_max < o.ell_max;
+    if (K != o.K) return K < o.K;
+    return prec < o.prec;
+  }
+};
+
+struct FieldInfo { int alpha, J, nu; };
+
+struct KernelSet {
+  JitKey key;
+  std::vector<FieldInfo> fields;   // fields written by gen_fields, in slot order
+  int n_lm = 0;                    // number of (ell, mu) outputs, even ell <= ell_max
+  int n_ell = 0;                   // ell = 0, 2, .., ell_max
+  int jmax_lag = 0;                // harmonic degree needed on the lag grid by xi_lag
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t gen_fields = nullptr, kgeom = nullptr, rgeom = nullptr;
+  cudaKernel_t kcontract = nullptr, kcontract_x = nullptr, mid_combine = nullptr, xi_lag = nullptr;
+};
+
+// Source text for a configuration (exposed for build checks).
+std::string generate_source(const JitKey &key, KernelSet *meta);
+
+// Compile to a cubin for sm_103a; returns false and fills log on failure.
+bool compile_cubin(const std::string &src, std::vector<char> &cubin, std::string &log);
+
+// Process-wide cache: generate, compile, load.  Thread-safe.
+std::shared_ptr<KernelSet> get_kernels(const JitKey &key, std::string &err);
+
+}  // namespace bym
