@@ -1,0 +1,377 @@
+"""Benchmark: catalogs/s of the pairwise-LOS P_ell(k) + xi_ell(r) estimators on GB300.
+
+One step = one survey-like catalog through the whole hot path: painting, field
+generation, batched R2C/C2R transforms, k-space and lag-space contractions and
+FP64 shell binning, for the midpoint AND the bisector line of sight, both P_ell
+and xi_ell, ell <= 4, order 4 in theta, on a 512^3 TSC mesh.
+
+Workload (synthetic stand-in for the paper's BOSS DR12 NGC Patchy mocks):
+lognormal density with P(k) = 2e4 (k/0.1)^-1.5, Kaiser RSD (f = 0.7, b = 2)
+along each galaxy's radial direction, 1e6 galaxies in a 30 degree cap over
+800-1600 Mpc/h, 1e7 uniform randoms, FKP weights (P0 = 1e4), doubled bounding
+box; k bins 0.01..0.25 h/Mpc (dk = 0.01), r bins 10..190 Mpc/h (dr = 10),
+as in the paper's Sec. 7.2.  Inputs and fields (tens of GB) exceed the 129 MB
+L2, so no explicit flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank processes its own catalogs (independent replicas,
+weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "catalogs/s for P_ℓ,ξ_ℓ (ℓ≤4, order 4, 512³)"
+N_MESH = 512
+ORDER = 4
+ELL_MAX = 4
+KEDGES = np.round(np.arange(0.01, 0.2501, 0.01), 10)
+REDGES = np.arange(10.0, 190.01, 10.0)
+WORKLOAD = ("survey-like lognormal cap (30 deg, 800-1600 Mpc/h, 1e6 gal + 1e7 ran, FKP P0=1e4, "
+            "Kaiser f=0.7 b=2), 512^3 TSC compensated, midpoint+bisector LOS, order 4, ell<=4, P_ell+xi_ell")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mesh", type=int, default=N_MESH, help="mesh size (512 is the benchmark workload)")
+    ap.add_argument("--n-gal", type=int, default=1_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_catalog(seed, n_gal):
+    from synth import lognormal_cap_catalog
+    return lognormal_cap_catalog(seed=seed, n_gal=n_gal, ran_factor=10.0, half_angle_deg=30.0, r_min=800.0,
+                                 r_max=1600.0, gen_mesh=256)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle baseline
+def oracle_sample(cat, n_mesh_full):
+    """Time the FP64 oracle on a bounded sample of the same workload and scale it.
+
+    Sample: the same estimators (midpoint and bisector, P_ell and xi_ell, order
+    4, ell <= 4, TSC, compensated) on every 10th object of the catalog, on a
+    32^3 mesh.  Its painting time is measured separately and scaled by 10 (object
+    count); the rest (FFTs and field arithmetic) by the mesh work ratio
+    (512/32)^3 * log(512^3)/log(32^3)."""
+    from oracle import estimators as E
+    from oracle import mesh as M
+    sub = slice(None, None, 10)
+    gal, ran, rn = cat.gal[sub], cat.ran[sub], cat.ran_nbar[sub]
+    Ns = 32
+    kw = dict(N=Ns, box_lo=cat.box_lo, box_len=cat.box_len, assign=3, ell_max=ELL_MAX, order=ORDER,
+              compensate=True)
+    t0 = time.perf_counter()
+    M.density_mesh(gal, ran, Ns, cat.box_lo, cat.box_len, 3)
+    t_paint = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for los in ("midpoint", "bisector"):
+        E.pk_multipoles(gal, ran, rn, los=los, kedges=KEDGES, **kw)
+        E.xi_multipoles(gal, ran, rn, los=los, redges=REDGES, **kw)
+    t_sample = time.perf_counter() - t0
+    n_paint = 4
+    t_mesh = max(t_sample - n_paint * t_paint, 0.0)
+    ratio = (n_mesh_full / Ns) ** 3 * math.log(n_mesh_full ** 3) / math.log(Ns ** 3)
+    t_full = n_paint * t_paint * 10.0 + t_mesh * ratio
+    return {"value": 1.0 / t_full, "unit": "catalogs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"FP64 oracle (numpy/scipy.fft, all {os.cpu_count()} host cores) on every 10th object at "
+                       f"32^3: {t_sample:.1f} s measured (painting {t_paint:.2f} s per call); scaled to the "
+                       f"full catalog at {n_mesh_full}^3 by object count (painting) and by mesh work "
+                       f"(N^3 log N^3, x{ratio:.0f}) -> {t_full:.0f} s per catalog"),
+            "sample_seconds": t_sample}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    cat = make_catalog(1, args.n_gal)
+    if args.warmup > 0:
+        oracle_sample(cat, args.mesh)      # builds the oracle's coefficient caches
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(cat, args.mesh))
+    wall = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    cb.pop("sample_seconds", None)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "catalogs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_mesh": args.mesh, "order": ORDER, "ell_max": ELL_MAX,
+                       "parallelism": "host cores", "l2": "inputs larger than L2"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "catalogs/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_2102_08384_gb300 as pkg
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    cat = make_catalog(1 + rank, args.n_gal)
+    gal_d = torch.from_numpy(cat.gal).to(dev)
+    ran_d = torch.from_numpy(cat.ran).to(dev)
+    rnb_d = torch.from_numpy(cat.ran_nbar).to(dev)
+    ctx = pkg.Context(local)
+    params = [pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=args.mesh, assign=3,
+                              ell_max=ELL_MAX, los=los, order=ORDER, compensate=True, precision=32, norm=1)
+              for los in ("midpoint", "bisector")]
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def step(g, r, rn):
+        out = []
+        for p in params:
+            out.append(ctx.pk_xi_multipoles(g, r, p, KEDGES, REDGES, ran_nbar=rn, stream=sh))
+        return out
+
+    for _ in range(args.warmup):
+        step(gal_d, ran_d, rnb_d)
+    torch.cuda.synchronize(dev)
+
+    # device-resident timed region
+    pkg.lib().bym_profile_enable(ctx._h, 1)
+    _read_profile(pkg, ctx, reset=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    with ClockSampler(gpu_index) as cs:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(gal_d, ran_d, rnb_d)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = _read_profile(pkg, ctx, reset=True)
+    pkg.lib().bym_profile_enable(ctx._h, 0)
+    clocks = cs.summary()
+    ms_max = _max_over_ranks(ms, ws)
+    value = ws * args.steps / (ms_max / 1000.0)
+
+    # end to end: pinned host catalogs, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        g_h = torch.from_numpy(cat.gal).pin_memory().numpy()
+        r_h = torch.from_numpy(cat.ran).pin_memory().numpy()
+        rn_h = torch.from_numpy(cat.ran_nbar).pin_memory().numpy()
+        step(g_h, r_h, rn_h)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(g_h, r_h, rn_h)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_e = _max_over_ranks(e0.elapsed_time(e1), ws)
+        nl, nbk, nbr = ELL_MAX // 2 + 1, len(KEDGES) - 1, len(REDGES) - 1
+        h2d = 2 * (g_h.nbytes + r_h.nbytes + rn_h.nbytes)
+        d2h = 2 * (8 * 8 + nl * nbk * 8 + nl * nbr * 8)
+        e2e = {"value": ws * args.steps / (ms_e / 1000.0), "unit": "catalogs/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        ctx.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    roofline, kernels, launches = _roofline(prof, args.steps)
+    line = {"metric": METRIC, "value": value, "unit": "catalogs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_mesh": args.mesh, "order": ORDER, "ell_max": ELL_MAX,
+                       "n_gal": int(len(cat.gal)), "n_ran": int(len(cat.ran)), "box_len": cat.box_len,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (catalog 176 MB, fields > 30 GB)"},
+            "e2e": e2e, "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "kernels": kernels}
+    if ws == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(cat, args.mesh)
+        cb.pop("sample_seconds", None)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _read_profile(pkg, ctx, reset):
+    import ctypes
+    buf = ctypes.create_string_buffer(1 << 16)
+    pkg.lib().bym_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int]
+    pkg.lib().bym_profile_read(ctx._h, buf, len(buf), int(reset))
+    return json.loads(buf.value.decode() or "{}")
+
+
+def _max_over_ranks(ms, ws):
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _roofline(prof, steps):
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    kernels = {}
+    ours_launches = 0
+    for name, e in prof.items():
+        gbs = e["bytes"] / (e["ms"] * 1e-3) / 1e9 if e["ms"] > 0 else None
+        kernels[name] = {"launches": e["launches"], "ms_total": e["ms"],
+                         "ms_per_step": e["ms"] / steps, "algorithmic_GBps": gbs,
+                         "frac_of_" + src + "_hbm": (gbs / hbm) if gbs else None}
+        if not name.startswith("cufft"):
+            ours_launches += e["launches"]
+    ours = {k: v for k, v in prof.items() if not k.startswith("cufft")}
+    if not ours:
+        return None, kernels, ours_launches
+    top = max(ours, key=lambda k: ours[k]["ms"])
+    e = ours[top]
+    per_launch_bytes = e["bytes"] / e["launches"]
+    per_launch_s = e["ms"] / e["launches"] * 1e-3
+    ach = per_launch_bytes / per_launch_s / 1e9
+    roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "peak_source": src, "traffic": _ncu_traffic(top), "algorithmic_bytes_per_launch": per_launch_bytes}
+    return roof, kernels, ours_launches
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current build (profiles/traffic.md lists kernel | bytes | build id)."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    try:
+        import paper_2102_08384_gb300.build as b
+        build_id = b.source_hash()
+    except Exception:
+        return None
+    for line in open(path):
+        parts = [p.strip() for p in line.strip().strip("|").split("|")]
+        if len(parts) >= 3 and parts[0] == kernel and parts[2] == build_id:
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

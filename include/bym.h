@@ -86,7 +86,7 @@ typedef struct {
 
 typedef struct {
   const double *edges;   /* nbins + 1 increasing edges, host memory */
-  int nbins;             /* 1..4096 */
+  int nbins;             /* 1..1024 */
 } bym_bins;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
@@ -135,6 +135,16 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
 /* Compile (without running) the runtime-specialised kernels for these
  * parameters; works without a GPU.  Used by build checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
+
+/* Kernel tracing.  While enabled, every launch of the library's own kernels
+ * and every cuFFT execution on ctx is bracketed by CUDA events on its stream;
+ * bym_profile_read writes a JSON object
+ *   {"<kernel>": {"launches": n, "ms": total, "bytes": algorithmic bytes}, ...}
+ * into json (truncated to len) and, if reset != 0, clears the totals.
+ * Algorithmic bytes are the bytes each launch must move at minimum (inputs
+ * read once, outputs written once). */
+int bym_profile_enable(bym_ctx *ctx, int enable);
+int bym_profile_read(bym_ctx *ctx, char *json, size_t len, int reset);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,19 @@ def _deps():
         [os.path.join(ROOT, "include", "bym.h"), os.path.abspath(__file__)]
 
 
+def source_hash() -> str:
+    """Short content hash of the library sources (identifies a kernel build)."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in sorted(_deps()):
+        if os.path.basename(d) == "build.py":
+            continue
+        with open(d, "rb") as fh:
+            h.update(os.path.basename(d).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False

@@ -74,6 +74,57 @@ bool finite_all(const double *v, int n) {
   return true;
 }
 
+cudaEvent_t prof_event(bym_ctx *c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch with events when tracing is on; the totals are
+// gathered by prof_collect once the stream has been synchronised.
+struct ProfScope {
+  bym_ctx *c;
+  cudaStream_t st;
+  const char *name;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(bym_ctx *c_, cudaStream_t st_, const char *name_, double bytes_)
+      : c(c_), st(st_), name(name_), bytes(bytes_) {
+    if (c->prof) {
+      a = prof_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(c);
+    cudaEventRecord(b, st);
+    c->prof_pending.push_back({name, a, b, bytes});
+  }
+};
+
+void prof_collect(bym_ctx *c) {
+  for (auto &p : c->prof_pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto &e = c->prof_tab[p.name];
+      e.launches += 1;
+      e.ms += ms;
+      e.bytes += p.bytes;
+    } else {
+      cudaGetLastError();
+    }
+    c->prof_pool.push_back(p.a);
+    c->prof_pool.push_back(p.b);
+  }
+  c->prof_pending.clear();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -196,6 +247,8 @@ static int get_plan(bym_ctx *c, int N, int prec, int inverse, int batch, cufftHa
 
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
                      int first, int count) {
+  const double esz = prec == 64 ? 8.0 : 4.0;
+  ProfScope ps(c, st, inverse ? "cufft_c2r" : "cufft_r2c", count * 2.0 * esz * (double)N * N * N);
   for (int done = 0; done < count;) {
     const int b = std::min(kFftBatch, count - done);
     cufftHandle h;
@@ -436,15 +489,27 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   CUDA_TRY(cudaMemsetAsync(slots, 0, slot_bytes, st));
 
   // norms and painting
+  const double esz = (double)sizeof(T), n3 = (double)N * N * N, nhalf = (double)N * N * (N / 2 + 1);
   for (int w = 0; w < 2; ++w)
-    if (cat4[w]) launch_norm_reduce(cat4[w], catnb[w], catn[w], w, p->box_lo, inv_h, N, stats, c->nsm, st);
+    if (cat4[w]) {
+      ProfScope ps(c, st, "norm_reduce", catn[w] * (w ? 20.0 : 16.0));
+      launch_norm_reduce(cat4[w], catnb[w], catn[w], w, p->box_lo, inv_h, N, stats, c->nsm, st);
+    }
   for (int w = 0; w < 2; ++w)
-    if (cat4[w]) launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(0), N, p->box_lo, inv_h, p->assign, c->nsm, st);
+    if (cat4[w]) {
+      ProfScope ps(c, st, "paint", catn[w] * 16.0 + n3 * esz);
+      launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(0), N, p->box_lo, inv_h, p->assign, c->nsm, st);
+    }
   CUDA_TRY(cudaGetLastError());
+  static const char *kLosName[3] = {"yamamoto", "midpoint", "bisector"};
+  const std::string los_name = kLosName[p->los];
+  const std::string n_gen = "gen_fields_" + los_name, n_kc = "kcontract_" + los_name, n_xi = "xi_lag_" + los_name;
+  const double cplx = 2.0 * esz * nhalf;  // one half-spectrum
 
   // field generation
   {
     const long long ncell = (long long)N * N * N;
+    ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * n3 * esz);
     CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, 16), 256, 0, st, (const T *)slot_r(0), slot_r(1),
                     slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
   }
@@ -455,43 +520,62 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
 
   if (p->los == BYM_LOS_YAMAMOTO) {
     TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
-    if (want_pk)
+    if (want_pk) {
+      ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
+    }
     if (want_xi) {
-      launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+      {
+        ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
+        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+      }
       TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nlm * esz);
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
   } else if (p->los == BYM_LOS_MIDPOINT) {
     TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
-    launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+    {
+      ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
+      launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+    }
     TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
     if (want_xi) {
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nf * esz);
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
     if (want_pk) {
-      CUDA_TRY(launch(K.mid_combine, grid_of((long long)N * N * N, c->nsm, 16), 256, 0, st, (const T *)slot_r(1),
-                      slot_reals, slot_r(1 + nf), N, tscale));
+      {
+        ProfScope ps(c, st, "mid_combine", ((double)nf + nlm) * n3 * esz);
+        CUDA_TRY(launch(K.mid_combine, grid_of((long long)N * N * N, c->nsm, 16), 256, 0, st,
+                        (const T *)slot_r(1), slot_reals, slot_r(1 + nf), N, tscale));
+      }
       TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm));
+      ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
     }
   } else {
     TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf));
     if (want_xi) {
-      CUDA_TRY(launch(K.kcontract_x, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
-                      (const int *)kg->lut, nbk, ksum, slot_c(1 + nf), cslot, (const T *)invw));
+      {
+        ProfScope ps(c, st, "kcontract_bisector_x", ((double)nf + nlm) * cplx);
+        CUDA_TRY(launch(K.kcontract_x, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
+                        (const int *)kg->lut, nbk, ksum, slot_c(1 + nf), cslot, (const T *)invw));
+      }
       TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1 + nf, nlm));
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nlm * esz);
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
                       (const T *)slot_r(1 + nf), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
                       1.0 / ((double)N * N * N), tscale));
     } else {
+      ProfScope ps(c, st, n_kc.c_str(), (double)nf * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
     }
@@ -504,6 +588,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   CUDA_TRY(cudaMemcpyAsync(hk.data(), ksum, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hr.data(), rsum, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  prof_collect(c);
   if (hstats[3] > 0.0)
     return fail(c, BYM_E_OUT_OF_BOX,
                 std::to_string((long long)hstats[3]) + " objects lie outside the box or are not finite");
@@ -591,6 +676,11 @@ void bym_destroy(bym_ctx *c) {
   cudaStreamSynchronize(c->stream);
   shutdown_serving(c);
   for (auto &kv : c->plans) cufftDestroy(kv.second);
+  for (auto &p : c->prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
   if (c->fft_work) cudaFree(c->fft_work);
   for (auto *m : {&c->kgeo, &c->rgeo})
     for (auto &kv : *m)
@@ -635,6 +725,34 @@ int bym_pk_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *
   std::lock_guard<std::mutex> lock(c->mu);
   Request rq{gal, ran, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
   return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_profile_enable(bym_ctx *c, int enable) {
+  if (!c) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  c->prof = enable != 0;
+  return BYM_OK;
+}
+
+int bym_profile_read(bym_ctx *c, char *json, size_t len, int reset) {
+  if (!c || !json || !len) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  std::ostringstream o;
+  o.precision(17);
+  o << "{";
+  bool first = true;
+  for (auto &kv : c->prof_tab) {
+    o << (first ? "" : ", ") << "\"" << kv.first << "\": {\"launches\": " << kv.second.launches
+      << ", \"ms\": " << kv.second.ms << ", \"bytes\": " << kv.second.bytes << "}";
+    first = false;
+  }
+  o << "}";
+  const std::string s = o.str();
+  const size_t n = std::min(len - 1, s.size());
+  memcpy(json, s.data(), n);
+  json[n] = '\0';
+  if (reset) c->prof_tab.clear();
+  return s.size() < len ? BYM_OK : BYM_E_INVAL;
 }
 
 int bym_jit_check(const bym_params *p, char *log, size_t log_len) {

@@ -35,6 +35,16 @@ struct Request {
 
 struct Server;  // serving loop state (serve.cpp)
 
+struct ProfEntry {
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+struct ProfPending {
+  std::string name;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
 }  // namespace bym
 
 struct bym_ctx {
@@ -49,6 +59,10 @@ struct bym_ctx {
   size_t fft_work_size = 0;
   std::map<std::string, bym::Geom> kgeo, rgeo;
   bym::Server *server = nullptr;
+  bool prof = false;                                           // kernel tracing (bym_profile_enable)
+  std::map<std::string, bym::ProfEntry> prof_tab;
+  std::vector<bym::ProfPending> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
 };
 
 namespace bym {
