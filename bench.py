@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--n-gal", type=int, default=1_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--los", default="midpoint,bisector", help="comma-separated LOS list (profiling runs)")
     return ap.parse_args()
 
 
@@ -207,7 +208,7 @@ def run_ours(args):
     ctx = pkg.Context(local)
     params = [pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=args.mesh, assign=3,
                               ell_max=ELL_MAX, los=los, order=ORDER, compensate=True, precision=32, norm=1)
-              for los in ("midpoint", "bisector")]
+              for los in args.los.split(",")]
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
 
