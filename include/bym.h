@@ -146,6 +146,33 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 int bym_profile_enable(bym_ctx *ctx, int enable);
 int bym_profile_read(bym_ctx *ctx, char *json, size_t len, int reset);
 
+/* Yamamoto P_ell(k) from field spectra the caller already holds, for callers
+ * that cannot allocate device memory (an allocator owned by another framework,
+ * a fixed memory budget carved out up front, code that runs while allocation
+ * is not allowed).  The paper has no counterpart of this entry point; it is
+ * the k-space contraction and FP64 shell binning of bym_pk_multipoles with
+ * LOS = Yamamoto, run on the caller's data without any cudaMalloc.
+ *   F: device memory, (ell_max/2+1)^2 consecutive half-spectra of
+ *      n_mesh * n_mesh * (n_mesh/2 + 1) complex floats (re, im interleaved,
+ *      kz fastest), the forward transforms of Y_{l mu}(hat x) delta(x) for
+ *      even l <= ell_max, mu = -l..l, in that order.  Y_{l mu} are the real
+ *      spherical harmonics Y_{l,0} = Y_l^0, Y_{l,m} = sqrt2 (-1)^m Re Y_l^m,
+ *      Y_{l,-m} = sqrt2 (-1)^m Im Y_l^m (m > 0), Y_l^m as in DLMF 14.30.
+ *   D: device memory, the half-spectrum of delta in the same layout.
+ *   pk, n_modes: host outputs as for bym_pk_multipoles; P_ell = 4 pi / norm_A
+ *      times the bin mean (no compensation).
+ * Limits: FP32 spectra, n_mesh <= 512, ell_max <= 4, nbins <= 1024; larger
+ * requests return BYM_E_UNSUPPORTED.  Scratch lives in one static device array
+ * of 1 MiB that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other's sums.  The current device is used;
+ * the call is synchronous on cuda_stream (NULL: the legacy default stream). */
+int bym_pk_yamamoto_from_spectra_noalloc(const void *F, const void *D, int n_mesh, double box_len,
+                                         int ell_max, const bym_bins *kbins, double norm_A, double *pk,
+                                         int64_t *n_modes, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
