@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--los", default="midpoint,bisector", help="comma-separated LOS list (profiling runs)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving / batching leg")
+    ap.add_argument("--serve-requests", type=int, default=24)
     return ap.parse_args()
 
 
@@ -284,6 +286,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (catalog 176 MB, fields > 30 GB)"},
             "e2e": e2e, "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "kernels": kernels}
+    if ws == 1 and not args.no_serve:
+        line["serving"] = serving_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, args.serve_requests)
     if ws == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(cat, args.mesh)
         cb.pop("sample_seconds", None)
@@ -292,6 +296,71 @@ def run_ours(args):
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def serving_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_req, slots=4):
+    """Mixed requests (meshes 128-256^3, every LOS, orders 0-4, uneven catalogs: the first
+    10-100 % of the galaxies and randoms) run (a) one at a time, (b) as one batch through
+    the serving loop, (c) as a Poisson stream at 0.8x the sequential capacity, for p50/p99."""
+    rng = np.random.default_rng(3)
+    ng, nr = gal_d.shape[0], ran_d.shape[0]
+    items = []
+    for i in range(n_req):
+        N = int(rng.choice([128, 192, 256]))
+        los = ["yamamoto", "midpoint", "bisector"][i % 3]
+        K = 0 if los == "yamamoto" else int(rng.choice([2, 4]))
+        frac = float(10 ** rng.uniform(-1, 0))
+        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=ELL_MAX, los=los,
+                            order=K, compensate=True, precision=32, norm=1)
+        items.append(dict(gal=gal_d[: int(frac * ng)], ran=ran_d[: int(frac * nr)], ran_nbar=rnb_d[: int(frac * nr)],
+                          params=p, kedges=KEDGES, redges=REDGES))
+    ctx = pkg.Context(dev.index)
+
+    def alone(it):
+        return ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
+                                    ran_nbar=it["ran_nbar"])
+
+    for it in items:                       # compile kernels, build plans and tables
+        alone(it)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for it in items:
+        alone(it)
+    t_seq = time.perf_counter() - t0
+    ctx.serve_start(n_slots=slots)
+    for it in items:                       # per-slot plans
+        ctx.wait(ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"]))
+    t0 = time.perf_counter()
+    ts = [ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"])
+          for it in items]
+    for t in ts:
+        ctx.wait(t)
+    t_batch = time.perf_counter() - t0
+    ctx.serve_stop()
+    # Poisson arrivals at 0.8x the sequential capacity
+    rate = 0.8 * len(items) / t_seq
+    ctx.serve_start(n_slots=slots)
+    gaps = rng.exponential(1.0 / rate, size=len(items))
+    ts = []
+    t0 = time.perf_counter()
+    for it, g in zip(items, gaps):
+        time.sleep(g)
+        ts.append(ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"]))
+    for t in ts:
+        ctx.wait(t)
+    t_stream = time.perf_counter() - t0
+    st = ctx.serve_stats()
+    ctx.serve_stop()
+    ctx.close()
+    return {"requests": len(items), "slots": slots,
+            "mix": "meshes {128,192,256}^3, LOS cycling yamamoto/midpoint/bisector, order in {2,4}, "
+                   "10-100 % of the catalog (log-uniform), P_ell+xi_ell, FP32",
+            "sequential_catalogs_per_s": len(items) / t_seq,
+            "batched_catalogs_per_s": len(items) / t_batch,
+            "poisson_rate_per_s": rate, "poisson_catalogs_per_s": len(items) / t_stream,
+            "p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"],
+            "run_p50_s": st["run_p50_s"], "run_p99_s": st["run_p99_s"], "mean_queue_s": st["mean_queue_s"],
+            "peak_hbm_gb": st["peak_hbm_bytes"] / 1e9}
 
 
 def _read_profile(pkg, ctx, reset):

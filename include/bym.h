@@ -146,6 +146,53 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 int bym_profile_enable(bym_ctx *ctx, int enable);
 int bym_profile_read(bym_ctx *ctx, char *json, size_t len, int reset);
 
+/* ---------------------------------------------------------------------------
+ * Serving and batching.  A context can run a serving loop: n_slots worker
+ * slots, each with its own CUDA stream, cuFFT plans and work area, take
+ * requests from a queue as slots and HBM budget free up (continuous
+ * batching; first request that fits is admitted, so a large request does not
+ * block small ones behind it).  Work of different slots overlaps on the GPU.
+ * Each request's projected footprint (bym_footprint) is charged against the
+ * budget while it runs.  The caller owns every array a request points to and
+ * must keep it alive and unchanged until the request is done.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  bym_catalog gal, ran;   /* ran.n = 0: no randoms */
+  bym_params params;
+  bym_bins kbins, rbins;  /* nbins = 0: that statistic is not requested */
+} bym_request;
+
+typedef struct {          /* caller-allocated host outputs, as for bym_pk_xi_multipoles */
+  double *pk, *k_mean;
+  int64_t *n_modes;
+  double *xi, *r_mean;
+  int64_t *n_cells;
+} bym_result;
+
+/* Start the serving loop (n_slots 1..16; hbm_budget_bytes 0: 90 % of the
+ * free device memory).  BYM_E_BUSY if a loop is already running. */
+int bym_serve_start(bym_ctx *ctx, int n_slots, size_t hbm_budget_bytes);
+/* Stop after the queued and running requests have finished. */
+int bym_serve_stop(bym_ctx *ctx);
+/* Queue a request; *ticket identifies it.  BYM_E_NOMEM if its footprint can
+ * never fit the budget; BYM_E_INVAL for bad arguments (checked at submit). */
+int bym_submit(bym_ctx *ctx, const bym_request *req, const bym_result *out, uint64_t *ticket);
+/* *done = 1 once the request has finished (successfully or not). */
+int bym_poll(bym_ctx *ctx, uint64_t ticket, int *done);
+/* Wait up to timeout_s seconds (< 0: forever).  Returns BYM_E_TIMEOUT if the
+ * request is still queued or running (it keeps going); otherwise BYM_OK with
+ * the request's own return code in *status, and forgets the ticket. */
+int bym_wait(bym_ctx *ctx, uint64_t ticket, double timeout_s, int *status);
+/* Latency statistics of the requests finished since the loop started:
+ * stats[0] count, [1] p50 and [2] p99 of submit-to-done seconds, [3] p50 and
+ * [4] p99 of run (start-to-done) seconds, [5] mean queueing seconds,
+ * [6] peak HBM bytes charged at once. */
+int bym_serve_stats(bym_ctx *ctx, double stats[7]);
+/* Run n requests through the serving loop (started with 4 slots and the
+ * default budget for the call if none is running) and wait for all;
+ * status[i] receives each request's return code. */
+int bym_batch_run(bym_ctx *ctx, int n, const bym_request *reqs, const bym_result *outs, int *status);
+
 /* Yamamoto P_ell(k) from field spectra the caller already holds, for callers
  * that cannot allocate device memory (an allocator owned by another framework,
  * a fixed memory budget carved out up front, code that runs while allocation

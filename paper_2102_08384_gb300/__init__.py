@@ -51,6 +51,15 @@ class Bins(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_void_p), ("nbins", ctypes.c_int)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("gal", Catalog), ("ran", Catalog), ("params", Params), ("kbins", Bins), ("rbins", Bins)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("pk", ctypes.c_void_p), ("k_mean", ctypes.c_void_p), ("n_modes", ctypes.c_void_p),
+                ("xi", ctypes.c_void_p), ("r_mean", ctypes.c_void_p), ("n_cells", ctypes.c_void_p)]
+
+
 _lib_handle = None
 
 
@@ -77,6 +86,16 @@ def lib():
         L.bym_pk_xi_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, dp, dp, i64p, dp, dp, i64p,
                                            vp]
         L.bym_jit_check.argtypes = [par_p, ctypes.c_char_p, ctypes.c_size_t]
+        L.bym_serve_start.argtypes = [vp, ctypes.c_int, ctypes.c_size_t]
+        L.bym_serve_stop.argtypes = [vp]
+        L.bym_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_uint64)]
+        L.bym_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+        L.bym_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+        L.bym_serve_stats.argtypes = [vp, dp]
+        L.bym_batch_run.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(Result),
+                                    ctypes.POINTER(ctypes.c_int)]
+        L.bym_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.bym_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int]
         _lib_handle = L
     return _lib_handle
 
@@ -202,6 +221,89 @@ class Context:
         self._check(rc)
         out["ells"] = list(range(0, params.ell_max + 1, 2))
         return out
+
+    # ------------------------------------------------------------ serving
+    def _request(self, gal, ran, params, kedges, redges, gal_nbar, ran_nbar):
+        """Request + Result structs and the output arrays (kept alive by the caller)."""
+        keep = []
+        req = Request()
+        g = _catalog(gal, gal_nbar, keep)
+        req.gal = g
+        r = _catalog(ran, ran_nbar, keep) if ran is not None else None
+        if r is not None:
+            req.ran = r
+        req.params = params
+        nl = params.ell_max // 2 + 1
+        out = {"ells": list(range(0, params.ell_max + 1, 2))}
+        res = Result()
+        if kedges is not None:
+            req.kbins = _bins(kedges, keep)
+            nb = req.kbins.nbins
+            out.update(pk=np.zeros((nl, nb)), k_mean=np.zeros(nb), n_modes=np.zeros(nb, dtype=np.int64))
+            res.pk, res.k_mean, res.n_modes = (out["pk"].ctypes.data, out["k_mean"].ctypes.data,
+                                               out["n_modes"].ctypes.data)
+        if redges is not None:
+            req.rbins = _bins(redges, keep)
+            nb = req.rbins.nbins
+            out.update(xi=np.zeros((nl, nb)), r_mean=np.zeros(nb), n_cells=np.zeros(nb, dtype=np.int64))
+            res.xi, res.r_mean, res.n_cells = (out["xi"].ctypes.data, out["r_mean"].ctypes.data,
+                                               out["n_cells"].ctypes.data)
+        return req, res, out, keep
+
+    def serve_start(self, n_slots=4, hbm_budget_bytes=0):
+        self._check(self._L.bym_serve_start(self._h, int(n_slots), int(hbm_budget_bytes)))
+        self._pending = {}
+
+    def serve_stop(self):
+        self._check(self._L.bym_serve_stop(self._h))
+
+    def submit(self, gal, ran, params, kedges=None, redges=None, gal_nbar=None, ran_nbar=None):
+        """Queue a request; returns a ticket.  Outputs are returned by wait()."""
+        req, res, out, keep = self._request(gal, ran, params, kedges, redges, gal_nbar, ran_nbar)
+        t = ctypes.c_uint64()
+        self._check(self._L.bym_submit(self._h, ctypes.byref(req), ctypes.byref(res), ctypes.byref(t)))
+        self._pending[t.value] = (req, res, out, keep)
+        return t.value
+
+    def poll(self, ticket):
+        d = ctypes.c_int()
+        self._check(self._L.bym_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_s=-1.0):
+        """Outputs of a finished request; raises BymError (code -5) on timeout."""
+        st = ctypes.c_int()
+        self._check(self._L.bym_wait(self._h, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(st)))
+        req, res, out, keep = self._pending.pop(ticket)
+        if st.value != BYM_OK:
+            raise BymError(st.value, f"request {ticket} failed")
+        return out
+
+    def serve_stats(self):
+        a = (ctypes.c_double * 7)()
+        self._check(self._L.bym_serve_stats(self._h, a))
+        return {"count": int(a[0]), "p50_s": a[1], "p99_s": a[2], "run_p50_s": a[3], "run_p99_s": a[4],
+                "mean_queue_s": a[5], "peak_hbm_bytes": a[6]}
+
+    def batch_run(self, items):
+        """items: list of dicts with gal, ran, params, kedges, redges, ran_nbar.  Returns outputs."""
+        n = len(items)
+        reqs = (Request * n)()
+        ress = (Result * n)()
+        outs, keeps = [], []
+        for i, it in enumerate(items):
+            rq, rs, out, keep = self._request(it["gal"], it.get("ran"), it["params"], it.get("kedges"),
+                                              it.get("redges"), it.get("gal_nbar"), it.get("ran_nbar"))
+            reqs[i], ress[i] = rq, rs
+            outs.append(out)
+            keeps.append(keep)
+        status = (ctypes.c_int * n)()
+        rc = self._L.bym_batch_run(self._h, n, reqs, ress, status)
+        for i in range(n):
+            if status[i] != BYM_OK:
+                raise BymError(status[i], f"batch item {i} failed")
+        self._check(rc)
+        return outs
 
     def pk_multipoles(self, gal, ran, params, kedges, gal_nbar=None, ran_nbar=None, stream=None):
         return self._run("pk", gal, ran, params, kedges, None, gal_nbar, ran_nbar, stream)

@@ -510,6 +510,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   {
     const long long ncell = (long long)N * N * N;
     ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * n3 * esz);
+    CUDA_TRY(cudaMemsetAsync(slot_r(1), 0, (size_t)nf * slot_bytes, st));
     CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, 16), 256, 0, st, (const T *)slot_r(0), slot_r(1),
                     slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
   }

@@ -82,14 +82,16 @@ void emit_ylm(std::ostream &o, int L, bool f32, const std::string &P, const std:
 
 const char *kPrelude = R"(
 #define BYM_FULL 0xffffffffu
-__device__ __forceinline__ double bym_wsum(double v) {
+template <typename V>
+__device__ __forceinline__ V bym_wsum(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(BYM_FULL, v, o);
   return v;
 }
 // Per-block FP64 shell sums: every lane holds (bin, v[NL]); lanes that share a
-// bin are reduced with shuffles and the group leader adds to shared memory.
-template <int NL>
-__device__ __forceinline__ void bym_bin_flush(int bin, const double (&v)[NL], double *s) {
+// bin are pre-reduced with shuffles in the value type V (at most 32 terms) and
+// the group leader adds the partial sum to the FP64 shared accumulator.
+template <int NL, typename V>
+__device__ __forceinline__ void bym_bin_flush(int bin, const V (&v)[NL], double *s) {
   unsigned pending = __ballot_sync(BYM_FULL, bin >= 0);
   const int lane = threadIdx.x & 31;
   while (pending) {
@@ -99,8 +101,8 @@ __device__ __forceinline__ void bym_bin_flush(int bin, const double (&v)[NL], do
     const unsigned grp = __ballot_sync(BYM_FULL, mine);
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-      const double x = bym_wsum(mine ? v[l] : 0.0);
-      if (lane == leader) atomicAdd(s + bl * NL + l, x);
+      const V x = bym_wsum<V>(mine ? v[l] : (V)0);
+      if (lane == leader) atomicAdd(s + bl * NL + l, (double)x);
     }
     pending &= ~grp;
   }
@@ -171,7 +173,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
       Jmax = std::max(Jmax, fi.J);
       amax = std::max(amax, fi.alpha);
     }
-    o << "extern \"C\" __global__ void __launch_bounds__(256) gen_fields(const real* __restrict__ delta,"
+    o << "extern \"C\" __global__ void __launch_bounds__(256, 2) gen_fields(const real* __restrict__ delta,"
          " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
          " double inv_r0) {\n";
     o << "  const long long ncell = (long long)N * N * N;\n";
@@ -181,9 +183,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
     o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
     o << "    const real d = delta[off];\n";
-    o << "    if (d == (real)0) {\n";
-    for (int i = 0; i < nf; ++i) o << "      out[" << i << "LL * slot + off] = (real)0;\n";
-    o << "      continue;\n    }\n";
+    o << "    if (d == (real)0) continue;   // field slots are zero-filled before the launch\n";
     o << "    const double x = lo0 + ix * h, y = lo1 + iy * h, z = lo2 + iz * h;\n";
     o << "    const double r2 = x * x + y * y + z * z;\n";
     o << "    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;\n";
@@ -191,10 +191,11 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     o << "    const double rad0 = (double)d;\n";
     if (amax > 0) o << "    const double q = r2 > 0.0 ? 1.0 / (2.0 * sqrt(r2) * inv_r0) : 0.0;\n";
     for (int a = 1; a <= amax; ++a) o << "    const double rad" << a << " = rad" << a - 1 << " * q;\n";
+    for (int a = 0; a <= amax; ++a) o << "    const real rr" << a << " = (real)rad" << a << ";\n";
     emit_ylm(o, Jmax, false, "y", "ux", "uy", "uz", "zm");
     for (int i = 0; i < nf; ++i)
-      o << "    out[" << i << "LL * slot + off] = (real)(y" << ylm_index(F.list[i].J, F.list[i].nu) << " * rad"
-        << F.list[i].alpha << ");\n";
+      o << "    out[" << i << "LL * slot + off] = (real)y" << ylm_index(F.list[i].J, F.list[i].nu) << " * rr"
+        << F.list[i].alpha << ";\n";
     o << "  }\n}\n";
   }
 
@@ -212,7 +213,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   o << "      bin = lut[n2];\n";
   o << "      if (bin >= 0) { const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;"
        " v[0] = w; v[1] = w * kf * sqrt((double)n2); }\n";
-  o << "    }\n    bym_bin_flush<2>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
+  o << "    }\n    bym_bin_flush<2, double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
 
   o << "extern \"C\" __global__ void __launch_bounds__(256) rgeom(int N, int jm, int full,"
        " const int* __restrict__ lut, int nbins, double h, double* __restrict__ gsum) {\n";
@@ -228,7 +229,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
   o << "      bin = lut[j2];\n";
   o << "      if (bin >= 0) { v[0] = 1.0; v[1] = h * sqrt((double)j2); }\n";
-  o << "    }\n    bym_bin_flush<2>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
+  o << "    }\n    bym_bin_flush<2, double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
 
   // ------------------------------------------------------------------ k-space contraction
   auto emit_kcontract = [&](const char *name, bool with_x) {
@@ -238,8 +239,8 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
          " long long xslot, const real* __restrict__ invw) {\n";
     o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n  const int H = N / 2 + 1;\n";
     emit_bin_loop_head(o, "(long long)N * N * H");
-    o << "    int bin = -1; double v[" << NL << "] = {";
-    for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
+    o << "    int bin = -1; real v[" << NL << "] = {";
+    for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "(real)0";
     o << "};\n";
     o << "    if (m < total) {\n";
     o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
@@ -291,10 +292,10 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     for (int l = 0; l <= L; l += 2) {
       o << "          { real T = (real)0;";
       for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << even_lm_index(l, mu) << ";";
-      o << " v[" << l / 2 << "] = (double)(w * T); }\n";
+      o << " v[" << l / 2 << "] = w * T; }\n";
     }
     o << "        }\n      }\n    }\n";
-    o << "    bym_bin_flush<" << NL << ">(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+    o << "    bym_bin_flush<" << NL << ", real>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
   };
   emit_kcontract("kcontract", false);
   if (key.los == 2) emit_kcontract("kcontract_x", true);
@@ -412,7 +413,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     }
   }
   o << "      }\n    }\n";
-  o << "    bym_bin_flush<" << NL << ">(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
 
   if (meta) {
     meta->key = key;

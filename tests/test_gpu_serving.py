@@ -1,0 +1,109 @@
+"""Serving loop and batch runs: each result is the same alone and in the mix.
+
+Requests of different mesh sizes, lines of sight, orders and precisions are
+queued together on a serving loop with several slots (their work overlaps on
+the GPU) and compared with the same request run alone through
+bym_pk_xi_multipoles, within the parity tolerances."""
+import math
+
+import numpy as np
+import pytest
+
+from parity import check_multipoles
+from synth import lognormal_cap_catalog
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2102_08384_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def cap():
+    return lognormal_cap_catalog(seed=4, n_gal=20000, ran_factor=10.0, gen_mesh=64)
+
+
+def _mix(pkg, cat):
+    out = []
+    for i, (N, los, K, prec) in enumerate([(32, "midpoint", 4, 32), (48, "bisector", 4, 32), (24, "yamamoto", 0, 64),
+                                           (40, "midpoint", 2, 64), (64, "bisector", 2, 32), (32, "yamamoto", 0, 32),
+                                           (56, "midpoint", 3, 32), (32, "bisector", 6, 64)]):
+        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=2 + (i % 2), ell_max=4,
+                            los=los, order=K, precision=prec, compensate=bool(i % 3 == 0))
+        kedges = np.linspace(0.0, math.pi / (cat.box_len / N), 9)
+        redges = np.linspace(0.0, 6 * cat.box_len / N, 6)
+        out.append(dict(gal=cat.gal, ran=cat.ran, params=p, kedges=kedges, redges=redges, ran_nbar=cat.ran_nbar))
+    return out
+
+
+def _tol(prec):
+    return (1e-5, 1e-4) if prec == 32 else (1e-10, 1e-10)
+
+
+def test_results_same_alone_and_in_the_mix(pkg, cap):
+    items = _mix(pkg, cap)
+    ctx = pkg.Context(0)
+    alone = [ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
+                                  ran_nbar=it["ran_nbar"]) for it in items]
+    ctx.serve_start(n_slots=3)
+    tickets = [ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"])
+               for it in items]
+    mixed = [ctx.wait(t) for t in tickets]
+    stats = ctx.serve_stats()
+    ctx.serve_stop()
+    ctx.close()
+    assert stats["count"] == len(items)
+    assert stats["p99_s"] >= stats["p50_s"] > 0
+    for it, a, m in zip(items, alone, mixed):
+        r0, r = _tol(it["params"].precision)
+        check_multipoles(m["pk"], a["pk"], "pk", r0, r)
+        check_multipoles(m["xi"], a["xi"], "xi", r0, r)
+        np.testing.assert_array_equal(m["n_modes"], a["n_modes"])
+
+
+def test_batch_run_matches_sequential(pkg, cap):
+    items = _mix(pkg, cap)[:5]
+    ctx = pkg.Context(0)
+    seq = [ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
+                                ran_nbar=it["ran_nbar"]) for it in items]
+    bat = ctx.batch_run(items)
+    ctx.close()
+    for it, a, b in zip(items, seq, bat):
+        r0, r = _tol(it["params"].precision)
+        check_multipoles(b["pk"], a["pk"], "pk", r0, r)
+        check_multipoles(b["xi"], a["xi"], "xi", r0, r)
+
+
+def test_admission_timeout_and_errors(pkg, cap):
+    ctx = pkg.Context(0)
+    small = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=32, ell_max=4, los="midpoint", order=2)
+    fp = pkg.footprint(small, len(cap.gal), len(cap.ran))
+    ctx.serve_start(n_slots=2, hbm_budget_bytes=int(1.5 * fp))
+    big = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=256, ell_max=4, los="midpoint", order=4)
+    kedges = np.linspace(0.0, 0.2, 5)
+    with pytest.raises(pkg.BymError) as ei:          # can never fit the budget
+        ctx.submit(cap.gal, cap.ran, big, kedges, ran_nbar=cap.ran_nbar)
+    assert ei.value.code == -3
+    # only one of two equal requests fits at a time: the second waits for memory
+    t1 = ctx.submit(cap.gal, cap.ran, small, kedges, ran_nbar=cap.ran_nbar)
+    t2 = ctx.submit(cap.gal, cap.ran, small, kedges, ran_nbar=cap.ran_nbar)
+    with pytest.raises(pkg.BymError) as ei:
+        ctx.wait(t2, timeout_s=0.0)
+    assert ei.value.code == -5
+    a = ctx.wait(t1)
+    b = ctx.wait(t2)
+    np.testing.assert_allclose(a["pk"], b["pk"], rtol=1e-5, atol=1e-5 * np.abs(a["pk"]).max())
+    stats = ctx.serve_stats()
+    assert stats["peak_hbm_bytes"] <= 1.5 * fp
+    # a failing request reports its own error code
+    bad = np.array(cap.gal, copy=True)
+    bad[3, 0] = cap.box_lo[0] - 10.0
+    t3 = ctx.submit(bad, cap.ran, small, kedges, ran_nbar=cap.ran_nbar)
+    with pytest.raises(pkg.BymError) as ei:
+        ctx.wait(t3)
+    assert ei.value.code == -2
+    ctx.serve_stop()
+    ctx.close()
