@@ -202,7 +202,7 @@ size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, b
 // ---------------------------------------------------------------------------
 // cuFFT plans (in place, padded real layout), shared work area
 // ---------------------------------------------------------------------------
-static int get_plan(bym_ctx *c, int N, int prec, int inverse, int batch, cufftHandle *out) {
+static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, int batch, cufftHandle *out) {
   auto key = std::make_tuple(N, prec, inverse, batch);
   auto it = c->plans.find(key);
   if (it != c->plans.end()) {
@@ -229,11 +229,13 @@ static int get_plan(bym_ctx *c, int N, int prec, int inverse, int batch, cufftHa
     return fail(c, BYM_E_CUDA, "cufftMakePlanMany failed (" + std::to_string((int)r) + ")");
   }
   if (work > c->fft_work_size) {
-    cudaDeviceSynchronize();
-    if (c->fft_work) cudaFree(c->fft_work);
+    // grow the work area in the order of the request's stream (every use of it is on
+    // that stream, and the previous request finished before this one started): no
+    // device-wide synchronisation, so other contexts (serving slots) keep running
+    if (c->fft_work) cudaFreeAsync(c->fft_work, st);
     c->fft_work = nullptr;
     c->fft_work_size = 0;
-    if (cudaMalloc(&c->fft_work, work) != cudaSuccess) {
+    if (cudaMallocAsync(&c->fft_work, work, st) != cudaSuccess) {
       cudaGetLastError();
       cufftDestroy(h);
       return fail(c, BYM_E_NOMEM, "cuFFT work area allocation failed");
@@ -247,12 +249,13 @@ static int get_plan(bym_ctx *c, int N, int prec, int inverse, int batch, cufftHa
 
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
                      int first, int count) {
+
   const double esz = prec == 64 ? 8.0 : 4.0;
   ProfScope ps(c, st, inverse ? "cufft_c2r" : "cufft_r2c", count * 2.0 * esz * (double)N * N * N);
   for (int done = 0; done < count;) {
     const int b = std::min(kFftBatch, count - done);
     cufftHandle h;
-    int rc = get_plan(c, N, prec, inverse, b, &h);
+    int rc = get_plan(c, st, N, prec, inverse, b, &h);
     if (rc) return rc;
     cufftSetStream(h, st);
     cufftSetWorkArea(h, c->fft_work);
@@ -682,7 +685,8 @@ void bym_destroy(bym_ctx *c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
-  if (c->fft_work) cudaFree(c->fft_work);
+  if (c->fft_work) cudaFreeAsync(c->fft_work, c->stream);
+  cudaStreamSynchronize(c->stream);
   for (auto *m : {&c->kgeo, &c->rgeo})
     for (auto &kv : *m)
       if (kv.second.lut) cudaFree(kv.second.lut);
