@@ -48,6 +48,18 @@ def phi(alpha: int, ell: int, m: int, J1: int, J2: int, M: int) -> float:
       sum_k C_{Nk}^{ell/2} (-2)^(N-2k) sum_{L' = N-2k, N-2k-2, ..} c~^{L'}_{N-2k} 4pi/(2L'+1)
       G_{lam L' J1}^{mu (M-mu) (-M)} G_{(ell-lam) L' J2}^{(m-mu) (mu-M) (M-m)} (-1)^(m+M-mu)
     """
+    return _shift_sum(alpha, ell, m, J1, J2, M, ell)
+
+
+@lru_cache(maxsize=None)
+def omega(beta: int, ell: int, m: int, alpha: int, J1: int, J2: int, M: int) -> float:
+    """omega^{beta, ell m alpha}_{J1 J2 M} of Appendix C (eq. generalized-Ylm-tmp): phi with the
+    Gegenbauer coefficient C^{ell/2}_{Nk} replaced by C^{(ell+alpha)/2}_{Nk}."""
+    return _shift_sum(beta, ell, m, J1, J2, M, ell + alpha)
+
+
+def _shift_sum(alpha: int, ell: int, m: int, J1: int, J2: int, M: int, two_gamma: int) -> float:
+    """The sum of eq. shift-coeff-def with Gegenbauer parameter two_gamma / 2."""
     if abs(m) > ell or abs(M) > J1 or abs(m - M) > J2 or J1 < 0 or J2 < 0:
         return 0.0
     total = 0.0
@@ -60,7 +72,7 @@ def phi(alpha: int, ell: int, m: int, J1: int, J2: int, M: int) -> float:
             if A == 0.0:
                 continue
             for k in range(0, N // 2 + 1):
-                C = gegenbauer_coeff(Fraction(ell, 2), N, k)
+                C = gegenbauer_coeff(Fraction(two_gamma, 2), N, k)
                 if C == 0:
                     continue
                 pw = N - 2 * k
@@ -116,6 +128,17 @@ def f_leg(alpha: int, ell: int, J: int) -> float:
       sum_k C^{ell/2}_{(alpha-lam) k} (-2)^(alpha-lam-2k)
       sum_{L' = alpha-lam-2k, .., step -2} c~^{L'}_{alpha-lam-2k} (ell-lam L' J; 000)^2
     """
+    return _f_sum(alpha, ell, J, ell)
+
+
+@lru_cache(maxsize=None)
+def h_leg(beta: int, alpha: int, ell: int, J: int) -> float:
+    """h^{beta, alpha ell}_J of Appendix F.2: f^{beta, ell}_J with C^{ell/2} replaced by C^{(ell+alpha)/2}."""
+    return _f_sum(beta, ell, J, ell + alpha)
+
+
+def _f_sum(alpha: int, ell: int, J: int, two_gamma: int) -> float:
+    """The sum of eq. f-alpha-def with Gegenbauer parameter two_gamma / 2."""
     if J < 0:
         return 0.0
     total = 0.0
@@ -126,7 +149,7 @@ def f_leg(alpha: int, ell: int, J: int) -> float:
         pre = math.sqrt(binom(2 * ell, 2 * lam)) * t0
         N = alpha - lam
         for k in range(0, N // 2 + 1):
-            C = gegenbauer_coeff(Fraction(ell, 2), N, k)
+            C = gegenbauer_coeff(Fraction(two_gamma, 2), N, k)
             if C == 0:
                 continue
             pw = N - 2 * k
@@ -162,6 +185,118 @@ def shift_series_legendre(ell: int, a, A, K: int) -> np.ndarray:
     for alpha in range(K + 1):
         for J, c in f_table(alpha, ell).items():
             out = out + (2 * J + 1) / (2 * ell + 1) * c * eps ** alpha * legendre_L(J, mu)
+    return out
+
+
+# --------------------------------------------------------------------------
+# parity-even midpoint coefficients (Appendix C, D, F.2)
+# --------------------------------------------------------------------------
+@lru_cache(maxsize=None)
+def Omega(beta: int, alpha: int, J1: int, J2: int, m: int, M: int, S1: int, S2: int, T: int) -> float:
+    """Omega^{beta, alpha J1 J2 m M}_{S1 S2 T}, eq. generalized-shift-theorem:
+    sum_{J'} omega^{beta, J2 (m-M) alpha}_{J' S2 (T-M)} G_{J1 J' S1}^{M (T-M) (-T)} (-1)^T."""
+    total = 0.0
+    for Jp in range(0, beta + 1):
+        w = omega(beta, J2, m - M, alpha, Jp, S2, T - M)
+        if w == 0.0:
+            continue
+        g = gaunt(J1, Jp, S1, M, T - M, -T)
+        if g == 0.0:
+            continue
+        total += w * g * (-1.0 if T % 2 else 1.0)
+    return total
+
+
+@lru_cache(maxsize=None)
+def Phi_even(alpha: int, ell: int, m: int, J1: int, J2: int, M: int) -> float:
+    """Phi^{alpha, ell m}_{J1 J2 M} of the parity-even expansion (Appendix D, boxed 2 Y = sum over
+    even alpha), written out to alpha = 4 as the paper does:
+      Phi^0 = sqrt(4pi) delta delta delta, Phi^2 = -phi^2,
+      Phi^4 = -phi^4 + sum_{J1' J2' M'} phi^2_{J1' J2' M'} Omega^{2, 2 J1' J2' m M'}_{J1 J2 M}."""
+    if alpha == 0:
+        return phi(0, ell, m, J1, J2, M)
+    if alpha == 2:
+        return -phi(2, ell, m, J1, J2, M)
+    if alpha == 4:
+        total = -phi(4, ell, m, J1, J2, M)
+        for (J1p, J2p, Mp), c in phi_table(2, ell, m).items():
+            total += c * Omega(2, 2, J1p, J2p, m, Mp, J1, J2, M)
+        return total
+    if alpha % 2:
+        return 0.0
+    raise NotImplementedError("the parity-even coefficients are written out to alpha = 4")
+
+
+def Phi_table(alpha: int, ell: int, m: int, tol: float = 1e-13) -> dict:
+    out = {}
+    for J1 in range(0, alpha + 1):
+        for J2 in range(max(0, ell - alpha), ell + alpha + 1):
+            for M in range(-J1, J1 + 1):
+                v = Phi_even(alpha, ell, m, J1, J2, M)
+                if abs(v) > tol:
+                    out[(J1, J2, M)] = v
+    return out
+
+
+@lru_cache(maxsize=None)
+def F_even(alpha: int, ell: int, J: int) -> float:
+    """F^{alpha, ell}_J of the parity-even Legendre expansion (Appendix F.2, eq. F-coeff-def and the
+    explicit forms after it): F^0 = delta_{ell J}, F^2 = -f^2, F^4 = -f^4 + sum_S f^{2,ell}_S h^{2,2S}_J.
+    They enter as L_ell = 1/2 sum (2J+1)/(2ell+1) F [...] (the form of the boxed Appendix F.2 equation)."""
+    if alpha == 0:
+        return f_leg(0, ell, J)
+    if alpha == 2:
+        return -f_leg(2, ell, J)
+    if alpha == 4:
+        total = -f_leg(4, ell, J)
+        for S, c in f_table(2, ell).items():
+            total += c * h_leg(2, 2, S, J)
+        return total
+    if alpha % 2:
+        return 0.0
+    raise NotImplementedError("the parity-even coefficients are written out to alpha = 4")
+
+
+def F_table(alpha: int, ell: int, tol: float = 1e-13) -> dict:
+    out = {}
+    for J in range(max(ell - alpha, 0), ell + alpha + 1):
+        v = F_even(alpha, ell, J)
+        if abs(v) > tol:
+            out[J] = v
+    return out
+
+
+def even_series_ylm(ell: int, m: int, r1, r2, K: int) -> np.ndarray:
+    """Symmetric parity-even expansion of Y_ell^m(hat(r1 + r2)) to even alpha <= K (Appendix D boxed):
+    Y = 1/2 sum Phi Y_J1^M(hat Delta) [eps1^alpha Y_J2^{m-M}(hat r1) + eps2^alpha Y_J2^{m-M}(hat r2)]."""
+    r1 = np.asarray(r1, dtype=np.float64)
+    r2 = np.asarray(r2, dtype=np.float64)
+    D = r2 - r1
+    e1 = np.linalg.norm(D, axis=-1) / (2 * np.linalg.norm(r1, axis=-1))
+    e2 = np.linalg.norm(D, axis=-1) / (2 * np.linalg.norm(r2, axis=-1))
+    out = np.zeros(e1.shape, dtype=np.complex128)
+    for alpha in range(0, K + 1, 2):
+        for (J1, J2, M), c in Phi_table(alpha, ell, m).items():
+            out += 0.5 * c * ylm(J1, M, D) * (e1 ** alpha * ylm(J2, m - M, r1) + e2 ** alpha * ylm(J2, m - M, r2))
+    return out
+
+
+def even_series_legendre(ell: int, r1, r2, K: int) -> np.ndarray:
+    """Symmetric parity-even expansion of L_ell(hat Delta . hat(r1 + r2)) to even alpha <= K:
+    1/2 sum (2J+1)/(2ell+1) F [eps1^alpha L_J(mu1) + (-1)^(ell+J) eps2^alpha L_J(mu2)]."""
+    r1 = np.asarray(r1, dtype=np.float64)
+    r2 = np.asarray(r2, dtype=np.float64)
+    D = r2 - r1
+    nD = np.linalg.norm(D, axis=-1)
+    n1, n2 = np.linalg.norm(r1, axis=-1), np.linalg.norm(r2, axis=-1)
+    mu1 = np.sum(D * r1, axis=-1) / (nD * n1)
+    mu2 = np.sum(D * r2, axis=-1) / (nD * n2)
+    e1, e2 = nD / (2 * n1), nD / (2 * n2)
+    out = np.zeros(e1.shape)
+    for alpha in range(0, K + 1, 2):
+        for J, c in F_table(alpha, ell).items():
+            w = 0.5 * (2 * J + 1) / (2 * ell + 1) * c
+            out += w * (e1 ** alpha * legendre_L(J, mu1) + (-1) ** (ell + J) * e2 ** alpha * legendre_L(J, mu2))
     return out
 
 

@@ -8,6 +8,8 @@ Every estimator follows the paper's boxed equation literally, with full complex
   yamamoto  P: eq. Yamamoto-estimator      xi: eq. 2pcf-yama
   midpoint  P: eq. FFT-midpoint, g from eq. g-JM-form
             xi: eq. xi-parity-all-estimator (same g functions)
+  midpoint_even  the parity-even forms (Sec. 3.3 / Sec. 4.3 boxed): Phi and F
+            coefficients (Appendices D, F.2), even alpha only, same g functions
   bisector  P: eq. bisector-pk-fft (boxed form)
             xi: Sec. 6 boxed estimator, h summed over the B coefficients
                 before the inverse transform as Sec. 6 suggests
@@ -34,7 +36,7 @@ import math
 import numpy as np
 
 from . import mesh
-from .coeffs import B_table, f_table, phi_table
+from .coeffs import B_table, F_table, Phi_table, f_table, phi_table
 from .special import FOUR_PI, legendre_L, ylm
 
 
@@ -105,7 +107,7 @@ def _xi_out(g, ells, Z, A, v_cell, redges):
 # --------------------------------------------------------------------------
 # midpoint convolution fields g^alpha_JM (eq. g-JM-form)
 # --------------------------------------------------------------------------
-def g_fields(g: Grid, delta, D, K, ell_max, inv_w):
+def g_fields(g: Grid, delta, D, K, ell_max, inv_w, even=False):
     """g^alpha_JM(Delta) = (-1)^J IFFT[ delta*(k) F[(2r)^-alpha Y_J^M delta](k) ](Delta)
     for alpha <= K and J = alpha, alpha-2, ... <= ell_max + alpha (the J with
     non-zero phi / f for even ell).  Cells with delta = 0 carry no field; a
@@ -115,7 +117,7 @@ def g_fields(g: Grid, delta, D, K, ell_max, inv_w):
     Dc = np.conj(D)
     safe_r = np.where(g.r == 0.0, 1.0, g.r)
     out = {}
-    for alpha in range(K + 1):
+    for alpha in range(0, K + 1, 2 if even else 1):
         radial = np.where(delta != 0.0, (2.0 * safe_r) ** (-alpha), 0.0) * delta
         for J in range(alpha % 2, ell_max + alpha + 1, 2):
             for M in range(-J, J + 1):
@@ -130,7 +132,7 @@ def g_fields(g: Grid, delta, D, K, ell_max, inv_w):
 def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
                   order, kedges, compensate=False, norm=1):
     """P_ell(k) for ell = 0, 2, .., ell_max with LOS in
-    {'yamamoto', 'midpoint', 'bisector', 'fixed'}."""
+    {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
     g, delta, A, _, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
                                      assign, norm, compensate)
     ells = _ells(ell_max)
@@ -154,6 +156,19 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
                 for alpha in range(order + 1):
                     dpow = g.lag_mag ** alpha
                     for (J1, J2, M), c in phi_table(alpha, ell, m).items():
+                        H += c * ylm(J1, M, g.lag) * dpow * gf[(alpha, J2, m - M)]
+                acc += np.conj(ylm(ell, m, g.k)) * mesh.fftn(H)
+            T[ell] = acc.real
+    elif los == "midpoint_even":
+        # Sec. 3.3 boxed parity-even estimator: eq. FFT-midpoint with phi -> Phi, even alpha only
+        gf = g_fields(g, delta, D, order, ell_max, inv_w, even=True)
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for m in range(-ell, ell + 1):
+                H = np.zeros(D.shape, dtype=np.complex128)
+                for alpha in range(0, order + 1, 2):
+                    dpow = g.lag_mag ** alpha
+                    for (J1, J2, M), c in Phi_table(alpha, ell, m).items():
                         H += c * ylm(J1, M, g.lag) * dpow * gf[(alpha, J2, m - M)]
                 acc += np.conj(ylm(ell, m, g.k)) * mesh.fftn(H)
             T[ell] = acc.real
@@ -187,7 +202,7 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
 def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
                   order, redges, compensate=False, norm=1):
     """xi_ell(r) for ell = 0, 2, .., ell_max with LOS in
-    {'yamamoto', 'midpoint', 'bisector', 'fixed'}."""
+    {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
     g, delta, A, v_cell, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
                                           assign, norm, compensate)
     ells = _ells(ell_max)
@@ -209,6 +224,17 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
             for alpha in range(order + 1):
                 dpow = g.lag_mag ** alpha
                 for J, c in f_table(alpha, ell).items():
+                    for M in range(-J, J + 1):
+                        acc += c * np.conj(ylm(J, M, g.lag)) * dpow * gf[(alpha, J, M)]
+            Z[ell] = acc.real
+    elif los == "midpoint_even":
+        # Sec. 4.3 boxed parity-even estimator: f -> F, even alpha only
+        gf = g_fields(g, delta, D, order, ell_max, inv_w, even=True)
+        for ell in ells:
+            acc = np.zeros(D.shape, dtype=np.complex128)
+            for alpha in range(0, order + 1, 2):
+                dpow = g.lag_mag ** alpha
+                for J, c in F_table(alpha, ell).items():
                     for M in range(-J, J + 1):
                         acc += c * np.conj(ylm(J, M, g.lag)) * dpow * gf[(alpha, J, M)]
             Z[ell] = acc.real

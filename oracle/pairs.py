@@ -28,7 +28,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import mesh
-from .coeffs import B_table, f_table, phi_table
+from .coeffs import B_table, F_table, Phi_table, f_table, phi_table
 from .special import FOUR_PI, legendre_L, ylm
 
 
@@ -57,7 +57,7 @@ def _unit(v):
 def _los(los, xa, xb):
     if los == "yamamoto":
         return xb
-    if los == "midpoint":
+    if los in ("midpoint", "midpoint_even"):
         return xa + xb
     if los == "bisector":
         return _unit(xa) + _unit(xb)
@@ -74,6 +74,15 @@ def _ylm_pair(los, ell, m, xa, xb, lag, series):
         out = np.zeros(len(xb), dtype=np.complex128)
         for alpha in range(series + 1):
             for (J1, J2, M), c in phi_table(alpha, ell, m).items():
+                out += c * eps ** alpha * ylm(J1, M, -lag) * ylm(J2, m - M, xb)
+        return out
+    if los == "midpoint_even":
+        # r2-anchored parity-even series (Phi, even alpha): its pair sum equals that of the
+        # symmetric boxed form because every J1 is even
+        eps = np.linalg.norm(lag, axis=-1) / (2.0 * np.linalg.norm(xb, axis=-1))
+        out = np.zeros(len(xb), dtype=np.complex128)
+        for alpha in range(0, series + 1, 2):
+            for (J1, J2, M), c in Phi_table(alpha, ell, m).items():
                 out += c * eps ** alpha * ylm(J1, M, -lag) * ylm(J2, m - M, xb)
         return out
     if los == "bisector":
@@ -98,6 +107,14 @@ def _legendre_pair(los, ell, xa, xb, lag, series):
         out = np.zeros(len(xb))
         for alpha in range(series + 1):
             for J, c in f_table(alpha, ell).items():
+                out += (2 * J + 1) / (2 * ell + 1) * c * eps ** alpha * legendre_L(J, mu)
+        return out
+    if los == "midpoint_even":
+        eps = np.linalg.norm(lag, axis=-1) / (2.0 * np.linalg.norm(xb, axis=-1))
+        mu = np.sum(_unit(-lag) * _unit(xb), axis=-1)
+        out = np.zeros(len(xb))
+        for alpha in range(0, series + 1, 2):
+            for J, c in F_table(alpha, ell).items():
                 out += (2 * J + 1) / (2 * ell + 1) * c * eps ** alpha * legendre_L(J, mu)
         return out
     if los == "bisector":

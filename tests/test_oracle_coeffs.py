@@ -185,3 +185,63 @@ def test_f_equals_direct_taylor_expansion(ell):
         got = sum((2 * J + 1) / (2 * ell + 1) * v * legendre_L(J, pts)
                   for J, v in f_table(alpha, ell).items())
         np.testing.assert_allclose(got, want, atol=1e-11)
+
+
+# ---------------------------------------------------------------- parity-even midpoint (Appendices C, D, F.2)
+def test_F_matches_printed_L24_even():
+    from oracle.coeffs import F_table
+    gold = {k: v for k, v in load_golden("F_L24_even.txt")}
+    for ell in (2, 4):
+        for alpha in (0, 2, 4):
+            tab = F_table(alpha, ell)
+            keys = {J for (l, a, J) in gold if l == ell and a == alpha}
+            assert set(tab) == keys, (ell, alpha, sorted(set(tab) ^ keys))
+            for J in keys:
+                assert (2 * J + 1) / (2 * ell + 1) * tab[J] == pytest.approx(gold[(ell, alpha, J)], rel=1e-11)
+
+
+def test_Phi_matches_printed_Y21_even():
+    # eq. Y21-even: the second-order terms are those of eq. Y21-all with the opposite sign
+    # (Phi^2 = -phi^2, Appendix D); the zeroth-order term is unchanged and alpha = 1 is absent
+    from oracle.coeffs import Phi_table
+    gold = {k: v for k, v in load_golden("phi_Y21_midpoint.txt")}
+    assert Phi_table(0, 2, 1) == pytest.approx({(0, 2, 0): S4PI})
+    tab = Phi_table(2, 2, 1)
+    keys = {(J1, J2, M) for (a, J1, J2, M) in gold if a == 2}
+    assert set(tab) == keys
+    for k in keys:
+        assert tab[k] == pytest.approx(-gold[(2,) + k], rel=1e-12)
+    assert Phi_table(1, 2, 1) == {} and Phi_table(3, 2, 1) == {}
+
+
+@pytest.mark.parametrize("ell,m", [(2, 1), (4, 2), (4, -3)])
+def test_even_Ylm_series_convergence_rate(ell, m):
+    # the boxed parity-even expansion truncated at even alpha = K leaves O(theta^(K+2));
+    # Phi^4 (built from Omega) must give the theta^6 rate
+    from oracle.coeffs import even_series_ylm
+    rng = np.random.default_rng(40 + ell + m)
+    R = _rand_unit(rng, 6) * 1000.0
+    d = _rand_unit(rng, 6)
+    for K in (0, 2, 4):
+        err = []
+        for D in (40.0, 20.0):
+            r1, r2 = R - 0.5 * D * d, R + 0.5 * D * d
+            err.append(np.abs(ylm(ell, m, r1 + r2) - even_series_ylm(ell, m, r1, r2, K)))
+        ratio = np.median(err[0] / err[1])
+        assert 0.85 * 4 ** (K // 2 + 1) < ratio < 1.15 * 4 ** (K // 2 + 1), (K, ratio)
+
+
+@pytest.mark.parametrize("ell", [2, 4])
+def test_even_legendre_series_convergence_rate(ell):
+    from oracle.coeffs import even_series_legendre
+    rng = np.random.default_rng(50 + ell)
+    R = _rand_unit(rng, 6) * 1000.0
+    d = _rand_unit(rng, 6)
+    for K in (0, 2, 4):
+        err = []
+        for D in (40.0, 20.0):
+            r1, r2 = R - 0.5 * D * d, R + 0.5 * D * d
+            mu = np.sum(d * (r1 + r2), axis=1) / np.linalg.norm(r1 + r2, axis=1)
+            err.append(np.abs(legendre_L(ell, mu) - even_series_legendre(ell, r1, r2, K)))
+        ratio = np.median(err[0] / err[1])
+        assert 0.85 * 4 ** (K // 2 + 1) < ratio < 1.15 * 4 ** (K // 2 + 1), (K, ratio)

@@ -47,6 +47,8 @@ def test_midpoint_order0_equals_yamamoto(small_uniform):
     y = E.pk_multipoles(c.gal, c.ran, c.ran_nbar, los="yamamoto", order=0, kedges=ke, **_kw(c))
     m = E.pk_multipoles(c.gal, c.ran, c.ran_nbar, los="midpoint", order=0, kedges=ke, **_kw(c))
     assert _rel(m["pk"], y["pk"]) < 1e-12
+    m = E.pk_multipoles(c.gal, c.ran, c.ran_nbar, los="midpoint_even", order=0, kedges=ke, **_kw(c))
+    assert _rel(m["pk"], y["pk"]) < 1e-12
     y = E.xi_multipoles(c.gal, c.ran, c.ran_nbar, los="yamamoto", order=0, redges=REDGES, **_kw(c))
     m = E.xi_multipoles(c.gal, c.ran, c.ran_nbar, los="midpoint", order=0, redges=REDGES, **_kw(c))
     assert _rel(m["xi"], y["xi"]) < 1e-12
@@ -58,7 +60,7 @@ def test_monopole_independent_of_los(small_uniform):
     ke = _kedges(c.box_len, N)
     ref = E.pk_multipoles(c.gal, c.ran, c.ran_nbar, los="yamamoto", order=0, kedges=ke, **_kw(c))
     refx = E.xi_multipoles(c.gal, c.ran, c.ran_nbar, los="yamamoto", order=0, redges=REDGES, **_kw(c))
-    for los, K in (("midpoint", 2), ("midpoint", 3), ("bisector", 2), ("bisector", 4)):
+    for los, K in (("midpoint", 2), ("midpoint", 3), ("midpoint_even", 4), ("bisector", 2), ("bisector", 4)):
         p = E.pk_multipoles(c.gal, c.ran, c.ran_nbar, los=los, order=K, kedges=ke, **_kw(c))
         assert _rel(p["pk"][0], ref["pk"][0]) < 1e-12
         x = E.xi_multipoles(c.gal, c.ran, c.ran_nbar, los=los, order=K, redges=REDGES, **_kw(c))
@@ -72,7 +74,8 @@ def snapped():
                            fill=0.4, n_ran=30)
 
 
-@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("midpoint", 3), ("bisector", 2)])
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("midpoint", 3), ("bisector", 2),
+                                   ("midpoint_even", 4)])
 def test_pk_fft_equals_pairwise_series(snapped, los, K):
     # the convolution / relabelling steps of Secs. 3.2 and 5.2 are exact rewrites of the
     # truncated series summed pair by pair
@@ -84,7 +87,8 @@ def test_pk_fft_equals_pairwise_series(snapped, los, K):
     np.testing.assert_array_equal(o3["n_modes"], o2["n_modes"])
 
 
-@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("midpoint", 4), ("bisector", 2)])
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("midpoint", 4), ("bisector", 2),
+                                   ("midpoint_even", 4)])
 def test_xi_fft_equals_pairwise_series(snapped, los, K):
     c = snapped
     o3 = E.xi_multipoles(c.gal, c.ran, c.ran_nbar, los=los, order=K, redges=REDGES, **_kw(c))
