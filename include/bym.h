@@ -52,11 +52,14 @@ enum {
   BYM_E_NOMEM = -3,        /* device allocation failed or the request exceeds the HBM budget */
   BYM_E_CUDA = -4,         /* CUDA runtime / cuFFT / NVRTC failure */
   BYM_E_TIMEOUT = -5,      /* bym_wait deadline passed (the request keeps running) */
-  BYM_E_UNSUPPORTED = -6,  /* odd ell_max, order > 12, ell_max > 8, n_mesh out of range */
+  BYM_E_UNSUPPORTED = -6,  /* odd ell_max, order > 12 (> 4 parity-even), ell_max > 8, n_mesh out of range */
   BYM_E_BUSY = -7          /* no free serving slot */
 };
 
-typedef enum { BYM_LOS_YAMAMOTO = 0, BYM_LOS_MIDPOINT = 1, BYM_LOS_BISECTOR = 2 } bym_los;
+/* BYM_LOS_MIDPOINT_EVEN is the parity-even form of the midpoint series (Sec. 3.3 and Sec. 4.3
+ * boxed estimators; coefficients Phi and F of Appendices D and F.2): even alpha <= order only,
+ * available to order 4. */
+typedef enum { BYM_LOS_YAMAMOTO = 0, BYM_LOS_MIDPOINT = 1, BYM_LOS_BISECTOR = 2, BYM_LOS_MIDPOINT_EVEN = 3 } bym_los;
 
 typedef struct bym_ctx bym_ctx;
 

@@ -11,6 +11,7 @@ Estimators (Philcox & Slepian, arXiv:2102.08384):
   los="yamamoto"  Sec. 2, eq. Yamamoto-estimator / eq. 2pcf-yama
   los="midpoint"  Secs. 3-4, eq. FFT-midpoint / eq. xi-parity-all-estimator
   los="bisector"  Secs. 5-6, eq. bisector-pk-fft / the Sec. 6 estimator
+  los="midpoint_even"  the parity-even midpoint forms, Secs. 3.3 and 4.3 (order <= 4)
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbym.so")
 
-LOS = {"yamamoto": 0, "midpoint": 1, "bisector": 2}
+LOS = {"yamamoto": 0, "midpoint": 1, "bisector": 2, "midpoint_even": 3}
 
 BYM_OK = 0
 ERRORS = {-1: "INVAL", -2: "OUT_OF_BOX", -3: "NOMEM", -4: "CUDA", -5: "TIMEOUT", -6: "UNSUPPORTED",

@@ -46,8 +46,29 @@ inline double parity(int n) { return (n % 2 == 0) ? 1.0 : -1.0; }
 
 }  // namespace
 
-// Racah's closed form of the Wigner 3-j symbol, in long double.
+static double wigner3j_racah(int j1, int j2, int j3, int m1, int m2, int m3);
+
+// Wigner 3-j symbol, memoised (the tables call it many times with few distinct arguments).
 double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3) {
+  if (m1 + m2 + m3 != 0) return 0.0;
+  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
+  if (j3 < std::abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, double> cache;
+  const auto key = std::make_tuple(j1, j2, j3, m1, m2);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const double v = wigner3j_racah(j1, j2, j3, m1, m2, m3);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = v;
+  return v;
+}
+
+// Racah's closed form of the Wigner 3-j symbol, in long double.
+static double wigner3j_racah(int j1, int j2, int j3, int m1, int m2, int m3) {
   if (m1 + m2 + m3 != 0) return 0.0;
   if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
   if (j3 < std::abs(j1 - j2) || j3 > j1 + j2) return 0.0;
@@ -99,6 +120,14 @@ double gegenbauer_term(int two_a, int N, int k) {
 }
 
 double shift_phi(int alpha, int ell, int m, int J1, int J2, int M) {
+  return shift_sum(alpha, ell, m, J1, J2, M, ell);
+}
+
+double shift_omega(int beta, int ell, int m, int alpha, int J1, int J2, int M) {
+  return shift_sum(beta, ell, m, J1, J2, M, ell + alpha);
+}
+
+double shift_sum(int alpha, int ell, int m, int J1, int J2, int M, int two_gamma) {
   if (std::abs(m) > ell || std::abs(M) > J1 || std::abs(m - M) > J2 || J1 < 0 || J2 < 0) return 0.0;
   double total = 0.0;
   for (int lam = 0; lam <= ell; ++lam) {
@@ -108,7 +137,7 @@ double shift_phi(int alpha, int ell, int m, int J1, int J2, int M) {
       const double A = solid_coupling(ell, m, lam, mu);
       if (A == 0.0) continue;
       for (int k = 0; 2 * k <= N; ++k) {
-        const double C = gegenbauer_term(ell, N, k);
+        const double C = gegenbauer_term(two_gamma, N, k);
         if (C == 0.0) continue;
         const int pw = N - 2 * k;
         const double m2pow = std::pow(-2.0, pw);
@@ -127,7 +156,11 @@ double shift_phi(int alpha, int ell, int m, int J1, int J2, int M) {
   return total;
 }
 
-double legendre_shift_f(int alpha, int ell, int J) {
+double legendre_shift_f(int alpha, int ell, int J) { return legendre_shift_sum(alpha, ell, J, ell); }
+
+double legendre_shift_h(int beta, int alpha, int ell, int J) { return legendre_shift_sum(beta, ell, J, ell + alpha); }
+
+double legendre_shift_sum(int alpha, int ell, int J, int two_gamma) {
   if (J < 0) return 0.0;
   double total = 0.0;
   for (int lam = 0; lam <= std::min(alpha, ell); ++lam) {
@@ -136,7 +169,7 @@ double legendre_shift_f(int alpha, int ell, int J) {
     const double pre = std::sqrt(binomial(2 * ell, 2 * lam)) * t0;
     const int N = alpha - lam;
     for (int k = 0; 2 * k <= N; ++k) {
-      const double C = gegenbauer_term(ell, N, k);
+      const double C = gegenbauer_term(two_gamma, N, k);
       if (C == 0.0) continue;
       const int pw = N - 2 * k;
       for (int Lp = pw; Lp >= 0; Lp -= 2) {
@@ -178,6 +211,51 @@ double bisector_B(int beta, int ell, int m, int J1, int J2, int M) {
     }
   }
   return std::ldexp(total, -ell);
+}
+
+// Appendix C, eq. generalized-shift-theorem:
+// Omega^{beta, alpha J1 J2 m M}_{S1 S2 T} = sum_{J'} omega^{beta, J2 (m-M) alpha}_{J' S2 (T-M)} G_{J1 J' S1}^{M (T-M) (-T)} (-1)^T
+double shift_Omega(int beta, int alpha, int J1, int J2, int m, int M, int S1, int S2, int T) {
+  double total = 0.0;
+  for (int Jp = 0; Jp <= beta; ++Jp) {
+    const double w = shift_omega(beta, J2, m - M, alpha, Jp, S2, T - M);
+    if (w == 0.0) continue;
+    const double g = gaunt(J1, Jp, S1, M, T - M, -T);
+    if (g == 0.0) continue;
+    total += w * g * parity(T);
+  }
+  return total;
+}
+
+// Appendix D: Phi^0 = phi^0, Phi^2 = -phi^2,
+// Phi^4 = -phi^4 + sum_{J1' J2' M'} phi^2_{J1' J2' M'} Omega^{2, 2 J1' J2' m M'}_{J1 J2 M}.
+double parity_even_Phi(int alpha, int ell, int m, int J1, int J2, int M) {
+  if (alpha == 0) return shift_phi(0, ell, m, J1, J2, M);
+  if (alpha == 2) return -shift_phi(2, ell, m, J1, J2, M);
+  if (alpha != 4) throw std::runtime_error("parity-even coefficients are written out to alpha = 4");
+  double total = -shift_phi(4, ell, m, J1, J2, M);
+  for (int J1p = 0; J1p <= 2; J1p += 2)
+    for (int J2p = std::max(0, ell - 2); J2p <= ell + 2; ++J2p)
+      for (int Mp = -J1p; Mp <= J1p; ++Mp) {
+        const double c = shift_phi(2, ell, m, J1p, J2p, Mp);
+        if (std::fabs(c) < 1e-14) continue;
+        total += c * shift_Omega(2, 2, J1p, J2p, m, Mp, J1, J2, M);
+      }
+  return total;
+}
+
+// Appendix F.2: F^0 = f^0, F^2 = -f^2, F^4 = -f^4 + sum_S f^{2,ell}_S h^{2,2S}_J.
+double parity_even_F(int alpha, int ell, int J) {
+  if (alpha == 0) return legendre_shift_f(0, ell, J);
+  if (alpha == 2) return -legendre_shift_f(2, ell, J);
+  if (alpha != 4) throw std::runtime_error("parity-even coefficients are written out to alpha = 4");
+  double total = -legendre_shift_f(4, ell, J);
+  for (int S = std::max(0, ell - 2); S <= ell + 2; ++S) {
+    const double c = legendre_shift_f(2, ell, S);
+    if (std::fabs(c) < 1e-14) continue;
+    total += c * legendre_shift_h(2, 2, S, J);
+  }
+  return total;
 }
 
 // ---------------------------------------------------------------------------
@@ -249,17 +327,17 @@ void real_coupling(int l, int J1, int J2, Coef coef, Emit emit) {
 
 }  // namespace
 
-std::vector<GField> midpoint_gfields(int ell_max, int K) {
+std::vector<GField> midpoint_gfields(int ell_max, int K, bool even) {
   std::vector<GField> out;
-  for (int a = 0; a <= K; ++a)
+  for (int a = 0; a <= K; a += even ? 2 : 1)
     for (int J = a % 2; J <= ell_max + a; J += 2)
       for (int nu = -J; nu <= J; ++nu) out.push_back({a, J, nu});
   return out;
 }
 
-int midpoint_gfield_index(int ell_max, int alpha, int J, int nu) {
+int midpoint_gfield_index(int ell_max, int alpha, int J, int nu, bool even) {
   int idx = 0;
-  for (int a = 0; a <= alpha; ++a)
+  for (int a = 0; a <= alpha; a += even ? 2 : 1)
     for (int j = a % 2; j <= ell_max + a; j += 2) {
       if (a == alpha && j == J) return idx + nu + J;
       idx += 2 * j + 1;
@@ -297,30 +375,33 @@ std::vector<BisTerm> bisector_terms(int ell_max, int K) {
   return out;
 }
 
-std::vector<MidTerm> midpoint_terms(int ell_max, int K) {
+std::vector<MidTerm> midpoint_terms(int ell_max, int K, bool even) {
   std::vector<MidTerm> out;
   for (int l = 0; l <= ell_max; l += 2)
-    for (int a = 0; a <= K; ++a)
+    for (int a = 0; a <= K; a += even ? 2 : 1)
       for (int J1 = a % 2; J1 <= a; J1 += 2)
         for (int J2 = std::max(0, l - a); J2 <= l + a; ++J2) {
           if ((l + a + J2) % 2) continue;
           real_coupling(
-              l, J1, J2, [&](int m, int M) { return shift_phi(a, l, m, J1, J2, M); },
+              l, J1, J2,
+              [&](int m, int M) {
+                return even ? parity_even_Phi(a, l, m, J1, J2, M) : shift_phi(a, l, m, J1, J2, M);
+              },
               [&](int mu, int nu1, int nu2, double v) {
                 out.push_back({even_lm_index(l, mu), a, ylm_index(J1, nu1),
-                               midpoint_gfield_index(ell_max, a, J2, nu2), v});
+                               midpoint_gfield_index(ell_max, a, J2, nu2, even), v});
               });
         }
   return out;
 }
 
-std::vector<XiTerm> midpoint_xi_terms(int ell_max, int K) {
+std::vector<XiTerm> midpoint_xi_terms(int ell_max, int K, bool even) {
   std::vector<XiTerm> out;
   for (int l = 0; l <= ell_max; l += 2)
-    for (int a = 0; a <= K; ++a)
+    for (int a = 0; a <= K; a += even ? 2 : 1)
       for (int J = std::max(0, l - a); J <= l + a; ++J) {
         if ((a + l + J) % 2) continue;
-        const double f = legendre_shift_f(a, l, J);
+        const double f = even ? parity_even_F(a, l, J) : legendre_shift_f(a, l, J);
         if (std::fabs(f) > 1e-13) out.push_back({l, a, J, f});
       }
   return out;

@@ -12,7 +12,17 @@ double solid_coupling(int ell, int m, int lam, int mu);              // A_{ell m
 double legendre_inverse(int L, int n);                               // c~^L_n, eq. Leg-polynomial-inv-def
 double gegenbauer_term(int two_a, int N, int k);                     // C_{Nk}^{a}, a = two_a / 2, eq. gegenbauer-explicit
 double shift_phi(int alpha, int ell, int m, int J1, int J2, int M);  // eq. shift-coeff-def
+// the sum of eq. shift-coeff-def with Gegenbauer parameter two_gamma / 2 (phi: two_gamma = ell)
+double shift_sum(int alpha, int ell, int m, int J1, int J2, int M, int two_gamma);
+// omega^{beta, ell m alpha}_{J1 J2 M}: phi with C^{ell/2} -> C^{(ell+alpha)/2} (Appendix C)
+double shift_omega(int beta, int ell, int m, int alpha, int J1, int J2, int M);
+// Omega^{beta, alpha J1 J2 m M}_{S1 S2 T}, eq. generalized-shift-theorem
+double shift_Omega(int beta, int alpha, int J1, int J2, int m, int M, int S1, int S2, int T);
 double legendre_shift_f(int alpha, int ell, int J);                  // eq. f-alpha-def
+double legendre_shift_sum(int alpha, int ell, int J, int two_gamma);
+double legendre_shift_h(int beta, int alpha, int ell, int J);        // h^{beta, alpha ell}_J (Appendix F.2)
+double parity_even_Phi(int alpha, int ell, int m, int J1, int J2, int M);  // Appendix D, alpha <= 4
+double parity_even_F(int alpha, int ell, int J);                     // Appendix F.2, alpha <= 4
 double bisector_B(int beta, int ell, int m, int J1, int J2, int M);  // eq. B-def
 
 // ---- real-basis indexing ---------------------------------------------------
@@ -22,11 +32,11 @@ inline int ylm_index(int l, int nu) { return l * l + l + nu; }          // all l
 inline int even_lm_index(int l, int mu) { return l * (l + 1) / 2 + mu; } // even l only
 inline int n_even_lm(int ell_max) { return (ell_max + 1) * (ell_max + 2) / 2; }
 
-// Midpoint convolution fields g^alpha_{J nu}: alpha = 0..K, J = alpha mod 2,
-// alpha mod 2 + 2, .., <= ell_max + alpha, nu = -J..J.
+// Midpoint convolution fields g^alpha_{J nu}: alpha = 0..K (even alpha only for the
+// parity-even form), J = alpha mod 2, alpha mod 2 + 2, .., <= ell_max + alpha, nu = -J..J.
 struct GField { int alpha, J, nu; };
-std::vector<GField> midpoint_gfields(int ell_max, int K);
-int midpoint_gfield_index(int ell_max, int alpha, int J, int nu);
+std::vector<GField> midpoint_gfields(int ell_max, int K, bool even = false);
+int midpoint_gfield_index(int ell_max, int alpha, int J, int nu, bool even = false);
 
 // Bisector P / X: X_{lm}(k) = sum c * Re(conj F_i(k) F_j(k)), i <= j (field i = ylm_index),
 // summed over beta <= floor(K/2); c already symmetrised over (i, j) <-> (j, i).
@@ -36,10 +46,10 @@ std::vector<BisTerm> bisector_terms(int ell_max, int K);
 // Midpoint P: H_{lm}(Delta) = sum c t^alpha Y_{y}(hat Delta) g_{g}(Delta)
 // (t = |Delta| / r0, fields carry (2r/r0)^-alpha), y = ylm_index(J1, nu1).
 struct MidTerm { int lm, alpha, y, g; double c; };
-std::vector<MidTerm> midpoint_terms(int ell_max, int K);
+std::vector<MidTerm> midpoint_terms(int ell_max, int K, bool even = false);   // even: Phi instead of phi
 
 // Midpoint xi: T_l(Delta) = sum f t^alpha sum_nu Y_{J nu}(hat Delta) g^alpha_{J nu}(Delta).
 struct XiTerm { int l, alpha, J; double f; };
-std::vector<XiTerm> midpoint_xi_terms(int ell_max, int K);
+std::vector<XiTerm> midpoint_xi_terms(int ell_max, int K, bool even = false);  // even: F instead of f
 
 }  // namespace bym

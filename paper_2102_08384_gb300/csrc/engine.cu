@@ -138,7 +138,9 @@ int bym::validate_params(bym_ctx *c, const bym_params *p) {
   if (p->n_mesh < 8 || p->n_mesh > 1024 || p->n_mesh % 2)
     return fail(c, BYM_E_UNSUPPORTED, "n_mesh must be even and in 8..1024");
   if (p->assign != 2 && p->assign != 3) return fail(c, BYM_E_INVAL, "assign must be 2 (CIC) or 3 (TSC)");
-  if (p->los < 0 || p->los > 2) return fail(c, BYM_E_INVAL, "los must be 0, 1 or 2");
+  if (p->los < 0 || p->los > 3) return fail(c, BYM_E_INVAL, "los must be 0, 1, 2 or 3");
+  if (p->los == BYM_LOS_MIDPOINT_EVEN && p->order > 4)
+    return fail(c, BYM_E_UNSUPPORTED, "the parity-even midpoint form is available to order 4");
   if (p->precision != 32 && p->precision != 64) return fail(c, BYM_E_INVAL, "precision must be 32 or 64");
   if (p->norm != 0 && p->norm != 1) return fail(c, BYM_E_INVAL, "norm must be 0 or 1");
   if (p->compensate != 0 && p->compensate != 1) return fail(c, BYM_E_INVAL, "compensate must be 0 or 1");
@@ -179,11 +181,13 @@ static int n_fields(const bym_params *p) {
     const int J = p->ell_max + p->order / 2;
     return (J + 1) * (J + 1);
   }
-  return (int)midpoint_gfields(p->ell_max, p->order).size();
+  return (int)midpoint_gfields(p->ell_max, p->order, p->los == BYM_LOS_MIDPOINT_EVEN).size();
 }
 
+static bool is_midpoint(const bym_params *p) { return p->los == BYM_LOS_MIDPOINT || p->los == BYM_LOS_MIDPOINT_EVEN; }
+
 static int n_extra_slots(const bym_params *p, bool want_pk, bool want_xi) {
-  if (p->los == BYM_LOS_MIDPOINT && want_pk) return n_even_lm(p->ell_max);
+  if (is_midpoint(p) && want_pk) return n_even_lm(p->ell_max);
   if (p->los == BYM_LOS_BISECTOR && want_xi) return n_even_lm(p->ell_max);
   return 0;
 }
@@ -476,7 +480,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     std::vector<double> sc(nf);
     const double inv_n3 = 1.0 / ((double)N * N * N);
     for (int i = 0; i < nf; ++i) {
-      const double sign = (p->los == BYM_LOS_MIDPOINT && (K.fields[i].J % 2)) ? -1.0 : 1.0;
+      const double sign = (is_midpoint(p) && (K.fields[i].J % 2)) ? -1.0 : 1.0;
       sc[i] = sign * inv_n3;
     }
     TRY(alloc((void **)&scale, sizeof(double) * std::max(nf, 1)));
@@ -504,7 +508,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(0), N, p->box_lo, inv_h, p->assign, c->nsm, st);
     }
   CUDA_TRY(cudaGetLastError());
-  static const char *kLosName[3] = {"yamamoto", "midpoint", "bisector"};
+  static const char *kLosName[4] = {"yamamoto", "midpoint", "bisector", "midpoint_even"};
   const std::string los_name = kLosName[p->los];
   const std::string n_gen = "gen_fields_" + los_name, n_kc = "kcontract_" + los_name, n_xi = "xi_lag_" + los_name;
   const double cplx = 2.0 * esz * nhalf;  // one half-spectrum
@@ -540,7 +544,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
-  } else if (p->los == BYM_LOS_MIDPOINT) {
+  } else if (is_midpoint(p)) {
     TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
     {
       ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);

@@ -138,8 +138,8 @@ Fields field_set(const JitKey &k) {
     const int Jmax = k.ell_max + k.K / 2;
     for (int J = 0; J <= Jmax; ++J)
       for (int nu = -J; nu <= J; ++nu) f.list.push_back({0, J, nu});
-  } else {  // midpoint: g^alpha_{J nu}
-    for (auto &g : midpoint_gfields(k.ell_max, k.K)) f.list.push_back({g.alpha, g.J, g.nu});
+  } else {  // midpoint (all-parity, or even alpha only for the parity-even form): g^alpha_{J nu}
+    for (auto &g : midpoint_gfields(k.ell_max, k.K, k.los == 3)) f.list.push_back({g.alpha, g.J, g.nu});
   }
   return f;
 }
@@ -162,6 +162,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   const int NL = L / 2 + 1;
   const Fields F = field_set(key);
   const int nf = (int)F.list.size();
+  const bool midpoint = key.los == 1 || key.los == 3, even = key.los == 3;
   std::ostringstream o;
   o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
@@ -250,7 +251,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     o << "      bin = lut[n2];\n";
     o << "      if (" << (with_x ? "true" : "bin >= 0") << ") {\n";
     o << "        real cc = (real)1;\n";
-    if (key.los != 1)
+    if (!midpoint)
       o << "        if (invw) { cc = invw[ix] * invw[iy] * invw[iz]; cc = cc * cc; }\n";
     // X_{lm}
     for (int i = 0; i < n_lm; ++i) o << "        real X" << i << " = (real)0;\n";
@@ -258,7 +259,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
       o << "        const real2 d = D[m];\n";
       for (int i = 0; i < n_lm; ++i)
         o << "        { const real2 f = F[" << i << "LL * cslot + m]; X" << i << " = (f.x * d.x + f.y * d.y) * cc; }\n";
-    } else if (key.los == 1) {
+    } else if (midpoint) {
       for (int i = 0; i < n_lm; ++i) o << "        X" << i << " = F[" << i << "LL * cslot + m].x;\n";
     } else {
       for (int i = 0; i < nf; ++i) o << "        const real2 f" << i << " = F[" << i << "LL * cslot + m];\n";
@@ -301,8 +302,8 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   if (key.los == 2) emit_kcontract("kcontract_x", true);
 
   // ------------------------------------------------------------------ midpoint combine
-  if (key.los == 1) {
-    auto terms = midpoint_terms(key.ell_max, key.K);
+  if (midpoint) {
+    auto terms = midpoint_terms(key.ell_max, key.K, even);
     o << "extern \"C\" __global__ void __launch_bounds__(256) mid_combine(const real* __restrict__ G,"
          " long long slot, real* __restrict__ Hout, int N, double tscale) {\n";
     o << "  const long long ncell = (long long)N * N * N;\n";
@@ -353,8 +354,8 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   // ------------------------------------------------------------------ xi on the lag cube
   int jlag = L;
   std::vector<XiTerm> xterms;
-  if (key.los == 1) {
-    xterms = midpoint_xi_terms(key.ell_max, key.K);
+  if (midpoint) {
+    xterms = midpoint_xi_terms(key.ell_max, key.K, even);
     for (auto &x : xterms) jlag = std::max(jlag, x.J);
   }
   o << "extern \"C\" __global__ void __launch_bounds__(256) xi_lag(const real* __restrict__ Z, long long slot,"
@@ -385,7 +386,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     std::string line;
     while (std::getline(is, line)) o << "      " << line << "\n";
   }
-  if (key.los == 1) {
+  if (midpoint) {
     int amax = 0;
     for (auto &x : xterms) amax = std::max(amax, x.alpha);
     o << "        const double t1 = rr * tscale;\n";
@@ -397,7 +398,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
         o << "          { double S = 0.0;";
         for (int nu = -x.J; nu <= x.J; ++nu)
           o << " S += yl" << ylm_index(x.J, nu) << " * (double)Z["
-            << midpoint_gfield_index(key.ell_max, x.alpha, x.J, nu) << "LL * slot + off];";
+            << midpoint_gfield_index(key.ell_max, x.alpha, x.J, nu, even) << "LL * slot + off];";
         o << " T += " << lit(x.f, false);
         if (x.alpha > 0) o << " * t" << x.alpha;
         o << " * S; }\n";

@@ -83,6 +83,7 @@ def cap():
 @pytest.mark.parametrize("los,K,N", [
     ("yamamoto", 0, 48), ("midpoint", 4, 48), ("bisector", 4, 48),
     ("midpoint", 2, 40), ("bisector", 2, 40), ("midpoint", 3, 32), ("bisector", 6, 32),
+    ("midpoint_even", 4, 40), ("midpoint_even", 2, 32),
 ])
 def test_fp32_cap(pkg, ctx, cap, los, K, N):
     kedges = _kedges(cap.box_len, N, 12)
@@ -96,7 +97,7 @@ def test_fp32_cap(pkg, ctx, cap, los, K, N):
     np.testing.assert_array_equal(got["n_modes"], want["pk"]["n_modes"])
 
 
-@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("bisector", 4)])
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("bisector", 4), ("midpoint_even", 4)])
 def test_fp64_tsc_compensated(pkg, ctx, cap, los, K):
     N = 32
     kedges = _kedges(cap.box_len, N, 10)
@@ -136,7 +137,7 @@ def test_no_randoms_raw(pkg, ctx):
     N = 32
     kedges = _kedges(c.box_len, N, 8)
     redges = np.linspace(0.0, 300.0, 6)
-    for los, K in (("yamamoto", 0), ("midpoint", 3), ("bisector", 2)):
+    for los, K in (("yamamoto", 0), ("midpoint", 3), ("bisector", 2), ("midpoint_even", 4)):
         got = _run(pkg, ctx, c, N, 4, los, K, kedges, redges, 64, norm=0, ran=False)
         want = _oracle(c, N, 4, los, K, kedges, redges, norm=0, ran=False)
         check_multipoles(got["pk"], want["pk"]["pk"], "pk", 1e-10, 1e-10, f"{los}: ")
@@ -169,6 +170,7 @@ def test_out_of_box_is_an_error(pkg, ctx, cube):
 def test_bad_arguments(pkg, ctx, cube):
     ke = _kedges(cube.box_len, 16, 4)
     for kw, code in ((dict(ell_max=3), -6), (dict(order=13, los="midpoint"), -6), (dict(n_mesh=15), -6),
+                     (dict(order=6, los="midpoint_even"), -6),
                      (dict(assign=4), -1), (dict(precision=16), -1)):
         args = dict(box_lo=cube.box_lo, box_len=cube.box_len, n_mesh=16, ell_max=2)
         args.update(kw)
