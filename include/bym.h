@@ -139,6 +139,18 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
  * parameters; works without a GPU.  Used by build checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 
+/* FFT backend of ctx: native != 0 (the default) uses the library's own FP32
+ * 3D FFT kernels where they apply (n_mesh = 512, precision 32: two passes over
+ * HBM per transform, with the convolution product of the midpoint series
+ * fused between the forward and inverse transforms); 0 uses cuFFT always. */
+int bym_set_fft_backend(bym_ctx *ctx, int native);
+
+/* In-place batched FP32 3D FFTs of `count` meshes at `data` (device), each
+ * n_mesh * n_mesh * (n_mesh + 2) floats: forward R2C (inverse = 0) gives the
+ * half-spectrum n_mesh * n_mesh * (n_mesh/2 + 1) complex in the same memory;
+ * inverse C2R (inverse = 1) is unnormalised.  Sign e^{-i k.x} forward. */
+int bym_fft3d(bym_ctx *ctx, void *data, int n_mesh, int count, int inverse, void *cuda_stream);
+
 /* Kernel tracing.  While enabled, every launch of the library's own kernels
  * and every cuFFT execution on ctx is bracketed by CUDA events on its stream;
  * bym_profile_read writes a JSON object

@@ -25,6 +25,7 @@
 #include "bym.h"
 #include "coeff.h"
 #include "engine.h"
+#include "fft512.h"
 #include "jit.h"
 #include "kernels.cuh"
 
@@ -251,10 +252,20 @@ static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, i
   return BYM_OK;
 }
 
+static bool use_native_fft(bym_ctx *c, int N, int prec) { return c->native_fft && native_fft_supported(N, prec); }
+
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
                      int first, int count) {
-
   const double esz = prec == 64 ? 8.0 : 4.0;
+  if (use_native_fft(c, N, prec)) {
+    ProfScope ps(c, st, inverse ? "fft_native_c2r" : "fft_native_r2c", count * 2.0 * esz * (double)N * N * N);
+    cudaError_t e = native_fft_prepare();
+    if (e == cudaSuccess)
+      e = inverse ? native_fft_inverse((float *)base, (long long)(slot_bytes / 4), first, count, st)
+                  : native_fft_forward((float *)base, (long long)(slot_bytes / 4), first, count, st);
+    if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+    return BYM_OK;
+  }
   ProfScope ps(c, st, inverse ? "cufft_c2r" : "cufft_r2c", count * 2.0 * esz * (double)N * N * N);
   for (int done = 0; done < count;) {
     const int b = std::min(kFftBatch, count - done);
@@ -545,12 +556,23 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
   } else if (is_midpoint(p)) {
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
-    {
-      ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
-      launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+    if (use_native_fft(c, N, p->precision)) {
+      // delta forward, then every g field forward, times conj(delta) s W^-2, and back, in one pass
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1));
+      ProfScope ps(c, st, "fft_native_convolve", nf * (2.0 * n3 * esz + cplx));
+      cudaError_t e = native_fft_prepare();
+      if (e == cudaSuccess)
+        e = native_fft_convolve((float *)slots, slot_reals, 1, nf, (const float *)slot_r(0), scale,
+                                (const float *)invw, st);
+      if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+    } else {
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
+      {
+        ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
+        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+      }
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
     }
-    TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
     if (want_xi) {
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
       ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nf * esz);
@@ -734,6 +756,26 @@ int bym_pk_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *
   std::lock_guard<std::mutex> lock(c->mu);
   Request rq{gal, ran, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
   return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_set_fft_backend(bym_ctx *c, int native) {
+  if (!c) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  c->native_fft = native != 0;
+  return BYM_OK;
+}
+
+int bym_fft3d(bym_ctx *c, void *data, int n_mesh, int count, int inverse, void *stream) {
+  if (!c || !data || count < 0 || n_mesh < 8 || n_mesh % 2) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  const size_t slot_bytes = (size_t)n_mesh * n_mesh * (n_mesh + 2) * sizeof(float);
+  int rc = fft_slots(c, st, 32, inverse ? 1 : 0, n_mesh, data, slot_bytes, 0, count);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, BYM_E_CUDA, "FFT failed");
+  prof_collect(c);
+  return BYM_OK;
 }
 
 int bym_profile_enable(bym_ctx *c, int enable) {

@@ -59,6 +59,7 @@ struct bym_ctx {
   size_t fft_work_size = 0;
   std::map<std::string, bym::Geom> kgeo, rgeo;
   bym::Server *server = nullptr;
+  bool native_fft = true;                                      // library FFT kernels where they apply
   bool prof = false;                                           // kernel tracing (bym_profile_enable)
   std::map<std::string, bym::ProfEntry> prof_tab;
   std::vector<bym::ProfPending> prof_pending;

@@ -1,0 +1,79 @@
+"""The library's own 512^3 FP32 FFT kernels against cuFFT (through torch.fft), and
+whole requests computed with them against the same requests computed with cuFFT."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from parity import check_multipoles
+
+pytestmark = pytest.mark.gpu
+N = 512
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    import paper_2102_08384_gb300 as pkg
+    lib = pkg.lib()
+    lib.bym_fft3d.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_void_p]
+    lib.bym_set_fft_backend.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    ctx = pkg.Context(0)
+    yield torch, pkg, lib, ctx
+    ctx.close()
+
+
+def _slots(torch, x):
+    """(count, N, N, N) real -> padded slots (count, N, N, N + 2)."""
+    s = torch.zeros(x.shape[0], N, N, N + 2, dtype=torch.float32, device=x.device)
+    s[..., :N] = x
+    return s
+
+
+def test_forward_and_inverse_match_cufft(env):
+    torch, pkg, lib, ctx = env
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(2, N, N, N, device="cuda", generator=gen)
+    buf = _slots(torch, x)
+    assert lib.bym_fft3d(ctx._h, buf.data_ptr(), N, 2, 0, None) == 0
+    got = torch.view_as_complex(buf.view(2, N, N, N // 2 + 1, 2))
+    want = torch.fft.rfftn(x, dim=(1, 2, 3))
+    err = (got - want).abs().max().item() / want.abs().max().item()
+    rms = ((got - want).abs().pow(2).mean().sqrt() / want.abs().pow(2).mean().sqrt()).item()
+    assert err < 2e-6 and rms < 1e-6, (err, rms)
+    # inverse (unnormalised), from the native forward output
+    assert lib.bym_fft3d(ctx._h, buf.data_ptr(), N, 2, 1, None) == 0
+    back = buf[..., :N] / float(N) ** 3
+    err = (back - x).abs().max().item() / x.abs().max().item()
+    assert err < 2e-6, err
+    # inverse of a cuFFT spectrum against cuFFT's inverse
+    spec = torch.fft.rfftn(x[:1], dim=(1, 2, 3))
+    buf2 = torch.view_as_real(spec).contiguous().view(1, N, N, N + 2)
+    assert lib.bym_fft3d(ctx._h, buf2.data_ptr(), N, 1, 1, None) == 0
+    want_r = torch.fft.irfftn(spec, s=(N, N, N), dim=(1, 2, 3), norm="forward")
+    err = (buf2[..., :N] - want_r).abs().max().item() / want_r.abs().max().item()
+    assert err < 2e-6, err
+
+
+@pytest.fixture(scope="module")
+def cat():
+    from synth import lognormal_cap_catalog
+    return lognormal_cap_catalog(seed=9, n_gal=200_000, ran_factor=10.0, gen_mesh=128)
+
+
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 4), ("bisector", 4), ("midpoint_even", 2)])
+def test_requests_native_vs_cufft(env, cat, los, K):
+    torch, pkg, lib, ctx = env
+    p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
+                        compensate=True, precision=32)
+    kedges = np.round(np.arange(0.01, 0.2501, 0.01), 10)
+    redges = np.arange(10.0, 190.01, 10.0)
+    out = {}
+    for native in (0, 1):
+        assert lib.bym_set_fft_backend(ctx._h, native) == 0
+        out[native] = ctx.pk_xi_multipoles(cat.gal, cat.ran, p, kedges, redges, ran_nbar=cat.ran_nbar)
+    lib.bym_set_fft_backend(ctx._h, 1)
+    check_multipoles(out[1]["pk"], out[0]["pk"], "pk", label=f"{los} P: ")
+    check_multipoles(out[1]["xi"], out[0]["xi"], "xi", label=f"{los} xi: ")
