@@ -29,7 +29,10 @@
  *     norm = 0 sets A = V_cell = 1.
  *   - Outputs are host arrays owned by the caller, laid out [ell/2][bin].
  *   - Calls are synchronous on the given CUDA stream (NULL: the context's
- *     stream) unless submitted through bym_submit.
+ *     stream) unless submitted through bym_submit.  The context's stream is an
+ *     ordinary blocking stream, so it orders after work the caller queued on
+ *     the legacy default stream (device catalogs produced there are safe to
+ *     pass); device inputs produced on other streams must be complete first.
  *
  * Every function returns BYM_OK (0) or a negative BYM_E_* code; the message
  * of the last failure on a context is available from bym_last_error.  A

@@ -686,7 +686,7 @@ int bym_create(bym_ctx **out, int device, size_t hbm_budget_bytes) {
   c->budget = hbm_budget_bytes;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreate(&c->stream) != cudaSuccess) {   // a blocking stream: orders after legacy-stream work
     cudaGetLastError();
     delete c;
     return BYM_E_CUDA;

@@ -37,6 +37,7 @@ def test_forward_and_inverse_match_cufft(env):
     gen = torch.Generator(device="cuda").manual_seed(7)
     x = torch.randn(2, N, N, N, device="cuda", generator=gen)
     buf = _slots(torch, x)
+    torch.cuda.synchronize()
     assert lib.bym_fft3d(ctx._h, buf.data_ptr(), N, 2, 0, None) == 0
     got = torch.view_as_complex(buf.view(2, N, N, N // 2 + 1, 2))
     want = torch.fft.rfftn(x, dim=(1, 2, 3))
@@ -52,6 +53,7 @@ def test_forward_and_inverse_match_cufft(env):
     spec = torch.fft.rfftn(x[:1], dim=(1, 2, 3))
     want_r = torch.fft.irfftn(spec, s=(N, N, N), dim=(1, 2, 3), norm="forward")
     buf2 = torch.view_as_real(spec).clone().view(1, N, N, N + 2)
+    torch.cuda.synchronize()
     assert lib.bym_fft3d(ctx._h, buf2.data_ptr(), N, 1, 1, None) == 0
     err = (buf2[..., :N] - want_r).abs().max().item() / want_r.abs().max().item()
     assert err < 2e-6, err
