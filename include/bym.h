@@ -148,6 +148,18 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len);
  * fused between the forward and inverse transforms); 0 uses cuFFT always. */
 int bym_set_fft_backend(bym_ctx *ctx, int native);
 
+/* Autotuner.  Runs the given request (which must be valid) several times on
+ * ctx under candidate launch shapes -- blocks per SM of the grid-stride
+ * kernels, cuFFT batch size, library FFT kernels or cuFFT -- timing every
+ * kernel with the tracer, and keeps the fastest choice per kernel for requests
+ * with the same (n_mesh, precision, los) on ctx.  cache_path (may be NULL): a
+ * text file of earlier choices; a matching entry is used without measuring,
+ * a new choice is appended.  report (may be NULL) receives a one-line JSON
+ * summary of the choice. */
+int bym_autotune(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                 const bym_bins *kbins, const bym_bins *rbins, const char *cache_path, char *report,
+                 size_t report_len);
+
 /* In-place batched FP32 3D FFTs of `count` meshes at `data` (device), each
  * n_mesh * n_mesh * (n_mesh + 2) floats: forward R2C (inverse = 0) gives the
  * half-spectrum n_mesh * n_mesh * (n_mesh/2 + 1) complex in the same memory;

@@ -96,6 +96,10 @@ def lib():
         L.bym_batch_run.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(Result),
                                     ctypes.POINTER(ctypes.c_int)]
         L.bym_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.bym_autotune.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, ctypes.c_char_p, ctypes.c_char_p,
+                                   ctypes.c_size_t]
+        L.bym_set_fft_backend.argtypes = [vp, ctypes.c_int]
+        L.bym_fft3d.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
         L.bym_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int]
         _lib_handle = L
     return _lib_handle
@@ -222,6 +226,23 @@ class Context:
         self._check(rc)
         out["ells"] = list(range(0, params.ell_max + 1, 2))
         return out
+
+    def autotune(self, gal, ran, params, kedges=None, redges=None, gal_nbar=None, ran_nbar=None,
+                 cache_path=None):
+        """Pick launch shapes for requests like this one (see bym_autotune); returns the choice."""
+        import json
+        keep = []
+        g = _catalog(gal, gal_nbar, keep)
+        r = _catalog(ran, ran_nbar, keep)
+        kb = _bins(kedges, keep) if kedges is not None else None
+        rb = _bins(redges, keep) if redges is not None else None
+        rep = ctypes.create_string_buffer(1024)
+        self._check(self._L.bym_autotune(self._h, _ptr(g), _ptr(r), ctypes.byref(params), _ptr(kb), _ptr(rb),
+                                         cache_path.encode() if cache_path else None, rep, len(rep)))
+        return json.loads(rep.value.decode())
+
+    def set_fft_backend(self, native: bool):
+        self._check(self._L.bym_set_fft_backend(self._h, int(bool(native))))
 
     # ------------------------------------------------------------ serving
     def _request(self, gal, ran, params, kedges, redges, gal_nbar, ran_nbar):

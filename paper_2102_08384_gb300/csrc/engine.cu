@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -32,8 +33,6 @@
 using namespace bym;
 
 namespace {
-
-constexpr int kFftBatch = 8;
 
 int fail(bym_ctx *c, int code, const std::string &msg) {
   if (c) c->err = msg;
@@ -252,12 +251,20 @@ static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, i
   return BYM_OK;
 }
 
-static bool use_native_fft(bym_ctx *c, int N, int prec) { return c->native_fft && native_fft_supported(N, prec); }
+static const Tune &tune_for(bym_ctx *c, int N, int prec, int los) {
+  static const Tune kDefault;
+  auto it = c->tune.find(std::make_tuple(N, prec, los));
+  return it == c->tune.end() ? kDefault : it->second;
+}
+
+static bool use_native_fft(bym_ctx *c, int N, int prec, const Tune &tn) {
+  return c->native_fft && tn.native && native_fft_supported(N, prec);
+}
 
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
-                     int first, int count) {
+                     int first, int count, const Tune &tn) {
   const double esz = prec == 64 ? 8.0 : 4.0;
-  if (use_native_fft(c, N, prec)) {
+  if (use_native_fft(c, N, prec, tn)) {
     ProfScope ps(c, st, inverse ? "fft_native_c2r" : "fft_native_r2c", count * 2.0 * esz * (double)N * N * N);
     cudaError_t e = native_fft_prepare();
     if (e == cudaSuccess)
@@ -268,7 +275,7 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
   }
   ProfScope ps(c, st, inverse ? "cufft_c2r" : "cufft_r2c", count * 2.0 * esz * (double)N * N * N);
   for (int done = 0; done < count;) {
-    const int b = std::min(kFftBatch, count - done);
+    const int b = std::min(std::max(tn.fft_batch, 1), count - done);
     cufftHandle h;
     int rc = get_plan(c, st, N, prec, inverse, b, &h);
     if (rc) return rc;
@@ -404,6 +411,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   auto ks = get_kernels(JitKey{p->los, p->ell_max, order_key(p), p->precision}, jerr);
   if (!ks) return fail(c, BYM_E_CUDA, jerr);
   const KernelSet &K = *ks;
+  const Tune &tn = tune_for(c, N, p->precision, p->los);
   const int nf = (int)K.fields.size();
   const int nlm = K.n_lm, NL = K.n_ell;
   const int nextra = n_extra_slots(p, want_pk, want_xi);
@@ -529,16 +537,16 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     const long long ncell = (long long)N * N * N;
     ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * n3 * esz);
     CUDA_TRY(cudaMemsetAsync(slot_r(1), 0, (size_t)nf * slot_bytes, st));
-    CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, 16), 256, 0, st, (const T *)slot_r(0), slot_r(1),
+    CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
                     slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
   }
 
-  const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, 4);
+  const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, tn.per_sm_k);
   const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
   const double tscale = h * inv_r0;
 
   if (p->los == BYM_LOS_YAMAMOTO) {
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
     if (want_pk) {
       ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
@@ -547,18 +555,18 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (want_xi) {
       {
         ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
-        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm * tn.per_sm_spec / 8, st);
       }
-      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
       ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nlm * esz);
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
   } else if (is_midpoint(p)) {
-    if (use_native_fft(c, N, p->precision)) {
+    if (use_native_fft(c, N, p->precision, tn)) {
       // delta forward, then every g field forward, times conj(delta) s W^-2, and back, in one pass
-      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1));
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
       ProfScope ps(c, st, "fft_native_convolve", nf * (2.0 * n3 * esz + cplx));
       cudaError_t e = native_fft_prepare();
       if (e == cudaSuccess)
@@ -566,12 +574,12 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
                                 (const float *)invw, st);
       if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     } else {
-      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf));
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
       {
         ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
-        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm, st);
+        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm * tn.per_sm_spec / 8, st);
       }
-      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf));
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
     }
     if (want_xi) {
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
@@ -582,23 +590,23 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (want_pk) {
       {
         ProfScope ps(c, st, "mid_combine", ((double)nf + nlm) * n3 * esz);
-        CUDA_TRY(launch(K.mid_combine, grid_of((long long)N * N * N, c->nsm, 16), 256, 0, st,
+        CUDA_TRY(launch(K.mid_combine, grid_of((long long)N * N * N, c->nsm, tn.per_sm_comb), 256, 0, st,
                         (const T *)slot_r(1), slot_reals, slot_r(1 + nf), N, tscale));
       }
-      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm));
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm, tn));
       ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
     }
   } else {
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf, tn));
     if (want_xi) {
       {
         ProfScope ps(c, st, "kcontract_bisector_x", ((double)nf + nlm) * cplx);
         CUDA_TRY(launch(K.kcontract_x, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
                         (const int *)kg->lut, nbk, ksum, slot_c(1 + nf), cslot, (const T *)invw));
       }
-      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1 + nf, nlm));
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1 + nf, nlm, tn));
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
       ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nlm * esz);
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
@@ -771,10 +779,120 @@ int bym_fft3d(bym_ctx *c, void *data, int n_mesh, int count, int inverse, void *
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   const size_t slot_bytes = (size_t)n_mesh * n_mesh * (n_mesh + 2) * sizeof(float);
-  int rc = fft_slots(c, st, 32, inverse ? 1 : 0, n_mesh, data, slot_bytes, 0, count);
+  int rc = fft_slots(c, st, 32, inverse ? 1 : 0, n_mesh, data, slot_bytes, 0, count, Tune());
   if (rc) return rc;
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, BYM_E_CUDA, "FFT failed");
   prof_collect(c);
+  return BYM_OK;
+}
+
+// Autotuner: time real runs of the caller's request under candidate launch
+// shapes (per-kernel times from the tracer) and keep the fastest per kernel.
+int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                 const bym_bins *kbins, const bym_bins *rbins, const char *cache_path, char *report,
+                 size_t report_len) {
+  if (!c || !p) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  int rc = validate(c, gal, ran, p, kbins, rbins);
+  if (rc) return rc;
+  const auto key = std::make_tuple(p->n_mesh, p->precision, p->los);
+  char keybuf[96];
+  snprintf(keybuf, sizeof keybuf, "n%d_p%d_los%d", p->n_mesh, p->precision, p->los);
+  auto emit = [&](const Tune &t, const char *source) {
+    if (!report || !report_len) return;
+    char buf[512];
+    snprintf(buf, sizeof buf,
+             "{\"key\": \"%s\", \"source\": \"%s\", \"per_sm_gen\": %d, \"per_sm_comb\": %d, "
+             "\"per_sm_k\": %d, \"per_sm_spec\": %d, \"fft_batch\": %d, \"native_fft\": %d}",
+             keybuf, source, t.per_sm_gen, t.per_sm_comb, t.per_sm_k, t.per_sm_spec, t.fft_batch, t.native);
+    snprintf(report, report_len, "%s", buf);
+  };
+  if (cache_path) {   // "key per_sm_gen per_sm_comb per_sm_k per_sm_spec fft_batch native" lines
+    if (FILE *f = fopen(cache_path, "r")) {
+      char k[96];
+      Tune t;
+      while (fscanf(f, "%95s %d %d %d %d %d %d", k, &t.per_sm_gen, &t.per_sm_comb, &t.per_sm_k, &t.per_sm_spec,
+                    &t.fft_batch, &t.native) == 7) {
+        if (strcmp(k, keybuf) == 0) {
+          fclose(f);
+          c->tune[key] = t;
+          emit(t, "cache");
+          return BYM_OK;
+        }
+      }
+      fclose(f);
+    }
+  }
+  const bool want_pk = kbins != nullptr, want_xi = rbins != nullptr;
+  const int NL = p->ell_max / 2 + 1;
+  std::vector<double> pk(want_pk ? NL * kbins->nbins : 0), km(want_pk ? kbins->nbins : 0),
+      xi(want_xi ? NL * rbins->nbins : 0), rm(want_xi ? rbins->nbins : 0);
+  std::vector<int64_t> nm(want_pk ? kbins->nbins : 0), nc(want_xi ? rbins->nbins : 0);
+  Request rq{gal, ran, p, kbins, rbins, want_pk ? pk.data() : nullptr, want_pk ? km.data() : nullptr,
+             want_pk ? nm.data() : nullptr, want_xi ? xi.data() : nullptr, want_xi ? rm.data() : nullptr,
+             want_xi ? nc.data() : nullptr};
+  const bool prof_was = c->prof;
+  auto timed = [&](const Tune &t, std::map<std::string, ProfEntry> &out) -> int {
+    c->tune[key] = t;
+    c->prof_tab.clear();
+    c->prof = true;
+    int r = run_request(c, rq, c->stream);
+    c->prof = prof_was;
+    out = c->prof_tab;
+    c->prof_tab.clear();
+    return r;
+  };
+  std::map<std::string, ProfEntry> prof;
+  Tune best;
+  if ((rc = timed(best, prof))) return rc;   // warm: kernels, plans, tables
+  // grid shapes: one run per blocks-per-SM factor, best factor per kernel
+  const int factors[] = {2, 4, 8, 16, 32};
+  double bgen = 1e300, bcomb = 1e300, bk = 1e300, bspec = 1e300;
+  for (int f : factors) {
+    Tune t = best;
+    t.per_sm_gen = t.per_sm_comb = t.per_sm_k = t.per_sm_spec = f;
+    if ((rc = timed(t, prof))) return rc;
+    for (auto &kv : prof) {
+      const std::string &n = kv.first;
+      const double ms = kv.second.ms;
+      if (n.rfind("gen_fields", 0) == 0 && ms < bgen) bgen = ms, best.per_sm_gen = f;
+      if (n == "mid_combine" && ms < bcomb) bcomb = ms, best.per_sm_comb = f;
+      if (n.rfind("kcontract", 0) == 0 && ms < bk) bk = ms, best.per_sm_k = f;
+      if (n == "spec_mul" && ms < bspec) bspec = ms, best.per_sm_spec = f;
+    }
+  }
+  // transforms: library kernels against cuFFT, then cuFFT's batch size
+  auto fft_ms = [](const std::map<std::string, ProfEntry> &m) {
+    double s = 0.0;
+    for (auto &kv : m)
+      if (kv.first.rfind("cufft", 0) == 0 || kv.first.rfind("fft_native", 0) == 0 || kv.first == "spec_mul")
+        s += kv.second.ms;
+    return s;
+  };
+  double best_fft = 1e300;
+  for (int b : {4, 8, 16}) {
+    Tune t = best;
+    t.native = 0;
+    t.fft_batch = b;
+    if ((rc = timed(t, prof))) return rc;
+    const double ms = fft_ms(prof);
+    if (ms < best_fft) best_fft = ms, best.fft_batch = b, best.native = 0;
+  }
+  if (native_fft_supported(p->n_mesh, p->precision) && c->native_fft) {
+    Tune t = best;
+    t.native = 1;
+    if ((rc = timed(t, prof))) return rc;
+    if (fft_ms(prof) < best_fft) best.native = 1;
+  }
+  c->tune[key] = best;
+  if (cache_path) {
+    if (FILE *f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %d %d %d %d %d %d\n", keybuf, best.per_sm_gen, best.per_sm_comb, best.per_sm_k,
+              best.per_sm_spec, best.fft_batch, best.native);
+      fclose(f);
+    }
+  }
+  emit(best, "measured");
   return BYM_OK;
 }
 

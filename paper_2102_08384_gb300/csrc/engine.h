@@ -35,6 +35,16 @@ struct Request {
 
 struct Server;  // serving loop state (serve.cpp)
 
+// Launch shapes chosen by bym_autotune for one (n_mesh, precision, LOS).
+struct Tune {
+  int per_sm_gen = 16;    // blocks per SM of gen_fields (grid-stride, 256 threads)
+  int per_sm_comb = 16;   // mid_combine
+  int per_sm_k = 4;       // kcontract / kcontract_x
+  int per_sm_spec = 8;    // spec_mul
+  int fft_batch = 8;      // transforms per cuFFT call
+  int native = 1;         // library FFT kernels where they apply
+};
+
 struct ProfEntry {
   long long launches = 0;
   double ms = 0.0, bytes = 0.0;
@@ -60,6 +70,7 @@ struct bym_ctx {
   std::map<std::string, bym::Geom> kgeo, rgeo;
   bym::Server *server = nullptr;
   bool native_fft = true;                                      // library FFT kernels where they apply
+  std::map<std::tuple<int, int, int>, bym::Tune> tune;         // (n_mesh, precision, los) -> launch shapes
   bool prof = false;                                           // kernel tracing (bym_profile_enable)
   std::map<std::string, bym::ProfEntry> prof_tab;
   std::vector<bym::ProfPending> prof_pending;

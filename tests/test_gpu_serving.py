@@ -107,3 +107,23 @@ def test_admission_timeout_and_errors(pkg, cap):
     assert ei.value.code == -2
     ctx.serve_stop()
     ctx.close()
+
+
+def test_autotune_keeps_results_and_caches(pkg, cap, tmp_path):
+    ctx = pkg.Context(0)
+    p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=48, ell_max=4, los="bisector", order=4)
+    kedges = np.linspace(0.0, 0.3, 7)
+    redges = np.linspace(0.0, 300.0, 6)
+    ref = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
+    cache = str(tmp_path / "tune.txt")
+    choice = ctx.autotune(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar, cache_path=cache)
+    assert choice["source"] == "measured" and choice["fft_batch"] in (4, 8, 16)
+    tuned = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
+    check_multipoles(tuned["pk"], ref["pk"], "pk")
+    check_multipoles(tuned["xi"], ref["xi"], "xi")
+    ctx.close()
+    ctx2 = pkg.Context(0)
+    again = ctx2.autotune(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar, cache_path=cache)
+    ctx2.close()
+    assert again["source"] == "cache"
+    assert {k: v for k, v in again.items() if k != "source"} == {k: v for k, v in choice.items() if k != "source"}
