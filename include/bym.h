@@ -142,11 +142,13 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
  * parameters; works without a GPU.  Used by build checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 
-/* FFT backend of ctx: native != 0 (the default) uses the library's own FP32
- * 3D FFT kernels where they apply (n_mesh = 512, precision 32: two passes over
- * HBM per transform, with the convolution product of the midpoint series
- * fused between the forward and inverse transforms); 0 uses cuFFT always. */
-int bym_set_fft_backend(bym_ctx *ctx, int native);
+/* FFT backend of ctx.  The library has its own FP32 3D FFT kernels for
+ * n_mesh = 512 (two passes over HBM per transform, with the convolution
+ * product of the midpoint series fused between the forward and inverse
+ * transforms).  mode 0: cuFFT always; 1: the library's kernels wherever they
+ * apply; 2 (the default): whichever bym_autotune measured faster for the
+ * request's shape, cuFFT if it has not been tuned. */
+int bym_set_fft_backend(bym_ctx *ctx, int mode);
 
 /* Autotuner.  Runs the given request (which must be valid) several times on
  * ctx under candidate launch shapes -- blocks per SM of the grid-stride

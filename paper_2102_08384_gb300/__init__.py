@@ -241,8 +241,9 @@ class Context:
                                          cache_path.encode() if cache_path else None, rep, len(rep)))
         return json.loads(rep.value.decode())
 
-    def set_fft_backend(self, native: bool):
-        self._check(self._L.bym_set_fft_backend(self._h, int(bool(native))))
+    def set_fft_backend(self, mode: int):
+        """0: cuFFT, 1: the library's FFT kernels where they apply, 2: as tuned (default)."""
+        self._check(self._L.bym_set_fft_backend(self._h, int(mode)))
 
     # ------------------------------------------------------------ serving
     def _request(self, gal, ran, params, kedges, redges, gal_nbar, ran_nbar):

@@ -258,7 +258,7 @@ static const Tune &tune_for(bym_ctx *c, int N, int prec, int los) {
 }
 
 static bool use_native_fft(bym_ctx *c, int N, int prec, const Tune &tn) {
-  return c->native_fft && tn.native && native_fft_supported(N, prec);
+  return native_fft_supported(N, prec) && (c->fft_mode == 1 || (c->fft_mode == 2 && tn.native));
 }
 
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
@@ -766,10 +766,10 @@ int bym_pk_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *
   return run_request(c, rq, (cudaStream_t)stream);
 }
 
-int bym_set_fft_backend(bym_ctx *c, int native) {
-  if (!c) return BYM_E_INVAL;
+int bym_set_fft_backend(bym_ctx *c, int mode) {
+  if (!c || mode < 0 || mode > 2) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
-  c->native_fft = native != 0;
+  c->fft_mode = mode;
   return BYM_OK;
 }
 
@@ -878,7 +878,7 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
     const double ms = fft_ms(prof);
     if (ms < best_fft) best_fft = ms, best.fft_batch = b, best.native = 0;
   }
-  if (native_fft_supported(p->n_mesh, p->precision) && c->native_fft) {
+  if (native_fft_supported(p->n_mesh, p->precision) && c->fft_mode == 2) {
     Tune t = best;
     t.native = 1;
     if ((rc = timed(t, prof))) return rc;

@@ -42,7 +42,7 @@ struct Tune {
   int per_sm_k = 4;       // kcontract / kcontract_x
   int per_sm_spec = 8;    // spec_mul
   int fft_batch = 8;      // transforms per cuFFT call
-  int native = 1;         // library FFT kernels where they apply
+  int native = 0;         // library FFT kernels where they apply (off until the autotuner measures them faster)
 };
 
 struct ProfEntry {
@@ -69,7 +69,7 @@ struct bym_ctx {
   size_t fft_work_size = 0;
   std::map<std::string, bym::Geom> kgeo, rgeo;
   bym::Server *server = nullptr;
-  bool native_fft = true;                                      // library FFT kernels where they apply
+  int fft_mode = 2;                                            // 0 cuFFT, 1 library FFT kernels, 2 as tuned
   std::map<std::tuple<int, int, int>, bym::Tune> tune;         // (n_mesh, precision, los) -> launch shapes
   bool prof = false;                                           // kernel tracing (bym_profile_enable)
   std::map<std::string, bym::ProfEntry> prof_tab;

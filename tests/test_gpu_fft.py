@@ -21,6 +21,7 @@ def env():
                               ctypes.c_void_p]
     lib.bym_set_fft_backend.argtypes = [ctypes.c_void_p, ctypes.c_int]
     ctx = pkg.Context(0)
+    assert lib.bym_set_fft_backend(ctx._h, 1) == 0     # the library's kernels wherever they apply
     yield torch, pkg, lib, ctx
     ctx.close()
 
