@@ -139,15 +139,37 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
                          double *xi, double *r_mean, int64_t *n_cells, void *cuda_stream);
 
 /* Compile (without running) the runtime-specialised kernels for these
- * parameters; works without a GPU.  Used by build checks. */
+ * parameters (for the midpoint forms also the kernels of streamed field
+ * ranges, see bym_set_field_chunk); works without a GPU.  Used by build
+ * checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 
+/* Memory bound for the midpoint forms (Sec. 2.2: the g^alpha_{J M} functions
+ * of eq. g-JM-form are the largest memory item, 145 meshes at ell_max = 4,
+ * order 4).  The paper keeps every g field resident; the library can instead
+ * generate, convolve and consume them in ranges of at most max_fields fields.
+ * H_{ell m} of eq. FFT-midpoint and the xi shell sums of eq.
+ * xi-parity-all-estimator are sums over the fields, so the ranges add up to
+ * the same result.  A request then holds two delta meshes, one range and the
+ * 15 H meshes.  max_fields = 0 (the default): ranges only when the whole set
+ * does not fit the context's budget (or, with no budget, the device memory
+ * free at the start of the request), sized to fit; > 0: always, with ranges
+ * of that many fields.  No effect on the other lines of sight.  Returns
+ * BYM_E_INVAL for max_fields < 0. */
+int bym_set_field_chunk(bym_ctx *ctx, int max_fields);
+
 /* FFT backend of ctx.  The library has its own FP32 3D FFT kernels for
- * n_mesh = 512 (two passes over HBM per transform, with the convolution
- * product of the midpoint series fused between the forward and inverse
- * transforms).  mode 0: cuFFT always; 1: the library's kernels wherever they
- * apply; 2 (the default): whichever bym_autotune measured faster for the
- * request's shape, cuFFT if it has not been tuned. */
+ * n_mesh = 512: a plane pass (R2C along z and C2C along y of one x-plane per
+ * thread-block cluster of 8 or 16 CTAs) and an x pass (C2C along x), two
+ * passes over HBM per transform; in the midpoint convolution steps the
+ * product with conj(delta) sits inside the x pass, between its forward and
+ * inverse transforms.  mode 0: cuFFT 3D transforms always; 1: the library's
+ * two-pass kernels wherever they apply, 8-CTA clusters; 3: the same with
+ * 16-CTA clusters (a non-portable cluster size: a launch the device refuses
+ * returns BYM_E_CUDA); 4: cuFFT 2D transforms of the (y, z) planes with the
+ * library's x pass; 2 (the default): whichever bym_autotune measured fastest
+ * for the request's shape, cuFFT 3D if it has not been tuned.  Returns
+ * BYM_E_INVAL for other modes. */
 int bym_set_fft_backend(bym_ctx *ctx, int mode);
 
 /* Autotuner.  Runs the given request (which must be valid) several times on

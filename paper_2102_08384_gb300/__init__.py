@@ -99,6 +99,7 @@ def lib():
         L.bym_autotune.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, ctypes.c_char_p, ctypes.c_char_p,
                                    ctypes.c_size_t]
         L.bym_set_fft_backend.argtypes = [vp, ctypes.c_int]
+        L.bym_set_field_chunk.argtypes = [vp, ctypes.c_int]
         L.bym_fft3d.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
         L.bym_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int]
         _lib_handle = L
@@ -241,8 +242,13 @@ class Context:
                                          cache_path.encode() if cache_path else None, rep, len(rep)))
         return json.loads(rep.value.decode())
 
+    def set_field_chunk(self, max_fields: int):
+        """Midpoint g fields generated and consumed in ranges of at most max_fields (0: only when needed)."""
+        self._check(self._L.bym_set_field_chunk(self._h, int(max_fields)))
+
     def set_fft_backend(self, mode: int):
-        """0: cuFFT, 1: the library's FFT kernels where they apply, 2: as tuned (default)."""
+        """0: cuFFT, 1: the library's FFT kernels where they apply (8-CTA clusters), 2: as tuned (default),
+        3: the library's kernels with 16-CTA clusters, 4: cuFFT plane transforms + the library's x pass."""
         self._check(self._L.bym_set_fft_backend(self._h, int(mode)))
 
     # ------------------------------------------------------------ serving

@@ -60,6 +60,12 @@ cudaError_t launch(cudaKernel_t k, unsigned grid, unsigned block, size_t smem, c
   return cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), argv, smem, st);
 }
 
+#define TRY_RC(x)        \
+  do {                   \
+    int rc_ = (x);       \
+    if (rc_) return rc_; \
+  } while (0)
+
 unsigned grid_of(long long work, int nsm, int per_sm) {
   long long g = (work + 255) / 256;
   const long long cap = (long long)nsm * per_sm;
@@ -193,11 +199,13 @@ static int n_extra_slots(const bym_params *p, bool want_pk, bool want_xi) {
 }
 
 size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
-                            bool cats_on_device) {
+                            bool cats_on_device, int chunk) {
   const size_t N = (size_t)p->n_mesh;
   const size_t esz = p->precision == 64 ? 8 : 4;
   const size_t slot = N * N * (N + 2) * esz;
-  const size_t slots = 1 + (size_t)n_fields(p) + (size_t)n_extra_slots(p, want_pk, want_xi);
+  const size_t nf = (size_t)n_fields(p);
+  const size_t slots = (chunk > 0 && is_midpoint(p) ? 2 + std::min(nf, (size_t)chunk) : 1 + nf) +
+                       (size_t)n_extra_slots(p, want_pk, want_xi);
   size_t cats = 0;
   if (!cats_on_device) cats = (size_t)(std::max<int64_t>(n_gal, 0) + std::max<int64_t>(n_ran, 0)) * 20;
   return slots * slot + cats + (1 << 20);
@@ -206,8 +214,10 @@ size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, b
 // ---------------------------------------------------------------------------
 // cuFFT plans (in place, padded real layout), shared work area
 // ---------------------------------------------------------------------------
-static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, int batch, cufftHandle *out) {
-  auto key = std::make_tuple(N, prec, inverse, batch);
+// rank 3: whole N^3 slots (batch = slots); rank 2: the (y, z) planes of slots (batch = planes)
+static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, int batch, cufftHandle *out,
+                    int rank = 3) {
+  auto key = std::make_tuple(N, prec, inverse + (rank == 2 ? 2 : 0), batch);
   auto it = c->plans.find(key);
   if (it != c->plans.end()) {
     *out = it->second;
@@ -216,18 +226,20 @@ static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, i
   cufftHandle h;
   if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftCreate failed");
   cufftSetAutoAllocation(h, 0);
-  long long n[3] = {N, N, N};
-  long long real_emb[3] = {N, N, 2 * (N / 2 + 1)};
-  long long cplx_emb[3] = {N, N, N / 2 + 1};
-  const long long rdist = (long long)N * N * 2 * (N / 2 + 1);
-  const long long cdist = (long long)N * N * (N / 2 + 1);
+  long long n3[3] = {N, N, N};
+  long long real_emb3[3] = {N, N, 2 * (N / 2 + 1)};
+  long long cplx_emb3[3] = {N, N, N / 2 + 1};
+  long long *n = rank == 2 ? n3 + 1 : n3, *real_emb = rank == 2 ? real_emb3 + 1 : real_emb3,
+            *cplx_emb = rank == 2 ? cplx_emb3 + 1 : cplx_emb3;
+  const long long rdist = (long long)(rank == 2 ? 1 : N) * N * 2 * (N / 2 + 1);
+  const long long cdist = (long long)(rank == 2 ? 1 : N) * N * (N / 2 + 1);
   cufftType type = prec == 64 ? (inverse ? CUFFT_Z2D : CUFFT_D2Z) : (inverse ? CUFFT_C2R : CUFFT_R2C);
   size_t work = 0;
   cufftResult r;
   if (!inverse)
-    r = cufftMakePlanMany64(h, 3, n, real_emb, 1, rdist, cplx_emb, 1, cdist, type, batch, &work);
+    r = cufftMakePlanMany64(h, rank, n, real_emb, 1, rdist, cplx_emb, 1, cdist, type, batch, &work);
   else
-    r = cufftMakePlanMany64(h, 3, n, cplx_emb, 1, cdist, real_emb, 1, rdist, type, batch, &work);
+    r = cufftMakePlanMany64(h, rank, n, cplx_emb, 1, cdist, real_emb, 1, rdist, type, batch, &work);
   if (r != CUFFT_SUCCESS) {
     cufftDestroy(h);
     return fail(c, BYM_E_CUDA, "cufftMakePlanMany failed (" + std::to_string((int)r) + ")");
@@ -257,19 +269,56 @@ static const Tune &tune_for(bym_ctx *c, int N, int prec, int los) {
   return it == c->tune.end() ? kDefault : it->second;
 }
 
-static bool use_native_fft(bym_ctx *c, int N, int prec, const Tune &tn) {
-  return native_fft_supported(N, prec) && (c->fft_mode == 1 || (c->fft_mode == 2 && tn.native));
+// Which FFT path a request takes: 0 cuFFT 3D transforms; 1 cuFFT 2D transforms of the
+// (y, z) planes with the library's x pass (and the convolution product fused into
+// it); 8 / 16 the library's two-pass transforms with 8- / 16-CTA plane clusters.
+static int fft_kind(const bym_ctx *c, int N, int prec, const Tune &tn) {
+  if (!native_fft_supported(N, prec)) return 0;
+  switch (c->fft_mode) {
+    case 0: return 0;
+    case 1: return 8;
+    case 3: return 16;
+    case 4: return 1;
+    default: return (tn.native == 1 || tn.native == 8 || tn.native == 16) ? tn.native : 0;
+  }
+}
+
+// cuFFT 2D transforms of the planes of slots [first, first + count), tn.fft_batch slots per call
+static int fft_planes(bym_ctx *c, cudaStream_t st, int inverse, int N, void *base, size_t slot_bytes, int first,
+                      int count, const Tune &tn) {
+  for (int done = 0; done < count;) {
+    const int b = std::min(std::max(tn.fft_batch, 1), count - done);
+    cufftHandle h;
+    int rc = get_plan(c, st, N, 32, inverse, b * N, &h, 2);
+    if (rc) return rc;
+    cufftSetStream(h, st);
+    cufftSetWorkArea(h, c->fft_work);
+    char *ptr = (char *)base + (size_t)(first + done) * slot_bytes;
+    const cufftResult r = inverse ? cufftExecC2R(h, (cufftComplex *)ptr, (cufftReal *)ptr)
+                                  : cufftExecR2C(h, (cufftReal *)ptr, (cufftComplex *)ptr);
+    if (r != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftExec (planes) failed (" + std::to_string((int)r) + ")");
+    done += b;
+  }
+  return BYM_OK;
 }
 
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
                      int first, int count, const Tune &tn) {
   const double esz = prec == 64 ? 8.0 : 4.0;
-  if (use_native_fft(c, N, prec, tn)) {
+  const int kind = fft_kind(c, N, prec, tn);
+  if (kind) {
     ProfScope ps(c, st, inverse ? "fft_native_c2r" : "fft_native_r2c", count * 2.0 * esz * (double)N * N * N);
     cudaError_t e = native_fft_prepare();
-    if (e == cudaSuccess)
-      e = inverse ? native_fft_inverse((float *)base, (long long)(slot_bytes / 4), first, count, st)
-                  : native_fft_forward((float *)base, (long long)(slot_bytes / 4), first, count, st);
+    if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+    const long long sr = (long long)(slot_bytes / 4);
+    if (kind == 1) {
+      if (!inverse) TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn));
+      e = native_fft_xpass(inverse ? 1 : 0, (float *)base, sr, first, count, nullptr, nullptr, nullptr, st);
+      if (e == cudaSuccess && inverse) TRY_RC(fft_planes(c, st, 1, N, base, slot_bytes, first, count, tn));
+    } else {
+      e = inverse ? native_fft_inverse((float *)base, sr, first, count, kind, st)
+                  : native_fft_forward((float *)base, sr, first, count, kind, st);
+    }
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     return BYM_OK;
   }
@@ -293,6 +342,50 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
     done += b;
   }
   return BYM_OK;
+}
+
+// The convolution steps of the midpoint series for fields [first, first + count)
+// (slots hold real fields; D = slot 0 holds delta's half spectrum): forward,
+// times conj(D) scale W^-2, inverse.  With the library's kernels the product
+// sits between the forward and inverse x passes.
+template <typename T, typename T2>
+static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *slots, size_t slot_bytes, int first,
+                           int count, const double *scale, const T *invw, const Tune &tn) {
+  const int kind = fft_kind(c, N, prec, tn);
+  const double esz = sizeof(T), n3 = (double)N * N * N, cplx = 2.0 * esz * N * N * (N / 2 + 1);
+  const long long slot_reals = (long long)(slot_bytes / sizeof(T));
+  if (kind) {
+    cudaError_t e = native_fft_prepare();
+    if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+    if (kind == 1) {
+      {
+        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * n3);
+        TRY_RC(fft_planes(c, st, 0, N, slots, slot_bytes, first, count, tn));
+      }
+      {
+        ProfScope ps(c, st, "fft_native_x_convolve", count * (2.0 * cplx) + cplx);
+        e = native_fft_xpass(2, (float *)slots, slot_reals, first, count, (const float *)slots, scale,
+                             (const float *)invw, st);
+      }
+      if (e == cudaSuccess) {
+        ProfScope ps(c, st, "cufft_planes_c2r", count * 2.0 * esz * n3);
+        TRY_RC(fft_planes(c, st, 1, N, slots, slot_bytes, first, count, tn));
+      }
+    } else {
+      ProfScope ps(c, st, "fft_native_convolve", count * (2.0 * n3 * esz + cplx));
+      e = native_fft_convolve((float *)slots, slot_reals, first, count, (const float *)slots, scale,
+                              (const float *)invw, kind, st);
+    }
+    if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+    return BYM_OK;
+  }
+  TRY_RC(fft_slots(c, st, prec, 0, N, slots, slot_bytes, first, count, tn));
+  {
+    ProfScope ps(c, st, "spec_mul", (2.0 * count + 1.0) * cplx);
+    launch_spec_mul<T, T2>((T2 *)((char *)slots + (size_t)first * slot_bytes), slot_reals / 2, count,
+                           (const T2 *)slots, N, scale, invw, c->nsm * tn.per_sm_spec / 8, st);
+  }
+  return fft_slots(c, st, prec, 1, N, slots, slot_bytes, first, count, tn);
 }
 
 // ---------------------------------------------------------------------------
@@ -399,6 +492,24 @@ static int get_null_kgeom(bym_ctx *c, int N, Geom **out) {
   return BYM_OK;
 }
 
+// Device bytes a request may still take: free memory plus what the stream-ordered
+// pool holds unused, less headroom for one slot (FFT work areas and small buffers).
+static size_t device_available(bym_ctx *c, size_t slot_bytes) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+      free_b += (size_t)(reserved - used);
+  }
+  return free_b > slot_bytes ? free_b - slot_bytes : 0;
+}
+
 // ---------------------------------------------------------------------------
 // one request
 // ---------------------------------------------------------------------------
@@ -420,10 +531,26 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   const size_t slot_bytes = (size_t)slot_reals * sizeof(T);
   const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
 
-  if (c->budget) {
-    const size_t need = footprint_bytes(p, rq.gal->n, rq.ran ? rq.ran->n : 0, want_pk, want_xi,
-                                        rq.gal->on_device && (!rq.ran || rq.ran->on_device));
-    if (need > c->budget) return fail(c, BYM_E_NOMEM, "request exceeds the context's HBM budget");
+  // midpoint g fields streamed in ranges when forced, or when the whole set does not fit
+  const bool cats_dev = rq.gal->on_device && (!rq.ran || rq.ran->on_device);
+  const int64_t ngal = rq.gal->n, nran = rq.ran ? rq.ran->n : 0;
+  int chunk = 0;
+  if (is_midpoint(p)) {
+    if (c->field_chunk > 0) {
+      chunk = std::min(c->field_chunk, nf);
+    } else {
+      const size_t avail = c->budget ? c->budget : device_available(c, slot_bytes);
+      if (footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev) > avail)
+        for (int m = nf - 1; m >= 1 && !chunk; --m)
+          if (footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev, m) <= avail) chunk = m;
+    }
+  }
+  if (c->budget && footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev, chunk) > c->budget)
+    return fail(c, BYM_E_NOMEM, "request exceeds the context's HBM budget");
+  std::shared_ptr<ChunkSet> CK;
+  if (chunk) {
+    CK = get_chunk_kernels(JitKey{p->los, p->ell_max, order_key(p), p->precision}, chunk, jerr);
+    if (!CK) return fail(c, BYM_E_CUDA, jerr);
   }
 
   Geom *kg = nullptr, *rg = nullptr;
@@ -506,8 +633,10 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     CUDA_TRY(cudaMemcpyAsync(scale, sc.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
   }
 
-  // mesh slots: [0] delta, [1, 1+nf) fields, [1+nf, 1+nf+nextra) H or X
-  const int nslots = 1 + nf + nextra;
+  // mesh slots: [0] delta, [1, 1+nf) fields, [1+nf, 1+nf+nextra) H or X;
+  // streamed: [0] delta, [1] a real copy of delta, [2, 2+chunk) one field range, then H
+  const int fbase = chunk ? 2 : 1, nfs = chunk ? chunk : nf, xbase = fbase + nfs;
+  const int nslots = xbase + nextra;
   T *slots = nullptr;
   TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
   auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
@@ -532,8 +661,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   const std::string n_gen = "gen_fields_" + los_name, n_kc = "kcontract_" + los_name, n_xi = "xi_lag_" + los_name;
   const double cplx = 2.0 * esz * nhalf;  // one half-spectrum
 
-  // field generation
-  {
+  // field generation (streamed ranges generate their own fields below)
+  if (!chunk) {
     const long long ncell = (long long)N * N * N;
     ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * n3 * esz);
     CUDA_TRY(cudaMemsetAsync(slot_r(1), 0, (size_t)nf * slot_bytes, st));
@@ -563,24 +692,41 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
-  } else if (is_midpoint(p)) {
-    if (use_native_fft(c, N, p->precision, tn)) {
-      // delta forward, then every g field forward, times conj(delta) s W^-2, and back, in one pass
-      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
-      ProfScope ps(c, st, "fft_native_convolve", nf * (2.0 * n3 * esz + cplx));
-      cudaError_t e = native_fft_prepare();
-      if (e == cudaSuccess)
-        e = native_fft_convolve((float *)slots, slot_reals, 1, nf, (const float *)slot_r(0), scale,
-                                (const float *)invw, st);
-      if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
-    } else {
-      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
+  } else if (chunk) {
+    // delta's spectrum in slot 0, its real copy in slot 1 feeds gen_fields of every range
+    CUDA_TRY(cudaMemcpyAsync(slot_r(1), slot_r(0), slot_bytes, cudaMemcpyDeviceToDevice, st));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
+    for (size_t q = 0; q < CK->ranges.size(); ++q) {
+      const int f0 = CK->ranges[q].first, nq = CK->ranges[q].second - f0;
       {
-        ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
-        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm * tn.per_sm_spec / 8, st);
+        ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * n3 * esz);
+        CUDA_TRY(cudaMemsetAsync(slot_r(2), 0, (size_t)nq * slot_bytes, st));
+        CUDA_TRY(launch(CK->gen[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_gen), 256, 0, st,
+                        (const T *)slot_r(1), slot_r(2), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h,
+                        inv_r0));
       }
-      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
+      TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 2, nq, scale + f0, invw, tn)));
+      if (want_xi) {
+        const int Lc = rg->full ? N : 2 * rg->jm + 1;
+        ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nq * esz);
+        CUDA_TRY(launch(CK->xi[q], grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(2),
+                        slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
+      }
+      if (want_pk) {
+        ProfScope ps(c, st, "mid_combine", ((double)nq + (q ? 2.0 : 1.0) * nlm) * n3 * esz);
+        CUDA_TRY(launch(CK->comb[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_comb), 256, 0, st,
+                        (const T *)slot_r(2), slot_reals, slot_r(xbase), N, tscale));
+      }
     }
+    if (want_pk) {
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, xbase, nlm, tn));
+      ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
+      CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(xbase), cslot, (const T2 *)slot_c(0), N,
+                      (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
+    }
+  } else if (is_midpoint(p)) {
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
+    TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 1, nf, scale, invw, tn)));
     if (want_xi) {
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
       ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nf * esz);
@@ -767,9 +913,16 @@ int bym_pk_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *
 }
 
 int bym_set_fft_backend(bym_ctx *c, int mode) {
-  if (!c || mode < 0 || mode > 2) return BYM_E_INVAL;
+  if (!c || mode < 0 || mode > 4) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
   c->fft_mode = mode;
+  return BYM_OK;
+}
+
+int bym_set_field_chunk(bym_ctx *c, int max_fields) {
+  if (!c || max_fields < 0) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  c->field_chunk = max_fields;
   return BYM_OK;
 }
 
@@ -879,10 +1032,13 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
     if (ms < best_fft) best_fft = ms, best.fft_batch = b, best.native = 0;
   }
   if (native_fft_supported(p->n_mesh, p->precision) && c->fft_mode == 2) {
-    Tune t = best;
-    t.native = 1;
-    if ((rc = timed(t, prof))) return rc;
-    if (fft_ms(prof) < best_fft) best.native = 1;
+    for (int cl : {1, 8, 16}) {  // cuFFT planes + library x pass; library two-pass with 8- / 16-CTA clusters
+      Tune t = best;
+      t.native = cl;
+      if ((rc = timed(t, prof))) return rc;
+      const double ms = fft_ms(prof);
+      if (ms < best_fft) best_fft = ms, best.native = cl;
+    }
   }
   c->tune[key] = best;
   if (cache_path) {
@@ -935,7 +1091,16 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len) {
     lg = e.what();
   }
   std::vector<char> cubin;
-  const bool ok = !src.empty() && compile_cubin(src, cubin, lg);
+  bool ok = !src.empty() && compile_cubin(src, cubin, lg);
+  if (ok && is_midpoint(p)) {   // the streamed-range kernels too (ranges of 16 fields)
+    src.clear();
+    try {
+      src = generate_chunk_source(JitKey{p->los, p->ell_max, order_key(p), p->precision}, 16, nullptr);
+    } catch (const std::exception &e) {
+      lg = e.what();
+    }
+    ok = !src.empty() && compile_cubin(src, cubin, lg);
+  }
   if (log && log_len) {
     const size_t n = std::min(log_len - 1, lg.size());
     memcpy(log, lg.data(), n);

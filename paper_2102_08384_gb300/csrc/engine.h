@@ -42,7 +42,7 @@ struct Tune {
   int per_sm_k = 4;       // kcontract / kcontract_x
   int per_sm_spec = 8;    // spec_mul
   int fft_batch = 8;      // transforms per cuFFT call
-  int native = 0;         // library FFT kernels where they apply (off until the autotuner measures them faster)
+  int native = 0;         // library FFT kernels where they apply: 0 = cuFFT, else CTAs per plane-pass cluster (8, 16)
 };
 
 struct ProfEntry {
@@ -69,7 +69,8 @@ struct bym_ctx {
   size_t fft_work_size = 0;
   std::map<std::string, bym::Geom> kgeo, rgeo;
   bym::Server *server = nullptr;
-  int fft_mode = 2;                                            // 0 cuFFT, 1 library FFT kernels, 2 as tuned
+  int field_chunk = 0;  // midpoint g fields per streamed range: 0 = only when the whole set does not fit
+  int fft_mode = 2;  // 0 cuFFT, 1 library FFT kernels (8-CTA clusters), 2 as tuned, 3 library (16-CTA clusters)
   std::map<std::tuple<int, int, int>, bym::Tune> tune;         // (n_mesh, precision, los) -> launch shapes
   bool prof = false;                                           // kernel tracing (bym_profile_enable)
   std::map<std::string, bym::ProfEntry> prof_tab;
@@ -82,8 +83,10 @@ namespace bym {
 int validate_params(bym_ctx *c, const bym_params *p);
 int validate(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p, const bym_bins *kb,
              const bym_bins *rb);
+// Device bytes one request holds.  chunk > 0: the midpoint g fields are streamed
+// in ranges of at most chunk fields (two delta slots, one range, the H fields).
 size_t footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
-                       bool cats_on_device);
+                       bool cats_on_device, int chunk = 0);
 int run_request(bym_ctx *c, const Request &rq, cudaStream_t st);
 void shutdown_serving(bym_ctx *c);
 

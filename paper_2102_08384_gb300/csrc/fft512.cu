@@ -1,9 +1,11 @@
 // Native FP32 3D FFTs of 512^3 meshes in the library's padded in-place layout.
 //
 // A 3D real transform is done in two passes over HBM instead of three:
-//   plane pass  (one x-plane per 8-CTA thread-block cluster): R2C along z of the
-//               plane's 512 rows, then C2C along y of its 257 kz columns, the
-//               plane held in the cluster's distributed shared memory;
+//   plane pass  (one x-plane per thread-block cluster of CL CTAs): R2C along z of
+//               the plane's 512 rows, then C2C along y of its 257 kz columns;
+//               each CTA owns 512/CL rows and 256/CL columns, and the row
+//               spectra go straight to the owner of each column by stores into
+//               its distributed shared memory;
 //   x pass      (tiles of 16 kz columns of one ky): C2C along x.
 // The inverse runs the x pass then the mirrored plane pass (C2C along y, C2R
 // along z).  The x pass can also apply, between a forward and an inverse
@@ -11,15 +13,22 @@
 // (eq. g-JM-form, eq. 2pcf-yama), so a field goes forward, is multiplied and
 // comes back in one read and one write.
 //
-// 512-point transforms are computed by groups of 64 threads as 8 x 8 x 8
-// (three radix-8 stages in registers, two exchanges through shared memory,
-// twiddles from a shared FP32 table of exp(-2 pi i j / 512) evaluated in FP64
-// on the host).  Real rows are transformed two at a time as the real and
-// imaginary parts of one complex sequence.  Transforms are unnormalised, with
-// the e^{-i k.x} sign for the forward direction, like cuFFT's.
+// Every 512-point transform is computed by a group of 16 threads holding 32
+// values each, as 512 = 32 x 16: a 32-point DFT in registers, twiddles
+// W512^(j k1), one exchange through a padded (bank-conflict-free) shared
+// buffer, and 16-point DFTs in registers.  Thread j of a group starts with
+// x[16 m + j] (m = 0..31) and ends with X[ka + 32 k2] and X[kb + 32 k2]
+// (k2 = 0..15) for the column pair ka = j, kb = 32 - j (kb = 16 for j = 0), so
+// that X[k] and X[512 - k] always sit in the same thread: the packing of two
+// real sequences into one complex transform is undone in registers.  The
+// inverse runs the same steps backwards from that layout.  The kz = 0 and
+// kz = 256 columns of a plane, real sequences along y, share one complex
+// column transform.  Transforms are unnormalised, with the e^{-i k.x} sign for
+// the forward direction, like cuFFT's.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -33,307 +42,495 @@ namespace {
 constexpr int NM = 512;                  // mesh size handled natively
 constexpr int HZ = NM / 2 + 1;           // 257 kz values
 constexpr long long ROWF = NM + 2;       // padded real row (floats)
-constexpr int CL = 8;                    // CTAs per cluster (one x-plane)
-constexpr int ROWS = NM / CL;            // 64 rows per CTA
-constexpr int NG = 16;                   // 64-thread groups per CTA (1024 threads)
-constexpr int COLS = 32;                 // kz columns owned per CTA (the last owns 33)
-constexpr int CPAD = 33;                 // padded column count in the inverse column buffer
+constexpr int CS = 514;                  // column stride (float2) of the column buffer; even for float4 pairs
+constexpr int ES = 17;                   // row stride (float2) of the exchange buffer and twiddle table
+constexpr int EX = 32 * ES;              // exchange buffer of one group (float2)
+constexpr int XS = 545;                  // row stride (float2) of the x-pass tile (>= EX, odd)
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
-__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }   // a * i
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
-// In-register forward 8-point DFT, natural order in and out:
-// decimation in frequency with radix-2 butterflies, then bit reversal.
-__device__ __forceinline__ void dft8(float2 (&v)[8]) {
-  const float r = 0.70710678118654752f;
-  float2 a[8];
-  a[0] = cadd(v[0], v[4]);
-  a[1] = cadd(v[1], v[5]);
-  a[2] = cadd(v[2], v[6]);
-  a[3] = cadd(v[3], v[7]);
-  a[4] = csub(v[0], v[4]);
-  float2 t = csub(v[1], v[5]);
-  a[5] = make_float2((t.x + t.y) * r, (t.y - t.x) * r);      // * W8^1 = (1 - i)/sqrt2
-  a[6] = mul_mi(csub(v[2], v[6]));                            // * W8^2 = -i
-  t = csub(v[3], v[7]);
-  a[7] = make_float2((t.y - t.x) * r, -(t.x + t.y) * r);      // * W8^3 = -(1 + i)/sqrt2
-  float2 b[8];
-  b[0] = cadd(a[0], a[2]);
-  b[1] = cadd(a[1], a[3]);
-  b[2] = csub(a[0], a[2]);
-  b[3] = mul_mi(csub(a[1], a[3]));
-  b[4] = cadd(a[4], a[6]);
-  b[5] = cadd(a[5], a[7]);
-  b[6] = csub(a[4], a[6]);
-  b[7] = mul_mi(csub(a[5], a[7]));
-  v[0] = cadd(b[0], b[1]);
-  v[4] = csub(b[0], b[1]);
-  v[2] = cadd(b[2], b[3]);
-  v[6] = csub(b[2], b[3]);
-  v[1] = cadd(b[4], b[5]);
-  v[5] = csub(b[4], b[5]);
-  v[3] = cadd(b[6], b[7]);
-  v[7] = csub(b[6], b[7]);
-}
-
-// Forward 512-point DFT of the sequence held by a 64-thread group:
-// on entry thread t holds x[64 n1 + t] in v[n1]; on exit thread t = 8 k1 + j1
-// holds X[k1 + 8 j1 + 64 j2] in v[j2].  buf(e) addresses 512 scratch elements
-// of this group; sync() synchronises every thread that shares the scratch.
-template <class Buf, class Sync>
-__device__ __forceinline__ void fft512_group(float2 (&v)[8], int t, const float2 *__restrict__ tw, Buf buf,
-                                             Sync sync) {
-  // n = 64 n1 + n2 (n2 = t), k = k1 + 8 k2: 8-point DFTs over n1, twiddle W512^(n2 k1)
-  dft8(v);
-#pragma unroll
-  for (int k1 = 0; k1 < 8; ++k1) {
-    v[k1] = cmul(v[k1], tw[(t * k1) & 511]);
-    buf(k1 * 64 + t) = v[k1];
+// cos(pi p / 16), p = 0..8
+__device__ __forceinline__ float cos_pi16(int p) {
+  switch (p) {
+    case 0: return 1.0f;
+    case 1: return 0.98078528040323044913f;
+    case 2: return 0.92387953251128675613f;
+    case 3: return 0.83146961230254523708f;
+    case 4: return 0.70710678118654752440f;
+    case 5: return 0.55557023301960222474f;
+    case 6: return 0.38268343236508977173f;
+    case 7: return 0.19509032201612826785f;
+    default: return 0.0f;
   }
-  sync();
-  // 64-point DFTs over n2 = 8 m1 + m2 for each k1, k2 = j1 + 8 j2
-  const int k1 = t >> 3, m2 = t & 7;
+}
+
+// a * exp(-2 pi i p / 32), p = 0..15 (a compile-time constant after unrolling)
+__device__ __forceinline__ float2 w32mul(float2 a, int p) {
+  if (p == 0) return a;
+  if (p == 8) return make_float2(a.y, -a.x);
+  const float c = p < 8 ? cos_pi16(p) : -cos_pi16(16 - p);
+  const float s = p < 8 ? cos_pi16(8 - p) : cos_pi16(p - 8);
+  return make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+template <int BITS>
+__host__ __device__ constexpr int bitrev(int k) {
+  int r = 0;
+  for (int b = 0; b < BITS; ++b) r |= ((k >> b) & 1) << (BITS - 1 - b);
+  return r;
+}
+
+// In-register forward DFT of L = 2^LOG points (L <= 32), natural order in and out:
+// radix-2 decimation in frequency, then the bit-reversal permutation (a renaming).
+template <int L, int LOG>
+__device__ __forceinline__ void dft(float2 (&v)[L]) {
 #pragma unroll
-  for (int m1 = 0; m1 < 8; ++m1) v[m1] = buf(k1 * 64 + 8 * m1 + m2);
-  sync();
-  dft8(v);
+  for (int s = 0; s < LOG; ++s) {
+    const int h = L >> (s + 1);
 #pragma unroll
-  for (int j1 = 0; j1 < 8; ++j1) {
-    v[j1] = cmul(v[j1], tw[(8 * m2 * j1) & 511]);
-    buf(k1 * 64 + 8 * j1 + m2) = v[j1];
+    for (int b = 0; b < L; b += 2 * h) {
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const float2 a = v[b + i], c = v[b + i + h];
+        v[b + i] = cadd(a, c);
+        v[b + i + h] = w32mul(csub(a, c), i * (32 / (2 * h)));
+      }
+    }
   }
-  sync();
-  const int j1 = t & 7;
+  float2 t[L];
 #pragma unroll
-  for (int mm = 0; mm < 8; ++mm) v[mm] = buf(k1 * 64 + 8 * j1 + mm);
-  sync();
-  dft8(v);
+  for (int k = 0; k < L; ++k) t[k] = v[bitrev<LOG>(k)];
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = t[k];
 }
 
-__device__ __forceinline__ int out_index(int t, int j2) { return (t >> 3) + 8 * (t & 7) + 64 * j2; }
-
-__device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ gtw) {
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) tw[i] = gtw[i];
-  __syncthreads();
+template <int L, int LOG>
+__device__ __forceinline__ void idft(float2 (&v)[L]) {  // e^{+i} direction, unnormalised
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = cconj(v[k]);
+  dft<L, LOG>(v);
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = cconj(v[k]);
 }
+
+__device__ __forceinline__ int col_b(int j) { return j ? 32 - j : 16; }
+
+// Forward 512-point DFT by a 16-thread group.  In: v[m] = x[16 m + j].
+// Out: A[k2] = X[ka + 32 k2], B[k2] = X[kb + 32 k2].  TW[k1 * ES + j] = W512^(k1 j);
+// E: this group's exchange buffer (EX float2); gm: this group's lane mask.
+__device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
+                                       const float2 *__restrict__ TW, float2 *E) {
+  dft<32, 5>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], TW[k1 * ES + j]);
+  __syncwarp(gm);
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) E[k1 * ES + j] = v[k1];
+  __syncwarp(gm);
+  const int ka = j, kb = col_b(j);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    A[i] = E[ka * ES + i];
+    B[i] = E[kb * ES + i];
+  }
+  dft<16, 4>(A);
+  dft<16, 4>(B);
+}
+
+// Inverse (e^{+i}, unnormalised) 512-point DFT by a 16-thread group, from the
+// layout fwd512 produces to v[m] = x[16 m + j].
+__device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
+                                       const float2 *__restrict__ TW, float2 *E) {
+  idft<16, 4>(A);
+  idft<16, 4>(B);
+  const int ka = j, kb = col_b(j);
+#pragma unroll
+  for (int n1 = 1; n1 < 16; ++n1) {
+    A[n1] = cmulc(A[n1], TW[ka * ES + n1]);
+    B[n1] = cmulc(B[n1], TW[kb * ES + n1]);
+  }
+  __syncwarp(gm);
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) {
+    E[ka * ES + n1] = A[n1];
+    E[kb * ES + n1] = B[n1];
+  }
+  __syncwarp(gm);
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) v[k1] = E[k1 * ES + j];
+  idft<32, 5>(v);
+}
+
+// Two spectra from the transform of z = a + i b (a, b real sequences):
+// (A_k, B_k) = ((z_k + conj z_-k) / 2, (z_k - conj z_-k) / 2i); zm = conj z_-k.
+__device__ __forceinline__ float4 unpack2(float2 z, float2 zm) {
+  const float2 d = csub(z, zm);
+  return make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y + zm.y), 0.5f * d.y, -0.5f * d.x);
+}
+
+// z = a + i b for complex a, b
+__device__ __forceinline__ float2 pack2(float2 a, float2 b) { return make_float2(a.x - b.y, a.y + b.x); }
+
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <int CL>
+struct PlaneShape {
+  static constexpr int CPR = 256 / CL;          // kz columns per CTA (+ kz = 256 on rank 0)
+  static constexpr int RPR = NM / CL;           // rows per CTA
+  static constexpr int NG = CPR / 2;            // 16-thread groups per CTA
+  static constexpr int NT = NG * 16;            // threads per CTA
+  static constexpr int ITER = 2;                // row pairs and columns per group
+  static constexpr size_t SMEM = sizeof(float2) * (EX + (size_t)(CPR + 1) * CS + (size_t)NG * EX);
+};
 
 // ---------------------------------------------------------------------------
-// plane pass, forward: R2C along z, C2C along y, one x-plane per cluster
-// grid (8, 512, nslots), block 1024, cluster (8, 1, 1)
+// plane pass, forward: R2C along z, C2C along y; one x-plane per cluster
+// grid (CL, 512, nslots), cluster (CL, 1, 1)
 // ---------------------------------------------------------------------------
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024, 1)
+template <int CL>
+__global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
     fft512_plane_fwd(float *__restrict__ data, long long slot_reals, const float2 *__restrict__ gtw) {
+  using S = PlaneShape<CL>;
   extern __shared__ float4 smem4[];
-  float2 *tw = (float2 *)smem4;                // 512
-  float2 *S = tw + 512;                        // [ROWS][HZ] row spectra of this CTA
-  float2 *W = S + ROWS * HZ;                   // [NG][512] scratch, later [512][NG] staging
+  float2 *TW = (float2 *)smem4;                 // [32][ES]
+  float2 *C = TW + EX;                          // [CPR + 1][CS] columns of this CTA, all 512 y
+  float2 *E = C + (S::CPR + 1) * CS;            // [NG][EX]
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
-  const int x = blockIdx.y;
-  float *plane = data + (long long)blockIdx.z * slot_reals + (long long)x * NM * ROWF;
-  const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
-  load_twiddles(tw, gtw);
-  float2 *Wg = W + g * 512;
-  auto bufg = [&](int e) -> float2 & { return Wg[e]; };
-  auto sync = [] { __syncthreads(); };
-  // R2C along z: 32 row pairs, 16 at a time
+  cluster_arrive_relaxed();                     // every CTA of the cluster runs before remote stores
+  float *plane = data + (long long)blockIdx.z * slot_reals + (long long)blockIdx.y * NM * ROWF;
+  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
+  const unsigned gm = 0xFFFFu << (tid & 16);
+  const int ka = j, kb = col_b(j);
+  float2 *Eg = E + g * EX;
+  for (int i = tid; i < EX; i += S::NT) TW[i] = gtw[i];
+  __syncthreads();
+  // R2C along z, two rows at a time; the row spectra go to the owners of their kz
 #pragma unroll 1
-  for (int it = 0; it < ROWS / 2 / NG; ++it) {
-    const int p = it * NG + g;
-    const int ya = r * ROWS + 2 * p;
+  for (int it = 0; it < S::ITER; ++it) {
+    const int ya = r * S::RPR + 2 * (it * S::NG + g);
     const float *ra = plane + (long long)ya * ROWF, *rb = ra + ROWF;
-    float2 v[8];
+    float2 v[32], A[16], B[16];
 #pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = make_float2(ra[64 * n1 + t], rb[64 * n1 + t]);
-    fft512_group(v, t, tw, bufg, sync);
+    for (int m = 0; m < 32; ++m) v[m] = make_float2(ra[16 * m + j], rb[16 * m + j]);
+    fwd512(v, A, B, j, gm, TW, Eg);
+    if (it == 0) cluster_wait();
 #pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) Wg[out_index(t, j2)] = v[j2];
-    __syncthreads();
-    // unpack the two real rows: Xa = (Z_k + conj Z_-k)/2, Xb = (Z_k - conj Z_-k)/(2i)
-    float2 *Sa = S + (2 * p) * HZ, *Sb = Sa + HZ;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const int k = t + 64 * q;
-      if (k > 256) break;
-      const float2 zk = Wg[k], zm = cconj(Wg[(512 - k) & 511]);
-      Sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
-      const float2 d = csub(zk, zm);
-      Sb[k] = make_float2(0.5f * d.y, -0.5f * d.x);
+    for (int k2 = 0; k2 < 8; ++k2) {
+      float4 va = unpack2(A[k2], j ? cconj(B[15 - k2]) : cconj(A[(16 - k2) & 15]));
+      if (j == 0 && k2 == 0) {                  // kz = 0 and kz = 256 (both real) share a column
+        va.y = A[8].x;
+        va.w = A[8].y;
+      }
+      const float4 vb = unpack2(B[k2], j ? cconj(A[15 - k2]) : cconj(B[15 - k2]));
+      const int kza = ka + 32 * k2, kzb = kb + 32 * k2;
+      float2 *Ca = cluster.map_shared_rank(C, kza / S::CPR);
+      float2 *Cb = cluster.map_shared_rank(C, kzb / S::CPR);
+      *(float4 *)(Ca + (kza % S::CPR) * CS + ya) = va;
+      *(float4 *)(Cb + (kzb % S::CPR) * CS + ya) = vb;
     }
-    __syncthreads();
   }
-  cluster.sync();
-  // C2C along y for this CTA's kz columns, 16 at a time (one per group)
-  const int c0 = r * COLS, c1 = (r == CL - 1) ? HZ : c0 + COLS;
-  float2 *plane_c = (float2 *)plane;
+  cluster_arrive();
+  cluster_wait();
+  // C2C along y for this CTA's columns; rank 0's first column holds kz = 0 + i kz = 256
 #pragma unroll 1
-  for (int base = c0; base < c1; base += NG) {
-    const int kz = base + g;
-    float2 v[8];
-    if (kz < c1) {
+  for (int it = 0; it < S::ITER; ++it) {
+    const int kl = it * S::NG + g;
+    float2 *col = C + kl * CS;
+    float2 v[32], A[16], B[16];
 #pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) {
-        const float2 *Sr = cluster.map_shared_rank(S, n1);
-        v[n1] = Sr[t * HZ + kz];
+    for (int m = 0; m < 32; ++m) v[m] = col[16 * m + j];
+    fwd512(v, A, B, j, gm, TW, Eg);
+    if (r == 0 && kl == 0) {
+      float2 *col256 = C + S::CPR * CS;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const float4 a = unpack2(A[k2], j ? cconj(B[15 - k2]) : cconj(A[(16 - k2) & 15]));
+        const float4 b = unpack2(B[k2], j ? cconj(A[15 - k2]) : cconj(B[15 - k2]));
+        col[ka + 32 * k2] = make_float2(a.x, a.y);
+        col256[ka + 32 * k2] = make_float2(a.z, a.w);
+        col[kb + 32 * k2] = make_float2(b.x, b.y);
+        col256[kb + 32 * k2] = make_float2(b.z, b.w);
       }
     } else {
 #pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) v[n1] = make_float2(0.f, 0.f);
+      for (int k2 = 0; k2 < 16; ++k2) {
+        col[ka + 32 * k2] = A[k2];
+        col[kb + 32 * k2] = B[k2];
+      }
     }
-    fft512_group(v, t, tw, bufg, sync);
-    __syncthreads();
-    // stage [ky][g] and write 16 consecutive kz per ky row
-#pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) W[out_index(t, j2) * NG + g] = v[j2];
-    __syncthreads();
-    for (int i = threadIdx.x; i < 512 * NG; i += blockDim.x) {
-      const int ky = i / NG, gg = i % NG;
-      if (base + gg < c1) plane_c[(long long)ky * HZ + base + gg] = W[i];
-    }
-    __syncthreads();
   }
-  cluster.sync();
+  __syncthreads();
+  // coalesced write-out: rows ky, ky + 1 of this CTA's kz range
+  float2 *pc = (float2 *)plane;
+  for (int e = tid; e < 256 * S::CPR; e += S::NT) {
+    const int c = e % S::CPR, ky = 2 * (e / S::CPR);
+    const float4 val = *(const float4 *)(C + c * CS + ky);
+    pc[(long long)ky * HZ + r * S::CPR + c] = make_float2(val.x, val.y);
+    pc[(long long)(ky + 1) * HZ + r * S::CPR + c] = make_float2(val.z, val.w);
+  }
+  if (r == 0)
+    for (int ky = tid; ky < NM; ky += S::NT) pc[(long long)ky * HZ + 256] = C[S::CPR * CS + ky];
 }
 
 // ---------------------------------------------------------------------------
 // plane pass, inverse: C2C along y (inverse), C2R along z
 // ---------------------------------------------------------------------------
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024, 1)
+template <int CL>
+__global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
     fft512_plane_inv(float *__restrict__ data, long long slot_reals, const float2 *__restrict__ gtw) {
+  using S = PlaneShape<CL>;
   extern __shared__ float4 smem4[];
-  float2 *tw = (float2 *)smem4;                // 512
-  float2 *Tc = tw + 512;                       // [512][CPAD] y-transformed columns of this CTA
-  float2 *W = Tc + 512 * CPAD;                 // [512][NG] staging / [NG][512] scratch
+  float2 *TW = (float2 *)smem4;
+  float2 *C = TW + EX;
+  float2 *E = C + (S::CPR + 1) * CS;
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
-  const int x = blockIdx.y;
-  float *plane = data + (long long)blockIdx.z * slot_reals + (long long)x * NM * ROWF;
-  const float2 *plane_c = (const float2 *)plane;
-  const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
-  load_twiddles(tw, gtw);
-  float2 *Wg = W + g * 512;
-  auto bufg = [&](int e) -> float2 & { return Wg[e]; };
-  auto sync = [] { __syncthreads(); };
-  const int c0 = r * COLS, c1 = (r == CL - 1) ? HZ : c0 + COLS;
-#pragma unroll 1
-  for (int base = c0; base < c1; base += NG) {
-    for (int i = threadIdx.x; i < 512 * NG; i += blockDim.x) {
-      const int ky = i / NG, gg = i % NG;
-      W[i] = (base + gg < c1) ? plane_c[(long long)ky * HZ + base + gg] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2 v[8];
-#pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = cconj(W[(64 * n1 + t) * NG + g]);   // inverse via conjugation
-    __syncthreads();
-    fft512_group(v, t, tw, bufg, sync);
-    const int kl = base - c0 + g;
-    if (base + g < c1) {
-#pragma unroll
-      for (int j2 = 0; j2 < 8; ++j2) Tc[out_index(t, j2) * CPAD + kl] = cconj(v[j2]);
-    }
-    __syncthreads();
+  float *plane = data + (long long)blockIdx.z * slot_reals + (long long)blockIdx.y * NM * ROWF;
+  const float2 *pc = (const float2 *)plane;
+  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
+  const unsigned gm = 0xFFFFu << (tid & 16);
+  const int ka = j, kb = col_b(j);
+  float2 *Eg = E + g * EX;
+  for (int i = tid; i < EX; i += S::NT) TW[i] = gtw[i];
+  // coalesced read of this CTA's kz range
+  for (int e = tid; e < 256 * S::CPR; e += S::NT) {
+    const int c = e % S::CPR, ky = 2 * (e / S::CPR);
+    const float2 a = pc[(long long)ky * HZ + r * S::CPR + c];
+    const float2 b = pc[(long long)(ky + 1) * HZ + r * S::CPR + c];
+    *(float4 *)(C + c * CS + ky) = make_float4(a.x, a.y, b.x, b.y);
   }
-  cluster.sync();
-  // C2R along z: two rows at a time as Z = Xa + i Xb, Hermitian-extended to 512
+  if (r == 0)
+    for (int ky = tid; ky < NM; ky += S::NT) C[S::CPR * CS + ky] = pc[(long long)ky * HZ + 256];
+  __syncthreads();
+  // inverse C2C along y; rank 0 transforms kz = 0 + i kz = 256 (both real along y after it)
 #pragma unroll 1
-  for (int it = 0; it < ROWS / 2 / NG; ++it) {
-    const int p = it * NG + g;
-    const int ya = r * ROWS + 2 * p, yb = ya + 1;
-    float2 v[8];
+  for (int it = 0; it < S::ITER; ++it) {
+    const int kl = it * S::NG + g;
+    float2 *col = C + kl * CS;
+    float2 v[32], A[16], B[16];
 #pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) {
-      const int k = 64 * n1 + t;
-      const int kk = k <= 256 ? k : 512 - k;
-      const int own = kk / COLS < CL ? kk / COLS : CL - 1;
-      const float2 *To = cluster.map_shared_rank(Tc, min(own, CL - 1));
-      const int kl = kk - own * COLS;
-      float2 xa = To[ya * CPAD + kl], xb = To[yb * CPAD + kl];
-      if (k > 256) {
-        xa = cconj(xa);
-        xb = cconj(xb);
+    for (int k2 = 0; k2 < 16; ++k2) {
+      A[k2] = col[ka + 32 * k2];
+      B[k2] = col[kb + 32 * k2];
+    }
+    if (r == 0 && kl == 0) {
+      const float2 *col256 = C + S::CPR * CS;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        A[k2] = pack2(A[k2], col256[ka + 32 * k2]);
+        B[k2] = pack2(B[k2], col256[kb + 32 * k2]);
       }
-      v[n1] = cconj(cadd(xa, mul_i(xb)));      // inverse via conjugation
     }
-    fft512_group(v, t, tw, bufg, sync);
-    float *ra = plane + (long long)ya * ROWF, *rb = plane + (long long)yb * ROWF;
+    inv512(A, B, v, j, gm, TW, Eg);
 #pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) {
-      const int k = out_index(t, j2);
-      const float2 z = cconj(v[j2]);
-      ra[k] = z.x;
-      rb[k] = z.y;
-    }
-    __syncthreads();
+    for (int m = 0; m < 32; ++m) col[16 * m + j] = v[m];
   }
-  cluster.sync();
+  cluster_arrive();
+  cluster_wait();
+  // C2R along z, two rows at a time as z = a + i b; the half spectra come from the column owners
+#pragma unroll 1
+  for (int it = 0; it < S::ITER; ++it) {
+    const int ya = r * S::RPR + 2 * (it * S::NG + g);
+    float4 ca[8], cb[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const int kza = ka + 32 * k2, kzb = kb + 32 * k2;
+      const float2 *Ca = cluster.map_shared_rank(C, kza / S::CPR);
+      const float2 *Cb = cluster.map_shared_rank(C, kzb / S::CPR);
+      ca[k2] = *(const float4 *)(Ca + (kza % S::CPR) * CS + ya);
+      cb[k2] = *(const float4 *)(Cb + (kzb % S::CPR) * CS + ya);
+    }
+    float2 A[16], B[16], v[32];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      A[k2] = pack2(make_float2(ca[k2].x, ca[k2].y), make_float2(ca[k2].z, ca[k2].w));
+      B[k2] = pack2(make_float2(cb[k2].x, cb[k2].y), make_float2(cb[k2].z, cb[k2].w));
+    }
+#pragma unroll
+    for (int k2 = 8; k2 < 16; ++k2) {           // kz > 256 from the conjugate of 512 - kz
+      const float4 sa = j ? cb[15 - k2] : ca[(16 - k2) & 7];
+      const float4 sb = j ? ca[15 - k2] : cb[15 - k2];
+      A[k2] = pack2(make_float2(sa.x, -sa.y), make_float2(sa.z, -sa.w));
+      B[k2] = pack2(make_float2(sb.x, -sb.y), make_float2(sb.z, -sb.w));
+    }
+    if (j == 0) {                               // rank 0's packed column: (kz = 0, kz = 256) per row
+      A[0] = make_float2(ca[0].x, ca[0].z);
+      A[8] = make_float2(ca[0].y, ca[0].w);
+    }
+    inv512(A, B, v, j, gm, TW, Eg);
+    float *ra = plane + (long long)ya * ROWF, *rb = ra + ROWF;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+      ra[16 * m + j] = v[m].x;
+      rb[16 * m + j] = v[m].y;
+    }
+  }
+  cluster_arrive();                             // no CTA leaves while others read its columns
+  cluster_wait();
 }
 
 // ---------------------------------------------------------------------------
 // x pass: C2C along x for tiles of 16 kz columns of one ky
-// mode 0 forward, 1 inverse, 2 forward -> * conj(D) s_f W^-2 -> inverse
-// grid (17, 512, nslots), block 1024 (g = tid % 16 the column, t = tid / 16)
+// mode 0 forward, 1 inverse, 2 forward -> * conj(D) s W^-2 -> inverse
+// Persistent: one CTA per SM walks the tiles; each tile is copied into shared
+// memory with cp.async while the previous one is transformed (mode 2 also
+// prefetches the matching D tile), so loads overlap the FFT work.
+// block 256 (16 groups, one column each)
 // ---------------------------------------------------------------------------
+constexpr int XT = 256;
+constexpr int KZT = (HZ + 15) / 16;        // 17 kz tiles per ky
+constexpr size_t kXSmem01 = sizeof(float2) * (EX + 2 * 16 * XS);
+constexpr size_t kXSmem2 = sizeof(float2) * (EX + 3 * 16 * XS) + sizeof(float) * NM;
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+struct XTile {
+  long long off;   // (ky, kz0) offset within a slot, complex units
+  int slot, ky, kz0, nvalid;
+};
+
+__device__ __forceinline__ XTile x_tile(long long t) {
+  XTile r;
+  const int kzt = (int)(t % KZT);
+  const long long u = t / KZT;
+  r.ky = (int)(u % NM);
+  r.slot = (int)(u / NM);
+  r.kz0 = kzt * 16;
+  r.nvalid = HZ - r.kz0 < 16 ? HZ - r.kz0 : 16;
+  r.off = (long long)r.ky * HZ + r.kz0;
+  return r;
+}
+
+// asynchronous copy of one tile: T[c][x] = src[x][c], c < nvalid; one commit group
+__device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid) {
+  const long long xs = (long long)NM * HZ;
+  for (int e = threadIdx.x; e < NM * 16; e += XT) {
+    const int x = e >> 4, c = e & 15;
+    if (c < nvalid) cp_async8(T + c * XS + x, src + x * xs + c);
+  }
+  cp_async_commit();
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(1024, 1)
-    fft512_x(float2 *__restrict__ data, long long slot_cplx, const float2 *__restrict__ gtw,
+__global__ void __launch_bounds__(XT, 1)
+    fft512_x(float2 *__restrict__ data, long long slot_cplx, long long ntiles, const float2 *__restrict__ gtw,
              const float2 *__restrict__ D, const double *__restrict__ scale, const float *__restrict__ invw) {
   extern __shared__ float4 smem4[];
-  float2 *tw = (float2 *)smem4;   // 512
-  float2 *W = tw + 512;           // [512][16]
-  const int g = threadIdx.x & 15, t = threadIdx.x >> 4;
-  const int kz = blockIdx.x * 16 + g, ky = blockIdx.y;
-  const bool valid = kz < HZ;
-  float2 *col = data + (long long)blockIdx.z * slot_cplx + (long long)ky * HZ + kz;
-  const long long xs = (long long)NM * HZ;    // stride between consecutive x
-  load_twiddles(tw, gtw);
-  auto buf = [&](int e) -> float2 & { return W[e * 16 + g]; };
-  auto sync = [] { __syncthreads(); };
-  float2 v[8];
+  float2 *TW = (float2 *)smem4;   // [32][ES]
+  float2 *buf0 = TW + EX;         // tile buffers [16][XS]: column c, x = 0..511; double as exchange buffers
+  float2 *buf1 = buf0 + 16 * XS;
+  float2 *buf2 = buf1 + 16 * XS;  // mode 2: buf1 holds D, data alternates between buf0 and buf2
+  float *W1 = (float *)(buf2 + 16 * XS);   // mode 2: per-axis 1/W (compensation), when given
+  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
+  const unsigned gm = 0xFFFFu << (tid & 16);
+  const int ka = j, kb = col_b(j);
+  const long long xs = (long long)NM * HZ;
+  long long t = blockIdx.x;
+  XTile cur = x_tile(t);
+  x_tile_issue(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid);
+  if (MODE == 2) x_tile_issue(buf1, D + cur.off, cur.nvalid);
+  for (int i = tid; i < EX; i += XT) TW[i] = gtw[i];
+  if (MODE == 2 && invw)
+    for (int i = tid; i < NM; i += XT) W1[i] = invw[i];
+  float2 *A = buf0;
+  for (; t < ntiles; t += gridDim.x) {
+    if (MODE == 2)
+      cp_async_wait<1>();         // this tile's data (its D may still be in flight)
+    else
+      cp_async_wait<0>();
+    __syncthreads();
+    const long long tn = t + gridDim.x;
+    const bool has_next = tn < ntiles;
+    const XTile nxt = x_tile(has_next ? tn : t);
+    float2 *Anext = MODE == 2 ? (A == buf0 ? buf2 : buf0) : (A == buf0 ? buf1 : buf0);
+    if (has_next)
+      x_tile_issue(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid);
+    else
+      cp_async_commit();
+    float2 *col = A + g * XS;
+    float2 v[32], As[16], Bs[16];
+    if (MODE == 1) {
 #pragma unroll
-  for (int n1 = 0; n1 < 8; ++n1) {
-    const float2 a = valid ? col[(64 * n1 + t) * xs] : make_float2(0.f, 0.f);
-    v[n1] = MODE == 1 ? cconj(a) : a;
-  }
-  fft512_group(v, t, tw, buf, sync);
-  if (MODE == 2) {
-    const float s = (float)scale[blockIdx.z];
-    float cyz = 1.f;
-    if (invw) cyz = invw[ky] * invw[valid ? kz : 0];
-#pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) {
-      const int kx = out_index(t, j2);
-      float2 d = valid ? D[(long long)kx * xs + (long long)ky * HZ + kz] : make_float2(0.f, 0.f);
-      float c = s;
-      if (invw) {
-        const float cc = invw[kx] * cyz;
-        c *= cc * cc;
+      for (int k2 = 0; k2 < 16; ++k2) {
+        As[k2] = col[ka + 32 * k2];
+        Bs[k2] = col[kb + 32 * k2];
       }
-      const float2 p = cmul(v[j2], cconj(d));
-      v[j2] = make_float2(p.x * c, p.y * c);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 32; ++m) v[m] = col[16 * m + j];
+      fwd512(v, As, Bs, j, gm, TW, col);
+    }
+    if (MODE == 2) {
+      cp_async_wait<1>();         // this tile's D
+      __syncthreads();
+      const float2 *dcol = buf1 + g * XS;
+      const float s = (float)scale[cur.slot];
+      const float cyz = invw ? W1[cur.ky] * W1[cur.kz0 + (g < cur.nvalid ? g : 0)] : 1.f;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int kxa = ka + 32 * k2, kxb = kb + 32 * k2;
+        float ca = s, cb = s;
+        if (invw) {
+          const float wa = W1[kxa] * cyz, wb = W1[kxb] * cyz;
+          ca *= wa * wa;
+          cb *= wb * wb;
+        }
+        As[k2] = cscale(cmulc(As[k2], dcol[kxa]), ca);
+        Bs[k2] = cscale(cmulc(Bs[k2], dcol[kxb]), cb);
+      }
+      __syncthreads();            // every group is done with D: prefetch the next one
+      if (has_next)
+        x_tile_issue(buf1, D + nxt.off, nxt.nvalid);
+      else
+        cp_async_commit();
+    }
+    if (MODE == 0) {
+      __syncwarp(gm);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        col[ka + 32 * k2] = As[k2];
+        col[kb + 32 * k2] = Bs[k2];
+      }
+    } else {
+      inv512(As, Bs, v, j, gm, TW, col);
+      __syncwarp(gm);
+#pragma unroll
+      for (int m = 0; m < 32; ++m) col[16 * m + j] = v[m];
     }
     __syncthreads();
-#pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) W[out_index(t, j2) * 16 + g] = v[j2];
-    __syncthreads();
-#pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = cconj(W[(64 * n1 + t) * 16 + g]);
-    __syncthreads();
-    fft512_group(v, t, tw, buf, sync);
-  }
-  if (valid) {
-#pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) {
-      const float2 o = (MODE == 0) ? v[j2] : cconj(v[j2]);
-      col[(long long)out_index(t, j2) * xs] = o;
+    float2 *base = data + (long long)cur.slot * slot_cplx + cur.off;
+    for (int e = tid; e < NM * 16; e += XT) {
+      const int x = e >> 4, c = e & 15;
+      if (c < cur.nvalid) base[x * xs + c] = A[c * XS + x];
     }
+    cur = nxt;
+    A = Anext;
   }
+  cp_async_wait<0>();
 }
 
 float2 *g_twiddles[64] = {nullptr};
@@ -342,22 +539,90 @@ std::mutex g_tw_mu;
 const float2 *twiddles(int dev) {
   std::lock_guard<std::mutex> lock(g_tw_mu);
   if (!g_twiddles[dev]) {
-    float2 host[512];
-    for (int j = 0; j < 512; ++j) {
-      const double a = -2.0 * M_PI * j / 512.0;
-      host[j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
+    float2 host[EX];
+    for (int k1 = 0; k1 < 32; ++k1)
+      for (int j = 0; j < ES; ++j) {
+        const double a = -2.0 * M_PI * (double)(k1 * j) / 512.0;
+        host[k1 * ES + j] = j < 16 ? make_float2((float)std::cos(a), (float)std::sin(a)) : make_float2(0.f, 0.f);
+      }
     float2 *d = nullptr;
     if (cudaMalloc(&d, sizeof host) != cudaSuccess) return nullptr;
-    cudaMemcpy(d, host, sizeof host, cudaMemcpyHostToDevice);
+    if (cudaMemcpy(d, host, sizeof host, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(d);
+      return nullptr;
+    }
     g_twiddles[dev] = d;
   }
   return g_twiddles[dev];
 }
 
-constexpr size_t kPlaneFwdSmem = sizeof(float2) * (512 + ROWS * HZ + NG * 512);
-constexpr size_t kPlaneInvSmem = sizeof(float2) * (512 + 512 * CPAD + NG * 512);
-constexpr size_t kXSmem = sizeof(float2) * (512 + 512 * 16);
+template <int CL>
+cudaError_t plane_attrs() {
+  cudaError_t e;
+  const int smem = (int)PlaneShape<CL>::SMEM;
+  if ((e = cudaFuncSetAttribute(fft512_plane_fwd<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(fft512_plane_inv<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+      cudaSuccess)
+    return e;
+  if (CL > 8) {
+    if ((e = cudaFuncSetAttribute(fft512_plane_fwd<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(fft512_plane_inv<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+        cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+template <int CL>
+cudaError_t launch_plane(bool inverse, float *b, long long slot_reals, int n, const float2 *tw, cudaStream_t st) {
+  using S = PlaneShape<CL>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, NM, n);
+  cfg.blockDim = dim3(S::NT, 1, 1);
+  cfg.dynamicSmemBytes = S::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return inverse ? cudaLaunchKernelEx(&cfg, fft512_plane_inv<CL>, b, slot_reals, tw)
+                 : cudaLaunchKernelEx(&cfg, fft512_plane_fwd<CL>, b, slot_reals, tw);
+}
+
+cudaError_t plane(int cluster, bool inverse, float *b, long long slot_reals, int n, const float2 *tw,
+                  cudaStream_t st) {
+  return cluster == 16 ? launch_plane<16>(inverse, b, slot_reals, n, tw, st)
+                       : launch_plane<8>(inverse, b, slot_reals, n, tw, st);
+}
+
+int sm_count(int dev) {
+  static int n[64] = {0};
+  if (!n[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    n[dev] = v;
+  }
+  return n[dev];
+}
+
+template <int MODE>
+cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const float *D, const double *scale,
+                  const float *invw, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const long long ntiles = (long long)KZT * NM * n;
+  const long long grid = std::min<long long>(ntiles, sm_count(dev));
+  fft512_x<MODE><<<(unsigned)grid, XT, MODE == 2 ? kXSmem2 : kXSmem01, st>>>(
+      (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -367,23 +632,20 @@ cudaError_t native_fft_prepare() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!twiddles(dev)) return cudaErrorMemoryAllocation;
   static bool attrs[64] = {false};
   std::lock_guard<std::mutex> lock(g_tw_mu);
   if (!attrs[dev]) {
-    if ((e = cudaFuncSetAttribute(fft512_plane_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kPlaneFwdSmem)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(fft512_plane_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kPlaneInvSmem)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem)) !=
+    if ((e = plane_attrs<8>()) != cudaSuccess) return e;
+    if ((e = plane_attrs<16>()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(fft512_x<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem01)) !=
         cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem)) !=
+    if ((e = cudaFuncSetAttribute(fft512_x<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem01)) !=
         cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem)) !=
+    if ((e = cudaFuncSetAttribute(fft512_x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem2)) !=
         cudaSuccess)
       return e;
     attrs[dev] = true;
@@ -391,54 +653,78 @@ cudaError_t native_fft_prepare() {
   return cudaSuccess;
 }
 
-cudaError_t native_fft_forward(float *slots, long long slot_reals, int first, int count, cudaStream_t st) {
+cudaError_t native_fft_forward(float *slots, long long slot_reals, int first, int count, int cluster,
+                               cudaStream_t st) {
+  if (cluster != 8 && cluster != 16) return cudaErrorInvalidValue;
   if (count <= 0) return cudaSuccess;
   int dev = 0;
   cudaGetDevice(&dev);
   const float2 *tw = twiddles(dev);
   float *base = slots + (long long)first * slot_reals;
-  for (int done = 0; done < count; done += 65535) {
+  cudaError_t e = cudaSuccess;
+  for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
     const int n = count - done < 65535 ? count - done : 65535;
     float *b = base + (long long)done * slot_reals;
-    fft512_plane_fwd<<<dim3(CL, NM, n), 1024, kPlaneFwdSmem, st>>>(b, slot_reals, tw);
-    fft512_x<0><<<dim3((HZ + 15) / 16, NM, n), 1024, kXSmem, st>>>((float2 *)b, slot_reals / 2, tw, nullptr,
-                                                                   nullptr, nullptr);
+    if ((e = plane(cluster, false, b, slot_reals, n, tw, st)) == cudaSuccess)
+      e = xpass<0>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st);
   }
-  return cudaGetLastError();
+  return e;
 }
 
-cudaError_t native_fft_inverse(float *slots, long long slot_reals, int first, int count, cudaStream_t st) {
+cudaError_t native_fft_inverse(float *slots, long long slot_reals, int first, int count, int cluster,
+                               cudaStream_t st) {
+  if (cluster != 8 && cluster != 16) return cudaErrorInvalidValue;
   if (count <= 0) return cudaSuccess;
   int dev = 0;
   cudaGetDevice(&dev);
   const float2 *tw = twiddles(dev);
   float *base = slots + (long long)first * slot_reals;
-  for (int done = 0; done < count; done += 65535) {
+  cudaError_t e = cudaSuccess;
+  for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
     const int n = count - done < 65535 ? count - done : 65535;
     float *b = base + (long long)done * slot_reals;
-    fft512_x<1><<<dim3((HZ + 15) / 16, NM, n), 1024, kXSmem, st>>>((float2 *)b, slot_reals / 2, tw, nullptr,
-                                                                   nullptr, nullptr);
-    fft512_plane_inv<<<dim3(CL, NM, n), 1024, kPlaneInvSmem, st>>>(b, slot_reals, tw);
+    if ((e = xpass<1>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)) == cudaSuccess)
+      e = plane(cluster, true, b, slot_reals, n, tw, st);
   }
-  return cudaGetLastError();
+  return e;
+}
+
+cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int first, int count, const float *D,
+                             const double *scale, const float *invw, cudaStream_t st) {
+  if (mode < 0 || mode > 2 || (mode == 2 && (!D || !scale))) return cudaErrorInvalidValue;
+  if (count <= 0) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const float2 *tw = twiddles(dev);
+  float *base = slots + (long long)first * slot_reals;
+  cudaError_t e = cudaSuccess;
+  for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
+    const int n = count - done < 65535 ? count - done : 65535;
+    float *b = base + (long long)done * slot_reals;
+    e = mode == 0   ? xpass<0>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)
+        : mode == 1 ? xpass<1>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)
+                    : xpass<2>(b, slot_reals, n, tw, D, scale + done, invw, st);
+  }
+  return e;
 }
 
 cudaError_t native_fft_convolve(float *slots, long long slot_reals, int first, int count, const float *D,
-                                const double *scale, const float *invw, cudaStream_t st) {
+                                const double *scale, const float *invw, int cluster, cudaStream_t st) {
+  if (cluster != 8 && cluster != 16) return cudaErrorInvalidValue;
   if (count <= 0) return cudaSuccess;
   int dev = 0;
   cudaGetDevice(&dev);
   const float2 *tw = twiddles(dev);
   float *base = slots + (long long)first * slot_reals;
-  for (int done = 0; done < count; done += 65535) {
+  cudaError_t e = cudaSuccess;
+  for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
     const int n = count - done < 65535 ? count - done : 65535;
     float *b = base + (long long)done * slot_reals;
-    fft512_plane_fwd<<<dim3(CL, NM, n), 1024, kPlaneFwdSmem, st>>>(b, slot_reals, tw);
-    fft512_x<2><<<dim3((HZ + 15) / 16, NM, n), 1024, kXSmem, st>>>((float2 *)b, slot_reals / 2, tw,
-                                                                   (const float2 *)D, scale + done, invw);
-    fft512_plane_inv<<<dim3(CL, NM, n), 1024, kPlaneInvSmem, st>>>(b, slot_reals, tw);
+    if ((e = plane(cluster, false, b, slot_reals, n, tw, st)) != cudaSuccess) break;
+    if ((e = xpass<2>(b, slot_reals, n, tw, D, scale + done, invw, st)) != cudaSuccess) break;
+    e = plane(cluster, true, b, slot_reals, n, tw, st);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace bym

@@ -6,12 +6,20 @@ namespace bym {
 
 bool native_fft_supported(int n_mesh, int precision);
 cudaError_t native_fft_prepare();  // per device: twiddle table, shared-memory attributes
-// forward R2C / inverse C2R (unnormalised) of slots [first, first + count)
-cudaError_t native_fft_forward(float *slots, long long slot_reals, int first, int count, cudaStream_t st);
-cudaError_t native_fft_inverse(float *slots, long long slot_reals, int first, int count, cudaStream_t st);
+// forward R2C / inverse C2R (unnormalised) of slots [first, first + count); cluster = CTAs per
+// thread-block cluster in the plane pass, 8 or 16 (16 is a non-portable cluster size)
+cudaError_t native_fft_forward(float *slots, long long slot_reals, int first, int count, int cluster,
+                               cudaStream_t st);
+cudaError_t native_fft_inverse(float *slots, long long slot_reals, int first, int count, int cluster,
+                               cudaStream_t st);
 // for each slot f: real field -> forward -> * conj(D) scale[f] W(k)^-2 -> inverse, in place
 // (D: the half-spectrum of delta; invw: per-axis 1/W or null)
 cudaError_t native_fft_convolve(float *slots, long long slot_reals, int first, int count, const float *D,
-                                const double *scale, const float *invw, cudaStream_t st);
+                                const double *scale, const float *invw, int cluster, cudaStream_t st);
+
+// the x pass alone (C2C along x of half spectra) for slots [first, first + count):
+// mode 0 forward, 1 inverse, 2 forward -> * conj(D) scale[f] W(k)^-2 -> inverse
+cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int first, int count, const float *D,
+                             const double *scale, const float *invw, cudaStream_t st);
 
 }  // namespace bym

@@ -152,6 +152,176 @@ void emit_bin_loop_head(std::ostream &o, const std::string &count_expr) {
   o << "    const long long m = base + lane;\n";
 }
 
+// gen_fields kernel for fields [f0, f1) of the list, written to slots 0 .. f1 - f0 of out.
+void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldInfo> &list, int f0, int f1) {
+  int Jmax = 0, amax = 0;
+  for (int i = f0; i < f1; ++i) {
+    Jmax = std::max(Jmax, list[i].J);
+    amax = std::max(amax, list[i].alpha);
+  }
+  o << "extern \"C\" __global__ void __launch_bounds__(256, 2) " << name << "(const real* __restrict__ delta,"
+       " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
+       " double inv_r0) {\n";
+  o << "  const long long ncell = (long long)N * N * N;\n";
+  o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
+       " c += (long long)gridDim.x * blockDim.x) {\n";
+  o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
+  o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
+  o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "    const real d = delta[off];\n";
+  o << "    if (d == (real)0) continue;   // field slots are zero-filled before the launch\n";
+  o << "    const double x = lo0 + ix * h, y = lo1 + iy * h, z = lo2 + iz * h;\n";
+  o << "    const double r2 = x * x + y * y + z * z;\n";
+  o << "    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;\n";
+  o << "    const double ux = x * ir, uy = y * ir, uz = z * ir, zm = r2 > 0.0 ? 1.0 : 0.0;\n";
+  o << "    const double rad0 = (double)d;\n";
+  if (amax > 0) o << "    const double q = r2 > 0.0 ? 1.0 / (2.0 * sqrt(r2) * inv_r0) : 0.0;\n";
+  for (int a = 1; a <= amax; ++a) o << "    const double rad" << a << " = rad" << a - 1 << " * q;\n";
+  for (int a = 0; a <= amax; ++a) o << "    const real rr" << a << " = (real)rad" << a << ";\n";
+  emit_ylm(o, Jmax, false, "y", "ux", "uy", "uz", "zm");
+  for (int i = f0; i < f1; ++i)
+    o << "    out[" << i - f0 << "LL * slot + off] = (real)y" << ylm_index(list[i].J, list[i].nu) << " * rr"
+      << list[i].alpha << ";\n";
+  o << "  }\n}\n";
+}
+
+// mid_combine for the g fields [f0, f1) (read from slots 0 .. f1 - f0 of G): H = (or +=) the
+// terms of H_{l mu} = sum phi Y (|Delta|/r0)^alpha g that involve those fields.
+void emit_mid_combine(std::ostream &o, const char *name, const JitKey &key, const std::vector<MidTerm> &terms,
+                      int f0, int f1, bool accumulate) {
+  const bool f32 = key.prec == 32;
+  const int n_lm = n_even_lm(key.ell_max);
+  o << "extern \"C\" __global__ void __launch_bounds__(256) " << name << "(const real* __restrict__ G,"
+       " long long slot, real* __restrict__ Hout, int N, double tscale) {\n";
+  o << "  const long long ncell = (long long)N * N * N;\n";
+  o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
+       " c += (long long)gridDim.x * blockDim.x) {\n";
+  o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
+  o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
+  o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "    const int jx = bym_lab(ix, N), jy = bym_lab(iy, N), jz = bym_lab(iz, N);\n";
+  o << "    const int j2 = jx * jx + jy * jy + jz * jz;\n";
+  o << "    const real rr = bym_sqrt((real)j2);\n";
+  o << "    const real ir = j2 > 0 ? (real)1 / rr : (real)0;\n";
+  o << "    const real ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = j2 > 0 ? (real)1 : (real)0;\n";
+  o << "    const real t1 = (real)(rr * tscale);\n";
+  for (int a = 2; a <= key.K; ++a) o << "    const real t" << a << " = t" << a - 1 << " * t1;\n";
+  {
+    std::ostringstream yy;
+    emit_ylm(yy, key.K, f32, "yd", "ux", "uy", "uz", "zm");
+    std::istringstream is(yy.str());
+    std::string line;
+    while (std::getline(is, line)) o << "  " << line << "\n";
+  }
+  std::set<int> touched;
+  for (auto &tm : terms)
+    if (tm.g >= f0 && tm.g < f1) touched.insert(tm.lm);
+  for (int i = 0; i < n_lm; ++i) o << "    real H" << i << " = (real)0;\n";
+  for (int a = 0; a <= key.K; ++a) {
+    std::set<int> gs;
+    std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> groups;  // (lm, y) -> (g, c)
+    for (auto &tm : terms)
+      if (tm.alpha == a && tm.g >= f0 && tm.g < f1) {
+        gs.insert(tm.g);
+        groups[{tm.lm, tm.y}].push_back({tm.g, tm.c});
+      }
+    if (groups.empty()) continue;
+    o << "    {\n";
+    for (int g : gs) o << "      const real g" << g << " = G[" << g - f0 << "LL * slot + off];\n";
+    for (auto &kv : groups) {
+      o << "      { real S = (real)0;";
+      for (auto &gc : kv.second) o << " S += " << lit(gc.second, f32) << " * g" << gc.first << ";";
+      o << " H" << kv.first.first << " += yd" << kv.first.second;
+      if (a > 0) o << " * t" << a;
+      o << " * S; }\n";
+    }
+    o << "    }\n";
+  }
+  for (int i = 0; i < n_lm; ++i) {
+    if (!accumulate)
+      o << "    Hout[" << i << "LL * slot + off] = H" << i << ";\n";
+    else if (touched.count(i))
+      o << "    Hout[" << i << "LL * slot + off] += H" << i << ";\n";
+  }
+  o << "  }\n}\n";
+}
+
+// xi_lag: the configuration-space contraction over the lag cube.  For the
+// midpoint forms only the g fields [f0, f1) enter (read from slots 0 .. f1 - f0
+// of Z), so a field range adds its share of the shell sums.  Returns the
+// harmonic degree needed on the lag grid.
+int emit_xi_lag(std::ostream &o, const char *name, const JitKey &key, int f0, int f1) {
+  const int L = key.ell_max, NL = L / 2 + 1;
+  const bool midpoint = key.los == 1 || key.los == 3, even = key.los == 3;
+  int jlag = L;
+  std::vector<XiTerm> xterms;
+  if (midpoint) {
+    xterms = midpoint_xi_terms(key.ell_max, key.K, even);
+    for (auto &x : xterms) jlag = std::max(jlag, x.J);
+  }
+  o << "extern \"C\" __global__ void __launch_bounds__(256) " << name << "(const real* __restrict__ Z, long long slot,"
+       " int N, int jm, int full, const int* __restrict__ lut, int nbins, double* __restrict__ gsum,"
+       " double zscale, double tscale) {\n";
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n";
+  o << "  const int Lc = full ? N : 2 * jm + 1;\n";
+  emit_bin_loop_head(o, "(long long)Lc * Lc * Lc");
+  o << "    int bin = -1; double v[" << NL << "] = {";
+  for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
+  o << "};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int a = (int)(m % Lc); const long long t = m / Lc;\n";
+  o << "      const int b = (int)(t % Lc); const int c = (int)(t / Lc);\n";
+  o << "      const int jx = full ? bym_lab(c, N) : c - jm, jy = full ? bym_lab(b, N) : b - jm,"
+       " jz = full ? bym_lab(a, N) : a - jm;\n";
+  o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
+  o << "      bin = lut[j2];\n";
+  o << "      if (bin >= 0) {\n";
+  o << "        const int ix = jx < 0 ? jx + N : jx, iy = jy < 0 ? jy + N : jy, iz = jz < 0 ? jz + N : jz;\n";
+  o << "        const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "        const double rr = sqrt((double)j2); const double ir = 1.0 / rr;\n";
+  o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
+  {
+    std::ostringstream yy;
+    emit_ylm(yy, jlag, false, "yl", "ux", "uy", "uz", "zm");
+    std::istringstream is(yy.str());
+    std::string line;
+    while (std::getline(is, line)) o << "      " << line << "\n";
+  }
+  if (midpoint) {
+    int amax = 0;
+    for (auto &x : xterms) amax = std::max(amax, x.alpha);
+    o << "        const double t1 = rr * tscale;\n";
+    for (int a2 = 2; a2 <= amax; ++a2) o << "        const double t" << a2 << " = t" << a2 - 1 << " * t1;\n";
+    for (int l = 0; l <= L; l += 2) {
+      o << "        { double T = 0.0;\n";
+      for (auto &x : xterms) {
+        if (x.l != l) continue;
+        std::ostringstream sum;
+        for (int nu = -x.J; nu <= x.J; ++nu) {
+          const int g = midpoint_gfield_index(key.ell_max, x.alpha, x.J, nu, even);
+          if (g >= f0 && g < f1)
+            sum << " S += yl" << ylm_index(x.J, nu) << " * (double)Z[" << g - f0 << "LL * slot + off];";
+        }
+        if (sum.str().empty()) continue;
+        o << "          { double S = 0.0;" << sum.str() << " T += " << lit(x.f, false);
+        if (x.alpha > 0) o << " * t" << x.alpha;
+        o << " * S; }\n";
+      }
+      o << "          v[" << l / 2 << "] = T * zscale; }\n";
+    }
+  } else {
+    for (int l = 0; l <= L; l += 2) {
+      o << "        { double T = 0.0;";
+      for (int mu = -l; mu <= l; ++mu)
+        o << " T += yl" << ylm_index(l, mu) << " * (double)Z[" << even_lm_index(l, mu) << "LL * slot + off];";
+      o << " v[" << l / 2 << "] = T * zscale; }\n";
+    }
+  }
+  o << "      }\n    }\n";
+  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  return jlag;
+}
+
 }  // namespace
 
 std::string generate_source(const JitKey &key, KernelSet *meta) {
@@ -168,37 +338,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   o << kPrelude;
 
   // ------------------------------------------------------------------ gen_fields
-  {
-    int Jmax = 0, amax = 0;
-    for (auto &fi : F.list) {
-      Jmax = std::max(Jmax, fi.J);
-      amax = std::max(amax, fi.alpha);
-    }
-    o << "extern \"C\" __global__ void __launch_bounds__(256, 2) gen_fields(const real* __restrict__ delta,"
-         " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
-         " double inv_r0) {\n";
-    o << "  const long long ncell = (long long)N * N * N;\n";
-    o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
-         " c += (long long)gridDim.x * blockDim.x) {\n";
-    o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
-    o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
-    o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
-    o << "    const real d = delta[off];\n";
-    o << "    if (d == (real)0) continue;   // field slots are zero-filled before the launch\n";
-    o << "    const double x = lo0 + ix * h, y = lo1 + iy * h, z = lo2 + iz * h;\n";
-    o << "    const double r2 = x * x + y * y + z * z;\n";
-    o << "    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;\n";
-    o << "    const double ux = x * ir, uy = y * ir, uz = z * ir, zm = r2 > 0.0 ? 1.0 : 0.0;\n";
-    o << "    const double rad0 = (double)d;\n";
-    if (amax > 0) o << "    const double q = r2 > 0.0 ? 1.0 / (2.0 * sqrt(r2) * inv_r0) : 0.0;\n";
-    for (int a = 1; a <= amax; ++a) o << "    const double rad" << a << " = rad" << a - 1 << " * q;\n";
-    for (int a = 0; a <= amax; ++a) o << "    const real rr" << a << " = (real)rad" << a << ";\n";
-    emit_ylm(o, Jmax, false, "y", "ux", "uy", "uz", "zm");
-    for (int i = 0; i < nf; ++i)
-      o << "    out[" << i << "LL * slot + off] = (real)y" << ylm_index(F.list[i].J, F.list[i].nu) << " * rr"
-        << F.list[i].alpha << ";\n";
-    o << "  }\n}\n";
-  }
+  emit_gen_fields(o, "gen_fields", F.list, 0, nf);
 
   // ------------------------------------------------------------------ geometry
   o << "extern \"C\" __global__ void __launch_bounds__(256) kgeom(int N, const int* __restrict__ lut, int nbins,"
@@ -302,119 +442,10 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   if (key.los == 2) emit_kcontract("kcontract_x", true);
 
   // ------------------------------------------------------------------ midpoint combine
-  if (midpoint) {
-    auto terms = midpoint_terms(key.ell_max, key.K, even);
-    o << "extern \"C\" __global__ void __launch_bounds__(256) mid_combine(const real* __restrict__ G,"
-         " long long slot, real* __restrict__ Hout, int N, double tscale) {\n";
-    o << "  const long long ncell = (long long)N * N * N;\n";
-    o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
-         " c += (long long)gridDim.x * blockDim.x) {\n";
-    o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
-    o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
-    o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
-    o << "    const int jx = bym_lab(ix, N), jy = bym_lab(iy, N), jz = bym_lab(iz, N);\n";
-    o << "    const int j2 = jx * jx + jy * jy + jz * jz;\n";
-    o << "    const real rr = bym_sqrt((real)j2);\n";
-    o << "    const real ir = j2 > 0 ? (real)1 / rr : (real)0;\n";
-    o << "    const real ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = j2 > 0 ? (real)1 : (real)0;\n";
-    o << "    const real t1 = (real)(rr * tscale);\n";
-    for (int a = 2; a <= key.K; ++a) o << "    const real t" << a << " = t" << a - 1 << " * t1;\n";
-    {
-      std::ostringstream yy;
-      emit_ylm(yy, key.K, f32, "yd", "ux", "uy", "uz", "zm");
-      std::istringstream is(yy.str());
-      std::string line;
-      while (std::getline(is, line)) o << "  " << line << "\n";
-    }
-    for (int i = 0; i < n_lm; ++i) o << "    real H" << i << " = (real)0;\n";
-    for (int a = 0; a <= key.K; ++a) {
-      std::set<int> gs;
-      std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> groups;  // (lm, y) -> (g, c)
-      for (auto &tm : terms)
-        if (tm.alpha == a) {
-          gs.insert(tm.g);
-          groups[{tm.lm, tm.y}].push_back({tm.g, tm.c});
-        }
-      if (groups.empty()) continue;
-      o << "    {\n";
-      for (int g : gs) o << "      const real g" << g << " = G[" << g << "LL * slot + off];\n";
-      for (auto &kv : groups) {
-        o << "      { real S = (real)0;";
-        for (auto &gc : kv.second) o << " S += " << lit(gc.second, f32) << " * g" << gc.first << ";";
-        o << " H" << kv.first.first << " += yd" << kv.first.second;
-        if (a > 0) o << " * t" << a;
-        o << " * S; }\n";
-      }
-      o << "    }\n";
-    }
-    for (int i = 0; i < n_lm; ++i) o << "    Hout[" << i << "LL * slot + off] = H" << i << ";\n";
-    o << "  }\n}\n";
-  }
+  if (midpoint) emit_mid_combine(o, "mid_combine", key, midpoint_terms(key.ell_max, key.K, even), 0, nf, false);
 
   // ------------------------------------------------------------------ xi on the lag cube
-  int jlag = L;
-  std::vector<XiTerm> xterms;
-  if (midpoint) {
-    xterms = midpoint_xi_terms(key.ell_max, key.K, even);
-    for (auto &x : xterms) jlag = std::max(jlag, x.J);
-  }
-  o << "extern \"C\" __global__ void __launch_bounds__(256) xi_lag(const real* __restrict__ Z, long long slot,"
-       " int N, int jm, int full, const int* __restrict__ lut, int nbins, double* __restrict__ gsum,"
-       " double zscale, double tscale) {\n";
-  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n";
-  o << "  const int Lc = full ? N : 2 * jm + 1;\n";
-  emit_bin_loop_head(o, "(long long)Lc * Lc * Lc");
-  o << "    int bin = -1; double v[" << NL << "] = {";
-  for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
-  o << "};\n";
-  o << "    if (m < total) {\n";
-  o << "      const int a = (int)(m % Lc); const long long t = m / Lc;\n";
-  o << "      const int b = (int)(t % Lc); const int c = (int)(t / Lc);\n";
-  o << "      const int jx = full ? bym_lab(c, N) : c - jm, jy = full ? bym_lab(b, N) : b - jm,"
-       " jz = full ? bym_lab(a, N) : a - jm;\n";
-  o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
-  o << "      bin = lut[j2];\n";
-  o << "      if (bin >= 0) {\n";
-  o << "        const int ix = jx < 0 ? jx + N : jx, iy = jy < 0 ? jy + N : jy, iz = jz < 0 ? jz + N : jz;\n";
-  o << "        const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
-  o << "        const double rr = sqrt((double)j2); const double ir = 1.0 / rr;\n";
-  o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
-  {
-    std::ostringstream yy;
-    emit_ylm(yy, jlag, false, "yl", "ux", "uy", "uz", "zm");
-    std::istringstream is(yy.str());
-    std::string line;
-    while (std::getline(is, line)) o << "      " << line << "\n";
-  }
-  if (midpoint) {
-    int amax = 0;
-    for (auto &x : xterms) amax = std::max(amax, x.alpha);
-    o << "        const double t1 = rr * tscale;\n";
-    for (int a2 = 2; a2 <= amax; ++a2) o << "        const double t" << a2 << " = t" << a2 - 1 << " * t1;\n";
-    for (int l = 0; l <= L; l += 2) {
-      o << "        { double T = 0.0;\n";
-      for (auto &x : xterms) {
-        if (x.l != l) continue;
-        o << "          { double S = 0.0;";
-        for (int nu = -x.J; nu <= x.J; ++nu)
-          o << " S += yl" << ylm_index(x.J, nu) << " * (double)Z["
-            << midpoint_gfield_index(key.ell_max, x.alpha, x.J, nu, even) << "LL * slot + off];";
-        o << " T += " << lit(x.f, false);
-        if (x.alpha > 0) o << " * t" << x.alpha;
-        o << " * S; }\n";
-      }
-      o << "          v[" << l / 2 << "] = T * zscale; }\n";
-    }
-  } else {
-    for (int l = 0; l <= L; l += 2) {
-      o << "        { double T = 0.0;";
-      for (int mu = -l; mu <= l; ++mu)
-        o << " T += yl" << ylm_index(l, mu) << " * (double)Z[" << even_lm_index(l, mu) << "LL * slot + off];";
-      o << " v[" << l / 2 << "] = T * zscale; }\n";
-    }
-  }
-  o << "      }\n    }\n";
-  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  const int jlag = emit_xi_lag(o, "xi_lag", key, 0, nf);
 
   if (meta) {
     meta->key = key;
@@ -423,6 +454,28 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     meta->n_ell = NL;
     meta->jmax_lag = jlag;
   }
+  return o.str();
+}
+
+std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *meta) {
+  const bool f32 = key.prec == 32;
+  const char *real = f32 ? "float" : "double";
+  const Fields F = field_set(key);
+  const int nf = (int)F.list.size();
+  const bool even = key.los == 3;
+  std::vector<std::pair<int, int>> ranges;
+  for (int f0 = 0; f0 < nf; f0 += max_fields) ranges.push_back({f0, std::min(nf, f0 + max_fields)});
+  std::ostringstream o;
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << kPrelude;
+  const auto terms = midpoint_terms(key.ell_max, key.K, even);
+  for (size_t q = 0; q < ranges.size(); ++q) {
+    const std::string sfx = "_c" + std::to_string(q);
+    emit_gen_fields(o, ("gen_fields" + sfx).c_str(), F.list, ranges[q].first, ranges[q].second);
+    emit_mid_combine(o, ("mid_combine" + sfx).c_str(), key, terms, ranges[q].first, ranges[q].second, q > 0);
+    emit_xi_lag(o, ("xi_lag" + sfx).c_str(), key, ranges[q].first, ranges[q].second);
+  }
+  if (meta) meta->ranges = ranges;
   return o.str();
 }
 
@@ -494,6 +547,52 @@ std::shared_ptr<KernelSet> get_kernels(const JitKey &key, std::string &err) {
   }
   cache[key] = ks;
   return ks;
+}
+
+std::shared_ptr<ChunkSet> get_chunk_kernels(const JitKey &key, int max_fields, std::string &err) {
+  static std::mutex mu;
+  static std::map<std::pair<JitKey, int>, std::shared_ptr<ChunkSet>> cache;
+  if ((key.los != 1 && key.los != 3) || max_fields < 1) {
+    err = "field chunks apply to the midpoint forms only";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({key, max_fields});
+  if (it != cache.end()) return it->second;
+  auto cs = std::make_shared<ChunkSet>();
+  std::string src;
+  try {
+    src = generate_chunk_source(key, max_fields, cs.get());
+  } catch (const std::exception &e) {
+    err = std::string("kernel generation failed: ") + e.what();
+    return nullptr;
+  }
+  std::vector<char> cubin;
+  std::string log;
+  if (!compile_cubin(src, cubin, log)) {
+    err = "NVRTC compile failed: " + log.substr(0, 2000);
+    return nullptr;
+  }
+  if (cudaLibraryLoadData(&cs->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+    err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(cudaGetLastError());
+    return nullptr;
+  }
+  for (size_t q = 0; q < cs->ranges.size(); ++q) {
+    const std::string sfx = "_c" + std::to_string(q);
+    cudaKernel_t k[3] = {nullptr, nullptr, nullptr};
+    const std::string names[3] = {"gen_fields" + sfx, "mid_combine" + sfx, "xi_lag" + sfx};
+    for (int i = 0; i < 3; ++i)
+      if (cudaLibraryGetKernel(&k[i], cs->lib, names[i].c_str()) != cudaSuccess) {
+        cudaGetLastError();
+        err = "generated chunk module is missing " + names[i];
+        return nullptr;
+      }
+    cs->gen.push_back(k[0]);
+    cs->comb.push_back(k[1]);
+    cs->xi.push_back(k[2]);
+  }
+  cache[{key, max_fields}] = cs;
+  return cs;
 }
 
 }  // namespace bym

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <memory>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -33,13 +34,25 @@ struct KernelSet {
   cudaKernel_t kcontract = nullptr, kcontract_x = nullptr, mid_combine = nullptr, xi_lag = nullptr;
 };
 
+// Midpoint forms under a memory bound: the g fields in ranges of at most
+// max_fields, each with its own gen_fields / mid_combine (accumulating into
+// H after the first range) / xi_lag (adding its share of the shell sums).
+struct ChunkSet {
+  std::vector<std::pair<int, int>> ranges;   // field ranges [f0, f1) in slot order
+  cudaLibrary_t lib = nullptr;
+  std::vector<cudaKernel_t> gen, comb, xi;   // one of each per range
+};
+
 // Source text for a configuration (exposed for build checks).
 std::string generate_source(const JitKey &key, KernelSet *meta);
+
+std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *meta);
 
 // Compile to a cubin for sm_103a; returns false and fills log on failure.
 bool compile_cubin(const std::string &src, std::vector<char> &cubin, std::string &log);
 
 // Process-wide cache: generate, compile, load.  Thread-safe.
 std::shared_ptr<KernelSet> get_kernels(const JitKey &key, std::string &err);
+std::shared_ptr<ChunkSet> get_chunk_kernels(const JitKey &key, int max_fields, std::string &err);
 
 }  // namespace bym

@@ -57,7 +57,8 @@ def test_rejects_unsupported_parameters(pkg):
 
 
 @pytest.mark.parametrize("los,order,precision", [("yamamoto", 0, 32), ("midpoint", 4, 32),
-                                                 ("bisector", 4, 32), ("midpoint", 2, 64)])
+                                                 ("bisector", 4, 32), ("midpoint", 2, 64),
+                                                 ("midpoint_even", 4, 32)])
 def test_generated_kernels_compile(pkg, los, order, precision):
     p = pkg.make_params(box_lo=(0, 0, 0), box_len=1000.0, n_mesh=64, ell_max=4, los=los, order=order,
                         precision=precision)

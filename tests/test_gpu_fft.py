@@ -1,5 +1,7 @@
 """The library's own 512^3 FP32 FFT kernels against cuFFT (through torch.fft), and
-whole requests computed with them against the same requests computed with cuFFT."""
+whole requests computed with them against the same requests computed with cuFFT,
+with 8-CTA (backend mode 1) and 16-CTA (mode 3) clusters in the plane pass, and
+with cuFFT's plane transforms around the library's x pass (mode 4)."""
 import ctypes
 import math
 
@@ -33,8 +35,10 @@ def _slots(torch, x):
     return s
 
 
-def test_forward_and_inverse_match_cufft(env):
+@pytest.mark.parametrize("mode", [1, 3, 4])
+def test_forward_and_inverse_match_cufft(env, mode):
     torch, pkg, lib, ctx = env
+    assert lib.bym_set_fft_backend(ctx._h, mode) == 0
     gen = torch.Generator(device="cuda").manual_seed(7)
     x = torch.randn(2, N, N, N, device="cuda", generator=gen)
     buf = _slots(torch, x)
@@ -66,17 +70,38 @@ def cat():
     return lognormal_cap_catalog(seed=9, n_gal=200_000, ran_factor=10.0, gen_mesh=128)
 
 
-@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 4), ("bisector", 4), ("midpoint_even", 2)])
-def test_requests_native_vs_cufft(env, cat, los, K):
+@pytest.mark.parametrize("los,K,mode", [("yamamoto", 0, 1), ("midpoint", 4, 1), ("bisector", 4, 1),
+                                        ("midpoint_even", 2, 1), ("midpoint", 2, 3), ("bisector", 2, 3),
+                                        ("midpoint", 4, 4), ("bisector", 4, 4), ("yamamoto", 0, 4)])
+def test_requests_native_vs_cufft(env, cat, los, K, mode):
     torch, pkg, lib, ctx = env
     p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
                         compensate=True, precision=32)
     kedges = np.round(np.arange(0.01, 0.2501, 0.01), 10)
     redges = np.arange(10.0, 190.01, 10.0)
     out = {}
-    for native in (0, 1):
-        assert lib.bym_set_fft_backend(ctx._h, native) == 0
-        out[native] = ctx.pk_xi_multipoles(cat.gal, cat.ran, p, kedges, redges, ran_nbar=cat.ran_nbar)
-    lib.bym_set_fft_backend(ctx._h, 1)
-    check_multipoles(out[1]["pk"], out[0]["pk"], "pk", label=f"{los} P: ")
-    check_multipoles(out[1]["xi"], out[0]["xi"], "xi", label=f"{los} xi: ")
+    for m in (0, mode):
+        assert lib.bym_set_fft_backend(ctx._h, m) == 0
+        out[m] = ctx.pk_xi_multipoles(cat.gal, cat.ran, p, kedges, redges, ran_nbar=cat.ran_nbar)
+    check_multipoles(out[mode]["pk"], out[0]["pk"], "pk", label=f"{los} P: ")
+    check_multipoles(out[mode]["xi"], out[0]["xi"], "xi", label=f"{los} xi: ")
+
+
+@pytest.mark.parametrize("mode", [1, 4])
+def test_streamed_ranges_with_library_kernels(env, cat, mode):
+    # midpoint g fields in ranges of 9 (slots 2.. of the request) through the library's kernels
+    torch, pkg, lib, ctx = env
+    p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=4, los="midpoint",
+                        order=2, compensate=True, precision=32)
+    kedges = np.round(np.arange(0.01, 0.2501, 0.01), 10)
+    redges = np.arange(10.0, 190.01, 10.0)
+    assert lib.bym_set_fft_backend(ctx._h, 0) == 0
+    ref = ctx.pk_xi_multipoles(cat.gal, cat.ran, p, kedges, redges, ran_nbar=cat.ran_nbar)
+    assert lib.bym_set_fft_backend(ctx._h, mode) == 0
+    ctx.set_field_chunk(9)
+    try:
+        got = ctx.pk_xi_multipoles(cat.gal, cat.ran, p, kedges, redges, ran_nbar=cat.ran_nbar)
+    finally:
+        ctx.set_field_chunk(0)
+    check_multipoles(got["pk"], ref["pk"], "pk", label=f"mode {mode} ranges P: ")
+    check_multipoles(got["xi"], ref["xi"], "xi", label=f"mode {mode} ranges xi: ")
