@@ -20,6 +20,14 @@ Discrete normalisation (the reading of Sec. 2 used throughout):
   P_ell(k_b)  = 4 pi / A * mean_{k in b} Re[ sum_m Y_ell^m*(k) X_ell^m(k) ]
   xi_ell(r_b) = 4 pi / (A V_cell) * mean_{Delta in b} Re[ sum_m Y_ell^m*(Delta) Z_ell^m(Delta) ]
 with A the FKP normalisation (``norm=1``) or 1 and V_cell = 1 (``norm=0``).
+``norm=2`` keeps the FKP A for P and divides xi_ell by the random-random count
+RR_0(r_b) of the same mesh estimator applied to alpha_r n_r (ell = 0, where the
+line of sight drops out): xi_ell = [DD - 2 DR + RR]_ell / RR_0, the
+Landy-Szalay form Sec. 2.2 names for catalogs (the pair counts of eq.
+general-2pcf-form with delta = n_g - alpha_r n_r).
+
+``shot_noise`` is the FKP shot-noise level (sum_g w^2 + alpha_r^2 sum_r w^2) / A
+that eq. Pk-def includes in P_0 (Sec. 2.1); the estimators do not subtract it.
 The order K is the highest power of theta kept: midpoint alpha <= K, bisector
 beta <= floor(K/2).
 
@@ -62,10 +70,14 @@ def _flip_k(a: np.ndarray) -> np.ndarray:
     return np.roll(a[::-1, ::-1, ::-1], 1, axis=(0, 1, 2))
 
 
-def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate):
+def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate, xi=False):
     g = Grid(N, box_lo, box_len)
     delta, _ = mesh.density_mesh(gal, ran, g.N, g.box_lo, g.box_len, assign)
-    if norm:
+    if norm == 2 and xi:
+        if ran is None or len(ran) == 0:
+            raise ValueError("norm=2 needs randoms")
+        A, v_cell = 1.0, 1.0            # raw sums; divided by RR_0 afterwards
+    elif norm:
         _, A = mesh.norm_factors(gal, ran, ran_nbar)
         if A is None:
             raise ValueError("norm=1 needs randoms with nbar")
@@ -204,7 +216,7 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
     """xi_ell(r) for ell = 0, 2, .., ell_max with LOS in
     {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
     g, delta, A, v_cell, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
-                                          assign, norm, compensate)
+                                          assign, norm, compensate, xi=True)
     ells = _ells(ell_max)
     D = _fwd(delta, inv_w)
     Z = {}
@@ -262,4 +274,34 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
             Z[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * c
     else:
         raise ValueError(f"unknown los {los!r}")
-    return _xi_out(g, ells, Z, A, v_cell, redges)
+    out = _xi_out(g, ells, Z, A, v_cell, redges)
+    if norm == 2:
+        out["xi"] = out["xi"] / _rr0(gal, ran, N, box_lo, box_len, assign, redges, compensate)[None, :]
+    return out
+
+
+def _rr0(gal, ran, N, box_lo, box_len, assign, redges, compensate):
+    """RR_0(r_b): the raw ell = 0 sum of the mesh estimator for alpha_r n_r (any
+    line of sight gives the same ell = 0 sum; Yamamoto is used), bins without
+    random pairs set to infinity so that their ratio is 0."""
+    alpha, _ = mesh.norm_factors(gal, ran, None)
+    rr = xi_multipoles(ran, None, None, N=N, box_lo=box_lo, box_len=box_len, assign=assign, ell_max=0,
+                       los="yamamoto", order=0, redges=redges, compensate=compensate, norm=0)["xi"][0]
+    rr = alpha * alpha * rr
+    return np.where(rr != 0.0, rr, np.inf)
+
+
+def shot_noise(gal, ran, ran_nbar, norm=1):
+    """FKP shot-noise level of P_0: (sum_g w^2 + alpha_r^2 sum_r w^2) / A, with A
+    the FKP normalisation (norm 1 or 2) or 1 (norm 0)."""
+    w_g = np.asarray(gal, dtype=np.float64)[:, 3]
+    alpha, A = mesh.norm_factors(gal, ran, ran_nbar)
+    s = float(np.sum(w_g * w_g))
+    if ran is not None and len(ran):
+        w_r = np.asarray(ran, dtype=np.float64)[:, 3]
+        s += alpha * alpha * float(np.sum(w_r * w_r))
+    if norm == 0:
+        return s
+    if A is None:
+        raise ValueError("norm 1 or 2 needs randoms with nbar")
+    return s / A
