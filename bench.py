@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--los", default="midpoint,bisector", help="comma-separated LOS list (profiling runs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving / batching leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--fft-backend", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="force an FFT backend (bym_set_fft_backend) instead of the tuned choice (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=24)
     return ap.parse_args()
 
@@ -209,6 +211,8 @@ def run_ours(args):
     ran_d = torch.from_numpy(cat.ran).to(dev)
     rnb_d = torch.from_numpy(cat.ran_nbar).to(dev)
     ctx = pkg.Context(local)
+    if args.fft_backend is not None:
+        ctx.set_fft_backend(args.fft_backend)
     params = [pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=args.mesh, assign=3,
                               ell_max=ELL_MAX, los=los, order=ORDER, compensate=True, precision=32, norm=1)
               for los in args.los.split(",")]

@@ -26,7 +26,12 @@
  *     magnitudes in [edges[b], edges[b+1]); k = 0 and Delta = 0 never enter.
  *   - Normalisation (norm = 1): P_ell = 4 pi / A * (bin mean), xi_ell =
  *     4 pi / (A V_cell) * (bin mean), A = alpha_r sum_r nbar_r w_r^2 (FKP);
- *     norm = 0 sets A = V_cell = 1.
+ *     norm = 0 sets A = V_cell = 1.  norm = 2: P as norm = 1; xi_ell divided
+ *     instead by the random-random count, xi_ell(r_b) = S_ell[delta](b) /
+ *     (alpha_r^2 S_0[n_r](b)) with S the raw bin sums of the same mesh
+ *     estimator (the Landy-Szalay form of the pair counts Sec. 2.2 refers to;
+ *     S_0 is line-of-sight independent and taken with the Yamamoto form, one
+ *     more painting and two more transforms); bins with no random pairs give 0.
  *   - Outputs are host arrays owned by the caller, laid out [ell/2][bin].
  *   - Calls are synchronous on the given CUDA stream (NULL: the context's
  *     stream) unless submitted through bym_submit.  The context's stream is an
@@ -67,7 +72,7 @@ typedef enum { BYM_LOS_YAMAMOTO = 0, BYM_LOS_MIDPOINT = 1, BYM_LOS_BISECTOR = 2,
 typedef struct bym_ctx bym_ctx;
 
 /* A catalog: n objects as (x, y, z, w) float quadruples, row major, and an
- * optional per-object nbar (needed for the randoms when norm = 1).
+ * optional per-object nbar (needed for the randoms when norm = 1 or 2).
  * on_device = 1: the pointers are device pointers of the context's GPU.
  * The caller owns the memory; it is only read during the call. */
 typedef struct {
@@ -87,7 +92,7 @@ typedef struct {
   int order;          /* K = highest power of theta kept, 0..12 */
   int compensate;     /* 1: divide each painted-field transform by the assignment window W(k) */
   int precision;      /* 32: FP32 fields and FFTs; 64: FP64 throughout. Shell sums are FP64 either way */
-  int norm;           /* 1: FKP normalisation A; 0: raw (A = V_cell = 1) */
+  int norm;           /* 1: FKP normalisation A; 0: raw (A = V_cell = 1); 2: FKP for P, RR for xi */
 } bym_params;
 
 typedef struct {
@@ -143,6 +148,15 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
  * ranges, see bym_set_field_chunk); works without a GPU.  Used by build
  * checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
+
+/* Shot-noise level of P_0 (Sec. 2.1: eq. Pk-def includes a shot-noise term that
+ * does not depend on the line of sight; the estimators above do not subtract
+ * it): *shot = (sum_g w^2 + alpha_r^2 sum_r w^2) / A, with A the FKP
+ * normalisation for norm = 1 or 2 and A = 1 for norm = 0 (same conventions as
+ * the estimators; ran may be NULL, alpha_r = 0).  The sums run on the GPU.
+ * Returns BYM_E_OUT_OF_BOX like the estimators. */
+int bym_shot_noise(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                   double *shot);
 
 /* Memory bound for the midpoint forms (Sec. 2.2: the g^alpha_{J M} functions
  * of eq. g-JM-form are the largest memory item, 145 meshes at ell_max = 4,

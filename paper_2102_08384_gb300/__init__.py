@@ -87,6 +87,7 @@ def lib():
         L.bym_pk_xi_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, dp, dp, i64p, dp, dp, i64p,
                                            vp]
         L.bym_jit_check.argtypes = [par_p, ctypes.c_char_p, ctypes.c_size_t]
+        L.bym_shot_noise.argtypes = [vp, cat_p, cat_p, par_p, dp]
         L.bym_serve_start.argtypes = [vp, ctypes.c_int, ctypes.c_size_t]
         L.bym_serve_stop.argtypes = [vp]
         L.bym_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_uint64)]
@@ -342,6 +343,16 @@ class Context:
 
     def pk_xi_multipoles(self, gal, ran, params, kedges, redges, gal_nbar=None, ran_nbar=None, stream=None):
         return self._run("both", gal, ran, params, kedges, redges, gal_nbar, ran_nbar, stream)
+
+    def shot_noise(self, gal, ran, params, gal_nbar=None, ran_nbar=None) -> float:
+        """(sum_g w^2 + alpha_r^2 sum_r w^2) / A, the shot-noise level of P_0 (not subtracted by the estimators)."""
+        keep = []
+        g = _catalog(gal, gal_nbar, keep)
+        r = _catalog(ran, ran_nbar, keep)
+        out = ctypes.c_double(0.0)
+        self._check(self._L.bym_shot_noise(self._h, ctypes.byref(g), ctypes.byref(r) if r is not None else None,
+                                           ctypes.byref(params), ctypes.byref(out)))
+        return out.value
 
 
 def footprint(params: Params, n_gal: int, n_ran: int, want_pk=True, want_xi=True) -> int:

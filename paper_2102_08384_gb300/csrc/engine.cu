@@ -148,7 +148,7 @@ int bym::validate_params(bym_ctx *c, const bym_params *p) {
   if (p->los == BYM_LOS_MIDPOINT_EVEN && p->order > 4)
     return fail(c, BYM_E_UNSUPPORTED, "the parity-even midpoint form is available to order 4");
   if (p->precision != 32 && p->precision != 64) return fail(c, BYM_E_INVAL, "precision must be 32 or 64");
-  if (p->norm != 0 && p->norm != 1) return fail(c, BYM_E_INVAL, "norm must be 0 or 1");
+  if (p->norm < 0 || p->norm > 2) return fail(c, BYM_E_INVAL, "norm must be 0, 1 or 2");
   if (p->compensate != 0 && p->compensate != 1) return fail(c, BYM_E_INVAL, "compensate must be 0 or 1");
   if (!(p->box_len > 0.0) || !std::isfinite(p->box_len) || !finite_all(p->box_lo, 3))
     return fail(c, BYM_E_INVAL, "box must be finite with box_len > 0");
@@ -162,8 +162,8 @@ int bym::validate(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, co
   if (!gal || gal->n < 0 || (gal->n > 0 && !gal->xyzw)) return fail(c, BYM_E_INVAL, "bad galaxy catalog");
   if (ran && (ran->n < 0 || (ran->n > 0 && !ran->xyzw))) return fail(c, BYM_E_INVAL, "bad random catalog");
   const bool have_ran = ran && ran->n > 0;
-  if (p->norm == 1 && (!have_ran || !ran->nbar))
-    return fail(c, BYM_E_INVAL, "norm = 1 needs randoms with nbar");
+  if (p->norm >= 1 && (!have_ran || !ran->nbar))
+    return fail(c, BYM_E_INVAL, "norm = 1 or 2 needs randoms with nbar");
   for (const bym_catalog *cat : {gal, ran}) {
     if (cat && cat->n > 0 && cat->on_device && ((uintptr_t)cat->xyzw % 16))
       return fail(c, BYM_E_INVAL, "device xyzw must be 16-byte aligned");
@@ -307,15 +307,28 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
   const double esz = prec == 64 ? 8.0 : 4.0;
   const int kind = fft_kind(c, N, prec, tn);
   if (kind) {
-    ProfScope ps(c, st, inverse ? "fft_native_c2r" : "fft_native_r2c", count * 2.0 * esz * (double)N * N * N);
     cudaError_t e = native_fft_prepare();
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     const long long sr = (long long)(slot_bytes / 4);
-    if (kind == 1) {
-      if (!inverse) TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn));
-      e = native_fft_xpass(inverse ? 1 : 0, (float *)base, sr, first, count, nullptr, nullptr, nullptr, st);
-      if (e == cudaSuccess && inverse) TRY_RC(fft_planes(c, st, 1, N, base, slot_bytes, first, count, tn));
-    } else {
+    const double cplx = 2.0 * esz * (double)N * N * (N / 2 + 1);
+    if (kind == 1) {   // cuFFT over the (y, z) planes, the library's x pass
+      if (!inverse) {
+        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * (double)N * N * N);
+        TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn));
+      }
+      {
+        ProfScope ps(c, st, inverse ? "fft_native_x_inv" : "fft_native_x_fwd", count * 2.0 * cplx);
+        e = native_fft_xpass(inverse ? 1 : 0, (float *)base, sr, first, count, nullptr, nullptr, nullptr, st);
+      }
+      if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+      if (inverse) {
+        ProfScope ps(c, st, "cufft_planes_c2r", count * 2.0 * esz * (double)N * N * N);
+        TRY_RC(fft_planes(c, st, 1, N, base, slot_bytes, first, count, tn));
+      }
+      return BYM_OK;
+    }
+    {
+      ProfScope ps(c, st, inverse ? "fft_native_c2r" : "fft_native_r2c", count * 2.0 * esz * (double)N * N * N);
       e = inverse ? native_fft_inverse((float *)base, sr, first, count, kind, st)
                   : native_fft_forward((float *)base, sr, first, count, kind, st);
     }
@@ -363,7 +376,7 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
         TRY_RC(fft_planes(c, st, 0, N, slots, slot_bytes, first, count, tn));
       }
       {
-        ProfScope ps(c, st, "fft_native_x_convolve", count * (2.0 * cplx) + cplx);
+        ProfScope ps(c, st, "fft_native_x_convolve", count * 3.0 * cplx);   // read F and D, write F
         e = native_fft_xpass(2, (float *)slots, slot_reals, first, count, (const float *)slots, scale,
                              (const float *)invw, st);
       }
@@ -493,8 +506,8 @@ static int get_null_kgeom(bym_ctx *c, int N, Geom **out) {
 }
 
 // Device bytes a request may still take: free memory plus what the stream-ordered
-// pool holds unused, less headroom for one slot (FFT work areas and small buffers).
-static size_t device_available(bym_ctx *c, size_t slot_bytes) {
+// pool holds unused, less the given headroom (FFT work areas and small buffers).
+static size_t device_available(bym_ctx *c, size_t headroom) {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     cudaGetLastError();
@@ -507,7 +520,7 @@ static size_t device_available(bym_ctx *c, size_t slot_bytes) {
         cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
       free_b += (size_t)(reserved - used);
   }
-  return free_b > slot_bytes ? free_b - slot_bytes : 0;
+  return free_b > headroom ? free_b - headroom : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -539,7 +552,9 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (c->field_chunk > 0) {
       chunk = std::min(c->field_chunk, nf);
     } else {
-      const size_t avail = c->budget ? c->budget : device_available(c, slot_bytes);
+      // without a budget: free memory less room for the FFT work area (up to a batch of transforms)
+      const size_t head = (size_t)(std::max(tn.fft_batch, 1) + 1) * slot_bytes;
+      const size_t avail = c->budget ? c->budget : device_available(c, head);
       if (footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev) > avail)
         for (int m = nf - 1; m >= 1 && !chunk; --m)
           if (footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev, m) <= avail) chunk = m;
@@ -776,13 +791,16 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   if (hstats[3] > 0.0)
     return fail(c, BYM_E_OUT_OF_BOX,
                 std::to_string((long long)hstats[3]) + " objects lie outside the box or are not finite");
+  if (rq.alpha) *rq.alpha = hstats[1] != 0.0 ? hstats[0] / hstats[1] : 0.0;
   double A = 1.0, vcell = 1.0;
-  if (p->norm == 1) {
+  if (p->norm >= 1) {
     const double alpha = hstats[0] / hstats[1];
     A = alpha * hstats[2];
     vcell = h * h * h;
     if (!(A > 0.0) || !std::isfinite(A)) return fail(c, BYM_E_INVAL, "FKP normalisation A is not positive");
   }
+  // norm 2: xi as raw sums here, divided by the random-random count afterwards
+  const double xden = p->norm == 2 ? 1.0 : A * vcell;
   const double four_pi = 4.0 * M_PI;
   if (want_pk) {
     for (int l = 0; l < NL; ++l)
@@ -795,13 +813,42 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     for (int l = 0; l < NL; ++l)
       for (int b = 0; b < nbr; ++b)
         rq.xi[l * nbr + b] =
-            rg->count[b] > 0 ? four_pi / (A * vcell) * hr[(size_t)b * NL + l] / (double)rg->count[b] : 0.0;
+            rg->count[b] > 0 ? four_pi / xden * hr[(size_t)b * NL + l] / (double)rg->count[b] : 0.0;
     if (rq.rmean) std::copy(rg->mean.begin(), rg->mean.end(), rq.rmean);
     if (rq.ncells) std::copy(rg->count.begin(), rg->count.end(), rq.ncells);
   }
   return BYM_OK;
 #undef TRY
 #undef CUDA_TRY
+}
+
+// norm 2 (Sec. 2.2: the Landy-Szalay form of the catalog pair counts): P with the
+// FKP normalisation; xi_ell(r_b) = S_ell[delta](b) / (alpha_r^2 S_0[n_r](b)), both raw
+// bin sums of the same mesh estimator; the random-random sum is the ell = 0 one, where
+// the line of sight drops out, computed with the Yamamoto form.  Bins without random
+// pairs give 0.
+static int run_rr_normalised(bym_ctx *c, const Request &rq, cudaStream_t st) {
+  const bool f64 = rq.p->precision == 64;
+  double alpha = 0.0;
+  Request main = rq;
+  main.alpha = &alpha;
+  int rc = f64 ? run_typed<double, double2>(c, main, st) : run_typed<float, float2>(c, main, st);
+  if (rc) return rc;
+  bym_params pr = *rq.p;
+  pr.los = BYM_LOS_YAMAMOTO;
+  pr.ell_max = 0;
+  pr.order = 0;
+  pr.norm = 0;
+  const int nbr = rq.rb->nbins, NL = rq.p->ell_max / 2 + 1;
+  std::vector<double> rr((size_t)nbr);
+  Request rrq{rq.ran, nullptr, &pr, nullptr, rq.rb, nullptr, nullptr, nullptr, rr.data(), nullptr, nullptr};
+  rc = f64 ? run_typed<double, double2>(c, rrq, st) : run_typed<float, float2>(c, rrq, st);
+  if (rc) return rc;
+  for (int b = 0; b < nbr; ++b) {
+    const double den = alpha * alpha * rr[b];
+    for (int l = 0; l < NL; ++l) rq.xi[l * nbr + b] = den != 0.0 ? rq.xi[l * nbr + b] / den : 0.0;
+  }
+  return BYM_OK;
 }
 
 int bym::run_request(bym_ctx *c, const Request &rq, cudaStream_t st) {
@@ -813,6 +860,7 @@ int bym::run_request(bym_ctx *c, const Request &rq, cudaStream_t st) {
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
   if (!st) st = c->stream;
   try {
+    if (rq.p->norm == 2 && rq.rb) return run_rr_normalised(c, rq, st);
     if (rq.p->precision == 64) return run_typed<double, double2>(c, rq, st);
     return run_typed<float, float2>(c, rq, st);
   } catch (const std::exception &e) {
@@ -916,6 +964,59 @@ int bym_set_fft_backend(bym_ctx *c, int mode) {
   if (!c || mode < 0 || mode > 4) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
   c->fft_mode = mode;
+  return BYM_OK;
+}
+
+int bym_shot_noise(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
+                   double *shot) {
+  if (!c || !shot) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  int rc = validate(c, gal, ran, p, nullptr, nullptr);
+  if (rc) return rc;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = c->stream;
+  DevBufs buf(st);
+  const bym_catalog *cats[2] = {gal, ran};
+  double *stats = nullptr;
+  if (buf.alloc((void **)&stats, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "device allocation failed");
+  }
+  cudaMemsetAsync(stats, 0, 8 * sizeof(double), st);
+  const double inv_h = p->n_mesh / p->box_len;
+  for (int w = 0; w < 2; ++w) {
+    const bym_catalog *cat = cats[w];
+    if (!cat || cat->n <= 0) continue;
+    const float4 *d4 = (const float4 *)cat->xyzw;
+    const float *dn = cat->nbar;
+    if (!cat->on_device) {
+      void *a = nullptr, *b = nullptr;
+      if (buf.alloc(&a, (size_t)cat->n * 16) != cudaSuccess ||
+          (cat->nbar && buf.alloc(&b, (size_t)cat->n * 4) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(c, BYM_E_NOMEM, "device allocation failed");
+      }
+      cudaMemcpyAsync(a, cat->xyzw, (size_t)cat->n * 16, cudaMemcpyHostToDevice, st);
+      if (cat->nbar) cudaMemcpyAsync(b, cat->nbar, (size_t)cat->n * 4, cudaMemcpyHostToDevice, st);
+      d4 = (const float4 *)a;
+      dn = (const float *)b;
+    }
+    launch_norm_reduce(d4, dn, cat->n, w, p->box_lo, inv_h, p->n_mesh, stats, c->nsm, st);
+  }
+  double hs[8];
+  cudaError_t e = cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("shot noise: ") + cudaGetErrorString(e));
+  if (hs[3] > 0.0)
+    return fail(c, BYM_E_OUT_OF_BOX, std::to_string((long long)hs[3]) + " objects lie outside the box or are not finite");
+  const double alpha = hs[1] != 0.0 ? hs[0] / hs[1] : 0.0;
+  double S = hs[4] + alpha * alpha * hs[5];
+  if (p->norm >= 1) {
+    const double A = alpha * hs[2];
+    if (!(A > 0.0) || !std::isfinite(A)) return fail(c, BYM_E_INVAL, "FKP normalisation A is not positive");
+    S /= A;
+  }
+  *shot = S;
   return BYM_OK;
 }
 

@@ -31,6 +31,7 @@ struct Request {
   int64_t *nmodes;
   double *xi, *rmean;
   int64_t *ncells;
+  double *alpha = nullptr;      // optional out: alpha_r = sum w_g / sum w_r of the request
 };
 
 struct Server;  // serving loop state (serve.cpp)

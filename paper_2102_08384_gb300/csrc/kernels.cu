@@ -26,11 +26,12 @@ __device__ __forceinline__ void atomic_add(T *p, T v) {
 
 // stats[0] += sum w (galaxies, which = 0) or stats[1] += sum w (randoms, which = 1);
 // randoms also add stats[2] += sum nbar w^2 (nbar may be null: 0); stats[3] counts
-// objects whose position is not finite or lies outside [lo, lo + N h).
+// objects whose position is not finite or lies outside [lo, lo + N h);
+// stats[4 + which] += sum w^2 (the shot-noise level of Sec. 2.1).
 __global__ void __launch_bounds__(256) bym_norm_reduce(const float4 *__restrict__ p, const float *__restrict__ nbar,
                                                        long long n, int which, double lo0, double lo1, double lo2,
                                                        double inv_h, int N, double *__restrict__ stats) {
-  double sw = 0.0, snw2 = 0.0, bad = 0.0;
+  double sw = 0.0, snw2 = 0.0, bad = 0.0, sw2 = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float4 q = p[i];
     const double ux = ((double)q.x - lo0) * inv_h, uy = ((double)q.y - lo1) * inv_h, uz = ((double)q.z - lo2) * inv_h;
@@ -38,26 +39,31 @@ __global__ void __launch_bounds__(256) bym_norm_reduce(const float4 *__restrict_
                     isfinite((double)q.w);
     if (!ok) bad += 1.0;
     sw += (double)q.w;
+    sw2 += (double)q.w * (double)q.w;
     if (which == 1 && nbar) snw2 += (double)nbar[i] * (double)q.w * (double)q.w;
   }
-  __shared__ double red[3][8];
+  __shared__ double red[4][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   sw = warp_sum(sw);
   snw2 = warp_sum(snw2);
   bad = warp_sum(bad);
+  sw2 = warp_sum(sw2);
   if (lane == 0) {
     red[0][wid] = sw;
     red[1][wid] = snw2;
     red[2][wid] = bad;
+    red[3][wid] = sw2;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
+    double a = 0, b = 0, c = 0, d = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       a += red[0][w];
       b += red[1][w];
       c += red[2][w];
+      d += red[3][w];
     }
+    atomicAdd(stats + 4 + which, d);
     atomicAdd(stats + which, a);
     if (which == 1) atomicAdd(stats + 2, b);
     if (c != 0.0) atomicAdd(stats + 3, c);
