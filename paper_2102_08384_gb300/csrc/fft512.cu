@@ -45,7 +45,6 @@ constexpr long long ROWF = NM + 2;       // padded real row (floats)
 constexpr int CS = 514;                  // column stride (float2) of the column buffer; even for float4 pairs
 constexpr int ES = 17;                   // row stride (float2) of the exchange buffer and twiddle table
 constexpr int EX = 32 * ES;              // exchange buffer of one group (float2)
-constexpr int XS = 545;                  // row stride (float2) of the x-pass tile (>= EX, odd)
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -126,21 +125,37 @@ __device__ __forceinline__ int col_b(int j) { return j ? 32 - j : 16; }
 
 // Forward 512-point DFT by a 16-thread group.  In: v[m] = x[16 m + j].
 // Out: A[k2] = X[ka + 32 k2], B[k2] = X[kb + 32 k2].  TW[k1 * ES + j] = W512^(k1 j);
-// E: this group's exchange buffer (EX float2); gm: this group's lane mask.
+// E: this group's exchange buffer, EX float2, or EX / 2 with HALF (the exchange then
+// runs in two rounds, k1 < 16 then k1 >= 16); gm: this group's lane mask.
+template <bool HALF = false>
 __device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
                                        const float2 *__restrict__ TW, float2 *E) {
   dft<32, 5>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], TW[k1 * ES + j]);
-  __syncwarp(gm);
-#pragma unroll
-  for (int k1 = 0; k1 < 32; ++k1) E[k1 * ES + j] = v[k1];
-  __syncwarp(gm);
   const int ka = j, kb = col_b(j);
+  __syncwarp(gm);
+  if (HALF) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    A[i] = E[ka * ES + i];
-    B[i] = E[kb * ES + i];
+    for (int k1 = 0; k1 < 16; ++k1) E[k1 * ES + j] = v[k1];
+    __syncwarp(gm);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) A[i] = E[ka * ES + i];
+    __syncwarp(gm);
+#pragma unroll
+    for (int k1 = 16; k1 < 32; ++k1) E[(k1 - 16) * ES + j] = v[k1];
+    __syncwarp(gm);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) B[i] = E[(kb - 16) * ES + i];
+  } else {
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) E[k1 * ES + j] = v[k1];
+    __syncwarp(gm);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      A[i] = E[ka * ES + i];
+      B[i] = E[kb * ES + i];
+    }
   }
   dft<16, 4>(A);
   dft<16, 4>(B);
@@ -148,6 +163,7 @@ __device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 
 
 // Inverse (e^{+i}, unnormalised) 512-point DFT by a 16-thread group, from the
 // layout fwd512 produces to v[m] = x[16 m + j].
+template <bool HALF = false>
 __device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
                                        const float2 *__restrict__ TW, float2 *E) {
   idft<16, 4>(A);
@@ -159,14 +175,28 @@ __device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 
     B[n1] = cmulc(B[n1], TW[kb * ES + n1]);
   }
   __syncwarp(gm);
+  if (HALF) {
 #pragma unroll
-  for (int n1 = 0; n1 < 16; ++n1) {
-    E[ka * ES + n1] = A[n1];
-    E[kb * ES + n1] = B[n1];
+    for (int n1 = 0; n1 < 16; ++n1) E[ka * ES + n1] = A[n1];
+    __syncwarp(gm);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) v[k1] = E[k1 * ES + j];
+    __syncwarp(gm);
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) E[(kb - 16) * ES + n1] = B[n1];
+    __syncwarp(gm);
+#pragma unroll
+    for (int k1 = 16; k1 < 32; ++k1) v[k1] = E[(k1 - 16) * ES + j];
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+      E[ka * ES + n1] = A[n1];
+      E[kb * ES + n1] = B[n1];
+    }
+    __syncwarp(gm);
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) v[k1] = E[k1 * ES + j];
   }
-  __syncwarp(gm);
-#pragma unroll
-  for (int k1 = 0; k1 < 32; ++k1) v[k1] = E[k1 * ES + j];
   idft<32, 5>(v);
 }
 
@@ -188,14 +218,21 @@ __device__ __forceinline__ void cluster_arrive() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
+// CL CTAs per cluster.  8: 256 threads, two row pairs and two columns per group, one
+// CTA per SM.  16: 256 threads, one row pair and one column per group, the exchange
+// in two rounds, 107 KB of shared memory and at most 128 registers so that two CTAs
+// (of different clusters) share an SM and overlap their loads and transforms.
 template <int CL>
 struct PlaneShape {
   static constexpr int CPR = 256 / CL;          // kz columns per CTA (+ kz = 256 on rank 0)
   static constexpr int RPR = NM / CL;           // rows per CTA
-  static constexpr int NG = CPR / 2;            // 16-thread groups per CTA
+  static constexpr int NG = 16;                 // 16-thread groups per CTA
   static constexpr int NT = NG * 16;            // threads per CTA
-  static constexpr int ITER = 2;                // row pairs and columns per group
-  static constexpr size_t SMEM = sizeof(float2) * (EX + (size_t)(CPR + 1) * CS + (size_t)NG * EX);
+  static constexpr int ITER = CPR / NG;         // row pairs (RPR / 2) and columns per group
+  static constexpr bool HALF = CL == 16;        // half-size exchange buffers
+  static constexpr int EXG = HALF ? EX / 2 : EX;
+  static constexpr int MINB = CL == 16 ? 2 : 1; // CTAs per SM the register budget allows
+  static constexpr size_t SMEM = sizeof(float2) * (EX + (size_t)(CPR + 1) * CS + (size_t)NG * EXG);
 };
 
 // ---------------------------------------------------------------------------
@@ -203,7 +240,7 @@ struct PlaneShape {
 // grid (CL, 512, nslots), cluster (CL, 1, 1)
 // ---------------------------------------------------------------------------
 template <int CL>
-__global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
+__global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
     fft512_plane_fwd(float *__restrict__ data, long long slot_reals, const float2 *__restrict__ gtw) {
   using S = PlaneShape<CL>;
   extern __shared__ float4 smem4[];
@@ -217,7 +254,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
   const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
   const unsigned gm = 0xFFFFu << (tid & 16);
   const int ka = j, kb = col_b(j);
-  float2 *Eg = E + g * EX;
+  float2 *Eg = E + g * S::EXG;
   for (int i = tid; i < EX; i += S::NT) TW[i] = gtw[i];
   __syncthreads();
   // R2C along z, two rows at a time; the row spectra go to the owners of their kz
@@ -228,7 +265,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
     float2 v[32], A[16], B[16];
 #pragma unroll
     for (int m = 0; m < 32; ++m) v[m] = make_float2(ra[16 * m + j], rb[16 * m + j]);
-    fwd512(v, A, B, j, gm, TW, Eg);
+    fwd512<S::HALF>(v, A, B, j, gm, TW, Eg);
     if (it == 0) cluster_wait();
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) {
@@ -255,7 +292,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
     float2 v[32], A[16], B[16];
 #pragma unroll
     for (int m = 0; m < 32; ++m) v[m] = col[16 * m + j];
-    fwd512(v, A, B, j, gm, TW, Eg);
+    fwd512<S::HALF>(v, A, B, j, gm, TW, Eg);
     if (r == 0 && kl == 0) {
       float2 *col256 = C + S::CPR * CS;
 #pragma unroll
@@ -292,7 +329,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
 // plane pass, inverse: C2C along y (inverse), C2R along z
 // ---------------------------------------------------------------------------
 template <int CL>
-__global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
+__global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
     fft512_plane_inv(float *__restrict__ data, long long slot_reals, const float2 *__restrict__ gtw) {
   using S = PlaneShape<CL>;
   extern __shared__ float4 smem4[];
@@ -306,7 +343,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
   const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
   const unsigned gm = 0xFFFFu << (tid & 16);
   const int ka = j, kb = col_b(j);
-  float2 *Eg = E + g * EX;
+  float2 *Eg = E + g * S::EXG;
   for (int i = tid; i < EX; i += S::NT) TW[i] = gtw[i];
   // coalesced read of this CTA's kz range
   for (int e = tid; e < 256 * S::CPR; e += S::NT) {
@@ -337,7 +374,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
         B[k2] = pack2(B[k2], col256[kb + 32 * k2]);
       }
     }
-    inv512(A, B, v, j, gm, TW, Eg);
+    inv512<S::HALF>(A, B, v, j, gm, TW, Eg);
 #pragma unroll
     for (int m = 0; m < 32; ++m) col[16 * m + j] = v[m];
   }
@@ -373,7 +410,7 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
       A[0] = make_float2(ca[0].x, ca[0].z);
       A[8] = make_float2(ca[0].y, ca[0].w);
     }
-    inv512(A, B, v, j, gm, TW, Eg);
+    inv512<S::HALF>(A, B, v, j, gm, TW, Eg);
     float *ra = plane + (long long)ya * ROWF, *rb = ra + ROWF;
 #pragma unroll
     for (int m = 0; m < 32; ++m) {
@@ -386,17 +423,26 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, 1)
 }
 
 // ---------------------------------------------------------------------------
-// x pass: C2C along x for tiles of 16 kz columns of one ky
+// x pass: C2C along x for tiles of TC kz columns of one ky
 // mode 0 forward, 1 inverse, 2 forward -> * conj(D) s W^-2 -> inverse
-// Persistent: one CTA per SM walks the tiles; each tile is copied into shared
+// Persistent: a few CTAs per SM walk the tiles; each tile is copied into shared
 // memory with cp.async while the previous one is transformed (mode 2 also
 // prefetches the matching D tile), so loads overlap the FFT work.
-// block 256 (16 groups, one column each)
+// block TC * 16 (TC groups, one column each)
 // ---------------------------------------------------------------------------
-constexpr int XT = 256;
-constexpr int KZT = (HZ + 15) / 16;        // 17 kz tiles per ky
-constexpr size_t kXSmem01 = sizeof(float2) * (EX + 2 * 16 * XS);
-constexpr size_t kXSmem2 = sizeof(float2) * (EX + 3 * 16 * XS) + sizeof(float) * NM;
+constexpr int XTC = 16;                    // kz columns per tile (128-byte row segments; 8 measured slower)
+template <int TC>
+struct XShape {
+  static constexpr int NT = TC * 16;                   // threads
+  static constexpr int KZT = (HZ + TC - 1) / TC;       // kz tiles per ky
+  // tile row stride (float2): >= EX for the exchange buffer; TC * XS + x spreads the
+  // tile writes of a half-warp (16 / TC rows of x) over distinct banks
+  static constexpr int XS = TC == 16 ? 545 : 546;
+  static constexpr size_t SMEM01 = sizeof(float2) * (EX + 2 * TC * XS);
+  static constexpr size_t SMEM2 = sizeof(float2) * (EX + 3 * TC * XS) + sizeof(float) * NM;
+  static constexpr int PER_SM01 = TC == 16 ? 1 : 3;   // CTAs per SM the grid is sized for
+  static constexpr int PER_SM2 = TC == 16 ? 1 : 2;
+};
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -413,49 +459,53 @@ struct XTile {
   int slot, ky, kz0, nvalid;
 };
 
+template <int TC>
 __device__ __forceinline__ XTile x_tile(long long t) {
   XTile r;
-  const int kzt = (int)(t % KZT);
-  const long long u = t / KZT;
+  const int kzt = (int)(t % XShape<TC>::KZT);
+  const long long u = t / XShape<TC>::KZT;
   r.ky = (int)(u % NM);
   r.slot = (int)(u / NM);
-  r.kz0 = kzt * 16;
-  r.nvalid = HZ - r.kz0 < 16 ? HZ - r.kz0 : 16;
+  r.kz0 = kzt * TC;
+  r.nvalid = HZ - r.kz0 < TC ? HZ - r.kz0 : TC;
   r.off = (long long)r.ky * HZ + r.kz0;
   return r;
 }
 
 // asynchronous copy of one tile: T[c][x] = src[x][c], c < nvalid; one commit group
+template <int TC>
 __device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid) {
   const long long xs = (long long)NM * HZ;
-  for (int e = threadIdx.x; e < NM * 16; e += XT) {
-    const int x = e >> 4, c = e & 15;
-    if (c < nvalid) cp_async8(T + c * XS + x, src + x * xs + c);
+  for (int e = threadIdx.x; e < NM * TC; e += XShape<TC>::NT) {
+    const int x = e / TC, c = e % TC;
+    if (c < nvalid) cp_async8(T + c * XShape<TC>::XS + x, src + x * xs + c);
   }
   cp_async_commit();
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(XT, 1)
+template <int MODE, int TC>
+__global__ void __launch_bounds__(XShape<TC>::NT, 1)
     fft512_x(float2 *__restrict__ data, long long slot_cplx, long long ntiles, const float2 *__restrict__ gtw,
              const float2 *__restrict__ D, const double *__restrict__ scale, const float *__restrict__ invw) {
+  using X = XShape<TC>;
+  constexpr int XS_ = X::XS;
   extern __shared__ float4 smem4[];
   float2 *TW = (float2 *)smem4;   // [32][ES]
-  float2 *buf0 = TW + EX;         // tile buffers [16][XS]: column c, x = 0..511; double as exchange buffers
-  float2 *buf1 = buf0 + 16 * XS;
-  float2 *buf2 = buf1 + 16 * XS;  // mode 2: buf1 holds D, data alternates between buf0 and buf2
-  float *W1 = (float *)(buf2 + 16 * XS);   // mode 2: per-axis 1/W (compensation), when given
+  float2 *buf0 = TW + EX;         // tile buffers [TC][XS_]: column c, x = 0..511; double as exchange buffers
+  float2 *buf1 = buf0 + TC * XS_;
+  float2 *buf2 = buf1 + TC * XS_;  // mode 2: buf1 holds D, data alternates between buf0 and buf2
+  float *W1 = (float *)(buf2 + TC * XS_);   // mode 2: per-axis 1/W (compensation), when given
   const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
   const unsigned gm = 0xFFFFu << (tid & 16);
   const int ka = j, kb = col_b(j);
   const long long xs = (long long)NM * HZ;
   long long t = blockIdx.x;
-  XTile cur = x_tile(t);
-  x_tile_issue(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid);
-  if (MODE == 2) x_tile_issue(buf1, D + cur.off, cur.nvalid);
-  for (int i = tid; i < EX; i += XT) TW[i] = gtw[i];
+  XTile cur = x_tile<TC>(t);
+  x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid);
+  if (MODE == 2) x_tile_issue<TC>(buf1, D + cur.off, cur.nvalid);
+  for (int i = tid; i < EX; i += X::NT) TW[i] = gtw[i];
   if (MODE == 2 && invw)
-    for (int i = tid; i < NM; i += XT) W1[i] = invw[i];
+    for (int i = tid; i < NM; i += X::NT) W1[i] = invw[i];
   float2 *A = buf0;
   for (; t < ntiles; t += gridDim.x) {
     if (MODE == 2)
@@ -465,13 +515,13 @@ __global__ void __launch_bounds__(XT, 1)
     __syncthreads();
     const long long tn = t + gridDim.x;
     const bool has_next = tn < ntiles;
-    const XTile nxt = x_tile(has_next ? tn : t);
+    const XTile nxt = x_tile<TC>(has_next ? tn : t);
     float2 *Anext = MODE == 2 ? (A == buf0 ? buf2 : buf0) : (A == buf0 ? buf1 : buf0);
     if (has_next)
-      x_tile_issue(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid);
+      x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid);
     else
       cp_async_commit();
-    float2 *col = A + g * XS;
+    float2 *col = A + g * XS_;
     float2 v[32], As[16], Bs[16];
     if (MODE == 1) {
 #pragma unroll
@@ -487,7 +537,7 @@ __global__ void __launch_bounds__(XT, 1)
     if (MODE == 2) {
       cp_async_wait<1>();         // this tile's D
       __syncthreads();
-      const float2 *dcol = buf1 + g * XS;
+      const float2 *dcol = buf1 + g * XS_;
       const float s = (float)scale[cur.slot];
       const float cyz = invw ? W1[cur.ky] * W1[cur.kz0 + (g < cur.nvalid ? g : 0)] : 1.f;
 #pragma unroll
@@ -504,7 +554,7 @@ __global__ void __launch_bounds__(XT, 1)
       }
       __syncthreads();            // every group is done with D: prefetch the next one
       if (has_next)
-        x_tile_issue(buf1, D + nxt.off, nxt.nvalid);
+        x_tile_issue<TC>(buf1, D + nxt.off, nxt.nvalid);
       else
         cp_async_commit();
     }
@@ -523,9 +573,9 @@ __global__ void __launch_bounds__(XT, 1)
     }
     __syncthreads();
     float2 *base = data + (long long)cur.slot * slot_cplx + cur.off;
-    for (int e = tid; e < NM * 16; e += XT) {
-      const int x = e >> 4, c = e & 15;
-      if (c < cur.nvalid) base[x * xs + c] = A[c * XS + x];
+    for (int e = tid; e < NM * TC; e += X::NT) {
+      const int x = e / TC, c = e % TC;
+      if (c < cur.nvalid) base[x * xs + c] = A[c * XS_ + x];
     }
     cur = nxt;
     A = Anext;
@@ -615,11 +665,12 @@ int sm_count(int dev) {
 template <int MODE>
 cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const float *D, const double *scale,
                   const float *invw, cudaStream_t st) {
+  using X = XShape<XTC>;
   int dev = 0;
   cudaGetDevice(&dev);
-  const long long ntiles = (long long)KZT * NM * n;
-  const long long grid = std::min<long long>(ntiles, sm_count(dev));
-  fft512_x<MODE><<<(unsigned)grid, XT, MODE == 2 ? kXSmem2 : kXSmem01, st>>>(
+  const long long ntiles = (long long)X::KZT * NM * n;
+  const long long grid = std::min<long long>(ntiles, (long long)sm_count(dev) * (MODE == 2 ? X::PER_SM2 : X::PER_SM01));
+  fft512_x<MODE, XTC><<<(unsigned)grid, X::NT, MODE == 2 ? X::SMEM2 : X::SMEM01, st>>>(
       (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw);
   return cudaGetLastError();
 }
@@ -639,13 +690,14 @@ cudaError_t native_fft_prepare() {
   if (!attrs[dev]) {
     if ((e = plane_attrs<8>()) != cudaSuccess) return e;
     if ((e = plane_attrs<16>()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem01)) !=
+    using X = XShape<XTC>;
+    if ((e = cudaFuncSetAttribute(fft512_x<0, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM01)) !=
         cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem01)) !=
+    if ((e = cudaFuncSetAttribute(fft512_x<1, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM01)) !=
         cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmem2)) !=
+    if ((e = cudaFuncSetAttribute(fft512_x<2, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM2)) !=
         cudaSuccess)
       return e;
     attrs[dev] = true;

@@ -105,3 +105,21 @@ def test_streamed_ranges_with_library_kernels(env, cat, mode):
         ctx.set_field_chunk(0)
     check_multipoles(got["pk"], ref["pk"], "pk", label=f"mode {mode} ranges P: ")
     check_multipoles(got["xi"], ref["xi"], "xi", label=f"mode {mode} ranges xi: ")
+
+
+def test_xi_only_ranges_of_two(env, cat):
+    # a small-memory midpoint request (xi only, order 1, g fields two at a time: four meshes on
+    # the device) through cuFFT and through the hybrid backend's fused convolution x pass
+    torch, pkg, lib, ctx = env
+    p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=4, los="midpoint",
+                        order=1, compensate=True, precision=32)
+    redges = np.arange(10.0, 190.01, 10.0)
+    out = {}
+    ctx.set_field_chunk(2)
+    try:
+        for mode in (0, 4):
+            assert lib.bym_set_fft_backend(ctx._h, mode) == 0
+            out[mode] = ctx.xi_multipoles(cat.gal, cat.ran, p, redges, ran_nbar=cat.ran_nbar)
+    finally:
+        ctx.set_field_chunk(0)
+    check_multipoles(out[4]["xi"], out[0]["xi"], "xi", label="xi-only ranges of two: ")
