@@ -144,8 +144,8 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
                          double *xi, double *r_mean, int64_t *n_cells, void *cuda_stream);
 
 /* Compile (without running) the runtime-specialised kernels for these
- * parameters (for the midpoint forms also the kernels of streamed field
- * ranges, see bym_set_field_chunk); works without a GPU.  Used by build
+ * parameters (for the midpoint forms and the bisector also the kernels of
+ * field ranges, see bym_set_field_chunk); works without a GPU.  Used by build
  * checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 
@@ -158,18 +158,25 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 int bym_shot_noise(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
                    double *shot);
 
-/* Memory bound for the midpoint forms (Sec. 2.2: the g^alpha_{J M} functions
- * of eq. g-JM-form are the largest memory item, 145 meshes at ell_max = 4,
- * order 4).  The paper keeps every g field resident; the library can instead
- * generate, convolve and consume them in ranges of at most max_fields fields.
- * H_{ell m} of eq. FFT-midpoint and the xi shell sums of eq.
- * xi-parity-all-estimator are sums over the fields, so the ranges add up to
- * the same result.  A request then holds two delta meshes, one range and the
- * 15 H meshes.  max_fields = 0 (the default): ranges only when the whole set
- * does not fit the context's budget (or, with no budget, the device memory
- * free at the start of the request), sized to fit; > 0: always, with ranges
- * of that many fields.  No effect on the other lines of sight.  Returns
- * BYM_E_INVAL for max_fields < 0. */
+/* Memory bound (Sec. 2.2 and Sec. 6: the g^alpha_{J M} functions of eq.
+ * g-JM-form, 145 meshes at ell_max = 4, order 4, and the bisector's F[Y_J^M
+ * delta] transforms are the largest memory items).  The paper keeps every
+ * field resident; the library can instead hold them in ranges of at most
+ * max_fields fields.
+ *   Midpoint forms: H_{ell m} of eq. FFT-midpoint and the xi shell sums of
+ *   eq. xi-parity-all-estimator are sums over the fields, so the ranges are
+ *   generated, convolved and consumed one after another and add up to the same
+ *   result; a request holds two delta meshes, one range and the 15 H meshes.
+ *   Bisector: the bilinear sum of eq. bisector-pk-fft runs over field pairs,
+ *   so two blocks are resident and every block pair adds its share; a block is
+ *   transformed again for every earlier block (nb + nb (nb - 1) / 2 block
+ *   transforms for nb blocks); a request holds delta, two blocks and, for xi,
+ *   the 15 X meshes.
+ * max_fields = 0 (the default): ranges only when the whole set does not fit
+ * the context's budget (or, with no budget, the device memory free at the
+ * start of the request, less room for the FFT work area), sized to fit;
+ * > 0: always, with ranges of that many fields.  No effect on the Yamamoto
+ * line of sight.  Returns BYM_E_INVAL for max_fields < 0. */
 int bym_set_field_chunk(bym_ctx *ctx, int max_fields);
 
 /* FFT backend of ctx.  The library has its own FP32 3D FFT kernels for

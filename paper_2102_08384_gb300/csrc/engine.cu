@@ -204,8 +204,10 @@ size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, b
   const size_t esz = p->precision == 64 ? 8 : 4;
   const size_t slot = N * N * (N + 2) * esz;
   const size_t nf = (size_t)n_fields(p);
-  const size_t slots = (chunk > 0 && is_midpoint(p) ? 2 + std::min(nf, (size_t)chunk) : 1 + nf) +
-                       (size_t)n_extra_slots(p, want_pk, want_xi);
+  size_t fslots = 1 + nf;                                   // delta + every field
+  if (chunk > 0 && is_midpoint(p)) fslots = 2 + std::min(nf, (size_t)chunk);          // two deltas, a range
+  if (chunk > 0 && p->los == BYM_LOS_BISECTOR) fslots = 1 + 2 * std::min(nf, (size_t)chunk);  // two blocks
+  const size_t slots = fslots + (size_t)n_extra_slots(p, want_pk, want_xi);
   size_t cats = 0;
   if (!cats_on_device) cats = (size_t)(std::max<int64_t>(n_gal, 0) + std::max<int64_t>(n_ran, 0)) * 20;
   return slots * slot + cats + (1 << 20);
@@ -548,7 +550,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   const bool cats_dev = rq.gal->on_device && (!rq.ran || rq.ran->on_device);
   const int64_t ngal = rq.gal->n, nran = rq.ran ? rq.ran->n : 0;
   int chunk = 0;
-  if (is_midpoint(p)) {
+  if (is_midpoint(p) || p->los == BYM_LOS_BISECTOR) {
     if (c->field_chunk > 0) {
       chunk = std::min(c->field_chunk, nf);
     } else {
@@ -650,7 +652,9 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
 
   // mesh slots: [0] delta, [1, 1+nf) fields, [1+nf, 1+nf+nextra) H or X;
   // streamed: [0] delta, [1] a real copy of delta, [2, 2+chunk) one field range, then H
-  const int fbase = chunk ? 2 : 1, nfs = chunk ? chunk : nf, xbase = fbase + nfs;
+  const bool bis_blocks = chunk && p->los == BYM_LOS_BISECTOR;
+  const int fbase = (chunk && !bis_blocks) ? 2 : 1;
+  const int nfs = !chunk ? nf : (bis_blocks ? 2 * chunk : chunk), xbase = fbase + nfs;
   const int nslots = xbase + nextra;
   T *slots = nullptr;
   TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
@@ -707,7 +711,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
                       slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
-  } else if (chunk) {
+  } else if (chunk && is_midpoint(p)) {
     // delta's spectrum in slot 0, its real copy in slot 1 feeds gen_fields of every range
     CUDA_TRY(cudaMemcpyAsync(slot_r(1), slot_r(0), slot_bytes, cudaMemcpyDeviceToDevice, st));
     TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
@@ -758,6 +762,44 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
+    }
+  } else if (bis_blocks) {
+    // blocks A (slots 1..) and B (slots 1 + chunk..); every block pair a <= b adds its
+    // share of the bilinear sum: block a transformed once, every later block once per a
+    const int nb = (int)CK->ranges.size();
+    auto make_block = [&](int q, int base) -> int {
+      const int q0 = CK->ranges[q].first, nq = CK->ranges[q].second - q0;
+      {
+        ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * n3 * esz);
+        CUDA_TRY(cudaMemsetAsync(slot_r(base), 0, (size_t)nq * slot_bytes, st));
+        CUDA_TRY(launch(CK->gen[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_gen), 256, 0, st,
+                        (const T *)slot_r(0), slot_r(base), slot_reals, N, p->box_lo[0], p->box_lo[1],
+                        p->box_lo[2], h, inv_r0));
+      }
+      return fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, base, nq, tn);
+    };
+    T2 *xout = want_xi ? slot_c(xbase) : nullptr;
+    int accumulate = 0;
+    for (int a = 0; a < nb; ++a) {
+      TRY(make_block(a, 1));
+      for (int b = a; b < nb; ++b) {
+        if (b > a) TRY(make_block(b, 1 + chunk));
+        const double nfa = CK->ranges[a].second - CK->ranges[a].first;
+        const double nfb = b > a ? CK->ranges[b].second - CK->ranges[b].first : 0.0;
+        ProfScope ps(c, st, "kcontract_bisector_pair", (nfa + nfb + (want_xi ? 2.0 * nlm : 0.0)) * cplx);
+        CUDA_TRY(launch(CK->pair[(size_t)a * nb + b], gk, 256, smk, st, (const T2 *)slot_c(1),
+                        (const T2 *)slot_c(b > a ? 1 + chunk : 1), cslot, N, (const int *)kg->lut, nbk, ksum, xout,
+                        cslot, (const T *)invw, accumulate));
+        accumulate = 1;
+      }
+    }
+    if (want_xi) {
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, xbase, nlm, tn));
+      const int Lc = rg->full ? N : 2 * rg->jm + 1;
+      ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nlm * esz);
+      CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
+                      (const T *)slot_r(xbase), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
+                      1.0 / ((double)N * N * N), tscale));
     }
   } else {
     TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf, tn));
@@ -1193,7 +1235,7 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len) {
   }
   std::vector<char> cubin;
   bool ok = !src.empty() && compile_cubin(src, cubin, lg);
-  if (ok && is_midpoint(p)) {   // the streamed-range kernels too (ranges of 16 fields)
+  if (ok && (is_midpoint(p) || p->los == BYM_LOS_BISECTOR)) {   // the field-range kernels too (16 fields)
     src.clear();
     try {
       src = generate_chunk_source(JitKey{p->los, p->ell_max, order_key(p), p->precision}, 16, nullptr);

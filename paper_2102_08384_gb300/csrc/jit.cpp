@@ -322,6 +322,77 @@ int emit_xi_lag(std::ostream &o, const char *name, const JitKey &key, int f0, in
   return jlag;
 }
 
+// Bisector contraction for the field pairs (i, j), i <= j, with i in [a0, a1) read
+// from FA and j in [b0, b1) read from FB (slot i - a0, j - b0): adds that share of
+// X_{lm}(k) = sum c Re(conj F_i F_j) to the P shell sums and, when xout is given,
+// writes (accumulate = 0) or adds (accumulate = 1) it to X_{lm}(k).
+void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, int a0, int a1, int b0, int b1) {
+  const bool f32 = key.prec == 32;
+  const int L = key.ell_max, NL = L / 2 + 1, n_lm = n_even_lm(L);
+  o << "extern \"C\" __global__ void __launch_bounds__(256) " << name
+    << "(const real2* __restrict__ FA, const real2* __restrict__ FB, long long cslot, int N,"
+       " const int* __restrict__ lut, int nbins, double* __restrict__ gsum, real2* __restrict__ xout,"
+       " long long xslot, const real* __restrict__ invw, int accumulate) {\n";
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n  const int H = N / 2 + 1;\n";
+  emit_bin_loop_head(o, "(long long)N * N * H");
+  o << "    int bin = -1; real v[" << NL << "] = {";
+  for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "(real)0";
+  o << "};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+  o << "      const int ix = (int)(row / N), iy = (int)(row % N);\n";
+  o << "      const int nx = bym_lab(ix, N), ny = bym_lab(iy, N), nz = (iz == N / 2) ? -N / 2 : iz;\n";
+  o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
+  o << "      bin = lut[n2];\n";
+  o << "      if (xout || bin >= 0) {\n";
+  o << "        real cc = (real)1;\n";
+  o << "        if (invw) { cc = invw[ix] * invw[iy] * invw[iz]; cc = cc * cc; }\n";
+  for (int i = 0; i < n_lm; ++i) o << "        real X" << i << " = (real)0;\n";
+  std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> by_pair;
+  for (auto &t : bisector_terms(key.ell_max, key.K))
+    if (t.i >= a0 && t.i < a1 && t.j >= b0 && t.j < b1) by_pair[{t.i, t.j}].push_back({t.lm, t.c});
+  std::set<int> ua, ub;
+  for (auto &kv : by_pair) {
+    ua.insert(kv.first.first);
+    ub.insert(kv.first.second);
+  }
+  const bool same = a0 == b0;
+  for (int i : ua) o << "        const real2 f" << i << " = FA[" << i - a0 << "LL * cslot + m];\n";
+  for (int j : ub)
+    if (!(same && ua.count(j)))
+      o << "        const real2 f" << j << " = " << (same ? "FA[" : "FB[") << j - b0 << "LL * cslot + m];\n";
+  for (auto &kv : by_pair) {
+    const int i = kv.first.first, j = kv.first.second;
+    o << "        { const real q = f" << i << ".x * f" << j << ".x + f" << i << ".y * f" << j << ".y;";
+    for (auto &lc : kv.second) o << " X" << lc.first << " += " << lit(lc.second, f32) << " * q;";
+    o << " }\n";
+  }
+  for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
+  o << "        if (xout) {\n";
+  for (int i = 0; i < n_lm; ++i)
+    o << "          { real2 xv; xv.x = X" << i << " + (accumulate ? xout[" << i << "LL * xslot + m].x : (real)0);"
+      << " xv.y = (real)0; xout[" << i << "LL * xslot + m] = xv; }\n";
+  o << "        }\n";
+  o << "        if (bin >= 0) {\n";
+  o << "          const real w = (iz == 0 || iz == N / 2) ? (real)1 : (real)2;\n";
+  o << "          const real r2 = (real)n2; const real ir = bym_rsqrt(r2);\n";
+  o << "          const real ux = nx * ir, uy = ny * ir, uz = nz * ir; const real zm = (real)1;\n";
+  {
+    std::ostringstream yy;
+    emit_ylm(yy, L, f32, "yk", "ux", "uy", "uz", "zm");
+    std::istringstream is(yy.str());
+    std::string line;
+    while (std::getline(is, line)) o << "        " << line << "\n";
+  }
+  for (int l = 0; l <= L; l += 2) {
+    o << "          { real T = (real)0;";
+    for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << even_lm_index(l, mu) << ";";
+    o << " v[" << l / 2 << "] = w * T; }\n";
+  }
+  o << "        }\n      }\n    }\n";
+  o << "    bym_bin_flush<" << NL << ", real>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+}
+
 }  // namespace
 
 std::string generate_source(const JitKey &key, KernelSet *meta) {
@@ -468,6 +539,17 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
   std::ostringstream o;
   o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
+  if (key.los == 2) {   // bisector: field blocks and one contraction per block pair a <= b
+    const int nb = (int)ranges.size();
+    for (int a = 0; a < nb; ++a) {
+      emit_gen_fields(o, ("gen_fields_c" + std::to_string(a)).c_str(), F.list, ranges[a].first, ranges[a].second);
+      for (int b = a; b < nb; ++b)
+        emit_kcontract_pair(o, ("kcontract_p" + std::to_string(a) + "_" + std::to_string(b)).c_str(), key,
+                            ranges[a].first, ranges[a].second, ranges[b].first, ranges[b].second);
+    }
+    if (meta) meta->ranges = ranges;
+    return o.str();
+  }
   const auto terms = midpoint_terms(key.ell_max, key.K, even);
   for (size_t q = 0; q < ranges.size(); ++q) {
     const std::string sfx = "_c" + std::to_string(q);
@@ -552,8 +634,8 @@ std::shared_ptr<KernelSet> get_kernels(const JitKey &key, std::string &err) {
 std::shared_ptr<ChunkSet> get_chunk_kernels(const JitKey &key, int max_fields, std::string &err) {
   static std::mutex mu;
   static std::map<std::pair<JitKey, int>, std::shared_ptr<ChunkSet>> cache;
-  if ((key.los != 1 && key.los != 3) || max_fields < 1) {
-    err = "field chunks apply to the midpoint forms only";
+  if (key.los == 0 || max_fields < 1) {
+    err = "field ranges apply to the midpoint forms and the bisector";
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(mu);
@@ -576,6 +658,28 @@ std::shared_ptr<ChunkSet> get_chunk_kernels(const JitKey &key, int max_fields, s
   if (cudaLibraryLoadData(&cs->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
     err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(cudaGetLastError());
     return nullptr;
+  }
+  if (key.los == 2) {
+    const int nb = (int)cs->ranges.size();
+    cs->pair.assign((size_t)nb * nb, nullptr);
+    for (int a = 0; a < nb; ++a) {
+      std::vector<std::string> names = {"gen_fields_c" + std::to_string(a)};
+      for (int b = a; b < nb; ++b) names.push_back("kcontract_p" + std::to_string(a) + "_" + std::to_string(b));
+      for (size_t n = 0; n < names.size(); ++n) {
+        cudaKernel_t k = nullptr;
+        if (cudaLibraryGetKernel(&k, cs->lib, names[n].c_str()) != cudaSuccess) {
+          cudaGetLastError();
+          err = "generated block module is missing " + names[n];
+          return nullptr;
+        }
+        if (n == 0)
+          cs->gen.push_back(k);
+        else
+          cs->pair[(size_t)a * nb + a + (n - 1)] = k;
+      }
+    }
+    cache[{key, max_fields}] = cs;
+    return cs;
   }
   for (size_t q = 0; q < cs->ranges.size(); ++q) {
     const std::string sfx = "_c" + std::to_string(q);

@@ -34,13 +34,16 @@ struct KernelSet {
   cudaKernel_t kcontract = nullptr, kcontract_x = nullptr, mid_combine = nullptr, xi_lag = nullptr;
 };
 
-// Midpoint forms under a memory bound: the g fields in ranges of at most
-// max_fields, each with its own gen_fields / mid_combine (accumulating into
-// H after the first range) / xi_lag (adding its share of the shell sums).
+// Field sets under a memory bound.  Midpoint forms: the g fields in ranges of at
+// most max_fields, each with its own gen_fields / mid_combine (accumulating into H
+// after the first range) / xi_lag (adding its share of the shell sums).  Bisector:
+// the fields in blocks of at most max_fields, gen_fields per block and one
+// contraction per block pair a <= b (pair[a * nblocks + b]).
 struct ChunkSet {
   std::vector<std::pair<int, int>> ranges;   // field ranges [f0, f1) in slot order
   cudaLibrary_t lib = nullptr;
-  std::vector<cudaKernel_t> gen, comb, xi;   // one of each per range
+  std::vector<cudaKernel_t> gen, comb, xi;   // one of each per range (bisector: gen only)
+  std::vector<cudaKernel_t> pair;            // bisector block-pair contractions
 };
 
 // Source text for a configuration (exposed for build checks).

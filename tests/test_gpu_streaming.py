@@ -1,9 +1,11 @@
-"""Midpoint g fields streamed in ranges (bym_set_field_chunk) against the
-resident path and against the FP64 oracle.
+"""Field sets under a memory bound (bym_set_field_chunk) against the resident
+path and against the FP64 oracle.
 
-H_{l m} (eq. FFT-midpoint) and the xi shell sums (eq. xi-parity-all-estimator)
-are sums over the g fields, so any partition of the fields into ranges gives
-the same estimator up to rounding order."""
+Midpoint: H_{l m} (eq. FFT-midpoint) and the xi shell sums (eq.
+xi-parity-all-estimator) are sums over the g fields, so any partition of the
+fields into ranges gives the same estimator up to rounding order.  Bisector:
+the bilinear sum of eq. bisector-pk-fft runs over field pairs, so summing the
+pairs block pair by block pair gives it too."""
 import math
 
 import numpy as np
@@ -89,6 +91,60 @@ def test_budget_turns_on_ranges(pkg, cap):
         finally:
             tiny.close()
     assert ei.value.code == -3
+    small.close()
+    check_multipoles(parts["pk"], whole["pk"], "pk")
+    check_multipoles(parts["xi"], whole["xi"], "xi")
+
+
+# ---------------------------------------------------------------- bisector blocks
+@pytest.mark.parametrize("K,N,block", [(4, 40, 16), (4, 32, 49), (2, 36, 5), (6, 32, 20), (2, 32, 1)])
+def test_bisector_blocks_match_resident_fp32(pkg, cap, K, N, block):
+    kedges, redges = _bins(cap, N)
+    p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=4, los="bisector", order=K,
+                        precision=32, assign=3, compensate=True)
+    ctx = pkg.Context(0)
+    whole = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
+    pk_only = ctx.pk_multipoles(cap.gal, cap.ran, p, kedges, ran_nbar=cap.ran_nbar)
+    ctx.set_field_chunk(block)
+    parts = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
+    parts_pk = ctx.pk_multipoles(cap.gal, cap.ran, p, kedges, ran_nbar=cap.ran_nbar)
+    ctx.close()
+    check_multipoles(parts["pk"], whole["pk"], "pk", label=f"bisector K={K} block={block} P: ")
+    check_multipoles(parts["xi"], whole["xi"], "xi", label=f"bisector K={K} block={block} xi: ")
+    check_multipoles(parts_pk["pk"], pk_only["pk"], "pk", label=f"bisector K={K} block={block} P only: ")
+
+
+def test_bisector_blocks_match_oracle_fp64(pkg):
+    cube = uniform_cube_catalog(seed=0, n_gal=4096, n_ran=40960, side=500.0, distance=1000.0)
+    N = 32
+    kedges = np.linspace(0.0, math.pi / (cube.box_len / N), 9)
+    redges = np.linspace(0.0, 200.0, 9)
+    p = pkg.make_params(box_lo=cube.box_lo, box_len=cube.box_len, n_mesh=N, ell_max=4, los="bisector", order=2,
+                        precision=64, assign=3, compensate=True)
+    ctx = pkg.Context(0)
+    ctx.set_field_chunk(7)       # 36 fields: blocks of 7, 7, 7, 7, 7, 1
+    got = ctx.pk_xi_multipoles(cube.gal, cube.ran, p, kedges, redges, ran_nbar=cube.ran_nbar)
+    ctx.close()
+    kw = dict(N=N, box_lo=cube.box_lo, box_len=cube.box_len, assign=3, ell_max=4, los="bisector", order=2,
+              compensate=True)
+    want_p = E.pk_multipoles(cube.gal, cube.ran, cube.ran_nbar, kedges=kedges, **kw)
+    want_x = E.xi_multipoles(cube.gal, cube.ran, cube.ran_nbar, redges=redges, **kw)
+    check_multipoles(got["pk"], want_p["pk"], "pk", 1e-10, 1e-10, "bisector blocks P: ")
+    check_multipoles(got["xi"], want_x["xi"], "xi", 1e-10, 1e-10, "bisector blocks xi: ")
+
+
+def test_budget_turns_on_bisector_blocks(pkg, cap):
+    N = 40
+    kedges, redges = _bins(cap, N)
+    p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=4, los="bisector", order=4,
+                        precision=32)
+    full = pkg.footprint(p, len(cap.gal), len(cap.ran))      # 1 + 49 + 15 slots
+    slot = N * N * (N + 2) * 4
+    ctx = pkg.Context(0)
+    whole = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
+    ctx.close()
+    small = pkg.Context(0, hbm_budget_bytes=full - 25 * slot)  # room for blocks of 12 fields
+    parts = small.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
     small.close()
     check_multipoles(parts["pk"], whole["pk"], "pk")
     check_multipoles(parts["xi"], whole["xi"], "xi")
