@@ -267,6 +267,35 @@ int bym_serve_stats(bym_ctx *ctx, double stats[7]);
  * default budget for the call if none is running) and wait for all;
  * status[i] receives each request's return code. */
 int bym_batch_run(bym_ctx *ctx, int n, const bym_request *reqs, const bym_result *outs, int *status);
+/* Run n requests as one CUDA graph: host catalogs are first copied to the
+ * device, one request of every distinct shape (mesh, precision, LOS, ell_max,
+ * order, compensation, box, bins) runs uncaptured so that its kernels, bin
+ * tables, FFT plans and work area exist, then every request (and, for
+ * norm = 2, its random-random pass) is enqueued under stream capture on four
+ * parallel branches (as bym_batch_plan_create below), the graph is launched
+ * once, and the results are normalised on the host.  Suits many mocks of few shapes (the warm-up is paid once per shape
+ * and process).  The context's serving loop, if running, is not used.
+ * status[i] receives each request's return code; a failure of the capture or
+ * of the graph is reported for every request.  Returns the first error. */
+int bym_batch_graph(bym_ctx *ctx, int n, const bym_request *reqs, const bym_result *outs, int *status);
+
+/* The same batch kept as an instantiated graph for repeated launches (a
+ * persistent batch of mocks: new catalog contents written into the same
+ * device buffers, same sizes, between launches).  The graph has n_streams
+ * parallel branches (0: 4), each with its own engine (FFT plans, work area,
+ * bin tables, settings copied from ctx) like a serving slot; requests go to
+ * the least loaded branch, largest first, so their work overlaps on the GPU.
+ * create captures and instantiates (status[i]: each request's validation /
+ * warm-up outcome; the others are captured); launch runs the graph once and
+ * fills the result arrays given at creation (status may be NULL); destroy
+ * frees the plan (branch engines, device copies of host catalogs, pinned
+ * areas, graph).  Host catalogs are copied to the device once, at creation.
+ * The context must outlive the plan. */
+typedef struct bym_batch bym_batch;
+int bym_batch_plan_create(bym_ctx *ctx, int n, const bym_request *reqs, const bym_result *outs, int n_streams,
+                          bym_batch **plan, int *status);
+int bym_batch_plan_launch(bym_batch *plan, int *status);
+void bym_batch_plan_destroy(bym_batch *plan);
 
 /* Yamamoto P_ell(k) from field spectra the caller already holds, for callers
  * that cannot allocate device memory (an allocator owned by another framework,

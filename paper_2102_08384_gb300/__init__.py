@@ -96,6 +96,12 @@ def lib():
         L.bym_serve_stats.argtypes = [vp, dp]
         L.bym_batch_run.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(Result),
                                     ctypes.POINTER(ctypes.c_int)]
+        L.bym_batch_graph.argtypes = L.bym_batch_run.argtypes
+        L.bym_batch_plan_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(Result),
+                                            ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
+        L.bym_batch_plan_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.bym_batch_plan_destroy.argtypes = [vp]
+        L.bym_batch_plan_destroy.restype = None
         L.bym_profile_enable.argtypes = [vp, ctypes.c_int]
         L.bym_autotune.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, ctypes.c_char_p, ctypes.c_char_p,
                                    ctypes.c_size_t]
@@ -315,7 +321,15 @@ class Context:
         return {"count": int(a[0]), "p50_s": a[1], "p99_s": a[2], "run_p50_s": a[3], "run_p99_s": a[4],
                 "mean_queue_s": a[5], "peak_hbm_bytes": a[6]}
 
-    def batch_run(self, items):
+    def batch_graph(self, items):
+        """As batch_run, but all requests captured into one CUDA graph and launched once."""
+        return self.batch_run(items, graph=True)
+
+    def batch_plan(self, items, n_streams=0):
+        """A captured batch kept for repeated launches: BatchPlan.launch() returns the outputs."""
+        return BatchPlan(self, items, n_streams)
+
+    def batch_run(self, items, graph=False):
         """items: list of dicts with gal, ran, params, kedges, redges, ran_nbar.  Returns outputs."""
         n = len(items)
         reqs = (Request * n)()
@@ -328,7 +342,8 @@ class Context:
             outs.append(out)
             keeps.append(keep)
         status = (ctypes.c_int * n)()
-        rc = self._L.bym_batch_run(self._h, n, reqs, ress, status)
+        fn = self._L.bym_batch_graph if graph else self._L.bym_batch_run
+        rc = fn(self._h, n, reqs, ress, status)
         for i in range(n):
             if status[i] != BYM_OK:
                 raise BymError(status[i], f"batch item {i} failed")
@@ -353,6 +368,49 @@ class Context:
         self._check(self._L.bym_shot_noise(self._h, ctypes.byref(g), ctypes.byref(r) if r is not None else None,
                                            ctypes.byref(params), ctypes.byref(out)))
         return out.value
+
+
+class BatchPlan:
+    """A batch of requests captured once as a CUDA graph (bym_batch_plan_*).  Each launch()
+    recomputes every request from the current contents of its catalogs (device catalogs can
+    be rewritten in place between launches; host catalogs were copied at creation)."""
+
+    def __init__(self, ctx, items, n_streams=0):
+        self._ctx, self._L = ctx, ctx._L
+        n = len(items)
+        self._reqs = (Request * n)()
+        self._ress = (Result * n)()
+        self.outputs, self._keeps = [], []
+        for i, it in enumerate(items):
+            rq, rs, out, keep = ctx._request(it["gal"], it.get("ran"), it["params"], it.get("kedges"),
+                                             it.get("redges"), it.get("gal_nbar"), it.get("ran_nbar"))
+            self._reqs[i], self._ress[i] = rq, rs
+            self.outputs.append(out)
+            self._keeps.append(keep)
+        self._n = n
+        self._h = ctypes.c_void_p()
+        status = (ctypes.c_int * n)()
+        rc = self._L.bym_batch_plan_create(ctx._h, n, self._reqs, self._ress, int(n_streams), ctypes.byref(self._h),
+                                           status)
+        for i in range(n):
+            if status[i] != BYM_OK:
+                self.close()
+                raise BymError(status[i], f"batch item {i} failed")
+        ctx._check(rc)
+
+    def launch(self):
+        status = (ctypes.c_int * self._n)()
+        rc = self._L.bym_batch_plan_launch(self._h, status)
+        for i in range(self._n):
+            if status[i] != BYM_OK:
+                raise BymError(status[i], f"batch item {i} failed")
+        self._ctx._check(rc)
+        return self.outputs
+
+    def close(self):
+        if self._h:
+            self._L.bym_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
 
 def footprint(params: Params, n_gal: int, n_ran: int, want_pk=True, want_xi=True) -> int:

@@ -18,6 +18,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <sstream>
 #include <string>
 #include <tuple>
@@ -528,8 +529,61 @@ static size_t device_available(bym_ctx *c, size_t headroom) {
 // ---------------------------------------------------------------------------
 // one request
 // ---------------------------------------------------------------------------
+// A request enqueued without waiting (CUDA-graph batches): pinned host areas for the
+// small uploads and for the results, and what the host step after the launch needs.
+struct Pending {
+  double *host = nullptr;       // pinned: [8 stats][NL * nbk P sums][NL * nbr xi sums]
+  char *stage = nullptr;        // pinned: [nf scale factors (double)][n_mesh 1/W values (T)]
+  size_t host_len = 0, stage_len = 0;
+  Geom *kg = nullptr, *rg = nullptr;
+  int NL = 0, nbk = 0, nbr = 0;
+  double h = 0.0;
+};
+
+// Host normalisation of the FP64 sums (Sec. 2 with the readings of the library's
+// normalisation: P = 4 pi / A * bin mean, xi = 4 pi / (A V_cell) * bin mean).
+static int finish_results(bym_ctx *c, const Request &rq, const double *hstats, const double *hk, const double *hr,
+                          const Geom *kg, const Geom *rg, int NL, int nbk, int nbr, double h) {
+  const bym_params *p = rq.p;
+  if (hstats[3] > 0.0)
+    return fail(c, BYM_E_OUT_OF_BOX,
+                std::to_string((long long)hstats[3]) + " objects lie outside the box or are not finite");
+  if (rq.alpha) *rq.alpha = hstats[1] != 0.0 ? hstats[0] / hstats[1] : 0.0;
+  double A = 1.0, vcell = 1.0;
+  if (p->norm >= 1) {
+    const double alpha = hstats[0] / hstats[1];
+    A = alpha * hstats[2];
+    vcell = h * h * h;
+    if (!(A > 0.0) || !std::isfinite(A)) return fail(c, BYM_E_INVAL, "FKP normalisation A is not positive");
+  }
+  // norm 2: xi as raw sums here, divided by the random-random count afterwards
+  const double xden = p->norm == 2 ? 1.0 : A * vcell;
+  const double four_pi = 4.0 * M_PI;
+  if (rq.kb) {
+    for (int l = 0; l < NL; ++l)
+      for (int b = 0; b < nbk; ++b)
+        rq.pk[l * nbk + b] = kg->count[b] > 0 ? four_pi / A * hk[(size_t)b * NL + l] / (double)kg->count[b] : 0.0;
+    if (rq.kmean) std::copy(kg->mean.begin(), kg->mean.end(), rq.kmean);
+    if (rq.nmodes) std::copy(kg->count.begin(), kg->count.end(), rq.nmodes);
+  }
+  if (rq.rb) {
+    for (int l = 0; l < NL; ++l)
+      for (int b = 0; b < nbr; ++b)
+        rq.xi[l * nbr + b] =
+            rg->count[b] > 0 ? four_pi / xden * hr[(size_t)b * NL + l] / (double)rg->count[b] : 0.0;
+    if (rq.rmean) std::copy(rg->mean.begin(), rg->mean.end(), rq.rmean);
+    if (rq.ncells) std::copy(rg->count.begin(), rg->count.end(), rq.ncells);
+  }
+  return BYM_OK;
+}
+
+// pd == nullptr: run the request and wait.  pd != nullptr: enqueue it on st (nothing
+// waits; uploads come from pd->stage, results land in pd->host) for finish_results
+// after the stream (or the graph it was captured into) has run; catalogs must then be
+// device catalogs, and every cache the request uses (kernels, geometry, FFT plans and
+// work area) must exist already, as they do after one run of a request of that shape.
 template <typename T, typename T2>
-static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
+static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd = nullptr) {
   const bym_params *p = rq.p;
   const int N = p->n_mesh;
   const bool want_pk = rq.kb != nullptr, want_xi = rq.rb != nullptr;
@@ -606,6 +660,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (cat->on_device) {
       cat4[w] = (const float4 *)cat->xyzw;
       catnb[w] = cat->nbar;
+    } else if (pd) {
+      return fail(c, BYM_E_INVAL, "an enqueued request needs device catalogs");
     } else {
       void *d4 = nullptr;
       TRY(alloc(&d4, (size_t)cat->n * 16));
@@ -637,7 +693,13 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       w[i] = (T)(1.0 / std::pow(s, p->assign));
     }
     TRY(alloc((void **)&invw, sizeof(T) * N));
-    CUDA_TRY(cudaMemcpyAsync(invw, w.data(), sizeof(T) * N, cudaMemcpyHostToDevice, st));
+    const void *src = w.data();
+    if (pd) {
+      T *dst = (T *)(pd->stage + sizeof(double) * (size_t)nf);
+      std::copy(w.begin(), w.end(), dst);
+      src = dst;
+    }
+    CUDA_TRY(cudaMemcpyAsync(invw, src, sizeof(T) * N, cudaMemcpyHostToDevice, st));
   }
   {
     std::vector<double> sc(nf);
@@ -647,7 +709,12 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
       sc[i] = sign * inv_n3;
     }
     TRY(alloc((void **)&scale, sizeof(double) * std::max(nf, 1)));
-    CUDA_TRY(cudaMemcpyAsync(scale, sc.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
+    const void *src = sc.data();
+    if (pd) {
+      std::copy(sc.begin(), sc.end(), (double *)pd->stage);
+      src = pd->stage;
+    }
+    CUDA_TRY(cudaMemcpyAsync(scale, src, sizeof(double) * nf, cudaMemcpyHostToDevice, st));
   }
 
   // mesh slots: [0] delta, [1, 1+nf) fields, [1+nf, 1+nf+nextra) H or X;
@@ -824,42 +891,26 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st) {
   CUDA_TRY(cudaGetLastError());
 
   // results
+  if (pd) {
+    double *hs = pd->host;
+    CUDA_TRY(cudaMemcpyAsync(hs, stats, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs + 8, ksum, sizeof(double) * NL * nbk, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs + 8 + NL * nbk, rsum, sizeof(double) * NL * nbr, cudaMemcpyDeviceToHost, st));
+    pd->kg = kg;
+    pd->rg = rg;
+    pd->NL = NL;
+    pd->nbk = nbk;
+    pd->nbr = nbr;
+    pd->h = h;
+    return BYM_OK;
+  }
   std::vector<double> hstats(8), hk((size_t)NL * nbk), hr((size_t)NL * nbr);
   CUDA_TRY(cudaMemcpyAsync(hstats.data(), stats, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hk.data(), ksum, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hr.data(), rsum, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   prof_collect(c);
-  if (hstats[3] > 0.0)
-    return fail(c, BYM_E_OUT_OF_BOX,
-                std::to_string((long long)hstats[3]) + " objects lie outside the box or are not finite");
-  if (rq.alpha) *rq.alpha = hstats[1] != 0.0 ? hstats[0] / hstats[1] : 0.0;
-  double A = 1.0, vcell = 1.0;
-  if (p->norm >= 1) {
-    const double alpha = hstats[0] / hstats[1];
-    A = alpha * hstats[2];
-    vcell = h * h * h;
-    if (!(A > 0.0) || !std::isfinite(A)) return fail(c, BYM_E_INVAL, "FKP normalisation A is not positive");
-  }
-  // norm 2: xi as raw sums here, divided by the random-random count afterwards
-  const double xden = p->norm == 2 ? 1.0 : A * vcell;
-  const double four_pi = 4.0 * M_PI;
-  if (want_pk) {
-    for (int l = 0; l < NL; ++l)
-      for (int b = 0; b < nbk; ++b)
-        rq.pk[l * nbk + b] = kg->count[b] > 0 ? four_pi / A * hk[(size_t)b * NL + l] / (double)kg->count[b] : 0.0;
-    if (rq.kmean) std::copy(kg->mean.begin(), kg->mean.end(), rq.kmean);
-    if (rq.nmodes) std::copy(kg->count.begin(), kg->count.end(), rq.nmodes);
-  }
-  if (want_xi) {
-    for (int l = 0; l < NL; ++l)
-      for (int b = 0; b < nbr; ++b)
-        rq.xi[l * nbr + b] =
-            rg->count[b] > 0 ? four_pi / xden * hr[(size_t)b * NL + l] / (double)rg->count[b] : 0.0;
-    if (rq.rmean) std::copy(rg->mean.begin(), rg->mean.end(), rq.rmean);
-    if (rq.ncells) std::copy(rg->count.begin(), rg->count.end(), rq.ncells);
-  }
-  return BYM_OK;
+  return finish_results(c, rq, hstats.data(), hk.data(), hr.data(), kg, rg, NL, nbk, nbr, h);
 #undef TRY
 #undef CUDA_TRY
 }
@@ -1006,7 +1057,323 @@ int bym_set_fft_backend(bym_ctx *c, int mode) {
   if (!c || mode < 0 || mode > 4) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
   c->fft_mode = mode;
+  c->graph_warm.clear();   // other plans and kernels: warm again before the next captured batch
   return BYM_OK;
+}
+
+// A batch captured as one CUDA graph.  Every request (and, for norm 2, its
+// random-random pass) is enqueued on one stream under capture; a launch runs the
+// graph and normalises the results on the host.  Before the capture host catalogs
+// are copied to the device and one request of every distinct shape not yet warmed on
+// the context runs uncaptured, so that the captured requests find their kernels, bin
+// tables, FFT plans and work area ready.
+struct bym_batch {
+  struct Item {
+    bym_catalog gal{}, ran{};
+    bym_params p{}, prr{};
+    Request rq{}, rrq{};
+    std::vector<double> rr;
+    double alpha = 0.0;
+    Pending pd, pdr;
+    bool ok = false;
+    int status = BYM_OK;          // validation / warm-up outcome
+    int branch = 0;               // graph branch (engine and stream) that runs it
+  };
+  bym_ctx *c = nullptr;
+  std::vector<bym_ctx *> eng;     // one engine per branch: its own FFT plans, work area, bin tables
+  std::vector<cudaStream_t> bst;  // one stream per branch, forked from and joined to cs in the capture
+  std::vector<cudaEvent_t> ev;
+  std::vector<Item> it;
+  std::vector<void *> dev;        // device copies of host catalogs
+  char *pinned = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  ~bym_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaStream_t q : bst) cudaStreamDestroy(q);
+    for (bym_ctx *e : eng) bym_destroy(e);
+    if (cs) cudaStreamDestroy(cs);
+    if (pinned) cudaFreeHost(pinned);
+    for (void *q : dev) cudaFree(q);
+    if (c) cudaDeviceGraphMemTrim(c->device);
+  }
+};
+
+static int batch_create(bym_ctx *c, int n, const bym_request *reqs, const bym_result *outs, int n_streams,
+                        std::unique_ptr<bym_batch> &out) {
+  auto B = std::make_unique<bym_batch>();
+  B->c = c;
+  B->it.resize((size_t)n);
+  cudaStream_t st = c->stream;   // warm-up runs here; the capture runs on its own non-blocking stream
+  for (int i = 0; i < n; ++i) {
+    auto &m = B->it[(size_t)i];
+    m.gal = reqs[i].gal;
+    m.ran = reqs[i].ran;
+    m.p = reqs[i].params;
+    const bym_bins *kb = reqs[i].kbins.nbins > 0 ? &reqs[i].kbins : nullptr;
+    const bym_bins *rb = reqs[i].rbins.nbins > 0 ? &reqs[i].rbins : nullptr;
+    const bym_catalog *ranp = m.ran.n > 0 ? &m.ran : nullptr;
+    int rc = validate(c, &m.gal, ranp, &m.p, kb, rb);
+    if (!rc && ((kb && !outs[i].pk) || (rb && !outs[i].xi) || (!kb && !rb)))
+      rc = fail(c, BYM_E_INVAL, "missing output array");
+    if (rc) {
+      m.status = rc;
+      continue;
+    }
+    for (bym_catalog *cat : {&m.gal, &m.ran}) {
+      if (cat->n <= 0 || cat->on_device) continue;
+      void *d4 = nullptr, *dn = nullptr;
+      if (cudaMalloc(&d4, (size_t)cat->n * 16) != cudaSuccess ||
+          (cat->nbar && cudaMalloc(&dn, (size_t)cat->n * 4) != cudaSuccess)) {
+        cudaGetLastError();
+        if (d4) cudaFree(d4);
+        return fail(c, BYM_E_NOMEM, "batch: device copy of a catalog failed");
+      }
+      B->dev.push_back(d4);
+      cudaMemcpy(d4, cat->xyzw, (size_t)cat->n * 16, cudaMemcpyHostToDevice);
+      if (dn) {
+        B->dev.push_back(dn);
+        cudaMemcpy(dn, cat->nbar, (size_t)cat->n * 4, cudaMemcpyHostToDevice);
+      }
+      cat->xyzw = (const float *)d4;
+      cat->nbar = (const float *)dn;
+      cat->on_device = 1;
+    }
+    ranp = m.ran.n > 0 ? &m.ran : nullptr;
+    m.rq = Request{&m.gal, ranp, &m.p, kb, rb, outs[i].pk, outs[i].k_mean, outs[i].n_modes,
+                   outs[i].xi, outs[i].r_mean, outs[i].n_cells};
+    m.rq.alpha = &m.alpha;
+    if (m.p.norm == 2 && rb) {   // the random-random pass: Yamamoto, ell = 0, raw, xi only, on the randoms
+      m.prr = m.p;
+      m.prr.los = BYM_LOS_YAMAMOTO;
+      m.prr.ell_max = 0;
+      m.prr.order = 0;
+      m.prr.norm = 0;
+      m.rr.assign((size_t)rb->nbins, 0.0);
+      m.rrq = Request{&m.ran, nullptr, &m.prr, nullptr, rb, nullptr, nullptr, nullptr, m.rr.data(), nullptr, nullptr};
+    }
+    m.ok = true;
+  }
+  // branches: engines created like serving slots, with this context's settings; the
+  // requests go to the least loaded branch, largest first
+  int n_ok = 0;
+  for (auto &m : B->it) n_ok += m.ok ? 1 : 0;
+  const int nb = std::max(1, std::min(n_streams > 0 ? n_streams : 4, std::max(n_ok, 1)));
+  for (int b = 0; b < nb; ++b) {
+    bym_ctx *e = nullptr;
+    if (bym_create(&e, c->device, 0) != BYM_OK) return fail(c, BYM_E_CUDA, "batch: could not create a branch");
+    e->tune = c->tune;
+    e->fft_mode = c->fft_mode;
+    e->field_chunk = c->field_chunk;
+    B->eng.push_back(e);
+  }
+  {
+    std::vector<std::pair<double, int>> order;
+    for (int i = 0; i < n; ++i)
+      if (B->it[(size_t)i].ok) {
+        const bym_params &p = B->it[(size_t)i].p;
+        order.push_back({std::pow((double)p.n_mesh, 3) * (2.0 + n_fields(&p)), i});
+      }
+    std::sort(order.rbegin(), order.rend());
+    std::vector<double> load((size_t)nb, 0.0);
+    for (auto &oi : order) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      B->it[(size_t)oi.second].branch = b;
+      load[(size_t)b] += oi.first;
+    }
+  }
+  auto shape_key = [](const Request &rq) {
+    std::ostringstream o;
+    const bym_params *p = rq.p;
+    o << p->n_mesh << ':' << p->precision << ':' << p->los << ':' << p->ell_max << ':' << p->order << ':'
+      << p->compensate << ':' << p->box_len << ':' << (rq.ran != nullptr) << ':';
+    for (const bym_bins *b : {rq.kb, rq.rb}) {
+      o << '|';
+      if (b) o.write((const char *)b->edges, sizeof(double) * (b->nbins + 1));
+    }
+    return o.str();
+  };
+  for (auto &m : B->it) {        // an item whose warm-up fails reports it and leaves the batch
+    if (!m.ok) continue;
+    bym_ctx *e = B->eng[(size_t)m.branch];
+    for (Request *rq : {&m.rq, m.rr.empty() ? nullptr : &m.rrq}) {
+      if (!m.ok || !rq) continue;
+      const std::string key = shape_key(*rq);
+      if (e->graph_warm.count(key)) continue;
+      const int NL = rq->p->ell_max / 2 + 1, nbk = rq->kb ? rq->kb->nbins : 0, nbr = rq->rb ? rq->rb->nbins : 0;
+      std::vector<double> a((size_t)NL * nbk + 1), b((size_t)nbk + 1), d((size_t)NL * nbr + 1), f2((size_t)nbr + 1);
+      std::vector<int64_t> f((size_t)nbk + 1), g((size_t)nbr + 1);
+      Request w{rq->gal, rq->ran, rq->p, rq->kb, rq->rb, a.data(), b.data(), f.data(), d.data(), f2.data(), g.data()};
+      const int rc = rq->p->precision == 64 ? run_typed<double, double2>(e, w, e->stream)
+                                            : run_typed<float, float2>(e, w, e->stream);
+      if (rc) {
+        m.status = fail(c, rc, std::string("batch: ") + e->err);
+        m.ok = false;
+      } else {
+        e->graph_warm.insert(key);
+      }
+    }
+  }
+  // pinned host areas
+  size_t total = 0;
+  auto sizes = [&](const Request &rq, Pending &pd) {
+    const int NL = rq.p->ell_max / 2 + 1;
+    pd.host_len =
+        sizeof(double) * (8 + (size_t)NL * (rq.kb ? rq.kb->nbins : 1) + (size_t)NL * (rq.rb ? rq.rb->nbins : 1));
+    pd.stage_len = sizeof(double) * (size_t)(n_fields(rq.p) + rq.p->n_mesh + 2);
+    total += pd.host_len + pd.stage_len;
+  };
+  for (auto &m : B->it)
+    if (m.ok) {
+      sizes(m.rq, m.pd);
+      if (!m.rr.empty()) sizes(m.rrq, m.pdr);
+    }
+  if (total && cudaMallocHost((void **)&B->pinned, total) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "batch: pinned host allocation failed");
+  }
+  size_t off = 0;
+  auto place = [&](Pending &pd) {
+    pd.host = (double *)(B->pinned + off);
+    off += pd.host_len;
+    pd.stage = B->pinned + off;
+    off += pd.stage_len;
+  };
+  for (auto &m : B->it)
+    if (m.ok) {
+      place(m.pd);
+      if (!m.rr.empty()) place(m.pdr);
+    }
+  // capture (forked into one branch per engine, joined at the end) and instantiate
+  bool setup = cudaStreamSynchronize(st) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (int b = 0; setup && b < nb; ++b) {
+    cudaStream_t q = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    setup = cudaStreamSynchronize(B->eng[(size_t)b]->stream) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess;
+    if (q) B->bst.push_back(q);
+    if (e0) B->ev.push_back(e0);
+    if (e1) B->ev.push_back(e1);
+  }
+  if (!setup) return fail(c, BYM_E_CUDA, "batch: capture streams");
+  int rc = BYM_OK;
+  if (cudaStreamBeginCapture(B->cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    rc = fail(c, BYM_E_CUDA, "batch: stream capture could not start");
+  } else {
+    for (int b = 0; b < nb && !rc; ++b)   // fork
+      if (cudaEventRecord(B->ev[2 * b], B->cs) != cudaSuccess || cudaStreamWaitEvent(B->bst[b], B->ev[2 * b], 0))
+        rc = fail(c, BYM_E_CUDA, "batch: fork");
+    for (auto &m : B->it) {
+      if (!m.ok || rc) continue;
+      bym_ctx *e = B->eng[(size_t)m.branch];
+      cudaStream_t q = B->bst[(size_t)m.branch];
+      const bool prof_was = e->prof;
+      e->prof = false;
+      const auto enq = [&](const Request &rq, Pending *pd) {
+        return rq.p->precision == 64 ? run_typed<double, double2>(e, rq, q, pd)
+                                     : run_typed<float, float2>(e, rq, q, pd);
+      };
+      rc = enq(m.rq, &m.pd);
+      if (!rc && !m.rr.empty()) rc = enq(m.rrq, &m.pdr);
+      e->prof = prof_was;
+      if (rc) rc = fail(c, rc, std::string("batch: ") + e->err);
+    }
+    for (int b = 0; b < nb && !rc; ++b)   // join
+      if (cudaEventRecord(B->ev[2 * b + 1], B->bst[b]) != cudaSuccess ||
+          cudaStreamWaitEvent(B->cs, B->ev[2 * b + 1], 0) != cudaSuccess)
+        rc = fail(c, BYM_E_CUDA, "batch: join");
+    const cudaError_t ec = cudaStreamEndCapture(B->cs, &B->graph);
+    if (!rc && ec != cudaSuccess) rc = fail(c, BYM_E_CUDA, std::string("batch: capture: ") + cudaGetErrorString(ec));
+  }
+  if (!rc && cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess)
+    rc = fail(c, BYM_E_CUDA, std::string("batch: graph instantiation: ") + cudaGetErrorString(cudaGetLastError()));
+  if (rc) return rc;
+  out = std::move(B);
+  return BYM_OK;
+}
+
+static int batch_launch(bym_batch *B, int *status) {
+  bym_ctx *c = B->c;
+  int first_err = BYM_OK;
+  int rc = BYM_OK;
+  if (cudaSetDevice(c->device) != cudaSuccess) rc = fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  if (!rc && cudaGraphLaunch(B->exec, B->cs) != cudaSuccess)
+    rc = fail(c, BYM_E_CUDA, std::string("batch: graph launch: ") + cudaGetErrorString(cudaGetLastError()));
+  if (!rc && cudaStreamSynchronize(B->cs) != cudaSuccess)
+    rc = fail(c, BYM_E_CUDA, std::string("batch: graph run: ") + cudaGetErrorString(cudaGetLastError()));
+  for (size_t i = 0; i < B->it.size(); ++i) {
+    auto &m = B->it[i];
+    int r = m.status;
+    if (m.ok && rc) r = rc;
+    if (m.ok && !rc) {
+      const Pending &pd = m.pd;
+      r = finish_results(c, m.rq, pd.host, pd.host + 8, pd.host + 8 + pd.NL * pd.nbk, pd.kg, pd.rg, pd.NL, pd.nbk,
+                         pd.nbr, pd.h);
+      if (!r && !m.rr.empty()) {
+        const Pending &q = m.pdr;
+        r = finish_results(c, m.rrq, q.host, q.host + 8, q.host + 8 + q.NL * q.nbk, q.kg, q.rg, q.NL, q.nbk, q.nbr,
+                           q.h);
+        const int nbr = m.rq.rb->nbins, NL = m.p.ell_max / 2 + 1;
+        for (int b = 0; !r && b < nbr; ++b) {
+          const double den = m.alpha * m.alpha * m.rr[(size_t)b];
+          for (int l = 0; l < NL; ++l) m.rq.xi[l * nbr + b] = den != 0.0 ? m.rq.xi[l * nbr + b] / den : 0.0;
+        }
+      }
+    }
+    if (status) status[i] = r;
+    if (r && !first_err) first_err = r;
+  }
+  return first_err;
+}
+
+int bym_batch_plan_create(bym_ctx *c, int n, const bym_request *reqs, const bym_result *outs, int n_streams,
+                          bym_batch **plan, int *status) {
+  if (!c || !plan || n < 0 || (n > 0 && (!reqs || !outs || !status))) return BYM_E_INVAL;
+  *plan = nullptr;
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  std::unique_ptr<bym_batch> B;
+  const int rc = batch_create(c, n, reqs, outs, n_streams, B);
+  if (rc) return rc;
+  int first_err = BYM_OK;
+  for (int i = 0; i < n; ++i) {
+    status[i] = B->it[(size_t)i].status;
+    if (status[i] && !first_err) first_err = status[i];
+  }
+  *plan = B.release();
+  return first_err;
+}
+
+int bym_batch_plan_launch(bym_batch *plan, int *status) {
+  if (!plan) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(plan->c->mu);
+  return batch_launch(plan, status);
+}
+
+void bym_batch_plan_destroy(bym_batch *plan) {
+  if (!plan) return;
+  bym_ctx *c = plan->c;
+  std::lock_guard<std::mutex> lock(c->mu);
+  delete plan;
+}
+
+int bym_batch_graph(bym_ctx *c, int n, const bym_request *reqs, const bym_result *outs, int *status) {
+  if (!c || n < 0 || (n > 0 && (!reqs || !outs || !status))) return BYM_E_INVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  std::unique_ptr<bym_batch> B;
+  const int rc = batch_create(c, n, reqs, outs, 0, B);
+  if (rc) {
+    for (int i = 0; i < n; ++i) status[i] = rc;
+    return rc;
+  }
+  return batch_launch(B.get(), status);
 }
 
 int bym_shot_noise(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const bym_params *p,
@@ -1066,6 +1433,7 @@ int bym_set_field_chunk(bym_ctx *c, int max_fields) {
   if (!c || max_fields < 0) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
   c->field_chunk = max_fields;
+  c->graph_warm.clear();
   return BYM_OK;
 }
 
@@ -1112,6 +1480,7 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
         if (strcmp(k, keybuf) == 0) {
           fclose(f);
           c->tune[key] = t;
+          c->graph_warm.clear();
           emit(t, "cache");
           return BYM_OK;
         }
@@ -1184,6 +1553,7 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
     }
   }
   c->tune[key] = best;
+  c->graph_warm.clear();
   if (cache_path) {
     if (FILE *f = fopen(cache_path, "a")) {
       fprintf(f, "%s %d %d %d %d %d %d\n", keybuf, best.per_sm_gen, best.per_sm_comb, best.per_sm_k,

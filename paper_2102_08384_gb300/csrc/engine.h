@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -70,6 +71,7 @@ struct bym_ctx {
   size_t fft_work_size = 0;
   std::map<std::string, bym::Geom> kgeo, rgeo;
   bym::Server *server = nullptr;
+  std::set<std::string> graph_warm;  // request shapes bym_batch_graph has warmed on this context
   int field_chunk = 0;  // midpoint g fields per streamed range: 0 = only when the whole set does not fit
   int fft_mode = 2;  // 0 cuFFT, 1 library FFT kernels (8-CTA clusters), 2 as tuned, 3 library (16-CTA clusters)
   std::map<std::tuple<int, int, int>, bym::Tune> tune;         // (n_mesh, precision, los) -> launch shapes

@@ -127,3 +127,67 @@ def test_autotune_keeps_results_and_caches(pkg, cap, tmp_path):
     ctx2.close()
     assert again["source"] == "cache"
     assert {k: v for k, v in again.items() if k != "source"} == {k: v for k, v in choice.items() if k != "source"}
+
+
+def test_batch_graph_matches_sequential(pkg, cap):
+    # the mix (meshes, LOS, orders, precisions, compensation) plus a norm-2 item, as one CUDA graph
+    items = _mix(pkg, cap)
+    p2 = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=40, ell_max=4, los="midpoint", order=2,
+                         precision=32, norm=2)
+    items.append(dict(gal=cap.gal, ran=cap.ran, params=p2, kedges=np.linspace(0.0, 0.3, 7),
+                      redges=np.linspace(0.0, 300.0, 6), ran_nbar=cap.ran_nbar))
+    items = items + items[:3]            # repeated shapes reuse the warmed caches
+    ctx = pkg.Context(0)
+    seq = [ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
+                                ran_nbar=it["ran_nbar"]) for it in items]
+    gr = ctx.batch_graph(items)
+    again = ctx.batch_graph(items)       # a second graph on the same context
+    ctx.close()
+    for it, a, b, c in zip(items, seq, gr, again):
+        r0, r = _tol(it["params"].precision)
+        for out in (b, c):
+            check_multipoles(out["pk"], a["pk"], "pk", r0, r)
+            check_multipoles(out["xi"], a["xi"], "xi", r0, r)
+            np.testing.assert_array_equal(out["n_modes"], a["n_modes"])
+
+
+def test_batch_graph_reports_item_errors(pkg, cap):
+    ctx = pkg.Context(0)
+    p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=32, ell_max=4, los="bisector", order=2)
+    bad = np.array(cap.gal, copy=True)
+    bad[0, 2] = np.nan
+    good = dict(gal=cap.gal, ran=cap.ran, params=p, kedges=np.linspace(0, 0.2, 5), ran_nbar=cap.ran_nbar)
+    for items in ([good, dict(good, gal=bad)], [dict(good, gal=bad), good]):   # bad item captured / in warm-up
+        with pytest.raises(pkg.BymError) as ei:
+            ctx.batch_graph(items)
+        assert ei.value.code == -2
+    ctx.close()
+
+
+def test_batch_plan_relaunch_follows_device_catalogs(pkg, cap):
+    # a persistent captured batch: relaunching recomputes from the current device catalogs
+    torch = pytest.importorskip("torch")
+    g = torch.from_numpy(cap.gal).cuda()
+    r = torch.from_numpy(cap.ran).cuda()
+    rn = torch.from_numpy(cap.ran_nbar).cuda()
+    items = []
+    for N, los, K in ((32, "midpoint", 2), (48, "bisector", 4), (40, "yamamoto", 0)):
+        p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=4, los=los, order=K)
+        items.append(dict(gal=g, ran=r, params=p, kedges=np.linspace(0.0, 0.3, 9), redges=np.linspace(0, 250, 6),
+                          ran_nbar=rn))
+    ctx = pkg.Context(0)
+    plan = ctx.batch_plan(items)
+
+    def seq():
+        return [ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
+                                     ran_nbar=it["ran_nbar"]) for it in items]
+
+    for _ in range(2):
+        got = [dict((k, v.copy()) for k, v in o.items() if k != "ells") for o in plan.launch()]
+        for a, b in zip(seq(), got):
+            check_multipoles(b["pk"], a["pk"], "pk")
+            check_multipoles(b["xi"], a["xi"], "xi")
+        g[:, 3] = g[:, 3] * torch.linspace(0.5, 1.5, g.shape[0], device="cuda")   # new weights, same buffer
+        torch.cuda.synchronize()
+    plan.close()
+    ctx.close()
