@@ -297,7 +297,12 @@ def run_ours(args):
                        "autotune": tuned or "off"},
             "e2e": e2e, "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "kernels": kernels}
     if ws == 1 and not args.no_serve:
-        line["serving"] = serving_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, args.serve_requests)
+        perm = torch.randperm(gal_d.shape[0], device=dev)   # random order: any prefix covers the whole cap
+        gal_p = gal_d[perm].contiguous()
+        permr = torch.randperm(ran_d.shape[0], device=dev)
+        ran_p, rnb_p = ran_d[permr].contiguous(), rnb_d[permr].contiguous()
+        line["batch"] = batch_leg(pkg, torch, dev, cat, gal_p, ran_p, rnb_p)
+        line["serving"] = serving_leg(pkg, torch, dev, cat, gal_p, ran_p, rnb_p, args.serve_requests)
     if ws == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(cat, args.mesh)
         cb.pop("sample_seconds", None)
@@ -308,23 +313,104 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _mock_subsets(torch, cat, gal_d, ran_d, rnb_d, rng, frac, half_angle_deg):
+    """An uneven mock from the benchmark catalog: a random fraction of its galaxies and randoms
+    (a fixed random order, so every prefix covers the whole cap) inside a narrower cap around
+    the same pole; nbar and FKP weights are those of the full catalog (same density)."""
+    pole = torch.tensor(cat.meta.get("pole", (1.0, 1.0, 1.0)), dtype=torch.float32, device=gal_d.device)
+    pole = pole / pole.norm()
+    cmin = math.cos(math.radians(half_angle_deg))
+    out = []
+    for x in (gal_d, ran_d):
+        n = int(frac * x.shape[0])
+        sub = x[:n]
+        c = (sub[:, :3] @ pole) / sub[:, :3].norm(dim=1)
+        out.append(c >= cmin)
+    g = gal_d[: int(frac * gal_d.shape[0])][out[0]].contiguous()
+    keep = out[1]
+    r = ran_d[: int(frac * ran_d.shape[0])][keep].contiguous()
+    rn = rnb_d[: int(frac * rnb_d.shape[0])][keep].contiguous()
+    return g, r, rn
+
+
+def batch_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mocks=64, slots=4):
+    """Many uneven mocks: meshes 128, 192, 256, 384^3 in turn, LOS midpoint for four mocks then
+    bisector for four, order 4, ell <= 4, P and xi; each mock a random 20-100 % of the benchmark's
+    galaxies and randoms in a cap of half-angle 10-30 degrees.  Run (a) one at a time,
+    (b) as one batch through the 4-slot serving loop, (c) as one captured CUDA graph with 4
+    branches (captured once, then relaunched)."""
+    rng = np.random.default_rng(100)
+    items = []
+    for i in range(n_mocks):
+        N = (128, 192, 256, 384)[i % 4]
+        los = ("midpoint", "bisector")[(i // 4) % 2]     # every mesh with both LOS within 8 mocks
+        frac = float(rng.uniform(0.2, 1.0))
+        g, r, rn = _mock_subsets(torch, cat, gal_d, ran_d, rnb_d, rng, frac, float(rng.uniform(10.0, 30.0)))
+        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=ELL_MAX, los=los,
+                            order=ORDER, compensate=True, precision=32, norm=1)
+        items.append(dict(gal=g, ran=r, ran_nbar=rn, params=p, kedges=KEDGES, redges=REDGES))
+    ctx = pkg.Context(dev.index)
+
+    def alone(it):
+        return ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
+                                    ran_nbar=it["ran_nbar"])
+
+    for it in items[:8]:                   # kernels, plans and bin tables of every shape
+        alone(it)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for it in items:
+        alone(it)
+    t_seq = time.perf_counter() - t0
+    ctx.serve_start(n_slots=slots)
+    ts = [ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"])
+          for it in items[:8] for _ in range(slots)]   # every slot meets every shape
+    for t in ts:
+        ctx.wait(t)
+    t0 = time.perf_counter()
+    ts = [ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"])
+          for it in items]
+    for t in ts:
+        ctx.wait(t)
+    t_batch = time.perf_counter() - t0
+    ctx.serve_stop()
+    t0 = time.perf_counter()
+    plan = ctx.batch_plan(items, n_streams=slots)
+    t_capture = time.perf_counter() - t0
+    plan.launch()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plan.launch()
+    t_graph = time.perf_counter() - t0
+    plan.close()
+    ctx.close()
+    n_gal = [int(it["gal"].shape[0]) for it in items]
+    return {"mocks": len(items),
+            "mix": "meshes 128/192/256/384^3 in turn, midpoint/bisector alternating, order 4, ell<=4, P_ell+xi_ell, "
+                   "FP32; each a random 20-100 % of the galaxies and randoms in a 10-30 deg cap "
+                   f"({min(n_gal)}-{max(n_gal)} galaxies)",
+            "sequential_catalogs_per_s": len(items) / t_seq,
+            "served_batch_catalogs_per_s": len(items) / t_batch,
+            "graph_batch_catalogs_per_s": len(items) / t_graph,
+            "graph_capture_s": t_capture, "branches": slots}
+
+
 def serving_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_req, slots=4):
-    """Mixed requests (meshes 128-256^3, every LOS, orders 0-4, uneven catalogs: the first
-    10-100 % of the galaxies and randoms) run (a) one at a time, (b) as one batch through
-    the serving loop, (c) as a Poisson stream at 0.8x the sequential capacity, for p50/p99,
-    (d) as one batch captured into a single CUDA graph (persistent: captured once, relaunched)."""
+    """A Poisson stream of requests at 0.8x the measured one-at-a-time capacity of the same mix:
+    meshes 128, 256, 384, 512^3, a random LOS, order in {0, 2, 4, 6} (0 for Yamamoto), a
+    random 10-100 % (log-uniform) of the galaxies and randoms; p50/p99 latency beside the
+    catalogs/s of the stream and of the plain path."""
     rng = np.random.default_rng(3)
-    ng, nr = gal_d.shape[0], ran_d.shape[0]
     items = []
     for i in range(n_req):
-        N = int(rng.choice([128, 192, 256]))
-        los = ["yamamoto", "midpoint", "bisector"][i % 3]
-        K = 0 if los == "yamamoto" else int(rng.choice([2, 4]))
+        N = int(rng.choice([128, 256, 384, 512]))
+        los = str(rng.choice(["yamamoto", "midpoint", "bisector"]))
+        K = 0 if los == "yamamoto" else int(rng.choice([0, 2, 4, 6]))
         frac = float(10 ** rng.uniform(-1, 0))
+        g, r, rn = _mock_subsets(torch, cat, gal_d, ran_d, rnb_d, rng, frac, 30.0)
         p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=ELL_MAX, los=los,
                             order=K, compensate=True, precision=32, norm=1)
-        items.append(dict(gal=gal_d[: int(frac * ng)], ran=ran_d[: int(frac * nr)], ran_nbar=rnb_d[: int(frac * nr)],
-                          params=p, kedges=KEDGES, redges=REDGES))
+        items.append(dict(gal=g, ran=r, ran_nbar=rn, params=p, kedges=KEDGES, redges=REDGES))
     ctx = pkg.Context(dev.index)
 
     def alone(it):
@@ -338,36 +424,23 @@ def serving_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_req, slots=4):
     for it in items:
         alone(it)
     t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    plan = ctx.batch_plan(items)           # (d) the whole batch captured as one CUDA graph
-    t_capture = time.perf_counter() - t0
-    plan.launch()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    plan.launch()
-    t_graph = time.perf_counter() - t0
-    plan.close()
+    shapes = {}
+    for it in items:                       # the smallest request of every shape warms every slot
+        key = (it["params"].n_mesh, int(it["params"].los), it["params"].order)
+        if key not in shapes or it["gal"].shape[0] < shapes[key]["gal"].shape[0]:
+            shapes[key] = it
     ctx.serve_start(n_slots=slots)
-    for _ in range(2):                     # every slot meets every configuration: plans and tables
-        ts = [ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"])
-              for it in items for _ in range(slots)]
-        for t in ts:
-            ctx.wait(t)
-    t0 = time.perf_counter()
     ts = [ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"])
-          for it in items]
+          for it in shapes.values() for _ in range(slots)]
     for t in ts:
         ctx.wait(t)
-    t_batch = time.perf_counter() - t0
-    ctx.serve_stop()
-    # Poisson arrivals at 0.8x the sequential capacity
+    ctx.serve_reset_stats()                # the same (warm) slots take the stream
     rate = 0.8 * len(items) / t_seq
-    ctx.serve_start(n_slots=slots)
     gaps = rng.exponential(1.0 / rate, size=len(items))
     ts = []
     t0 = time.perf_counter()
-    for it, g in zip(items, gaps):
-        time.sleep(g)
+    for it, gap in zip(items, gaps):
+        time.sleep(gap)
         ts.append(ctx.submit(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"], ran_nbar=it["ran_nbar"]))
     for t in ts:
         ctx.wait(t)
@@ -376,12 +449,9 @@ def serving_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_req, slots=4):
     ctx.serve_stop()
     ctx.close()
     return {"requests": len(items), "slots": slots,
-            "mix": "meshes {128,192,256}^3, LOS cycling yamamoto/midpoint/bisector, order in {2,4}, "
-                   "10-100 % of the catalog (log-uniform), P_ell+xi_ell, FP32",
+            "mix": "meshes 128/256/384/512^3, random LOS, order in {0,2,4,6}, 10-100 % of the galaxies and randoms "
+                   "(log-uniform), P_ell+xi_ell, FP32",
             "sequential_catalogs_per_s": len(items) / t_seq,
-            "graph_batch_catalogs_per_s": len(items) / t_graph,
-            "graph_capture_s": t_capture,
-            "batched_catalogs_per_s": len(items) / t_batch,
             "poisson_rate_per_s": rate, "poisson_catalogs_per_s": len(items) / t_stream,
             "p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"],
             "run_p50_s": st["run_p50_s"], "run_p99_s": st["run_p99_s"], "mean_queue_s": st["mean_queue_s"],

@@ -263,6 +263,9 @@ int bym_wait(bym_ctx *ctx, uint64_t ticket, double timeout_s, int *status);
  * [4] p99 of run (start-to-done) seconds, [5] mean queueing seconds,
  * [6] peak HBM bytes charged at once. */
 int bym_serve_stats(bym_ctx *ctx, double stats[7]);
+/* Forget the latency records and restart the peak at the bytes charged now
+ * (e.g. after warm-up requests).  BYM_E_INVAL if no loop is running. */
+int bym_serve_reset_stats(bym_ctx *ctx);
 /* Run n requests through the serving loop (started with 4 slots and the
  * default budget for the call if none is running) and wait for all;
  * status[i] receives each request's return code. */

@@ -94,6 +94,7 @@ def lib():
         L.bym_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
         L.bym_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
         L.bym_serve_stats.argtypes = [vp, dp]
+        L.bym_serve_reset_stats.argtypes = [vp]
         L.bym_batch_run.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(Result),
                                     ctypes.POINTER(ctypes.c_int)]
         L.bym_batch_graph.argtypes = L.bym_batch_run.argtypes
@@ -190,6 +191,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def last_error(self) -> str:
+        return self._L.bym_last_error(self._h).decode()
 
     def _check(self, rc):
         if rc != BYM_OK:
@@ -315,6 +319,9 @@ class Context:
             raise BymError(st.value, f"request {ticket} failed")
         return out
 
+    def serve_reset_stats(self):
+        self._check(self._L.bym_serve_reset_stats(self._h))
+
     def serve_stats(self):
         a = (ctypes.c_double * 7)()
         self._check(self._L.bym_serve_stats(self._h, a))
@@ -346,7 +353,7 @@ class Context:
         rc = fn(self._h, n, reqs, ress, status)
         for i in range(n):
             if status[i] != BYM_OK:
-                raise BymError(status[i], f"batch item {i} failed")
+                raise BymError(status[i], f"batch item {i} failed: {self.last_error()}")
         self._check(rc)
         return outs
 
@@ -394,8 +401,9 @@ class BatchPlan:
                                            status)
         for i in range(n):
             if status[i] != BYM_OK:
+                msg = ctx.last_error()
                 self.close()
-                raise BymError(status[i], f"batch item {i} failed")
+                raise BymError(status[i], f"batch item {i} failed: {msg}")
         ctx._check(rc)
 
     def launch(self):
@@ -403,7 +411,7 @@ class BatchPlan:
         rc = self._L.bym_batch_plan_launch(self._h, status)
         for i in range(self._n):
             if status[i] != BYM_OK:
-                raise BymError(status[i], f"batch item {i} failed")
+                raise BymError(status[i], f"batch item {i} failed: {self._ctx.last_error()}")
         self._ctx._check(rc)
         return self.outputs
 

@@ -1303,6 +1303,13 @@ static int batch_launch(bym_batch *B, int *status) {
   int first_err = BYM_OK;
   int rc = BYM_OK;
   if (cudaSetDevice(c->device) != cudaSuccess) rc = fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+  // the graph's buffers come from the graph memory pool: hand back what the stream-ordered
+  // pool holds unused (it keeps freed memory between requests) before the launch maps them
+  cudaMemPool_t pool;
+  if (!rc && cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    cudaStreamSynchronize(c->stream);
+    cudaMemPoolTrimTo(pool, 0);
+  }
   if (!rc && cudaGraphLaunch(B->exec, B->cs) != cudaSuccess)
     rc = fail(c, BYM_E_CUDA, std::string("batch: graph launch: ") + cudaGetErrorString(cudaGetLastError()));
   if (!rc && cudaStreamSynchronize(B->cs) != cudaSuccess)

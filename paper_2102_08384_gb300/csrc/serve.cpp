@@ -267,6 +267,17 @@ int bym_serve_stats(bym_ctx *c, double stats[7]) {
   return BYM_OK;
 }
 
+int bym_serve_reset_stats(bym_ctx *c) {
+  if (!c || !c->server) return BYM_E_INVAL;
+  Server *s = c->server;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->lat_total.clear();
+  s->lat_run.clear();
+  s->lat_queue.clear();
+  s->peak = s->in_use;
+  return BYM_OK;
+}
+
 int bym_batch_run(bym_ctx *c, int n, const bym_request *reqs, const bym_result *outs, int *status) {
   if (!c || n < 0 || (n > 0 && (!reqs || !outs || !status))) return BYM_E_INVAL;
   const bool temporary = c->server == nullptr;

@@ -184,4 +184,4 @@ def lognormal_cap_catalog(seed: int = 1, n_gal: int = 1_000_000, ran_factor: flo
                    centre - 0.5 * box_len, box_len,
                    {"kind": "lognormal_cap", "seed": seed, "n_gal": len(g), "n_ran": n_ran,
                     "half_angle_deg": half_angle_deg, "r_min": r_min, "r_max": r_max,
-                    "nbar": nbar, "P0": P0, "f": f_growth, "b": bias})
+                    "nbar": nbar, "P0": P0, "f": f_growth, "b": bias, "pole": tuple(float(v) for v in pole)})

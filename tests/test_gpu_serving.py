@@ -98,6 +98,8 @@ def test_admission_timeout_and_errors(pkg, cap):
     np.testing.assert_allclose(a["pk"], b["pk"], rtol=1e-5, atol=1e-5 * np.abs(a["pk"]).max())
     stats = ctx.serve_stats()
     assert stats["peak_hbm_bytes"] <= 1.5 * fp
+    ctx.serve_reset_stats()
+    assert ctx.serve_stats()["count"] == 0
     # a failing request reports its own error code
     bad = np.array(cap.gal, copy=True)
     bad[3, 0] = cap.box_lo[0] - 10.0
