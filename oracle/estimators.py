@@ -26,6 +26,10 @@ line of sight drops out): xi_ell = [DD - 2 DR + RR]_ell / RR_0, the
 Landy-Szalay form Sec. 2.2 names for catalogs (the pair counts of eq.
 general-2pcf-form with delta = n_g - alpha_r n_r).
 
+``interlace=True`` averages every forward transform of a painted field over the
+mesh and the mesh shifted by half a cell along each axis (``_Transforms``), which
+cancels the aliased images of odd index sum; the paper paints without it.
+
 ``shot_noise`` is the FKP shot-noise level (sum_g w^2 + alpha_r^2 sum_r w^2) / A
 that eq. Pk-def includes in P_0 (Sec. 2.1); the estimators do not subtract it.
 The order K is the highest power of theta kept: midpoint alpha <= K, bisector
@@ -70,9 +74,40 @@ def _flip_k(a: np.ndarray) -> np.ndarray:
     return np.roll(a[::-1, ::-1, ::-1], 1, axis=(0, 1, 2))
 
 
-def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate, xi=False):
+class _Transforms:
+    """Forward transforms of painted fields f(x) = w(x) delta(x), with the optional
+    compensation 1/W(k) (Sec. 2.1 footnote) and, with interlacing, the average of
+    the transforms on the mesh and on the mesh shifted by s = (h/2)(1, 1, 1):
+    F = [F_1(k) + P(k) F_2(k)] / 2, P(k) = prod_d p(n_d), p(n) = exp(-i pi n / N)
+    (the shift's phase in the mesh's frame) and p(-N/2) = 0, the mean of the phases
+    of the two labels of the Nyquist index, so that F stays Hermitian."""
+
+    def __init__(self, g, delta, delta2, inv_w):
+        self.g, self.delta, self.delta2, self.inv_w = g, delta, delta2, inv_w
+        if delta2 is not None:
+            self.x2 = g.x + 0.5 * g.h
+            if np.any((np.linalg.norm(self.x2, axis=-1) == 0.0) & (delta2 != 0.0)):
+                raise ValueError("a non-empty shifted mesh node sits on the observer")
+            n = mesh.fft_labels(g.N)
+            p = np.where(n == -g.N // 2, 0.0, np.exp(-1j * np.pi * n / g.N))
+            self.phase = p[:, None, None] * p[None, :, None] * p[None, None, :]
+
+    def fwd(self, wfun=None):
+        """F[w delta](k); wfun(x) gives w at positions x (None: w = 1)."""
+        f = self.delta if wfun is None else wfun(self.g.x) * self.delta
+        F = mesh.fftn(f)
+        if self.delta2 is not None:
+            f2 = self.delta2 if wfun is None else wfun(self.x2) * self.delta2
+            F = 0.5 * (F + self.phase * mesh.fftn(f2))
+        return F * self.inv_w if self.inv_w is not None else F
+
+
+def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate, xi=False, interlace=False):
     g = Grid(N, box_lo, box_len)
     delta, _ = mesh.density_mesh(gal, ran, g.N, g.box_lo, g.box_len, assign)
+    delta2 = None
+    if interlace:   # the same catalog painted on the nodes box_lo + (i + 1/2) h
+        delta2, _ = mesh.density_mesh(gal, ran, g.N, g.box_lo + 0.5 * g.h, g.box_len, assign)
     if norm == 2 and xi:
         if ran is None or len(ran) == 0:
             raise ValueError("norm=2 needs randoms")
@@ -85,13 +120,7 @@ def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate, x
     else:
         A, v_cell = 1.0, 1.0
     inv_w = 1.0 / mesh.compensation(g.N, assign) if compensate else None
-    return g, delta, A, v_cell, inv_w
-
-
-def _fwd(field, inv_w):
-    """Forward transform of a painted-derived field, with the optional 1/W(k)."""
-    F = mesh.fftn(field)
-    return F * inv_w if inv_w is not None else F
+    return g, delta, A, v_cell, inv_w, _Transforms(g, delta, delta2, inv_w)
 
 
 def _ells(ell_max):
@@ -119,7 +148,7 @@ def _xi_out(g, ells, Z, A, v_cell, redges):
 # --------------------------------------------------------------------------
 # midpoint convolution fields g^alpha_JM (eq. g-JM-form)
 # --------------------------------------------------------------------------
-def g_fields(g: Grid, delta, D, K, ell_max, inv_w, even=False):
+def g_fields(g: Grid, delta, D, K, ell_max, tr, even=False):
     """g^alpha_JM(Delta) = (-1)^J IFFT[ delta*(k) F[(2r)^-alpha Y_J^M delta](k) ](Delta)
     for alpha <= K and J = alpha, alpha-2, ... <= ell_max + alpha (the J with
     non-zero phi / f for even ell).  Cells with delta = 0 carry no field; a
@@ -127,13 +156,16 @@ def g_fields(g: Grid, delta, D, K, ell_max, inv_w, even=False):
     if np.any((g.r == 0.0) & (delta != 0.0)):
         raise ValueError("a non-empty mesh node sits on the observer")
     Dc = np.conj(D)
-    safe_r = np.where(g.r == 0.0, 1.0, g.r)
+
+    def radial(x, alpha):   # (2 r)^-alpha, 0 on the observer (where no painted node may sit)
+        r = np.linalg.norm(x, axis=-1)
+        return np.where(r == 0.0, 0.0, (2.0 * np.where(r == 0.0, 1.0, r)) ** (-alpha))
+
     out = {}
     for alpha in range(0, K + 1, 2 if even else 1):
-        radial = np.where(delta != 0.0, (2.0 * safe_r) ** (-alpha), 0.0) * delta
         for J in range(alpha % 2, ell_max + alpha + 1, 2):
             for M in range(-J, J + 1):
-                F = _fwd(radial * ylm(J, M, g.x), inv_w)
+                F = tr.fwd(lambda x: radial(x, alpha) * ylm(J, M, x))
                 out[(alpha, J, M)] = (-1) ** J * mesh.ifftn(Dc * F)
     return out
 
@@ -142,25 +174,25 @@ def g_fields(g: Grid, delta, D, K, ell_max, inv_w, even=False):
 # public entry points (mirror the library's pk_multipoles / xi_multipoles)
 # --------------------------------------------------------------------------
 def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
-                  order, kedges, compensate=False, norm=1):
+                  order, kedges, compensate=False, norm=1, interlace=False):
     """P_ell(k) for ell = 0, 2, .., ell_max with LOS in
     {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
-    g, delta, A, _, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
-                                     assign, norm, compensate)
+    g, delta, A, _, inv_w, tr = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
+                                         assign, norm, compensate, interlace=interlace)
     ells = _ells(ell_max)
-    D = _fwd(delta, inv_w)
+    D = tr.fwd()
     T = {}
     if los == "yamamoto":
         # eq. Yamamoto-estimator: sum_m Y*(k) F[Y delta](k) delta*(k)
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                F = _fwd(ylm(ell, m, g.x) * delta, inv_w)
+                F = tr.fwd(lambda x: ylm(ell, m, x))
                 acc += np.conj(ylm(ell, m, g.k)) * F * np.conj(D)
             T[ell] = acc.real
     elif los == "midpoint":
         # eq. FFT-midpoint: sum_m Y*(k) sum phi F[ Y_J1^M(Delta) Delta^alpha g^alpha_{J2 (m-M)}(Delta) ](k)
-        gf = g_fields(g, delta, D, order, ell_max, inv_w)
+        gf = g_fields(g, delta, D, order, ell_max, tr)
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
@@ -173,7 +205,7 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
             T[ell] = acc.real
     elif los == "midpoint_even":
         # Sec. 3.3 boxed parity-even estimator: eq. FFT-midpoint with phi -> Phi, even alpha only
-        gf = g_fields(g, delta, D, order, ell_max, inv_w, even=True)
+        gf = g_fields(g, delta, D, order, ell_max, tr, even=True)
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
@@ -188,7 +220,7 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
         # eq. bisector-pk-fft: sum_m Y*(k) sum B F[Y_J1^M delta](-k) F[Y_J2^{m-M} delta](k)
         bmax = order // 2
         Jmax = ell_max + bmax
-        F = {(J, M): _fwd(ylm(J, M, g.x) * delta, inv_w)
+        F = {(J, M): tr.fwd(lambda x, J=J, M=M: ylm(J, M, x))
              for J in range(Jmax + 1) for M in range(-J, J + 1)}
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
@@ -212,25 +244,25 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
 
 
 def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
-                  order, redges, compensate=False, norm=1):
+                  order, redges, compensate=False, norm=1, interlace=False):
     """xi_ell(r) for ell = 0, 2, .., ell_max with LOS in
     {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
-    g, delta, A, v_cell, inv_w = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
-                                          assign, norm, compensate, xi=True)
+    g, delta, A, v_cell, inv_w, tr = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
+                                              assign, norm, compensate, xi=True, interlace=interlace)
     ells = _ells(ell_max)
-    D = _fwd(delta, inv_w)
+    D = tr.fwd()
     Z = {}
     if los == "yamamoto":
         # eq. 2pcf-yama: sum_m Y*(Delta) IFFT[delta*(k) F[Y delta](k)](Delta)
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                F = _fwd(ylm(ell, m, g.x) * delta, inv_w)
+                F = tr.fwd(lambda x: ylm(ell, m, x))
                 acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(np.conj(D) * F)
             Z[ell] = acc.real
     elif los == "midpoint":
         # eq. xi-parity-all-estimator: sum f Y_J^M*(Delta) Delta^alpha g^alpha_JM(Delta)
-        gf = g_fields(g, delta, D, order, ell_max, inv_w)
+        gf = g_fields(g, delta, D, order, ell_max, tr)
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
             for alpha in range(order + 1):
@@ -241,7 +273,7 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
             Z[ell] = acc.real
     elif los == "midpoint_even":
         # Sec. 4.3 boxed parity-even estimator: f -> F, even alpha only
-        gf = g_fields(g, delta, D, order, ell_max, inv_w, even=True)
+        gf = g_fields(g, delta, D, order, ell_max, tr, even=True)
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
             for alpha in range(0, order + 1, 2):
@@ -254,7 +286,7 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
         # Sec. 6: sum_m Y*(Delta) IFFT[ sum B F[Y_J1^M delta](-k) F[Y_J2^{m-M} delta](k) ](Delta)
         bmax = order // 2
         Jmax = ell_max + bmax
-        F = {(J, M): _fwd(ylm(J, M, g.x) * delta, inv_w)
+        F = {(J, M): tr.fwd(lambda x, J=J, M=M: ylm(J, M, x))
              for J in range(Jmax + 1) for M in range(-J, J + 1)}
         for ell in ells:
             acc = np.zeros(D.shape, dtype=np.complex128)
@@ -276,17 +308,18 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
         raise ValueError(f"unknown los {los!r}")
     out = _xi_out(g, ells, Z, A, v_cell, redges)
     if norm == 2:
-        out["xi"] = out["xi"] / _rr0(gal, ran, N, box_lo, box_len, assign, redges, compensate)[None, :]
+        out["xi"] = out["xi"] / _rr0(gal, ran, N, box_lo, box_len, assign, redges, compensate, interlace)[None, :]
     return out
 
 
-def _rr0(gal, ran, N, box_lo, box_len, assign, redges, compensate):
+def _rr0(gal, ran, N, box_lo, box_len, assign, redges, compensate, interlace=False):
     """RR_0(r_b): the raw ell = 0 sum of the mesh estimator for alpha_r n_r (any
     line of sight gives the same ell = 0 sum; Yamamoto is used), bins without
     random pairs set to infinity so that their ratio is 0."""
     alpha, _ = mesh.norm_factors(gal, ran, None)
     rr = xi_multipoles(ran, None, None, N=N, box_lo=box_lo, box_len=box_len, assign=assign, ell_max=0,
-                       los="yamamoto", order=0, redges=redges, compensate=compensate, norm=0)["xi"][0]
+                       los="yamamoto", order=0, redges=redges, compensate=compensate, norm=0,
+                       interlace=interlace)["xi"][0]
     rr = alpha * alpha * rr
     return np.where(rr != 0.0, rr, np.inf)
 
