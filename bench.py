@@ -301,6 +301,7 @@ def run_ours(args):
         gal_p = gal_d[perm].contiguous()
         permr = torch.randperm(ran_d.shape[0], device=dev)
         ran_p, rnb_p = ran_d[permr].contiguous(), rnb_d[permr].contiguous()
+        line["next_rows"] = next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, args.mesh)
         line["batch"] = batch_leg(pkg, torch, dev, cat, gal_p, ran_p, rnb_p)
         line["serving"] = serving_leg(pkg, torch, dev, cat, gal_p, ran_p, rnb_p, args.serve_requests)
     if ws == 1 and not args.no_cpu_baseline:
@@ -331,6 +332,54 @@ def _mock_subsets(torch, cat, gal_d, ran_d, rnb_d, rng, frac, half_angle_deg):
     r = ran_d[: int(frac * ran_d.shape[0])][keep].contiguous()
     rn = rnb_d[: int(frac * rnb_d.shape[0])][keep].contiguous()
     return g, r, rn
+
+
+def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
+    """The benchmark catalog at the benchmark mesh through the extensions beyond the paper's
+    boxed estimators (hybrid FFT backend), each timed (CUDA events, after one warm-up run)
+    beside its device footprint: the parity-even midpoint form; the midpoint g fields streamed in ranges of 45;
+    the bisector fields in blocks of 16; xi normalised by the random-random count."""
+    ctx = pkg.Context(dev.index)
+    ctx.set_fft_backend(4)        # the FFT path the autotuner picks for the benchmark step
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    cases = [("midpoint_even order 4", "midpoint_even", 4, 1, 0),
+             ("midpoint order 4, g fields in ranges of 45", "midpoint", 4, 1, 45),
+             ("bisector order 4, fields in blocks of 16", "bisector", 4, 1, 16),
+             ("midpoint order 4, xi / RR (norm 2)", "midpoint", 4, 2, 0),
+             ("bisector order 4, interlaced", "bisector", 4, 1, -1)]
+    out = {}
+    for label, los, K, norm, chunk in cases:
+        il = chunk < 0                   # -1: interlaced, resident
+        chunk = max(chunk, 0)
+        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=n_mesh, assign=3, ell_max=ELL_MAX, los=los,
+                            order=K, compensate=True, precision=32, norm=norm, interlace=il)
+        ctx.set_field_chunk(chunk)
+        ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        n_f = {"midpoint_even": 88, "midpoint": 145, "bisector": 49}[los]
+        slot = n_mesh * n_mesh * (n_mesh + 2) * 4
+        if chunk and los == "midpoint":
+            slots = 2 + chunk + 15
+        elif chunk:
+            slots = 1 + 2 * chunk + 15
+        elif il:
+            slots = 2 + 2 * n_f + 15
+        else:
+            slots = 1 + n_f + 15
+        out[label] = {"ms_per_catalog": ms, "catalogs_per_s": 1000.0 / ms, "mesh_slots": slots,
+                      "field_memory_gb": slots * slot / 1e9}
+    ctx.set_field_chunk(0)
+    ctx.close()
+    return out
 
 
 def batch_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mocks=64, slots=4):

@@ -93,6 +93,11 @@ typedef struct {
   int compensate;     /* 1: divide each painted-field transform by the assignment window W(k) */
   int precision;      /* 32: FP32 fields and FFTs; 64: FP64 throughout. Shell sums are FP64 either way */
   int norm;           /* 1: FKP normalisation A; 0: raw (A = V_cell = 1); 2: FKP for P, RR for xi */
+  int interlace;      /* 1: every painted-field transform averaged with the one on the mesh shifted by
+                         half a cell, (F_1 + P F_2) / 2, P(k) = prod_d exp(-i pi n_d / N) (0 at the
+                         Nyquist index): cancels the aliased images of odd index sum.  Doubles the
+                         paintings, field generations and forward transforms and the field memory;
+                         not combined with field ranges (bym_set_field_chunk) */
 } bym_params;
 
 typedef struct {

@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
     _fields_ = [("box_lo", ctypes.c_double * 3), ("box_len", ctypes.c_double), ("n_mesh", ctypes.c_int),
                 ("assign", ctypes.c_int), ("ell_max", ctypes.c_int), ("los", ctypes.c_int),
                 ("order", ctypes.c_int), ("compensate", ctypes.c_int), ("precision", ctypes.c_int),
-                ("norm", ctypes.c_int)]
+                ("norm", ctypes.c_int),
+                ("interlace", ctypes.c_int)]
 
 
 class Bins(ctypes.Structure):
@@ -115,7 +116,7 @@ def lib():
 
 
 def make_params(*, box_lo, box_len, n_mesh, assign=2, ell_max=4, los="yamamoto", order=0,
-                compensate=False, precision=32, norm=1) -> Params:
+                compensate=False, precision=32, norm=1, interlace=False) -> Params:
     p = Params()
     p.box_lo[:] = [float(v) for v in box_lo]
     p.box_len = float(box_len)
@@ -127,6 +128,7 @@ def make_params(*, box_lo, box_len, n_mesh, assign=2, ell_max=4, los="yamamoto",
     p.compensate = int(bool(compensate))
     p.precision = int(precision)
     p.norm = int(norm)
+    p.interlace = int(bool(interlace))
     return p
 
 

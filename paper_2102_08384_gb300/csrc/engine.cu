@@ -151,6 +151,7 @@ int bym::validate_params(bym_ctx *c, const bym_params *p) {
   if (p->precision != 32 && p->precision != 64) return fail(c, BYM_E_INVAL, "precision must be 32 or 64");
   if (p->norm < 0 || p->norm > 2) return fail(c, BYM_E_INVAL, "norm must be 0, 1 or 2");
   if (p->compensate != 0 && p->compensate != 1) return fail(c, BYM_E_INVAL, "compensate must be 0 or 1");
+  if (p->interlace != 0 && p->interlace != 1) return fail(c, BYM_E_INVAL, "interlace must be 0 or 1");
   if (!(p->box_len > 0.0) || !std::isfinite(p->box_len) || !finite_all(p->box_lo, 3))
     return fail(c, BYM_E_INVAL, "box must be finite with box_len > 0");
   return BYM_OK;
@@ -208,6 +209,7 @@ size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, b
   size_t fslots = 1 + nf;                                   // delta + every field
   if (chunk > 0 && is_midpoint(p)) fslots = 2 + std::min(nf, (size_t)chunk);          // two deltas, a range
   if (chunk > 0 && p->los == BYM_LOS_BISECTOR) fslots = 1 + 2 * std::min(nf, (size_t)chunk);  // two blocks
+  if (p->interlace) fslots = 2 + 2 * nf;                  // the second set on the shifted mesh
   const size_t slots = fslots + (size_t)n_extra_slots(p, want_pk, want_xi);
   size_t cats = 0;
   if (!cats_on_device) cats = (size_t)(std::max<int64_t>(n_gal, 0) + std::max<int64_t>(n_ran, 0)) * 20;
@@ -533,7 +535,7 @@ static size_t device_available(bym_ctx *c, size_t headroom) {
 // small uploads and for the results, and what the host step after the launch needs.
 struct Pending {
   double *host = nullptr;       // pinned: [8 stats][NL * nbk P sums][NL * nbr xi sums]
-  char *stage = nullptr;        // pinned: [nf scale factors (double)][n_mesh 1/W values (T)]
+  char *stage = nullptr;        // pinned: [nf scale factors (double)][n_mesh 1/W (T)][n_mesh phases (T2)]
   size_t host_len = 0, stage_len = 0;
   Geom *kg = nullptr, *rg = nullptr;
   int NL = 0, nbk = 0, nbr = 0;
@@ -604,7 +606,9 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   const bool cats_dev = rq.gal->on_device && (!rq.ran || rq.ran->on_device);
   const int64_t ngal = rq.gal->n, nran = rq.ran ? rq.ran->n : 0;
   int chunk = 0;
-  if (is_midpoint(p) || p->los == BYM_LOS_BISECTOR) {
+  if (p->interlace && c->field_chunk > 0 && p->los != BYM_LOS_YAMAMOTO)
+    return fail(c, BYM_E_UNSUPPORTED, "interlacing keeps every field resident: no field ranges");
+  if (!p->interlace && (is_midpoint(p) || p->los == BYM_LOS_BISECTOR)) {
     if (c->field_chunk > 0) {
       chunk = std::min(c->field_chunk, nf);
     } else {
@@ -722,12 +726,16 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   const bool bis_blocks = chunk && p->los == BYM_LOS_BISECTOR;
   const int fbase = (chunk && !bis_blocks) ? 2 : 1;
   const int nfs = !chunk ? nf : (bis_blocks ? 2 * chunk : chunk), xbase = fbase + nfs;
-  const int nslots = xbase + nextra;
+  // interlacing: [ibase] delta on the shifted mesh, then its field set
+  const bool il = p->interlace != 0;
+  const int ibase = xbase + nextra;
+  const int nslots = ibase + (il ? 1 + nf : 0);
   T *slots = nullptr;
   TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
   auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
   auto slot_c = [&](int i) { return (T2 *)(slots + (long long)i * slot_reals); };
   CUDA_TRY(cudaMemsetAsync(slots, 0, slot_bytes, st));
+  if (il) CUDA_TRY(cudaMemsetAsync(slot_r(ibase), 0, slot_bytes, st));
 
   // norms and painting
   const double esz = (double)sizeof(T), n3 = (double)N * N * N, nhalf = (double)N * N * (N / 2 + 1);
@@ -740,6 +748,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     if (cat4[w]) {
       ProfScope ps(c, st, "paint", catn[w] * 16.0 + n3 * esz);
       launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(0), N, p->box_lo, inv_h, p->assign, c->nsm, st);
+      if (il)
+        launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(ibase), N, p->box_lo, inv_h, p->assign, c->nsm, st, 0.5);
     }
   CUDA_TRY(cudaGetLastError());
   static const char *kLosName[4] = {"yamamoto", "midpoint", "bisector", "midpoint_even"};
@@ -754,6 +764,35 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     CUDA_TRY(cudaMemsetAsync(slot_r(1), 0, (size_t)nf * slot_bytes, st));
     CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
                     slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+    if (il) {   // the same fields on the shifted mesh, from its delta and node positions
+      CUDA_TRY(cudaMemsetAsync(slot_r(ibase + 1), 0, (size_t)nf * slot_bytes, st));
+      CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(ibase),
+                      slot_r(ibase + 1), slot_reals, N, p->box_lo[0] + 0.5 * h, p->box_lo[1] + 0.5 * h,
+                      p->box_lo[2] + 0.5 * h, h, inv_r0));
+    }
+  }
+  if (il) {
+    // forward transforms of both sets (delta and the fields), then F <- (F + P G) / 2
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, ibase, 1 + nf, tn));
+    std::vector<T2> ph((size_t)N);
+    for (int i = 0; i < N; ++i) {
+      const int n = lab(i, N);
+      const double a = -M_PI * n / N;
+      ph[(size_t)i].x = n == -N / 2 ? (T)0 : (T)std::cos(a);
+      ph[(size_t)i].y = n == -N / 2 ? (T)0 : (T)std::sin(a);
+    }
+    T2 *dph = nullptr;
+    TRY(alloc((void **)&dph, sizeof(T2) * N));
+    const void *src = ph.data();
+    if (pd) {
+      T2 *dst = (T2 *)(pd->stage + sizeof(double) * (size_t)nf + sizeof(T) * (size_t)N);
+      std::copy(ph.begin(), ph.end(), dst);
+      src = dst;
+    }
+    CUDA_TRY(cudaMemcpyAsync(dph, src, sizeof(T2) * N, cudaMemcpyHostToDevice, st));
+    ProfScope ps(c, st, "interlace", (1.0 + nf) * 3.0 * cplx);
+    launch_interlace<T, T2>(slot_c(0), slot_c(ibase), cslot, 1 + nf, N, dph, c->nsm, st);
   }
 
   const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, tn.per_sm_k);
@@ -761,7 +800,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   const double tscale = h * inv_r0;
 
   if (p->los == BYM_LOS_YAMAMOTO) {
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
+    if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
     if (want_pk) {
       ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
@@ -811,8 +850,16 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
     }
   } else if (is_midpoint(p)) {
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
-    TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 1, nf, scale, invw, tn)));
+    if (il) {   // spectra ready (interlaced): the product and the inverse transforms
+      {
+        ProfScope ps(c, st, "spec_mul", (2.0 * nf + 1.0) * cplx);
+        launch_spec_mul<T, T2>(slot_c(1), cslot, nf, slot_c(0), N, scale, invw, c->nsm * tn.per_sm_spec / 8, st);
+      }
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
+    } else {
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
+      TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 1, nf, scale, invw, tn)));
+    }
     if (want_xi) {
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
       ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nf * esz);
@@ -869,7 +916,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
                       1.0 / ((double)N * N * N), tscale));
     }
   } else {
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf, tn));
+    if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf, tn));
     if (want_xi) {
       {
         ProfScope ps(c, st, "kcontract_bisector_x", ((double)nf + nlm) * cplx);
@@ -1223,7 +1270,7 @@ static int batch_create(bym_ctx *c, int n, const bym_request *reqs, const bym_re
     const int NL = rq.p->ell_max / 2 + 1;
     pd.host_len =
         sizeof(double) * (8 + (size_t)NL * (rq.kb ? rq.kb->nbins : 1) + (size_t)NL * (rq.rb ? rq.rb->nbins : 1));
-    pd.stage_len = sizeof(double) * (size_t)(n_fields(rq.p) + rq.p->n_mesh + 2);
+    pd.stage_len = sizeof(double) * (size_t)(n_fields(rq.p) + 3 * rq.p->n_mesh + 2);   // scale, 1/W, phases
     total += pd.host_len + pd.stage_len;
   };
   for (auto &m : B->it)

@@ -5,7 +5,9 @@
 //   bym_paint         CIC / TSC mass assignment of signed weights w and -alpha_r w
 //                     into the padded real mesh (periodic, FP64 cell geometry);
 //   bym_spec_mul      F(k) <- F(k) conj(delta(k)) s_f W(k)^-2 for a run of field
-//                     spectra (the convolution step of eq. g-JM-form / eq. 2pcf-yama).
+//                     spectra (the convolution step of eq. g-JM-form / eq. 2pcf-yama);
+//   bym_interlace     F(k) <- (F(k) + P(k) G(k)) / 2 with G the transform on the mesh
+//                     shifted by half a cell (interlaced mass assignment).
 #include "kernels.cuh"
 
 namespace bym {
@@ -72,11 +74,13 @@ __global__ void __launch_bounds__(256) bym_norm_reduce(const float4 *__restrict_
 
 // One thread per object.  Galaxies carry +w, randoms -alpha_r w with
 // alpha_r = stats[0] / stats[1] read on the device.  Objects outside the box
-// are skipped (the call reports them as an error).
+// are skipped (the call reports them as an error).  shift (in cells, 0 or 1/2):
+// paint onto the nodes box_lo + (i + shift) h, periodically (interlacing).
 template <typename T>
 __global__ void __launch_bounds__(256) bym_paint(const float4 *__restrict__ p, long long n, int is_ran,
                                                  const double *__restrict__ stats, T *__restrict__ delta, int N,
-                                                 double lo0, double lo1, double lo2, double inv_h, int assign) {
+                                                 double lo0, double lo1, double lo2, double inv_h, int assign,
+                                                 double shift) {
   const double scale = is_ran ? -(stats[0] / stats[1]) : 1.0;
   const long long row = (long long)(N + 2);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -88,21 +92,22 @@ __global__ void __launch_bounds__(256) bym_paint(const float4 *__restrict__ p, l
       int b[3];
       double f[3];
       for (int a = 0; a < 3; ++a) {
-        const double fl = floor(u[a]);
+        const double us = u[a] - shift;
+        const double fl = floor(us);
         b[a] = (int)fl;
-        f[a] = u[a] - fl;
+        f[a] = us - fl;
       }
 #pragma unroll
       for (int ox = 0; ox < 2; ++ox) {
-        const int ix = (b[0] + ox) % N;
+        const int ix = (b[0] + ox + N) % N;
         const double wx = ox ? f[0] : 1.0 - f[0];
 #pragma unroll
         for (int oy = 0; oy < 2; ++oy) {
-          const int iy = (b[1] + oy) % N;
+          const int iy = (b[1] + oy + N) % N;
           const double wy = oy ? f[1] : 1.0 - f[1];
 #pragma unroll
           for (int oz = 0; oz < 2; ++oz) {
-            const int iz = (b[2] + oz) % N;
+            const int iz = (b[2] + oz + N) % N;
             const double wz = oz ? f[2] : 1.0 - f[2];
             atomic_add(delta + ((long long)ix * N + iy) * row + iz, (T)(w * wx * wy * wz));
           }
@@ -112,9 +117,10 @@ __global__ void __launch_bounds__(256) bym_paint(const float4 *__restrict__ p, l
       int b[3];
       double wt[3][3];
       for (int a = 0; a < 3; ++a) {
-        const double fl = floor(u[a] + 0.5);
+        const double us = u[a] - shift;
+        const double fl = floor(us + 0.5);
         b[a] = (int)fl;
-        const double d = u[a] - fl;
+        const double d = us - fl;
         wt[a][0] = 0.5 * (0.5 - d) * (0.5 - d);
         wt[a][1] = 0.75 - d * d;
         wt[a][2] = 0.5 * (0.5 + d) * (0.5 + d);
@@ -166,6 +172,34 @@ __global__ void __launch_bounds__(256) bym_spec_mul(T2 *__restrict__ F, long lon
   }
 }
 
+// Interlacing: F_f(k) <- (F_f(k) + P(k) G_f(k)) / 2 for f = 0..nf-1, with G the transform of
+// the same field on the mesh shifted by half a cell along each axis and P(k) = prod over the
+// axes of ph[n_axis] (per-axis phase exp(-i pi n / N) of the shift, 0 at the Nyquist index).
+template <typename T, typename T2>
+__global__ void __launch_bounds__(256) bym_interlace(T2 *__restrict__ F, const T2 *__restrict__ G, long long cslot,
+                                                     int nf, int N, const T2 *__restrict__ ph) {
+  const int H = N / 2 + 1;
+  const long long nm = (long long)N * N * H;
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += (long long)gridDim.x * blockDim.x) {
+    const int iz = (int)(m % H);
+    const long long row = m / H;
+    const T2 px = ph[(int)(row / N)], py = ph[(int)(row % N)], pz = ph[iz];
+    T2 pxy, p;
+    pxy.x = px.x * py.x - px.y * py.y;
+    pxy.y = px.x * py.y + px.y * py.x;
+    p.x = pxy.x * pz.x - pxy.y * pz.y;
+    p.y = pxy.x * pz.y + pxy.y * pz.x;
+    for (int f = 0; f < nf; ++f) {
+      const long long o = (long long)f * cslot + m;
+      const T2 a = F[o], b = G[o];
+      T2 r;
+      r.x = (T)0.5 * (a.x + p.x * b.x - p.y * b.y);
+      r.y = (T)0.5 * (a.y + p.x * b.y + p.y * b.x);
+      F[o] = r;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 static unsigned grid_for(long long work, int nsm) {
   long long g = (work + 255) / 256;
@@ -183,10 +217,10 @@ void launch_norm_reduce(const float4 *p, const float *nbar, long long n, int whi
 
 template <typename T>
 void launch_paint(const float4 *p, long long n, int is_ran, const double *stats, T *delta, int N, const double lo[3],
-                  double inv_h, int assign, int nsm, cudaStream_t st) {
+                  double inv_h, int assign, int nsm, cudaStream_t st, double shift) {
   if (n <= 0) return;
   bym_paint<T><<<grid_for(n, nsm * 4), 256, 0, st>>>(p, n, is_ran, stats, delta, N, lo[0], lo[1], lo[2], inv_h,
-                                                      assign);
+                                                      assign, shift);
 }
 
 template <typename T, typename T2>
@@ -197,10 +231,21 @@ void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const d
   bym_spec_mul<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(F, cslot, nf, D, N, scale, invw);
 }
 
+template <typename T, typename T2>
+void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st) {
+  if (nf <= 0) return;
+  const long long nm = (long long)N * N * (N / 2 + 1);
+  bym_interlace<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(F, G, cslot, nf, N, ph);
+}
+
+template void launch_interlace<float, float2>(float2 *, const float2 *, long long, int, int, const float2 *, int,
+                                              cudaStream_t);
+template void launch_interlace<double, double2>(double2 *, const double2 *, long long, int, int, const double2 *, int,
+                                                cudaStream_t);
 template void launch_paint<float>(const float4 *, long long, int, const double *, float *, int, const double *, double,
-                                  int, int, cudaStream_t);
+                                  int, int, cudaStream_t, double);
 template void launch_paint<double>(const float4 *, long long, int, const double *, double *, int, const double *,
-                                   double, int, int, cudaStream_t);
+                                   double, int, int, cudaStream_t, double);
 template void launch_spec_mul<float, float2>(float2 *, long long, int, const float2 *, int, const double *,
                                              const float *, int, cudaStream_t);
 template void launch_spec_mul<double, double2>(double2 *, long long, int, const double2 *, int, const double *,

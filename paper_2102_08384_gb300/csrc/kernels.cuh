@@ -7,12 +7,17 @@ namespace bym {
 void launch_norm_reduce(const float4 *p, const float *nbar, long long n, int which, const double lo[3], double inv_h,
                         int N, double *stats, int nsm, cudaStream_t st);
 
+// shift (cells): paint onto the nodes box_lo + (i + shift) h (interlacing uses 1/2)
 template <typename T>
 void launch_paint(const float4 *p, long long n, int is_ran, const double *stats, T *delta, int N, const double lo[3],
-                  double inv_h, int assign, int nsm, cudaStream_t st);
+                  double inv_h, int assign, int nsm, cudaStream_t st, double shift = 0.0);
 
 template <typename T, typename T2>
 void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const double *scale, const T *invw, int nsm,
                      cudaStream_t st);
+
+// F_f <- (F_f + P G_f) / 2, P(k) = ph[n_x] ph[n_y] ph[n_z] (half-spectrum slots)
+template <typename T, typename T2>
+void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st);
 
 }  // namespace bym

@@ -1,5 +1,6 @@
 """GPU parity of the LOS-independent extras against the FP64 oracle: the
-random-random normalised xi_ell (norm=2) and the shot-noise level of P_0."""
+random-random normalised xi_ell (norm=2), the shot-noise level of P_0 and
+interlaced mass assignment."""
 import math
 
 import numpy as np
@@ -108,3 +109,43 @@ def test_shot_noise_device_and_errors(pkg, ctx, cube):
         ctx.pk_multipoles(cube.gal, cube.ran, pkg.make_params(box_lo=cube.box_lo, box_len=cube.box_len, n_mesh=16,
                                                               norm=3), np.linspace(0, 0.1, 3), ran_nbar=cube.ran_nbar)
     assert ei.value.code == -1
+
+
+# ---------------------------------------------------------------- interlacing
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("bisector", 2), ("midpoint_even", 2)])
+def test_interlaced_fp64(pkg, ctx, cube, los, K):
+    N = 32
+    kedges = np.linspace(0.0, math.pi / (cube.box_len / N), 9)
+    redges = np.linspace(0.0, 250.0, 11)
+    p = pkg.make_params(box_lo=cube.box_lo, box_len=cube.box_len, n_mesh=N, ell_max=4, los=los, order=K,
+                        precision=64, assign=3, compensate=True, interlace=True)
+    got = ctx.pk_xi_multipoles(cube.gal, cube.ran, p, kedges, redges, ran_nbar=cube.ran_nbar)
+    kw = dict(N=N, box_lo=cube.box_lo, box_len=cube.box_len, assign=3, ell_max=4, los=los, order=K,
+              compensate=True, interlace=True)
+    want_p = E.pk_multipoles(cube.gal, cube.ran, cube.ran_nbar, kedges=kedges, **kw)["pk"]
+    want_x = E.xi_multipoles(cube.gal, cube.ran, cube.ran_nbar, redges=redges, **kw)["xi"]
+    check_multipoles(got["pk"], want_p, "pk", 1e-10, 1e-10, f"{los} interlaced P: ")
+    check_multipoles(got["xi"], want_x, "xi", 1e-10, 1e-10, f"{los} interlaced xi: ")
+
+
+def test_interlaced_fp32_cap_and_errors(pkg, ctx):
+    cap = lognormal_cap_catalog(seed=6, n_gal=30000, ran_factor=10.0, gen_mesh=64)
+    N = 40
+    kedges = np.linspace(0.0, math.pi / (cap.box_len / N), 11)
+    redges = np.linspace(0.0, 8 * cap.box_len / N, 9)
+    p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=4, los="midpoint", order=4,
+                        precision=32, assign=2, compensate=True, interlace=True)
+    got = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
+    kw = dict(N=N, box_lo=cap.box_lo, box_len=cap.box_len, assign=2, ell_max=4, los="midpoint", order=4,
+              compensate=True, interlace=True)
+    check_multipoles(got["pk"], E.pk_multipoles(cap.gal, cap.ran, cap.ran_nbar, kedges=kedges, **kw)["pk"], "pk",
+                     label="interlaced FP32 P: ")
+    check_multipoles(got["xi"], E.xi_multipoles(cap.gal, cap.ran, cap.ran_nbar, redges=redges, **kw)["xi"], "xi",
+                     label="interlaced FP32 xi: ")
+    ctx.set_field_chunk(8)
+    try:
+        with pytest.raises(pkg.BymError) as ei:      # interlacing keeps every field resident
+            ctx.pk_multipoles(cap.gal, cap.ran, p, kedges, ran_nbar=cap.ran_nbar)
+        assert ei.value.code == -6
+    finally:
+        ctx.set_field_chunk(0)

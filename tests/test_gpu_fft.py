@@ -70,13 +70,14 @@ def cat():
     return lognormal_cap_catalog(seed=9, n_gal=200_000, ran_factor=10.0, gen_mesh=128)
 
 
-@pytest.mark.parametrize("los,K,mode", [("yamamoto", 0, 1), ("midpoint", 4, 1), ("bisector", 4, 1),
-                                        ("midpoint_even", 2, 1), ("midpoint", 2, 3), ("bisector", 2, 3),
-                                        ("midpoint", 4, 4), ("bisector", 4, 4), ("yamamoto", 0, 4)])
-def test_requests_native_vs_cufft(env, cat, los, K, mode):
+@pytest.mark.parametrize("los,K,mode,il", [("yamamoto", 0, 1, 0), ("midpoint", 4, 1, 0), ("bisector", 4, 1, 0),
+                                           ("midpoint_even", 2, 1, 0), ("midpoint", 2, 3, 0), ("bisector", 2, 3, 0),
+                                           ("midpoint", 4, 4, 0), ("bisector", 4, 4, 0), ("yamamoto", 0, 4, 0),
+                                           ("midpoint", 2, 4, 1), ("bisector", 2, 1, 1)])
+def test_requests_native_vs_cufft(env, cat, los, K, mode, il):
     torch, pkg, lib, ctx = env
     p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
-                        compensate=True, precision=32)
+                        compensate=True, precision=32, interlace=bool(il))
     kedges = np.round(np.arange(0.01, 0.2501, 0.01), 10)
     redges = np.arange(10.0, 190.01, 10.0)
     out = {}

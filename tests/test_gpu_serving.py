@@ -138,6 +138,10 @@ def test_batch_graph_matches_sequential(pkg, cap):
                          precision=32, norm=2)
     items.append(dict(gal=cap.gal, ran=cap.ran, params=p2, kedges=np.linspace(0.0, 0.3, 7),
                       redges=np.linspace(0.0, 300.0, 6), ran_nbar=cap.ran_nbar))
+    p3 = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=36, ell_max=4, los="bisector", order=2,
+                         precision=64, interlace=True)
+    items.append(dict(gal=cap.gal, ran=cap.ran, params=p3, kedges=np.linspace(0.0, 0.3, 7),
+                      redges=np.linspace(0.0, 300.0, 6), ran_nbar=cap.ran_nbar))
     items = items + items[:3]            # repeated shapes reuse the warmed caches
     ctx = pkg.Context(0)
     seq = [ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], it["kedges"], it["redges"],
