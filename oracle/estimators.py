@@ -30,6 +30,16 @@ general-2pcf-form with delta = n_g - alpha_r n_r).
 mesh and the mesh shifted by half a cell along each axis (``_Transforms``), which
 cancels the aliased images of odd index sum; the paper paints without it.
 
+Cross spectra of two tracers (``gal_b``, ``ran_b``, ``ran_nbar_b``): delta_A from
+(gal, ran), delta_B from the second pair, normalisation A = sqrt(A_A A_B) (V_cell
+unchanged).  With two densities the two anchored terms of the midpoint series are
+no longer equal, so the estimator keeps both (Sec. 3.2, the bracket before eq.
+P-ell-k-symm): for even ell they give g = [g^AB + g^BA] / 2, with
+g^XY = (-1)^J IFFT[delta_X*(k) F[(2r)^-alpha Y_J^M delta_Y](k)] (eq. g-JM-form with
+the two densities in place of one).  Yamamoto takes the mean of its two endpoint
+lines of sight in the same way; the bisector sum of eq. bisector-pk-fft takes
+F[Y delta_A](-k) F[Y delta_B](k).  norm=2 is not defined for cross correlations.
+
 ``shot_noise`` is the FKP shot-noise level (sum_g w^2 + alpha_r^2 sum_r w^2) / A
 that eq. Pk-def includes in P_0 (Sec. 2.1); the estimators do not subtract it.
 The order K is the highest power of theta kept: midpoint alpha <= K, bisector
@@ -123,6 +133,40 @@ def _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate, x
     return g, delta, A, v_cell, inv_w, _Transforms(g, delta, delta2, inv_w)
 
 
+class _Tracer:
+    """One density on the mesh: its painted delta, transforms and spectrum D."""
+
+    def __init__(self, delta, tr):
+        self.delta, self.tr = delta, tr
+        self.D = tr.fwd()
+
+
+def _tracers(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign, norm, compensate,
+             xi=False, interlace=False):
+    """(grid, tracer A, tracer B, A, V_cell); tracer B is tracer A for an auto spectrum."""
+    g, delta, A, v_cell, _, tr = _prepare(gal, ran, ran_nbar, N, box_lo, box_len, assign, norm, compensate,
+                                          xi, interlace)
+    ta = _Tracer(delta, tr)
+    if gal_b is None:
+        return g, ta, ta, A, v_cell
+    if norm == 2 and xi:
+        raise ValueError("norm=2 is not defined for a cross correlation")
+    _, delta_b, A_b, _, _, tr_b = _prepare(gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign, norm, compensate,
+                                           xi, interlace)
+    return g, ta, _Tracer(delta_b, tr_b), float(np.sqrt(A * A_b)), v_cell
+
+
+def _cross_g_fields(g, ta, tb, K, ell_max, even=False):
+    """g fields of the midpoint series: g^AB (delta_A conjugated, delta_B carrying
+    the weights, anchored on the second galaxy) averaged with g^BA (anchored on the
+    first); one density: g^AA."""
+    gab = g_fields(g, tb.delta, ta.D, K, ell_max, tb.tr, even)
+    if tb is ta:
+        return gab
+    gba = g_fields(g, ta.delta, tb.D, K, ell_max, ta.tr, even)
+    return {key: 0.5 * (gab[key] + gba[key]) for key in gab}
+
+
 def _ells(ell_max):
     if ell_max < 0 or ell_max % 2:
         raise ValueError("only even ell_max is supported (the paper assumes even ell)")
@@ -174,134 +218,130 @@ def g_fields(g: Grid, delta, D, K, ell_max, tr, even=False):
 # public entry points (mirror the library's pk_multipoles / xi_multipoles)
 # --------------------------------------------------------------------------
 def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
-                  order, kedges, compensate=False, norm=1, interlace=False):
+                  order, kedges, compensate=False, norm=1, interlace=False,
+                  gal_b=None, ran_b=None, ran_nbar_b=None):
     """P_ell(k) for ell = 0, 2, .., ell_max with LOS in
-    {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
-    g, delta, A, _, inv_w, tr = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
-                                         assign, norm, compensate, interlace=interlace)
+    {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}; the cross
+    spectrum of (gal, ran) with (gal_b, ran_b) when gal_b is given."""
+    g, ta, tb, A, _ = _tracers(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign, norm,
+                               compensate, interlace=interlace)
     ells = _ells(ell_max)
-    D = tr.fwd()
+    shape = ta.D.shape
     T = {}
     if los == "yamamoto":
-        # eq. Yamamoto-estimator: sum_m Y*(k) F[Y delta](k) delta*(k)
+        # eq. Yamamoto-estimator: sum_m Y*(k) F[Y delta](k) delta*(k); two tracers: the
+        # mean of the lines of sight through either galaxy of the pair
         for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
+            acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                F = tr.fwd(lambda x: ylm(ell, m, x))
-                acc += np.conj(ylm(ell, m, g.k)) * F * np.conj(D)
+                acc += np.conj(ylm(ell, m, g.k)) * _yamamoto_product(ta, tb, ell, m)
             T[ell] = acc.real
-    elif los == "midpoint":
-        # eq. FFT-midpoint: sum_m Y*(k) sum phi F[ Y_J1^M(Delta) Delta^alpha g^alpha_{J2 (m-M)}(Delta) ](k)
-        gf = g_fields(g, delta, D, order, ell_max, tr)
+    elif los in ("midpoint", "midpoint_even"):
+        # eq. FFT-midpoint: sum_m Y*(k) sum phi F[ Y_J1^M(Delta) Delta^alpha g^alpha_{J2 (m-M)}(Delta) ](k);
+        # parity-even form (Sec. 3.3 boxed): phi -> Phi, even alpha only
+        even = los == "midpoint_even"
+        table = Phi_table if even else phi_table
+        gf = _cross_g_fields(g, ta, tb, order, ell_max, even)
         for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
+            acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                H = np.zeros(D.shape, dtype=np.complex128)
-                for alpha in range(order + 1):
+                H = np.zeros(shape, dtype=np.complex128)
+                for alpha in range(0, order + 1, 2 if even else 1):
                     dpow = g.lag_mag ** alpha
-                    for (J1, J2, M), c in phi_table(alpha, ell, m).items():
-                        H += c * ylm(J1, M, g.lag) * dpow * gf[(alpha, J2, m - M)]
-                acc += np.conj(ylm(ell, m, g.k)) * mesh.fftn(H)
-            T[ell] = acc.real
-    elif los == "midpoint_even":
-        # Sec. 3.3 boxed parity-even estimator: eq. FFT-midpoint with phi -> Phi, even alpha only
-        gf = g_fields(g, delta, D, order, ell_max, tr, even=True)
-        for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
-            for m in range(-ell, ell + 1):
-                H = np.zeros(D.shape, dtype=np.complex128)
-                for alpha in range(0, order + 1, 2):
-                    dpow = g.lag_mag ** alpha
-                    for (J1, J2, M), c in Phi_table(alpha, ell, m).items():
+                    for (J1, J2, M), c in table(alpha, ell, m).items():
                         H += c * ylm(J1, M, g.lag) * dpow * gf[(alpha, J2, m - M)]
                 acc += np.conj(ylm(ell, m, g.k)) * mesh.fftn(H)
             T[ell] = acc.real
     elif los == "bisector":
-        # eq. bisector-pk-fft: sum_m Y*(k) sum B F[Y_J1^M delta](-k) F[Y_J2^{m-M} delta](k)
-        bmax = order // 2
-        Jmax = ell_max + bmax
-        F = {(J, M): tr.fwd(lambda x, J=J, M=M: ylm(J, M, x))
-             for J in range(Jmax + 1) for M in range(-J, J + 1)}
+        # eq. bisector-pk-fft: sum_m Y*(k) sum B F[Y_J1^M delta_A](-k) F[Y_J2^{m-M} delta_B](k)
+        FA, FB = _bisector_fields(ta, tb, ell_max + order // 2)
         for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
+            acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                X = np.zeros(D.shape, dtype=np.complex128)
-                for beta in range(bmax + 1):
-                    for (J1, J2, M), c in B_table(beta, ell, m).items():
-                        X += c * _flip_k(F[(J1, M)]) * F[(J2, m - M)]
-                acc += np.conj(ylm(ell, m, g.k)) * X
+                acc += np.conj(ylm(ell, m, g.k)) * _bisector_X(FA, FB, order // 2, ell, m, shape)
             T[ell] = acc.real
     elif los == "fixed":
-        # |delta(k)|^2 L_ell(k . n) with n = the direction of the box centre
+        # Re[delta_A*(k) delta_B(k)] L_ell(k . n) with n = the direction of the box centre
         n = g.box_lo + 0.5 * g.box_len
         n = n / np.linalg.norm(n)
         mu = np.where(g.k_mag > 0, (g.k @ n) / np.where(g.k_mag > 0, g.k_mag, 1.0), 0.0)
         for ell in ells:
-            T[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * np.abs(D) ** 2
+            T[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * (np.conj(ta.D) * tb.D).real
     else:
         raise ValueError(f"unknown los {los!r}")
     return _pk_out(g, ells, T, A, kedges)
 
 
+def _yamamoto_product(ta, tb, ell, m):
+    """delta_A*(k) F[Y_ell^m delta_B](k), averaged with A and B swapped for two tracers."""
+    p = np.conj(ta.D) * tb.tr.fwd(lambda x: ylm(ell, m, x))
+    if tb is ta:
+        return p
+    return 0.5 * (p + np.conj(tb.D) * ta.tr.fwd(lambda x: ylm(ell, m, x)))
+
+
+def _bisector_fields(ta, tb, Jmax):
+    """F[Y_J^M delta](k) for J <= Jmax, of tracer A and of tracer B."""
+    FA = {(J, M): ta.tr.fwd(lambda x, J=J, M=M: ylm(J, M, x)) for J in range(Jmax + 1) for M in range(-J, J + 1)}
+    FB = FA if tb is ta else {(J, M): tb.tr.fwd(lambda x, J=J, M=M: ylm(J, M, x))
+                              for J in range(Jmax + 1) for M in range(-J, J + 1)}
+    return FA, FB
+
+
+def _bisector_X(FA, FB, bmax, ell, m, shape):
+    """X_ell^m(k) = sum_beta sum B^{beta, ell m}_{J1 J2 M} F_A[Y_J1^M](-k) F_B[Y_J2^{m-M}](k)."""
+    X = np.zeros(shape, dtype=np.complex128)
+    for beta in range(bmax + 1):
+        for (J1, J2, M), c in B_table(beta, ell, m).items():
+            X += c * _flip_k(FA[(J1, M)]) * FB[(J2, m - M)]
+    return X
+
+
 def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
-                  order, redges, compensate=False, norm=1, interlace=False):
+                  order, redges, compensate=False, norm=1, interlace=False,
+                  gal_b=None, ran_b=None, ran_nbar_b=None):
     """xi_ell(r) for ell = 0, 2, .., ell_max with LOS in
-    {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}."""
-    g, delta, A, v_cell, inv_w, tr = _prepare(gal, ran, ran_nbar, N, box_lo, box_len,
-                                              assign, norm, compensate, xi=True, interlace=interlace)
+    {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}; the cross
+    correlation of (gal, ran) with (gal_b, ran_b) when gal_b is given."""
+    g, ta, tb, A, v_cell = _tracers(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign,
+                                    norm, compensate, xi=True, interlace=interlace)
     ells = _ells(ell_max)
-    D = tr.fwd()
+    shape = ta.D.shape
     Z = {}
     if los == "yamamoto":
-        # eq. 2pcf-yama: sum_m Y*(Delta) IFFT[delta*(k) F[Y delta](k)](Delta)
+        # eq. 2pcf-yama: sum_m Y*(Delta) IFFT[delta*(k) F[Y delta](k)](Delta); two tracers as for P
         for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
+            acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                F = tr.fwd(lambda x: ylm(ell, m, x))
-                acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(np.conj(D) * F)
+                acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(_yamamoto_product(ta, tb, ell, m))
             Z[ell] = acc.real
-    elif los == "midpoint":
-        # eq. xi-parity-all-estimator: sum f Y_J^M*(Delta) Delta^alpha g^alpha_JM(Delta)
-        gf = g_fields(g, delta, D, order, ell_max, tr)
+    elif los in ("midpoint", "midpoint_even"):
+        # eq. xi-parity-all-estimator: sum f Y_J^M*(Delta) Delta^alpha g^alpha_JM(Delta);
+        # parity-even form (Sec. 4.3 boxed): f -> F, even alpha only
+        even = los == "midpoint_even"
+        table = F_table if even else f_table
+        gf = _cross_g_fields(g, ta, tb, order, ell_max, even)
         for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
-            for alpha in range(order + 1):
+            acc = np.zeros(shape, dtype=np.complex128)
+            for alpha in range(0, order + 1, 2 if even else 1):
                 dpow = g.lag_mag ** alpha
-                for J, c in f_table(alpha, ell).items():
-                    for M in range(-J, J + 1):
-                        acc += c * np.conj(ylm(J, M, g.lag)) * dpow * gf[(alpha, J, M)]
-            Z[ell] = acc.real
-    elif los == "midpoint_even":
-        # Sec. 4.3 boxed parity-even estimator: f -> F, even alpha only
-        gf = g_fields(g, delta, D, order, ell_max, tr, even=True)
-        for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
-            for alpha in range(0, order + 1, 2):
-                dpow = g.lag_mag ** alpha
-                for J, c in F_table(alpha, ell).items():
+                for J, c in table(alpha, ell).items():
                     for M in range(-J, J + 1):
                         acc += c * np.conj(ylm(J, M, g.lag)) * dpow * gf[(alpha, J, M)]
             Z[ell] = acc.real
     elif los == "bisector":
-        # Sec. 6: sum_m Y*(Delta) IFFT[ sum B F[Y_J1^M delta](-k) F[Y_J2^{m-M} delta](k) ](Delta)
-        bmax = order // 2
-        Jmax = ell_max + bmax
-        F = {(J, M): tr.fwd(lambda x, J=J, M=M: ylm(J, M, x))
-             for J in range(Jmax + 1) for M in range(-J, J + 1)}
+        # Sec. 6: sum_m Y*(Delta) IFFT[ sum B F[Y_J1^M delta_A](-k) F[Y_J2^{m-M} delta_B](k) ](Delta)
+        FA, FB = _bisector_fields(ta, tb, ell_max + order // 2)
         for ell in ells:
-            acc = np.zeros(D.shape, dtype=np.complex128)
+            acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
-                X = np.zeros(D.shape, dtype=np.complex128)
-                for beta in range(bmax + 1):
-                    for (J1, J2, M), c in B_table(beta, ell, m).items():
-                        X += c * _flip_k(F[(J1, M)]) * F[(J2, m - M)]
-                acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(X)
+                acc += np.conj(ylm(ell, m, g.lag)) * mesh.ifftn(_bisector_X(FA, FB, order // 2, ell, m, shape))
             Z[ell] = acc.real
     elif los == "fixed":
         n = g.box_lo + 0.5 * g.box_len
         n = n / np.linalg.norm(n)
         mu = np.where(g.lag_mag > 0, (g.lag @ n) / np.where(g.lag_mag > 0, g.lag_mag, 1.0), 0.0)
-        c = mesh.ifftn(np.abs(D) ** 2).real
+        c = mesh.ifftn(np.conj(ta.D) * tb.D).real
         for ell in ells:
             Z[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * c
     else:

@@ -16,6 +16,14 @@ Test infrastructure only (see ``oracle/__init__``).
   its truncated expansion taken pair by pair (midpoint: eq. Ylm-shift-theorem
   around A = 2 x_b, a = -Delta, and eq. Legendre-shift-theorem-all-parity;
   bisector: eq. bisector-ylm-expan and eq. bisector-leg-expan).
+* Cross spectra (``gal_b``, ``ran_b``, ``ran_nbar_b`` given): the pairs join an
+  occupied node a of delta_A to an occupied node b of delta_B, weight
+  delta_A(a) delta_B(b), lag Delta = x_b - x_a, normalisation sqrt(A_A A_B).  With
+  two densities the anchored forms are not interchangeable, so every pair takes the
+  mean of both: Yamamoto the mean of the two endpoint lines of sight, the midpoint
+  series the mean of its expansions anchored at x_b and at x_a (Sec. 3.2, the
+  bracket before the symmetrisation of eq. P-ell-k-symm); the bisector series is
+  symmetric in the pair already.
 * O1, ``particle_xi``: the same xi_ell sum over distinct particle pairs
   (weights w and -alpha_r w), no mesh, no periodic wrap; binned with the mesh
   lag-cell counts N_b so that node-snapped catalogs give O2 exactly.
@@ -39,14 +47,31 @@ def _occupied(delta, N, box_lo, box_len):
     return idx, x, delta[delta != 0.0]
 
 
-def _pairs(idx, x, d, N, box_len):
-    n = len(d)
-    ia = np.repeat(np.arange(n), n)
-    ib = np.tile(np.arange(n), n)
-    j = (idx[ib] - idx[ia] + N // 2) % N - N // 2          # minimal-image lag labels
+def _pairs(idx, x, d, N, box_len, idx_b=None, d_b=None):
+    """Every ordered pair (a, b) of occupied nodes (a of the first density, b of the
+    second; one density: both of it)."""
+    if idx_b is None:
+        idx_b, d_b = idx, d
+    ia = np.repeat(np.arange(len(d)), len(d_b))
+    ib = np.tile(np.arange(len(d_b)), len(d))
+    j = (idx_b[ib] - idx[ia] + N // 2) % N - N // 2       # minimal-image lag labels
     lag = j * (box_len / N)
     flat = np.ravel_multi_index(tuple((j % N).T), (N, N, N))
-    return ia, ib, lag, flat, d[ia] * d[ib]
+    return ia, ib, lag, flat, d[ia] * d_b[ib]
+
+
+def _densities(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign, norm):
+    """Occupied nodes of delta_A (and delta_B for a cross spectrum) and the
+    normalisation A (cross: sqrt(A_A A_B))."""
+    delta, _ = mesh.density_mesh(gal, ran, N, box_lo, box_len, assign)
+    A = mesh.norm_factors(gal, ran, ran_nbar)[1] if norm else 1.0
+    a = _occupied(delta, N, box_lo, box_len)
+    if gal_b is None:
+        return a, None, A
+    delta_b, _ = mesh.density_mesh(gal_b, ran_b, N, box_lo, box_len, assign)
+    if norm:
+        A = float(np.sqrt(A * mesh.norm_factors(gal_b, ran_b, ran_nbar_b)[1]))
+    return a, _occupied(delta_b, N, box_lo, box_len), A
 
 
 def _unit(v):
@@ -64,8 +89,17 @@ def _los(los, xa, xb):
     raise ValueError(los)
 
 
-def _ylm_pair(los, ell, m, xa, xb, lag, series):
-    """Y_ell^m of the pair's line of sight, exact or its truncated series."""
+def _ylm_pair(los, ell, m, xa, xb, lag, series, both=False):
+    """Y_ell^m of the pair's line of sight, exact or its truncated series.  both:
+    the mean over the two anchorings (Yamamoto: over the two endpoints; midpoint:
+    over the expansions about x_b and about x_a, found by swapping the ends, which
+    turns Delta into -Delta)."""
+    if both and los in ("yamamoto", "midpoint", "midpoint_even"):
+        if los == "yamamoto":
+            return 0.5 * (ylm(ell, m, xb) + ylm(ell, m, xa))
+        if series is not None:
+            return 0.5 * (_ylm_pair(los, ell, m, xa, xb, lag, series)
+                          + _ylm_pair(los, ell, m, xb, xa, -lag, series))
     if series is None or los == "yamamoto":
         return ylm(ell, m, _los(los, xa, xb))
     if los == "midpoint":
@@ -94,8 +128,16 @@ def _ylm_pair(los, ell, m, xa, xb, lag, series):
     raise ValueError(los)
 
 
-def _legendre_pair(los, ell, xa, xb, lag, series):
-    """L_ell(hat Delta . n) of the pair, exact or its truncated series."""
+def _legendre_pair(los, ell, xa, xb, lag, series, both=False):
+    """L_ell(hat Delta . n) of the pair, exact or its truncated series (both: as in
+    ``_ylm_pair``; L_ell is even in Delta for even ell)."""
+    if both and los in ("yamamoto", "midpoint", "midpoint_even"):
+        if los == "yamamoto":
+            return 0.5 * (_legendre_pair(los, ell, xa, xb, lag, None)
+                          + _legendre_pair(los, ell, xb, xa, -lag, None))
+        if series is not None:
+            return 0.5 * (_legendre_pair(los, ell, xa, xb, lag, series)
+                          + _legendre_pair(los, ell, xb, xa, -lag, series))
     if series is None or los == "yamamoto":
         n = _unit(_los(los, xa, xb))
         mu = np.sum(_unit(lag) * n, axis=-1)
@@ -127,13 +169,15 @@ def _legendre_pair(los, ell, xa, xb, lag, series):
 
 
 def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, kedges,
-            norm=1, series=None):
-    """O2 power-spectrum multipoles from explicit pairs of occupied nodes."""
-    delta, _ = mesh.density_mesh(gal, ran, N, box_lo, box_len, assign)
-    A = mesh.norm_factors(gal, ran, ran_nbar)[1] if norm else 1.0
-    idx, x, d = _occupied(delta, N, box_lo, box_len)
-    ia, ib, lag, flat, w = _pairs(idx, x, d, N, box_len)
-    xa, xb = x[ia], x[ib]
+            norm=1, series=None, gal_b=None, ran_b=None, ran_nbar_b=None):
+    """O2 power-spectrum multipoles from explicit pairs of occupied nodes (cross
+    spectrum of two tracers when gal_b is given)."""
+    (idx, x, d), other, A = _densities(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len,
+                                       assign, norm)
+    both = other is not None
+    idx_b, x_b, d_b = other if both else (idx, x, d)
+    ia, ib, lag, flat, w = _pairs(idx, x, d, N, box_len, idx_b, d_b)
+    xa, xb = x[ia], x_b[ib]
     kv = mesh.k_vectors(N, box_len)
     kmag = mesh.k_magnitude(N, box_len)
     ells = list(range(0, ell_max + 1, 2))
@@ -142,7 +186,7 @@ def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, ked
         acc = np.zeros((N, N, N), dtype=np.complex128)
         for m in range(-ell, ell + 1):
             G = np.zeros(N * N * N, dtype=np.complex128)
-            np.add.at(G, flat, w * _ylm_pair(los, ell, m, xa, xb, lag, series))
+            np.add.at(G, flat, w * _ylm_pair(los, ell, m, xa, xb, lag, series, both))
             acc += np.conj(ylm(ell, m, kv)) * mesh.fftn(G.reshape(N, N, N))
         mean, kmean, cnt = mesh.shell_mean(acc.real, kmag, kedges, kmag == 0.0)
         pk.append(FOUR_PI / A * mean)
@@ -150,16 +194,15 @@ def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, ked
 
 
 def mesh_xi(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, redges,
-            norm=1, series=None):
-    """O2 correlation-function multipoles from explicit pairs of occupied nodes."""
-    delta, _ = mesh.density_mesh(gal, ran, N, box_lo, box_len, assign)
-    if norm:
-        A = mesh.norm_factors(gal, ran, ran_nbar)[1]
-        v_cell = (box_len / N) ** 3
-    else:
-        A, v_cell = 1.0, 1.0
-    idx, x, d = _occupied(delta, N, box_lo, box_len)
-    ia, ib, lag, flat, w = _pairs(idx, x, d, N, box_len)
+            norm=1, series=None, gal_b=None, ran_b=None, ran_nbar_b=None):
+    """O2 correlation-function multipoles from explicit pairs of occupied nodes
+    (cross correlation of two tracers when gal_b is given)."""
+    (idx, x, d), other, A = _densities(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len,
+                                       assign, norm)
+    v_cell = (box_len / N) ** 3 if norm else 1.0
+    both = other is not None
+    idx_b, x_b, d_b = other if both else (idx, x, d)
+    ia, ib, lag, flat, w = _pairs(idx, x, d, N, box_len, idx_b, d_b)
     lmag = np.linalg.norm(lag, axis=-1)
     redges = np.asarray(redges, dtype=np.float64)
     b = mesh.shell_index(lmag, redges)
@@ -172,7 +215,7 @@ def mesh_xi(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, red
     nb = len(redges) - 1
     xi = []
     for ell in ells:
-        L = _legendre_pair(los, ell, x[ia][sel], x[ib][sel], lag[sel], series)
+        L = _legendre_pair(los, ell, x[ia][sel], x_b[ib][sel], lag[sel], series, both)
         s = np.bincount(b[sel], weights=w[sel] * L, minlength=nb)
         xi.append(np.where(ncell > 0, (2 * ell + 1) * s / (A * v_cell * np.maximum(ncell, 1)), 0.0))
     return {"ells": ells, "xi": np.array(xi), "r_mean": rmean, "n_cells": ncell}
