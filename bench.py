@@ -338,43 +338,60 @@ def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
     """The benchmark catalog at the benchmark mesh through the extensions beyond the paper's
     boxed estimators (hybrid FFT backend), each timed (CUDA events, after one warm-up run)
     beside its device footprint: the parity-even midpoint form; the midpoint g fields streamed in ranges of 45;
-    the bisector fields in blocks of 16; xi normalised by the random-random count."""
+    the bisector fields in blocks of 16; xi normalised by the random-random count; interlacing; the
+    cross spectra of two tracers (the catalog's even- and odd-numbered galaxies and randoms)."""
     ctx = pkg.Context(dev.index)
     ctx.set_fft_backend(4)        # the FFT path the autotuner picks for the benchmark step
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
-    cases = [("midpoint_even order 4", "midpoint_even", 4, 1, 0),
-             ("midpoint order 4, g fields in ranges of 45", "midpoint", 4, 1, 45),
-             ("bisector order 4, fields in blocks of 16", "bisector", 4, 1, 16),
-             ("midpoint order 4, xi / RR (norm 2)", "midpoint", 4, 2, 0),
-             ("bisector order 4, interlaced", "bisector", 4, 1, -1)]
+    halves = [(t[0::2].contiguous(), t[1::2].contiguous()) for t in (gal_d, ran_d, rnb_d)]
+    # label, los, order, norm, field chunk (-1: interlaced), cross
+    cases = [("midpoint_even order 4", "midpoint_even", 4, 1, 0, False),
+             ("midpoint order 4, g fields in ranges of 45", "midpoint", 4, 1, 45, False),
+             ("bisector order 4, fields in blocks of 16", "bisector", 4, 1, 16, False),
+             ("midpoint order 4, xi / RR (norm 2)", "midpoint", 4, 2, 0, False),
+             ("bisector order 4, interlaced", "bisector", 4, 1, -1, False),
+             ("bisector order 4, cross spectra of two tracers", "bisector", 4, 1, 0, True),
+             ("midpoint order 4, cross spectra of two tracers", "midpoint", 4, 1, 0, True)]
     out = {}
-    for label, los, K, norm, chunk in cases:
+    for label, los, K, norm, chunk, cross in cases:
         il = chunk < 0                   # -1: interlaced, resident
         chunk = max(chunk, 0)
         p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=n_mesh, assign=3, ell_max=ELL_MAX, los=los,
                             order=K, compensate=True, precision=32, norm=norm, interlace=il)
         ctx.set_field_chunk(chunk)
-        ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / reps
+        if cross:
+            (ga, gb), (ra, rb), (na, nb) = halves
+
+            def run():
+                ctx.pk_xi_cross(ga, ra, gb, rb, p, KEDGES, REDGES, ran_nbar_a=na, ran_nbar_b=nb, stream=sh)
+        else:
+            def run():
+                ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
         n_f = {"midpoint_even": 88, "midpoint": 145, "bisector": 49}[los]
         slot = n_mesh * n_mesh * (n_mesh + 2) * 4
         if chunk and los == "midpoint":
             slots = 2 + chunk + 15
         elif chunk:
             slots = 1 + 2 * chunk + 15
-        elif il:
+        elif il or cross:
             slots = 2 + 2 * n_f + 15
         else:
             slots = 1 + n_f + 15
+        try:
+            run()
+        except pkg.BymError as e:        # e.g. a footprint beyond this device's memory
+            out[label] = {"error": str(e), "mesh_slots": slots, "field_memory_gb": slots * slot / 1e9}
+            continue
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
         out[label] = {"ms_per_catalog": ms, "catalogs_per_s": 1000.0 / ms, "mesh_slots": slots,
                       "field_memory_gb": slots * slot / 1e9}
     ctx.set_field_chunk(0)

@@ -148,9 +148,31 @@ int bym_pk_xi_multipoles(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog
                          double *pk, double *k_mean, int64_t *n_modes,
                          double *xi, double *r_mean, int64_t *n_cells, void *cuda_stream);
 
+/* Cross spectra of two tracers on one mesh (even ell): delta_A painted from
+ * (gal_a, ran_a) and delta_B from (gal_b, ran_b), each with its own alpha_r.
+ * The estimators are those above with delta(r_1) delta(r_2) replaced by
+ * delta_A(r_1) delta_B(r_2).  With two densities the two anchored terms of the
+ * midpoint series (Sec. 3.2, the bracket before eq. P-ell-k-symm) differ and both
+ * are kept: for even ell the g functions become (g^AB + g^BA) / 2 with
+ * g^XY = (-1)^J IFFT[delta_X*(k) F[(2r)^-alpha Y_J^M delta_Y](k)] (eq. g-JM-form);
+ * the Yamamoto forms take the mean of the lines of sight through either galaxy;
+ * the bisector forms pair F[Y delta_A](-k) with F[Y delta_B](k) (eq.
+ * bisector-pk-fft, Sec. 6).  Normalisation (norm = 1): A = sqrt(A_A A_B).
+ * kbins or rbins may be NULL (that statistic is skipped; its outputs are then
+ * not written); outputs as for bym_pk_xi_multipoles.  Both field sets stay
+ * resident: the request holds 1 + (number of fields) more mesh slots than the
+ * auto spectrum.  BYM_E_UNSUPPORTED with norm = 2, interlacing, or field ranges
+ * forced by bym_set_field_chunk (midpoint forms and bisector). */
+int bym_pk_xi_cross(bym_ctx *ctx, const bym_catalog *gal_a, const bym_catalog *ran_a,
+                    const bym_catalog *gal_b, const bym_catalog *ran_b, const bym_params *p,
+                    const bym_bins *kbins, const bym_bins *rbins,
+                    double *pk, double *k_mean, int64_t *n_modes,
+                    double *xi, double *r_mean, int64_t *n_cells, void *cuda_stream);
+
 /* Compile (without running) the runtime-specialised kernels for these
  * parameters (for the midpoint forms and the bisector also the kernels of
- * field ranges, see bym_set_field_chunk); works without a GPU.  Used by build
+ * field ranges, see bym_set_field_chunk, and for the bisector the two-tracer
+ * contraction of bym_pk_xi_cross); works without a GPU.  Used by build
  * checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);
 

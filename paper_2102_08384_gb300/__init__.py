@@ -87,6 +87,8 @@ def lib():
         L.bym_xi_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, dp, dp, i64p, vp]
         L.bym_pk_xi_multipoles.argtypes = [vp, cat_p, cat_p, par_p, bins_p, bins_p, dp, dp, i64p, dp, dp, i64p,
                                            vp]
+        L.bym_pk_xi_cross.argtypes = [vp, cat_p, cat_p, cat_p, cat_p, par_p, bins_p, bins_p, dp, dp, i64p, dp, dp,
+                                      i64p, vp]
         L.bym_jit_check.argtypes = [par_p, ctypes.c_char_p, ctypes.c_size_t]
         L.bym_shot_noise.argtypes = [vp, cat_p, cat_p, par_p, dp]
         L.bym_serve_start.argtypes = [vp, ctypes.c_int, ctypes.c_size_t]
@@ -367,6 +369,37 @@ class Context:
 
     def pk_xi_multipoles(self, gal, ran, params, kedges, redges, gal_nbar=None, ran_nbar=None, stream=None):
         return self._run("both", gal, ran, params, kedges, redges, gal_nbar, ran_nbar, stream)
+
+    def pk_xi_cross(self, gal_a, ran_a, gal_b, ran_b, params, kedges=None, redges=None, ran_nbar_a=None,
+                    ran_nbar_b=None, stream=None):
+        """Cross multipoles of tracer A (gal_a, ran_a) with tracer B (gal_b, ran_b), even ell;
+        P_ell when kedges is given, xi_ell when redges is given."""
+        if kedges is None and redges is None:
+            raise ValueError("kedges or redges is required")
+        keep = []
+        cats = [_catalog(gal_a, None, keep), _catalog(ran_a, ran_nbar_a, keep), _catalog(gal_b, None, keep),
+                _catalog(ran_b, ran_nbar_b, keep)]
+        nl = params.ell_max // 2 + 1
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        out, ptrs = {}, []
+        for edges, keys in ((kedges, ("pk", "k_mean", "n_modes")), (redges, ("xi", "r_mean", "n_cells"))):
+            if edges is None:
+                ptrs += [None, None, None, None]
+                continue
+            b = _bins(edges, keep)
+            keep.append(b)
+            out[keys[0]] = np.zeros((nl, b.nbins))
+            out[keys[1]] = np.zeros(b.nbins)
+            out[keys[2]] = np.zeros(b.nbins, dtype=np.int64)
+            ptrs += [ctypes.byref(b), out[keys[0]].ctypes.data_as(dp), out[keys[1]].ctypes.data_as(dp),
+                     out[keys[2]].ctypes.data_as(i64p)]
+        st = ctypes.c_void_p(stream) if stream else None
+        rc = self._L.bym_pk_xi_cross(self._h, *[_ptr(c) for c in cats], ctypes.byref(params), ptrs[0], ptrs[4],
+                                     ptrs[1], ptrs[2], ptrs[3], ptrs[5], ptrs[6], ptrs[7], st)
+        self._check(rc)
+        out["ells"] = list(range(0, params.ell_max + 1, 2))
+        return out
 
     def shot_noise(self, gal, ran, params, gal_nbar=None, ran_nbar=None) -> float:
         """(sum_g w^2 + alpha_r^2 sum_r w^2) / A, the shot-noise level of P_0 (not subtracted by the estimators)."""

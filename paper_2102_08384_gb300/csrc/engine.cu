@@ -201,7 +201,7 @@ static int n_extra_slots(const bym_params *p, bool want_pk, bool want_xi) {
 }
 
 size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
-                            bool cats_on_device, int chunk) {
+                            bool cats_on_device, int chunk, bool cross) {
   const size_t N = (size_t)p->n_mesh;
   const size_t esz = p->precision == 64 ? 8 : 4;
   const size_t slot = N * N * (N + 2) * esz;
@@ -210,6 +210,7 @@ size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, b
   if (chunk > 0 && is_midpoint(p)) fslots = 2 + std::min(nf, (size_t)chunk);          // two deltas, a range
   if (chunk > 0 && p->los == BYM_LOS_BISECTOR) fslots = 1 + 2 * std::min(nf, (size_t)chunk);  // two blocks
   if (p->interlace) fslots = 2 + 2 * nf;                  // the second set on the shifted mesh
+  if (cross) fslots = 2 + 2 * nf;                         // the second tracer's delta and fields
   const size_t slots = fslots + (size_t)n_extra_slots(p, want_pk, want_xi);
   size_t cats = 0;
   if (!cats_on_device) cats = (size_t)(std::max<int64_t>(n_gal, 0) + std::max<int64_t>(n_ran, 0)) * 20;
@@ -544,17 +545,21 @@ struct Pending {
 
 // Host normalisation of the FP64 sums (Sec. 2 with the readings of the library's
 // normalisation: P = 4 pi / A * bin mean, xi = 4 pi / (A V_cell) * bin mean).
+// cross: hstats holds 16 sums, tracer B's at [8, 16); A = sqrt(A_A A_B).  pk_scale multiplies
+// the P sums (the Yamamoto cross spectrum adds its two endpoint terms without the 1/2).
 static int finish_results(bym_ctx *c, const Request &rq, const double *hstats, const double *hk, const double *hr,
-                          const Geom *kg, const Geom *rg, int NL, int nbk, int nbr, double h) {
+                          const Geom *kg, const Geom *rg, int NL, int nbk, int nbr, double h, bool cross = false,
+                          double pk_scale = 1.0) {
   const bym_params *p = rq.p;
-  if (hstats[3] > 0.0)
-    return fail(c, BYM_E_OUT_OF_BOX,
-                std::to_string((long long)hstats[3]) + " objects lie outside the box or are not finite");
+  const double bad = hstats[3] + (cross ? hstats[11] : 0.0);
+  if (bad > 0.0)
+    return fail(c, BYM_E_OUT_OF_BOX, std::to_string((long long)bad) + " objects lie outside the box or are not finite");
   if (rq.alpha) *rq.alpha = hstats[1] != 0.0 ? hstats[0] / hstats[1] : 0.0;
   double A = 1.0, vcell = 1.0;
   if (p->norm >= 1) {
     const double alpha = hstats[0] / hstats[1];
     A = alpha * hstats[2];
+    if (cross) A = std::sqrt(A * (hstats[8] / hstats[9]) * hstats[10]);
     vcell = h * h * h;
     if (!(A > 0.0) || !std::isfinite(A)) return fail(c, BYM_E_INVAL, "FKP normalisation A is not positive");
   }
@@ -564,7 +569,8 @@ static int finish_results(bym_ctx *c, const Request &rq, const double *hstats, c
   if (rq.kb) {
     for (int l = 0; l < NL; ++l)
       for (int b = 0; b < nbk; ++b)
-        rq.pk[l * nbk + b] = kg->count[b] > 0 ? four_pi / A * hk[(size_t)b * NL + l] / (double)kg->count[b] : 0.0;
+        rq.pk[l * nbk + b] =
+            kg->count[b] > 0 ? pk_scale * four_pi / A * hk[(size_t)b * NL + l] / (double)kg->count[b] : 0.0;
     if (rq.kmean) std::copy(kg->mean.begin(), kg->mean.end(), rq.kmean);
     if (rq.nmodes) std::copy(kg->count.begin(), kg->count.end(), rq.nmodes);
   }
@@ -603,12 +609,18 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
 
   // midpoint g fields streamed in ranges when forced, or when the whole set does not fit
-  const bool cats_dev = rq.gal->on_device && (!rq.ran || rq.ran->on_device);
-  const int64_t ngal = rq.gal->n, nran = rq.ran ? rq.ran->n : 0;
+  const bool cross = rq.gal_b != nullptr;
+  const bool cats_dev = rq.gal->on_device && (!rq.ran || rq.ran->on_device) &&
+                        (!cross || (rq.gal_b->on_device && (!rq.ran_b || rq.ran_b->on_device)));
+  const int64_t ngal = rq.gal->n + (cross ? rq.gal_b->n : 0);
+  const int64_t nran = (rq.ran ? rq.ran->n : 0) + (cross && rq.ran_b ? rq.ran_b->n : 0);
   int chunk = 0;
   if (p->interlace && c->field_chunk > 0 && p->los != BYM_LOS_YAMAMOTO)
     return fail(c, BYM_E_UNSUPPORTED, "interlacing keeps every field resident: no field ranges");
-  if (!p->interlace && (is_midpoint(p) || p->los == BYM_LOS_BISECTOR)) {
+  if (cross && (p->interlace || p->norm == 2 || (c->field_chunk > 0 && p->los != BYM_LOS_YAMAMOTO)))
+    return fail(c, BYM_E_UNSUPPORTED, "cross spectra: no interlacing, no norm 2, both field sets resident");
+  if (cross && pd) return fail(c, BYM_E_INVAL, "cross spectra are not enqueued");
+  if (!p->interlace && !cross && (is_midpoint(p) || p->los == BYM_LOS_BISECTOR)) {
     if (c->field_chunk > 0) {
       chunk = std::min(c->field_chunk, nf);
     } else {
@@ -620,8 +632,13 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
           if (footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev, m) <= avail) chunk = m;
     }
   }
-  if (c->budget && footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev, chunk) > c->budget)
+  if (c->budget && footprint_bytes(p, ngal, nran, want_pk, want_xi, cats_dev, chunk, cross) > c->budget)
     return fail(c, BYM_E_NOMEM, "request exceeds the context's HBM budget");
+  cudaKernel_t kx = nullptr;   // bisector cross contraction
+  if (cross && p->los == BYM_LOS_BISECTOR) {
+    kx = get_cross_kernel(JitKey{p->los, p->ell_max, order_key(p), p->precision}, jerr);
+    if (!kx) return fail(c, BYM_E_CUDA, jerr);
+  }
   std::shared_ptr<ChunkSet> CK;
   if (chunk) {
     CK = get_chunk_kernels(JitKey{p->los, p->ell_max, order_key(p), p->precision}, chunk, jerr);
@@ -653,12 +670,13 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     if (e_ != cudaSuccess) return fail(c, BYM_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-  // catalogs
-  const float4 *cat4[2] = {nullptr, nullptr};
-  const float *catnb[2] = {nullptr, nullptr};
-  long long catn[2] = {rq.gal->n, rq.ran ? rq.ran->n : 0};
-  const bym_catalog *cats[2] = {rq.gal, rq.ran};
-  for (int w = 0; w < 2; ++w) {
+  // catalogs: galaxies and randoms of tracer A, then of tracer B (cross spectra)
+  const float4 *cat4[4] = {nullptr, nullptr, nullptr, nullptr};
+  const float *catnb[4] = {nullptr, nullptr, nullptr, nullptr};
+  const bym_catalog *cats[4] = {rq.gal, rq.ran, cross ? rq.gal_b : nullptr, cross ? rq.ran_b : nullptr};
+  long long catn[4];
+  for (int w = 0; w < 4; ++w) catn[w] = cats[w] ? cats[w]->n : 0;
+  for (int w = 0; w < 4; ++w) {
     const bym_catalog *cat = cats[w];
     if (!cat || cat->n <= 0) continue;
     if (cat->on_device) {
@@ -682,8 +700,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
 
   double *stats = nullptr, *ksum = nullptr, *rsum = nullptr, *scale = nullptr;
   T *invw = nullptr;
-  TRY(alloc((void **)&stats, 8 * sizeof(double)));
-  CUDA_TRY(cudaMemsetAsync(stats, 0, 8 * sizeof(double), st));
+  TRY(alloc((void **)&stats, 16 * sizeof(double)));    // [0, 8) tracer A, [8, 16) tracer B
+  CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * sizeof(double), st));
   const int nbk = want_pk ? rq.kb->nbins : 1, nbr = want_xi ? rq.rb->nbins : 1;
   TRY(alloc((void **)&ksum, sizeof(double) * NL * nbk));
   TRY(alloc((void **)&rsum, sizeof(double) * NL * nbr));
@@ -729,25 +747,29 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   // interlacing: [ibase] delta on the shifted mesh, then its field set
   const bool il = p->interlace != 0;
   const int ibase = xbase + nextra;
-  const int nslots = ibase + (il ? 1 + nf : 0);
+  // cross spectra: [cbase] tracer B's delta, then its field set
+  const int cbase = ibase + (il ? 1 + nf : 0);
+  const int nslots = cbase + (cross ? 1 + nf : 0);
   T *slots = nullptr;
   TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
   auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
   auto slot_c = [&](int i) { return (T2 *)(slots + (long long)i * slot_reals); };
   CUDA_TRY(cudaMemsetAsync(slots, 0, slot_bytes, st));
   if (il) CUDA_TRY(cudaMemsetAsync(slot_r(ibase), 0, slot_bytes, st));
+  if (cross) CUDA_TRY(cudaMemsetAsync(slot_r(cbase), 0, slot_bytes, st));
 
   // norms and painting
   const double esz = (double)sizeof(T), n3 = (double)N * N * N, nhalf = (double)N * N * (N / 2 + 1);
-  for (int w = 0; w < 2; ++w)
+  for (int w = 0; w < 4; ++w)
     if (cat4[w]) {
-      ProfScope ps(c, st, "norm_reduce", catn[w] * (w ? 20.0 : 16.0));
-      launch_norm_reduce(cat4[w], catnb[w], catn[w], w, p->box_lo, inv_h, N, stats, c->nsm, st);
+      ProfScope ps(c, st, "norm_reduce", catn[w] * ((w & 1) ? 20.0 : 16.0));
+      launch_norm_reduce(cat4[w], catnb[w], catn[w], w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), c->nsm, st);
     }
-  for (int w = 0; w < 2; ++w)
+  for (int w = 0; w < 4; ++w)
     if (cat4[w]) {
       ProfScope ps(c, st, "paint", catn[w] * 16.0 + n3 * esz);
-      launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(0), N, p->box_lo, inv_h, p->assign, c->nsm, st);
+      launch_paint<T>(cat4[w], catn[w], w & 1, stats + 8 * (w >> 1), slot_r(w < 2 ? 0 : cbase), N, p->box_lo, inv_h,
+                      p->assign, c->nsm, st);
       if (il)
         launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(ibase), N, p->box_lo, inv_h, p->assign, c->nsm, st, 0.5);
     }
@@ -764,6 +786,11 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     CUDA_TRY(cudaMemsetAsync(slot_r(1), 0, (size_t)nf * slot_bytes, st));
     CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
                     slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+    if (cross) {   // tracer B's fields from its delta
+      CUDA_TRY(cudaMemsetAsync(slot_r(cbase + 1), 0, (size_t)nf * slot_bytes, st));
+      CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(cbase),
+                      slot_r(cbase + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+    }
     if (il) {   // the same fields on the shifted mesh, from its delta and node positions
       CUDA_TRY(cudaMemsetAsync(slot_r(ibase + 1), 0, (size_t)nf * slot_bytes, st));
       CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(ibase),
@@ -799,7 +826,66 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
   const double tscale = h * inv_r0;
 
-  if (p->los == BYM_LOS_YAMAMOTO) {
+  double pk_scale = 1.0;
+  if (cross) {
+    // two tracers: A's delta and fields in slots [0, 1 + nf), B's in [cbase, cbase + 1 + nf)
+    const bool bis = p->los == BYM_LOS_BISECTOR;
+    const int f0 = bis ? 1 : 0, cnt = bis ? nf : 1 + nf;
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn));
+    if (bis) {
+      {
+        ProfScope ps(c, st, "kcontract_bisector_cross", (2.0 * nf + (want_xi ? nlm : 0.0)) * cplx);
+        CUDA_TRY(launch(kx, gk, 256, smk, st, (const T2 *)slot_c(1), (const T2 *)slot_c(cbase + 1), cslot, N,
+                        (const int *)kg->lut, nbk, ksum, want_xi ? slot_c(xbase) : (T2 *)nullptr, cslot,
+                        (const T *)invw, 0));
+      }
+      if (want_xi) {
+        TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, xbase, nlm, tn));
+        const int Lc = rg->full ? N : 2 * rg->jm + 1;
+        ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nlm * esz);
+        CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
+                        (const T *)slot_r(xbase), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
+                        1.0 / ((double)N * N * N), tscale));
+      }
+    } else {
+      if (p->los == BYM_LOS_YAMAMOTO && want_pk) {
+        // the two endpoint lines of sight: F[Y delta_A] conj(D_B) + F[Y delta_B] conj(D_A), halved on the host
+        pk_scale = 0.5;
+        ProfScope ps(c, st, n_kc.c_str(), 2.0 * (nlm + 1.0) * cplx);
+        CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(cbase), N,
+                        (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
+        CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(cbase + 1), cslot, (const T2 *)slot_c(0),
+                        N, (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
+      }
+      if (is_midpoint(p) || want_xi) {
+        // g = (g^AB + g^BA) / 2 (midpoint), the same product for the Yamamoto xi
+        {
+          ProfScope ps(c, st, "spec_mul_cross", (3.0 * nf + 2.0) * cplx);
+          launch_spec_mul_cross<T, T2>(slot_c(1), slot_c(cbase + 1), cslot, nf, slot_c(0), slot_c(cbase), N, scale,
+                                       invw, c->nsm * tn.per_sm_spec / 8, st);
+        }
+        TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
+      }
+      if (want_xi) {
+        const int Lc = rg->full ? N : 2 * rg->jm + 1;
+        ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nf * esz);
+        CUDA_TRY(launch(K.xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
+                        slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
+      }
+      if (is_midpoint(p) && want_pk) {
+        {
+          ProfScope ps(c, st, "mid_combine", ((double)nf + nlm) * n3 * esz);
+          CUDA_TRY(launch(K.mid_combine, grid_of((long long)N * N * N, c->nsm, tn.per_sm_comb), 256, 0, st,
+                          (const T *)slot_r(1), slot_reals, slot_r(1 + nf), N, tscale));
+        }
+        TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm, tn));
+        ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
+        CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
+                        (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
+      }
+    }
+  } else if (p->los == BYM_LOS_YAMAMOTO) {
     if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
     if (want_pk) {
       ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * cplx);
@@ -951,13 +1037,13 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     pd->h = h;
     return BYM_OK;
   }
-  std::vector<double> hstats(8), hk((size_t)NL * nbk), hr((size_t)NL * nbr);
-  CUDA_TRY(cudaMemcpyAsync(hstats.data(), stats, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hstats(16), hk((size_t)NL * nbk), hr((size_t)NL * nbr);
+  CUDA_TRY(cudaMemcpyAsync(hstats.data(), stats, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hk.data(), ksum, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hr.data(), rsum, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   prof_collect(c);
-  return finish_results(c, rq, hstats.data(), hk.data(), hr.data(), kg, rg, NL, nbk, nbr, h);
+  return finish_results(c, rq, hstats.data(), hk.data(), hr.data(), kg, rg, NL, nbk, nbr, h, cross, pk_scale);
 #undef TRY
 #undef CUDA_TRY
 }
@@ -995,6 +1081,9 @@ int bym::run_request(bym_ctx *c, const Request &rq, cudaStream_t st) {
   if (!c) return BYM_E_INVAL;
   int rc = validate(c, rq.gal, rq.ran, rq.p, rq.kb, rq.rb);
   if (rc) return rc;
+  if (rq.gal_b && (rc = validate(c, rq.gal_b, rq.ran_b, rq.p, rq.kb, rq.rb))) return rc;
+  if (rq.gal_b && (rq.p->norm == 2 || rq.p->interlace))
+    return fail(c, BYM_E_UNSUPPORTED, "cross spectra: norm 2 and interlacing are not available");
   if ((rq.kb && !rq.pk) || (rq.rb && !rq.xi) || (!rq.kb && !rq.rb))
     return fail(c, BYM_E_INVAL, "missing output array");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
@@ -1097,6 +1186,20 @@ int bym_pk_xi_multipoles(bym_ctx *c, const bym_catalog *gal, const bym_catalog *
   if (!kbins || !rbins) return fail(c, BYM_E_INVAL, "kbins and rbins are required");
   std::lock_guard<std::mutex> lock(c->mu);
   Request rq{gal, ran, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
+  return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_pk_xi_cross(bym_ctx *c, const bym_catalog *gal_a, const bym_catalog *ran_a, const bym_catalog *gal_b,
+                    const bym_catalog *ran_b, const bym_params *p, const bym_bins *kbins, const bym_bins *rbins,
+                    double *pk, double *k_mean, int64_t *n_modes, double *xi, double *r_mean, int64_t *n_cells,
+                    void *stream) {
+  if (!c) return BYM_E_INVAL;
+  if (!gal_b) return fail(c, BYM_E_INVAL, "gal_b is NULL");
+  if (!kbins && !rbins) return fail(c, BYM_E_INVAL, "kbins or rbins is required");
+  std::lock_guard<std::mutex> lock(c->mu);
+  Request rq{gal_a, ran_a, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
+  rq.gal_b = gal_b;
+  rq.ran_b = ran_b;
   return run_request(c, rq, (cudaStream_t)stream);
 }
 
@@ -1663,6 +1766,15 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len) {
     src.clear();
     try {
       src = generate_chunk_source(JitKey{p->los, p->ell_max, order_key(p), p->precision}, 16, nullptr);
+    } catch (const std::exception &e) {
+      lg = e.what();
+    }
+    ok = !src.empty() && compile_cubin(src, cubin, lg);
+  }
+  if (ok && p->los == BYM_LOS_BISECTOR) {   // and the two-tracer contraction
+    src.clear();
+    try {
+      src = generate_cross_source(JitKey{p->los, p->ell_max, order_key(p), p->precision});
     } catch (const std::exception &e) {
       lg = e.what();
     }

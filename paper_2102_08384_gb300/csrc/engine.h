@@ -33,6 +33,7 @@ struct Request {
   double *xi, *rmean;
   int64_t *ncells;
   double *alpha = nullptr;      // optional out: alpha_r = sum w_g / sum w_r of the request
+  const bym_catalog *gal_b = nullptr, *ran_b = nullptr;   // second tracer of a cross spectrum (else NULL)
 };
 
 struct Server;  // serving loop state (serve.cpp)
@@ -88,8 +89,9 @@ int validate(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const b
              const bym_bins *rb);
 // Device bytes one request holds.  chunk > 0: the midpoint g fields are streamed
 // in ranges of at most chunk fields (two delta slots, one range, the H fields).
+// cross: two tracers, each with its own delta and field set (n_gal, n_ran summed over both).
 size_t footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
-                       bool cats_on_device, int chunk = 0);
+                       bool cats_on_device, int chunk = 0, bool cross = false);
 int run_request(bym_ctx *c, const Request &rq, cudaStream_t st);
 void shutdown_serving(bym_ctx *c);
 

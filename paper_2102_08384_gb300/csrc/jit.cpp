@@ -326,7 +326,12 @@ int emit_xi_lag(std::ostream &o, const char *name, const JitKey &key, int f0, in
 // from FA and j in [b0, b1) read from FB (slot i - a0, j - b0): adds that share of
 // X_{lm}(k) = sum c Re(conj F_i F_j) to the P shell sums and, when xout is given,
 // writes (accumulate = 0) or adds (accumulate = 1) it to X_{lm}(k).
-void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, int a0, int a1, int b0, int b1) {
+// cross: two tracers, FA = F[Y_i delta_A], FB = F[Y_j delta_B] (every field of each);
+// each symmetrised term c (i < j) splits into c/2 on (i, j) and c/2 on (j, i), so that
+// X_{lm}(k) = sum over ordered pairs of c_ij Re(conj F^A_i F^B_j): the Hermitian part of
+// the bilinear sum of eq. bisector-pk-fft with delta_A at r_1 and delta_B at r_2.
+void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, int a0, int a1, int b0, int b1,
+                         bool cross = false) {
   const bool f32 = key.prec == 32;
   const int L = key.ell_max, NL = L / 2 + 1, n_lm = n_even_lm(L);
   o << "extern \"C\" __global__ void __launch_bounds__(256) " << name
@@ -349,24 +354,45 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
   o << "        if (invw) { cc = invw[ix] * invw[iy] * invw[iz]; cc = cc * cc; }\n";
   for (int i = 0; i < n_lm; ++i) o << "        real X" << i << " = (real)0;\n";
   std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> by_pair;
-  for (auto &t : bisector_terms(key.ell_max, key.K))
-    if (t.i >= a0 && t.i < a1 && t.j >= b0 && t.j < b1) by_pair[{t.i, t.j}].push_back({t.lm, t.c});
+  for (auto &t : bisector_terms(key.ell_max, key.K)) {
+    if (cross) {
+      if (t.i == t.j) {
+        by_pair[{t.i, t.j}].push_back({t.lm, t.c});
+      } else {
+        by_pair[{t.i, t.j}].push_back({t.lm, 0.5 * t.c});
+        by_pair[{t.j, t.i}].push_back({t.lm, 0.5 * t.c});
+      }
+    } else if (t.i >= a0 && t.i < a1 && t.j >= b0 && t.j < b1) {
+      by_pair[{t.i, t.j}].push_back({t.lm, t.c});
+    }
+  }
   std::set<int> ua, ub;
   for (auto &kv : by_pair) {
     ua.insert(kv.first.first);
     ub.insert(kv.first.second);
   }
-  const bool same = a0 == b0;
-  for (int i : ua) o << "        const real2 f" << i << " = FA[" << i - a0 << "LL * cslot + m];\n";
+  const bool same = !cross && a0 == b0;
+  const char *na = cross ? "a" : "f", *nb = cross ? "b" : "f";
+  // cross: B's fields first, then each A field just before the terms that use it
+  if (!cross)
+    for (int i : ua) o << "        const real2 f" << i << " = FA[" << i - a0 << "LL * cslot + m];\n";
   for (int j : ub)
     if (!(same && ua.count(j)))
-      o << "        const real2 f" << j << " = " << (same ? "FA[" : "FB[") << j - b0 << "LL * cslot + m];\n";
+      o << "        const real2 " << nb << j << " = " << (same ? "FA[" : "FB[") << j - b0 << "LL * cslot + m];\n";
+  int cur = -1;
   for (auto &kv : by_pair) {
     const int i = kv.first.first, j = kv.first.second;
-    o << "        { const real q = f" << i << ".x * f" << j << ".x + f" << i << ".y * f" << j << ".y;";
+    if (cross && i != cur) {
+      if (cur >= 0) o << "        }\n";
+      o << "        { const real2 a" << i << " = FA[" << i - a0 << "LL * cslot + m];\n";
+      cur = i;
+    }
+    o << "        { const real q = " << na << i << ".x * " << nb << j << ".x + " << na << i << ".y * " << nb << j
+      << ".y;";
     for (auto &lc : kv.second) o << " X" << lc.first << " += " << lit(lc.second, f32) << " * q;";
     o << " }\n";
   }
+  if (cross && cur >= 0) o << "        }\n";
   for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
   o << "        if (xout) {\n";
   for (int i = 0; i < n_lm; ++i)
@@ -561,6 +587,17 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
   return o.str();
 }
 
+std::string generate_cross_source(const JitKey &key) {
+  const bool f32 = key.prec == 32;
+  const char *real = f32 ? "float" : "double";
+  const int nf = (int)field_set(key).list.size();
+  std::ostringstream o;
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << kPrelude;
+  emit_kcontract_pair(o, "kcontract_cross", key, 0, nf, 0, nf, true);
+  return o.str();
+}
+
 bool compile_cubin(const std::string &src, std::vector<char> &cubin, std::string &log) {
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "bym_generated.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
@@ -629,6 +666,40 @@ std::shared_ptr<KernelSet> get_kernels(const JitKey &key, std::string &err) {
   }
   cache[key] = ks;
   return ks;
+}
+
+cudaKernel_t get_cross_kernel(const JitKey &key, std::string &err) {
+  static std::mutex mu;
+  static std::map<JitKey, cudaKernel_t> cache;
+  if (key.los != 2) {
+    err = "the two-set contraction belongs to the bisector";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  std::string src;
+  try {
+    src = generate_cross_source(key);
+  } catch (const std::exception &e) {
+    err = std::string("kernel generation failed: ") + e.what();
+    return nullptr;
+  }
+  std::vector<char> cubin;
+  std::string log;
+  if (!compile_cubin(src, cubin, log)) {
+    err = "NVRTC compile failed: " + log.substr(0, 2000);
+    return nullptr;
+  }
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t k = nullptr;
+  if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+      cudaLibraryGetKernel(&k, lib, "kcontract_cross") != cudaSuccess) {
+    err = std::string("loading the cross contraction: ") + cudaGetErrorString(cudaGetLastError());
+    return nullptr;
+  }
+  cache[key] = k;   // the library stays loaded for the life of the process, as the other modules do
+  return k;
 }
 
 std::shared_ptr<ChunkSet> get_chunk_kernels(const JitKey &key, int max_fields, std::string &err) {

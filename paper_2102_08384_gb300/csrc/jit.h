@@ -51,6 +51,13 @@ std::string generate_source(const JitKey &key, KernelSet *meta);
 
 std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *meta);
 
+// Bisector cross spectra of two tracers: kcontract_cross(FA, FB, ...) with the arguments of
+// the block-pair contraction, FA / FB every field F[Y_J^M delta] of tracer A / B, summing
+// X_{lm}(k) = sum c_ij Re(conj F^A_i F^B_j) over ordered pairs (the Hermitian part of eq.
+// bisector-pk-fft with delta_A at r_1, delta_B at r_2).
+std::string generate_cross_source(const JitKey &key);
+cudaKernel_t get_cross_kernel(const JitKey &key, std::string &err);
+
 // Compile to a cubin for sm_103a; returns false and fills log on failure.
 bool compile_cubin(const std::string &src, std::vector<char> &cubin, std::string &log);
 

@@ -6,6 +6,9 @@
 //                     into the padded real mesh (periodic, FP64 cell geometry);
 //   bym_spec_mul      F(k) <- F(k) conj(delta(k)) s_f W(k)^-2 for a run of field
 //                     spectra (the convolution step of eq. g-JM-form / eq. 2pcf-yama);
+//   bym_spec_mul_cross  the same step for two tracers: F^A(k) <- [F^A(k) conj(delta_B(k))
+//                     + F^B(k) conj(delta_A(k))] s_f W(k)^-2 / 2 (both anchorings of the
+//                     midpoint series, and the two endpoint lines of sight of Yamamoto);
 //   bym_interlace     F(k) <- (F(k) + P(k) G(k)) / 2 with G the transform on the mesh
 //                     shifted by half a cell (interlaced mass assignment).
 #include "kernels.cuh"
@@ -172,6 +175,37 @@ __global__ void __launch_bounds__(256) bym_spec_mul(T2 *__restrict__ F, long lon
   }
 }
 
+// Two tracers: FA_f <- [FA_f conj(DB) + FB_f conj(DA)] s_f W^-2 / 2 for f = 0..nf-1, with FA / FB
+// the weighted-field spectra of tracer A / B and DA / DB their density spectra.
+template <typename T, typename T2>
+__global__ void __launch_bounds__(256) bym_spec_mul_cross(T2 *__restrict__ FA, const T2 *__restrict__ FB,
+                                                          long long cslot, int nf, const T2 *__restrict__ DA,
+                                                          const T2 *__restrict__ DB, int N,
+                                                          const double *__restrict__ scale,
+                                                          const T *__restrict__ invw) {
+  const int H = N / 2 + 1;
+  const long long nm = (long long)N * N * H;
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += (long long)gridDim.x * blockDim.x) {
+    const T2 da = DA[m], db = DB[m];
+    T cc = (T)0.5;
+    if (invw) {
+      const int iz = (int)(m % H);
+      const long long row = m / H;
+      const T w = invw[(int)(row / N)] * invw[(int)(row % N)] * invw[iz];
+      cc = (T)0.5 * w * w;
+    }
+    for (int f = 0; f < nf; ++f) {
+      T2 *q = FA + (long long)f * cslot + m;
+      const T2 a = *q, b = FB[(long long)f * cslot + m];
+      const T s = (T)scale[f] * cc;
+      T2 r;
+      r.x = (a.x * db.x + a.y * db.y + b.x * da.x + b.y * da.y) * s;
+      r.y = (a.y * db.x - a.x * db.y + b.y * da.x - b.x * da.y) * s;
+      *q = r;
+    }
+  }
+}
+
 // Interlacing: F_f(k) <- (F_f(k) + P(k) G_f(k)) / 2 for f = 0..nf-1, with G the transform of
 // the same field on the mesh shifted by half a cell along each axis and P(k) = prod over the
 // axes of ph[n_axis] (per-axis phase exp(-i pi n / N) of the shift, 0 at the Nyquist index).
@@ -232,6 +266,14 @@ void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const d
 }
 
 template <typename T, typename T2>
+void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const T2 *DA, const T2 *DB, int N,
+                           const double *scale, const T *invw, int nsm, cudaStream_t st) {
+  if (nf <= 0) return;
+  const long long nm = (long long)N * N * (N / 2 + 1);
+  bym_spec_mul_cross<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(FA, FB, cslot, nf, DA, DB, N, scale, invw);
+}
+
+template <typename T, typename T2>
 void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st) {
   if (nf <= 0) return;
   const long long nm = (long long)N * N * (N / 2 + 1);
@@ -250,5 +292,11 @@ template void launch_spec_mul<float, float2>(float2 *, long long, int, const flo
                                              const float *, int, cudaStream_t);
 template void launch_spec_mul<double, double2>(double2 *, long long, int, const double2 *, int, const double *,
                                                const double *, int, cudaStream_t);
+template void launch_spec_mul_cross<float, float2>(float2 *, const float2 *, long long, int, const float2 *,
+                                                   const float2 *, int, const double *, const float *, int,
+                                                   cudaStream_t);
+template void launch_spec_mul_cross<double, double2>(double2 *, const double2 *, long long, int, const double2 *,
+                                                     const double2 *, int, const double *, const double *, int,
+                                                     cudaStream_t);
 
 }  // namespace bym

@@ -16,6 +16,11 @@ template <typename T, typename T2>
 void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const double *scale, const T *invw, int nsm,
                      cudaStream_t st);
 
+// two tracers: FA_f <- [FA_f conj(DB) + FB_f conj(DA)] scale_f W^-2 / 2 (half-spectrum slots)
+template <typename T, typename T2>
+void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const T2 *DA, const T2 *DB, int N,
+                           const double *scale, const T *invw, int nsm, cudaStream_t st);
+
 // F_f <- (F_f + P G_f) / 2, P(k) = ph[n_x] ph[n_y] ph[n_z] (half-spectrum slots)
 template <typename T, typename T2>
 void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st);
