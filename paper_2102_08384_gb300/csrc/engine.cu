@@ -382,7 +382,8 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
         TRY_RC(fft_planes(c, st, 0, N, slots, slot_bytes, first, count, tn));
       }
       {
-        ProfScope ps(c, st, "fft_native_x_convolve", count * 3.0 * cplx);   // read F and D, write F
+        // read every F once and D once (each D tile serves all fields of the launch), write F
+        ProfScope ps(c, st, "fft_native_x_convolve", (2.0 * count + 1.0) * cplx);
         e = native_fft_xpass(2, (float *)slots, slot_reals, first, count, (const float *)slots, scale,
                              (const float *)invw, st);
       }

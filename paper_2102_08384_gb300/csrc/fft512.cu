@@ -426,8 +426,11 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 // x pass: C2C along x for tiles of TC kz columns of one ky
 // mode 0 forward, 1 inverse, 2 forward -> * conj(D) s W^-2 -> inverse
 // Persistent: a few CTAs per SM walk the tiles; each tile is copied into shared
-// memory with cp.async while the previous one is transformed (mode 2 also
-// prefetches the matching D tile), so loads overlap the FFT work.
+// memory with cp.async while the previous one is transformed, so loads overlap the
+// FFT work.  Mode 2 walks position-major: a CTA takes the tile positions (ky, kz0)
+// p = blockIdx.x, blockIdx.x + gridDim.x, ... and at each one every field of the
+// launch in turn, so the D tile of a position is copied once (prefetched during the
+// last field of the previous position) and serves all of them.
 // block TC * 16 (TC groups, one column each)
 // ---------------------------------------------------------------------------
 constexpr int XTC = 16;                    // kz columns per tile (128-byte row segments; 8 measured slower)
@@ -472,13 +475,19 @@ __device__ __forceinline__ XTile x_tile(long long t) {
   return r;
 }
 
-// asynchronous copy of one tile: T[c][x] = src[x][c], c < nvalid; one commit group
+// asynchronous copy of one tile: T[c][x] = src[x][c], c < nvalid; one commit group.
+// Thread e copies column c = e % TC at rows x = e / TC + (NT / TC) q, q = 0..NM TC / NT - 1,
+// unrolled so that no copy waits for the previous one to release its address registers.
 template <int TC>
 __device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid) {
+  constexpr int NT = XShape<TC>::NT, XR = NT / TC, NQ = NM * TC / NT;
   const long long xs = (long long)NM * HZ;
-  for (int e = threadIdx.x; e < NM * TC; e += XShape<TC>::NT) {
-    const int x = e / TC, c = e % TC;
-    if (c < nvalid) cp_async8(T + c * XShape<TC>::XS + x, src + x * xs + c);
+  const int c = threadIdx.x % TC, x0 = threadIdx.x / TC;
+  if (c < nvalid) {
+    float2 *t = T + c * XShape<TC>::XS + x0;
+    const float2 *g = src + x0 * xs + c;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) cp_async8(t + q * XR, g + (long long)q * XR * xs);
   }
   cp_async_commit();
 }
@@ -499,7 +508,12 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
   const unsigned gm = 0xFFFFu << (tid & 16);
   const int ka = j, kb = col_b(j);
   const long long xs = (long long)NM * HZ;
+  // modes 0, 1: t is the tile index; mode 2: t is the position, f the field
+  const long long npos = (long long)X::KZT * NM;
+  const int nf = MODE == 2 ? (int)(ntiles / npos) : 1;
+  const long long tend = MODE == 2 ? npos : ntiles;
   long long t = blockIdx.x;
+  int f = 0;
   XTile cur = x_tile<TC>(t);
   x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid);
   if (MODE == 2) x_tile_issue<TC>(buf1, D + cur.off, cur.nvalid);
@@ -507,15 +521,20 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
   if (MODE == 2 && invw)
     for (int i = tid; i < NM; i += X::NT) W1[i] = invw[i];
   float2 *A = buf0;
-  for (; t < ntiles; t += gridDim.x) {
+  while (t < tend) {
     if (MODE == 2)
       cp_async_wait<1>();         // this tile's data (its D may still be in flight)
     else
       cp_async_wait<0>();
     __syncthreads();
-    const long long tn = t + gridDim.x;
-    const bool has_next = tn < ntiles;
-    const XTile nxt = x_tile<TC>(has_next ? tn : t);
+    long long tn = t;
+    int fn = f + 1;
+    if (fn >= nf) {               // modes 0, 1 always; mode 2 after the last field of a position
+      tn = t + gridDim.x;
+      fn = 0;
+    }
+    const bool has_next = tn < tend;
+    const XTile nxt = has_next ? x_tile<TC>(tn + (long long)fn * npos) : cur;
     float2 *Anext = MODE == 2 ? (A == buf0 ? buf2 : buf0) : (A == buf0 ? buf1 : buf0);
     if (has_next)
       x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid);
@@ -523,6 +542,7 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
       cp_async_commit();
     float2 *col = A + g * XS_;
     float2 v[32], As[16], Bs[16];
+    const float s = MODE == 2 ? (float)scale[cur.slot] : 1.f;   // issued before the transform hides its latency
     if (MODE == 1) {
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
@@ -535,10 +555,11 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
       fwd512(v, As, Bs, j, gm, TW, col);
     }
     if (MODE == 2) {
-      cp_async_wait<1>();         // this tile's D
-      __syncthreads();
+      if (f == 0) {               // a new position: its D tile (the group before this tile's prefetch)
+        cp_async_wait<1>();
+        __syncthreads();
+      }
       const float2 *dcol = buf1 + g * XS_;
-      const float s = (float)scale[cur.slot];
       const float cyz = invw ? W1[cur.ky] * W1[cur.kz0 + (g < cur.nvalid ? g : 0)] : 1.f;
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
@@ -552,11 +573,12 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
         As[k2] = cscale(cmulc(As[k2], dcol[kxa]), ca);
         Bs[k2] = cscale(cmulc(Bs[k2], dcol[kxb]), cb);
       }
-      __syncthreads();            // every group is done with D: prefetch the next one
-      if (has_next)
+      if (has_next && fn == 0) {  // the next tile starts another position: prefetch its D
+        __syncthreads();          // once every group is done with this one
         x_tile_issue<TC>(buf1, D + nxt.off, nxt.nvalid);
-      else
+      } else {
         cp_async_commit();
+      }
     }
     if (MODE == 0) {
       __syncwarp(gm);
@@ -572,13 +594,22 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
       for (int m = 0; m < 32; ++m) col[16 * m + j] = v[m];
     }
     __syncthreads();
-    float2 *base = data + (long long)cur.slot * slot_cplx + cur.off;
-    for (int e = tid; e < NM * TC; e += X::NT) {
-      const int x = e / TC, c = e % TC;
-      if (c < cur.nvalid) base[x * xs + c] = A[c * XS_ + x];
+    {   // write-out: every value of this thread's rows is read from shared memory first, then stored
+      constexpr int XR = X::NT / TC, NQ = NM * TC / X::NT;
+      const int c = tid % TC, x0 = tid / TC;
+      if (c < cur.nvalid) {
+        float2 o[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) o[q] = A[c * XS_ + x0 + q * XR];
+        float2 *base = data + (long long)cur.slot * slot_cplx + cur.off + x0 * xs + c;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) base[(long long)q * XR * xs] = o[q];
+      }
     }
     cur = nxt;
     A = Anext;
+    t = tn;
+    f = fn;
   }
   cp_async_wait<0>();
 }
@@ -669,7 +700,9 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
   int dev = 0;
   cudaGetDevice(&dev);
   const long long ntiles = (long long)X::KZT * NM * n;
-  const long long grid = std::min<long long>(ntiles, (long long)sm_count(dev) * (MODE == 2 ? X::PER_SM2 : X::PER_SM01));
+  // mode 2 distributes tile positions (each with all n fields), modes 0 and 1 tiles
+  const long long units = MODE == 2 ? (long long)X::KZT * NM : ntiles;
+  const long long grid = std::min<long long>(units, (long long)sm_count(dev) * (MODE == 2 ? X::PER_SM2 : X::PER_SM01));
   fft512_x<MODE, XTC><<<(unsigned)grid, X::NT, MODE == 2 ? X::SMEM2 : X::SMEM01, st>>>(
       (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw);
   return cudaGetLastError();
