@@ -437,7 +437,10 @@ constexpr int XTC = 16;                    // kz columns per tile (128-byte row 
 template <int TC>
 struct XShape {
   static constexpr int NT = TC * 16;                   // threads
-  static constexpr int KZT = (HZ + TC - 1) / TC;       // kz tiles per ky
+  // tile positions of a slot: TC consecutive kz < 256 of one ky (KZF per ky), then the
+  // kz = 256 (Nyquist) columns of TC consecutive ky, so that no tile is mostly empty
+  static constexpr int KZF = 256 / TC;
+  static constexpr long long NPOS = (long long)KZF * NM + NM / TC;
   // tile row stride (float2): >= EX for the exchange buffer; TC * XS + x spreads the
   // tile writes of a half-warp (16 / TC rows of x) over distinct banks
   static constexpr int XS = TC == 16 ? 545 : 546;
@@ -458,19 +461,30 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 struct XTile {
-  long long off;   // (ky, kz0) offset within a slot, complex units
+  long long off;   // offset of column 0 within a slot, complex units
   int slot, ky, kz0, nvalid;
+  int nyq;         // 0: column c is (ky, kz0 + c); 1: column c is (ky + c, 256)
+  int cst;         // complex units from column c to column c + 1 (1, or HZ for the kz = 256 columns)
 };
 
 template <int TC>
 __device__ __forceinline__ XTile x_tile(long long t) {
+  using X = XShape<TC>;
   XTile r;
-  const int kzt = (int)(t % XShape<TC>::KZT);
-  const long long u = t / XShape<TC>::KZT;
-  r.ky = (int)(u % NM);
-  r.slot = (int)(u / NM);
-  r.kz0 = kzt * TC;
-  r.nvalid = HZ - r.kz0 < TC ? HZ - r.kz0 : TC;
+  const long long p = t % X::NPOS;
+  r.slot = (int)(t / X::NPOS);
+  if (p < (long long)X::KZF * NM) {
+    r.ky = (int)(p / X::KZF);
+    r.kz0 = (int)(p % X::KZF) * TC;
+    r.nyq = 0;
+    r.cst = 1;
+  } else {
+    r.ky = (int)(p - (long long)X::KZF * NM) * TC;
+    r.kz0 = NM / 2;
+    r.nyq = 1;
+    r.cst = HZ;
+  }
+  r.nvalid = TC;
   r.off = (long long)r.ky * HZ + r.kz0;
   return r;
 }
@@ -479,13 +493,13 @@ __device__ __forceinline__ XTile x_tile(long long t) {
 // Thread e copies column c = e % TC at rows x = e / TC + (NT / TC) q, q = 0..NM TC / NT - 1,
 // unrolled so that no copy waits for the previous one to release its address registers.
 template <int TC>
-__device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid) {
+__device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid, int cst) {
   constexpr int NT = XShape<TC>::NT, XR = NT / TC, NQ = NM * TC / NT;
   const long long xs = (long long)NM * HZ;
   const int c = threadIdx.x % TC, x0 = threadIdx.x / TC;
   if (c < nvalid) {
     float2 *t = T + c * XShape<TC>::XS + x0;
-    const float2 *g = src + x0 * xs + c;
+    const float2 *g = src + x0 * xs + (long long)c * cst;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) cp_async8(t + q * XR, g + (long long)q * XR * xs);
   }
@@ -509,14 +523,14 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
   const int ka = j, kb = col_b(j);
   const long long xs = (long long)NM * HZ;
   // modes 0, 1: t is the tile index; mode 2: t is the position, f the field
-  const long long npos = (long long)X::KZT * NM;
+  const long long npos = X::NPOS;
   const int nf = MODE == 2 ? (int)(ntiles / npos) : 1;
   const long long tend = MODE == 2 ? npos : ntiles;
   long long t = blockIdx.x;
   int f = 0;
   XTile cur = x_tile<TC>(t);
-  x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid);
-  if (MODE == 2) x_tile_issue<TC>(buf1, D + cur.off, cur.nvalid);
+  x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid, cur.cst);
+  if (MODE == 2) x_tile_issue<TC>(buf1, D + cur.off, cur.nvalid, cur.cst);
   for (int i = tid; i < EX; i += X::NT) TW[i] = gtw[i];
   if (MODE == 2 && invw)
     for (int i = tid; i < NM; i += X::NT) W1[i] = invw[i];
@@ -537,7 +551,7 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
     const XTile nxt = has_next ? x_tile<TC>(tn + (long long)fn * npos) : cur;
     float2 *Anext = MODE == 2 ? (A == buf0 ? buf2 : buf0) : (A == buf0 ? buf1 : buf0);
     if (has_next)
-      x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid);
+      x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid, nxt.cst);
     else
       cp_async_commit();
     float2 *col = A + g * XS_;
@@ -559,23 +573,33 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
         cp_async_wait<1>();
         __syncthreads();
       }
-      const float2 *dcol = buf1 + g * XS_;
-      const float cyz = invw ? W1[cur.ky] * W1[cur.kz0 + (g < cur.nvalid ? g : 0)] : 1.f;
+      float2 *dcol = buf1 + g * XS_;
+      if (f == 0) {
+        // D <- conj(D) W^-2 in place, once per position: every thread rewrites exactly the
+        // entries kx = ka + 32 k2, kb + 32 k2 of its column that it reads below (the pairs
+        // (ka, kb) of the 16 threads cover 0..31 once), so no other thread depends on them
+        const int gc = g < cur.nvalid ? g : 0;
+        const float cyz = invw ? W1[cur.ky + (cur.nyq ? gc : 0)] * W1[cur.kz0 + (cur.nyq ? 0 : gc)] : 1.f;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const int kxa = ka + 32 * k2, kxb = kb + 32 * k2;
+          float wa = 1.f, wb = 1.f;
+          if (invw) {
+            wa = W1[kxa] * cyz;
+            wb = W1[kxb] * cyz;
+          }
+          dcol[kxa] = cscale(cconj(dcol[kxa]), wa * wa);
+          dcol[kxb] = cscale(cconj(dcol[kxb]), wb * wb);
+        }
+      }
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
-        const int kxa = ka + 32 * k2, kxb = kb + 32 * k2;
-        float ca = s, cb = s;
-        if (invw) {
-          const float wa = W1[kxa] * cyz, wb = W1[kxb] * cyz;
-          ca *= wa * wa;
-          cb *= wb * wb;
-        }
-        As[k2] = cscale(cmulc(As[k2], dcol[kxa]), ca);
-        Bs[k2] = cscale(cmulc(Bs[k2], dcol[kxb]), cb);
+        As[k2] = cscale(cmul(As[k2], dcol[ka + 32 * k2]), s);
+        Bs[k2] = cscale(cmul(Bs[k2], dcol[kb + 32 * k2]), s);
       }
       if (has_next && fn == 0) {  // the next tile starts another position: prefetch its D
         __syncthreads();          // once every group is done with this one
-        x_tile_issue<TC>(buf1, D + nxt.off, nxt.nvalid);
+        x_tile_issue<TC>(buf1, D + nxt.off, nxt.nvalid, nxt.cst);
       } else {
         cp_async_commit();
       }
@@ -601,7 +625,7 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
         float2 o[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) o[q] = A[c * XS_ + x0 + q * XR];
-        float2 *base = data + (long long)cur.slot * slot_cplx + cur.off + x0 * xs + c;
+        float2 *base = data + (long long)cur.slot * slot_cplx + cur.off + x0 * xs + (long long)c * cur.cst;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) base[(long long)q * XR * xs] = o[q];
       }
@@ -699,9 +723,9 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
   using X = XShape<XTC>;
   int dev = 0;
   cudaGetDevice(&dev);
-  const long long ntiles = (long long)X::KZT * NM * n;
+  const long long ntiles = X::NPOS * n;
   // mode 2 distributes tile positions (each with all n fields), modes 0 and 1 tiles
-  const long long units = MODE == 2 ? (long long)X::KZT * NM : ntiles;
+  const long long units = MODE == 2 ? X::NPOS : ntiles;
   const long long grid = std::min<long long>(units, (long long)sm_count(dev) * (MODE == 2 ? X::PER_SM2 : X::PER_SM01));
   fft512_x<MODE, XTC><<<(unsigned)grid, X::NT, MODE == 2 ? X::SMEM2 : X::SMEM01, st>>>(
       (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw);
