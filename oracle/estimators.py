@@ -156,27 +156,34 @@ def _tracers(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, a
     return g, ta, _Tracer(delta_b, tr_b), float(np.sqrt(A * A_b)), v_cell
 
 
-def _cross_g_fields(g, ta, tb, K, ell_max, even=False):
-    """g fields of the midpoint series: g^AB (delta_A conjugated, delta_B carrying
-    the weights, anchored on the second galaxy) averaged with g^BA (anchored on the
-    first); one density: g^AA."""
-    gab = g_fields(g, tb.delta, ta.D, K, ell_max, tb.tr, even)
+def _cross_g_fields(g, ta, tb, K, ell_max, even=False, parities=(0,)):
+    """g fields of the midpoint series, both anchorings: [(-1)^ell g^AB + g^BA] / 2 with
+    g^AB (delta_A conjugated, delta_B carrying the weights) from the expansion anchored on
+    the second galaxy and g^BA from the one anchored on the first, after the relabelling
+    Delta -> -Delta, k -> -k that brings it to the same form (exact in shell means); ell's
+    parity is that of J - alpha.  One density: g^AA for even ell, 0 for odd ell."""
+    gab = g_fields(g, tb.delta, ta.D, K, ell_max, tb.tr, even, parities)
     if tb is ta:
-        return gab
-    gba = g_fields(g, ta.delta, tb.D, K, ell_max, ta.tr, even)
-    return {key: 0.5 * (gab[key] + gba[key]) for key in gab}
+        return {key: (v if (key[1] - key[0]) % 2 == 0 else np.zeros_like(v)) for key, v in gab.items()}
+    gba = g_fields(g, ta.delta, tb.D, K, ell_max, ta.tr, even, parities)
+    return {key: 0.5 * ((-1) ** (key[1] - key[0]) * gab[key] + gba[key]) for key in gab}
 
 
-def _ells(ell_max):
-    if ell_max < 0 or ell_max % 2:
-        raise ValueError("only even ell_max is supported (the paper assumes even ell)")
-    return list(range(0, ell_max + 1, 2))
+def _ells(ell_max, odd=False):
+    """ell = 0, 2, .., ell_max (the paper's even multipoles), or every ell <= ell_max with odd."""
+    if ell_max < 0 or (ell_max % 2 and not odd):
+        raise ValueError("odd ell_max needs odd=True (the paper assumes even ell)")
+    return list(range(0, ell_max + 1, 1 if odd else 2))
 
 
 def _pk_out(g, ells, T, A, kedges):
+    """Shell means of T_ell(k) = sum_m Y_ell^m*(k) X_ell^m(k): the real part for even ell, the
+    imaginary part for odd ell (the shell mean of an odd multipole is imaginary, since
+    T_ell(-k) = (-1)^ell conj T_ell(k) for real densities)."""
     pk, kmean, cnt = [], None, None
     for ell in ells:
-        mean, kmean, cnt = mesh.shell_mean(T[ell], g.k_mag, kedges, g.k_mag == 0.0)
+        t = np.real(T[ell]) if ell % 2 == 0 else np.imag(T[ell])
+        mean, kmean, cnt = mesh.shell_mean(t, g.k_mag, kedges, g.k_mag == 0.0)
         pk.append(FOUR_PI / A * mean)
     return {"ells": ells, "pk": np.array(pk), "k_mean": kmean, "n_modes": cnt}
 
@@ -184,7 +191,7 @@ def _pk_out(g, ells, T, A, kedges):
 def _xi_out(g, ells, Z, A, v_cell, redges):
     xi, rmean, cnt = [], None, None
     for ell in ells:
-        mean, rmean, cnt = mesh.shell_mean(Z[ell], g.lag_mag, redges, g.lag_mag == 0.0)
+        mean, rmean, cnt = mesh.shell_mean(np.real(Z[ell]), g.lag_mag, redges, g.lag_mag == 0.0)
         xi.append(FOUR_PI / (A * v_cell) * mean)
     return {"ells": ells, "xi": np.array(xi), "r_mean": rmean, "n_cells": cnt}
 
@@ -192,11 +199,13 @@ def _xi_out(g, ells, Z, A, v_cell, redges):
 # --------------------------------------------------------------------------
 # midpoint convolution fields g^alpha_JM (eq. g-JM-form)
 # --------------------------------------------------------------------------
-def g_fields(g: Grid, delta, D, K, ell_max, tr, even=False):
+def g_fields(g: Grid, delta, D, K, ell_max, tr, even=False, parities=(0,)):
     """g^alpha_JM(Delta) = (-1)^J IFFT[ delta*(k) F[(2r)^-alpha Y_J^M delta](k) ](Delta)
-    for alpha <= K and J = alpha, alpha-2, ... <= ell_max + alpha (the J with
-    non-zero phi / f for even ell).  Cells with delta = 0 carry no field; a
-    non-empty cell at the observer has no expansion and is rejected."""
+    for alpha <= K and J <= ell_max + alpha with J - alpha of the given parities: the J
+    with non-zero phi / f are J = alpha, alpha - 2, ... for even ell (parity 0) and
+    alpha + 1, alpha - 1, ... for odd ell (parity 1), since J1 = alpha mod 2 and
+    J1 + J2 = ell mod 2.  Cells with delta = 0 carry no field; a non-empty cell at the
+    observer has no expansion and is rejected."""
     if np.any((g.r == 0.0) & (delta != 0.0)):
         raise ValueError("a non-empty mesh node sits on the observer")
     Dc = np.conj(D)
@@ -207,10 +216,11 @@ def g_fields(g: Grid, delta, D, K, ell_max, tr, even=False):
 
     out = {}
     for alpha in range(0, K + 1, 2 if even else 1):
-        for J in range(alpha % 2, ell_max + alpha + 1, 2):
-            for M in range(-J, J + 1):
-                F = tr.fwd(lambda x: radial(x, alpha) * ylm(J, M, x))
-                out[(alpha, J, M)] = (-1) ** J * mesh.ifftn(Dc * F)
+        for par in parities:
+            for J in range((alpha + par) % 2, ell_max + alpha + 1, 2):
+                for M in range(-J, J + 1):
+                    F = tr.fwd(lambda x: radial(x, alpha) * ylm(J, M, x))
+                    out[(alpha, J, M)] = (-1) ** J * mesh.ifftn(Dc * F)
     return out
 
 
@@ -219,13 +229,16 @@ def g_fields(g: Grid, delta, D, K, ell_max, tr, even=False):
 # --------------------------------------------------------------------------
 def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
                   order, kedges, compensate=False, norm=1, interlace=False,
-                  gal_b=None, ran_b=None, ran_nbar_b=None):
-    """P_ell(k) for ell = 0, 2, .., ell_max with LOS in
+                  gal_b=None, ran_b=None, ran_nbar_b=None, odd=False):
+    """P_ell(k) for ell = 0, 2, .., ell_max (every ell <= ell_max with odd) with LOS in
     {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}; the cross
     spectrum of (gal, ran) with (gal_b, ran_b) when gal_b is given."""
     g, ta, tb, A, _ = _tracers(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign, norm,
                                compensate, interlace=interlace)
-    ells = _ells(ell_max)
+    ells = _ells(ell_max, odd)
+    if odd and los == "midpoint_even":
+        raise ValueError("the parity-even midpoint form is defined for even ell")
+    pars = (0, 1) if odd else (0,)
     shape = ta.D.shape
     T = {}
     if los == "yamamoto":
@@ -235,13 +248,13 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
             acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
                 acc += np.conj(ylm(ell, m, g.k)) * _yamamoto_product(ta, tb, ell, m)
-            T[ell] = acc.real
+            T[ell] = acc
     elif los in ("midpoint", "midpoint_even"):
         # eq. FFT-midpoint: sum_m Y*(k) sum phi F[ Y_J1^M(Delta) Delta^alpha g^alpha_{J2 (m-M)}(Delta) ](k);
         # parity-even form (Sec. 3.3 boxed): phi -> Phi, even alpha only
         even = los == "midpoint_even"
         table = Phi_table if even else phi_table
-        gf = _cross_g_fields(g, ta, tb, order, ell_max, even)
+        gf = _cross_g_fields(g, ta, tb, order, ell_max, even, pars)
         for ell in ells:
             acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
@@ -251,7 +264,7 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
                     for (J1, J2, M), c in table(alpha, ell, m).items():
                         H += c * ylm(J1, M, g.lag) * dpow * gf[(alpha, J2, m - M)]
                 acc += np.conj(ylm(ell, m, g.k)) * mesh.fftn(H)
-            T[ell] = acc.real
+            T[ell] = acc
     elif los == "bisector":
         # eq. bisector-pk-fft: sum_m Y*(k) sum B F[Y_J1^M delta_A](-k) F[Y_J2^{m-M} delta_B](k)
         FA, FB = _bisector_fields(ta, tb, ell_max + order // 2)
@@ -259,25 +272,28 @@ def pk_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
             acc = np.zeros(shape, dtype=np.complex128)
             for m in range(-ell, ell + 1):
                 acc += np.conj(ylm(ell, m, g.k)) * _bisector_X(FA, FB, order // 2, ell, m, shape)
-            T[ell] = acc.real
+            T[ell] = acc
     elif los == "fixed":
-        # Re[delta_A*(k) delta_B(k)] L_ell(k . n) with n = the direction of the box centre
+        # delta_A*(k) delta_B(k) L_ell(k . n) with n = the direction of the box centre
         n = g.box_lo + 0.5 * g.box_len
         n = n / np.linalg.norm(n)
         mu = np.where(g.k_mag > 0, (g.k @ n) / np.where(g.k_mag > 0, g.k_mag, 1.0), 0.0)
         for ell in ells:
-            T[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * (np.conj(ta.D) * tb.D).real
+            T[ell] = (2 * ell + 1) / FOUR_PI * legendre_L(ell, mu) * (np.conj(ta.D) * tb.D)
     else:
         raise ValueError(f"unknown los {los!r}")
     return _pk_out(g, ells, T, A, kedges)
 
 
 def _yamamoto_product(ta, tb, ell, m):
-    """delta_A*(k) F[Y_ell^m delta_B](k), averaged with A and B swapped for two tracers."""
+    """[delta_A*(k) F[Y_ell^m delta_B](k) + (-1)^ell delta_B*(k) F[Y_ell^m delta_A](k)] / 2:
+    the lines of sight through the second and through the first galaxy (the latter brought
+    to this form by k -> -k, exact in shell means).  One density: the first term for even
+    ell, 0 for odd ell."""
     p = np.conj(ta.D) * tb.tr.fwd(lambda x: ylm(ell, m, x))
     if tb is ta:
-        return p
-    return 0.5 * (p + np.conj(tb.D) * ta.tr.fwd(lambda x: ylm(ell, m, x)))
+        return p if ell % 2 == 0 else np.zeros_like(p)
+    return 0.5 * (p + (-1) ** ell * np.conj(tb.D) * ta.tr.fwd(lambda x: ylm(ell, m, x)))
 
 
 def _bisector_fields(ta, tb, Jmax):
@@ -299,13 +315,16 @@ def _bisector_X(FA, FB, bmax, ell, m, shape):
 
 def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los,
                   order, redges, compensate=False, norm=1, interlace=False,
-                  gal_b=None, ran_b=None, ran_nbar_b=None):
-    """xi_ell(r) for ell = 0, 2, .., ell_max with LOS in
+                  gal_b=None, ran_b=None, ran_nbar_b=None, odd=False):
+    """xi_ell(r) for ell = 0, 2, .., ell_max (every ell <= ell_max with odd) with LOS in
     {'yamamoto', 'midpoint', 'midpoint_even', 'bisector', 'fixed'}; the cross
     correlation of (gal, ran) with (gal_b, ran_b) when gal_b is given."""
     g, ta, tb, A, v_cell = _tracers(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len, assign,
                                     norm, compensate, xi=True, interlace=interlace)
-    ells = _ells(ell_max)
+    ells = _ells(ell_max, odd)
+    if odd and los == "midpoint_even":
+        raise ValueError("the parity-even midpoint form is defined for even ell")
+    pars = (0, 1) if odd else (0,)
     shape = ta.D.shape
     Z = {}
     if los == "yamamoto":
@@ -320,7 +339,7 @@ def xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, lo
         # parity-even form (Sec. 4.3 boxed): f -> F, even alpha only
         even = los == "midpoint_even"
         table = F_table if even else f_table
-        gf = _cross_g_fields(g, ta, tb, order, ell_max, even)
+        gf = _cross_g_fields(g, ta, tb, order, ell_max, even, pars)
         for ell in ells:
             acc = np.zeros(shape, dtype=np.complex128)
             for alpha in range(0, order + 1, 2 if even else 1):

@@ -130,28 +130,32 @@ def _ylm_pair(los, ell, m, xa, xb, lag, series, both=False):
 
 def _legendre_pair(los, ell, xa, xb, lag, series, both=False):
     """L_ell(hat Delta . n) of the pair, exact or its truncated series (both: as in
-    ``_ylm_pair``; L_ell is even in Delta for even ell)."""
+    ``_ylm_pair``; swapping the ends turns Delta into -Delta, so the swapped term takes
+    (-1)^ell to stay L_ell of the pair's own Delta)."""
     if both and los in ("yamamoto", "midpoint", "midpoint_even"):
+        sgn = (-1) ** ell
         if los == "yamamoto":
             return 0.5 * (_legendre_pair(los, ell, xa, xb, lag, None)
-                          + _legendre_pair(los, ell, xb, xa, -lag, None))
+                          + sgn * _legendre_pair(los, ell, xb, xa, -lag, None))
         if series is not None:
             return 0.5 * (_legendre_pair(los, ell, xa, xb, lag, series)
-                          + _legendre_pair(los, ell, xb, xa, -lag, series))
+                          + sgn * _legendre_pair(los, ell, xb, xa, -lag, series))
     if series is None or los == "yamamoto":
         n = _unit(_los(los, xa, xb))
         mu = np.sum(_unit(lag) * n, axis=-1)
         return legendre_L(ell, mu)
     if los == "midpoint":
-        # L_ell(hat Delta . hat R) = L_ell(hat a . hat(a + A)), a = -Delta, A = 2 x_b (even ell)
+        # L_ell(hat Delta . hat R) = (-1)^ell L_ell(hat a . hat(a + A)), a = -Delta, A = 2 x_b
         eps = np.linalg.norm(lag, axis=-1) / (2.0 * np.linalg.norm(xb, axis=-1))
         mu = np.sum(_unit(-lag) * _unit(xb), axis=-1)
         out = np.zeros(len(xb))
         for alpha in range(series + 1):
             for J, c in f_table(alpha, ell).items():
                 out += (2 * J + 1) / (2 * ell + 1) * c * eps ** alpha * legendre_L(J, mu)
-        return out
+        return (-1) ** ell * out
     if los == "midpoint_even":
+        if ell % 2:
+            raise ValueError("the parity-even midpoint form is defined for even ell")
         eps = np.linalg.norm(lag, axis=-1) / (2.0 * np.linalg.norm(xb, axis=-1))
         mu = np.sum(_unit(-lag) * _unit(xb), axis=-1)
         out = np.zeros(len(xb))
@@ -169,9 +173,10 @@ def _legendre_pair(los, ell, xa, xb, lag, series, both=False):
 
 
 def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, kedges,
-            norm=1, series=None, gal_b=None, ran_b=None, ran_nbar_b=None):
+            norm=1, series=None, gal_b=None, ran_b=None, ran_nbar_b=None, odd=False):
     """O2 power-spectrum multipoles from explicit pairs of occupied nodes (cross
-    spectrum of two tracers when gal_b is given)."""
+    spectrum of two tracers when gal_b is given); with odd, every ell <= ell_max, odd
+    ell as the imaginary part of the shell mean (real densities make it imaginary)."""
     (idx, x, d), other, A = _densities(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len,
                                        assign, norm)
     both = other is not None
@@ -180,7 +185,7 @@ def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, ked
     xa, xb = x[ia], x_b[ib]
     kv = mesh.k_vectors(N, box_len)
     kmag = mesh.k_magnitude(N, box_len)
-    ells = list(range(0, ell_max + 1, 2))
+    ells = list(range(0, ell_max + 1, 1 if odd else 2))
     pk, kmean, cnt = [], None, None
     for ell in ells:
         acc = np.zeros((N, N, N), dtype=np.complex128)
@@ -188,13 +193,13 @@ def mesh_pk(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, ked
             G = np.zeros(N * N * N, dtype=np.complex128)
             np.add.at(G, flat, w * _ylm_pair(los, ell, m, xa, xb, lag, series, both))
             acc += np.conj(ylm(ell, m, kv)) * mesh.fftn(G.reshape(N, N, N))
-        mean, kmean, cnt = mesh.shell_mean(acc.real, kmag, kedges, kmag == 0.0)
+        mean, kmean, cnt = mesh.shell_mean(acc.real if ell % 2 == 0 else acc.imag, kmag, kedges, kmag == 0.0)
         pk.append(FOUR_PI / A * mean)
     return {"ells": ells, "pk": np.array(pk), "k_mean": kmean, "n_modes": cnt}
 
 
 def mesh_xi(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, redges,
-            norm=1, series=None, gal_b=None, ran_b=None, ran_nbar_b=None):
+            norm=1, series=None, gal_b=None, ran_b=None, ran_nbar_b=None, odd=False):
     """O2 correlation-function multipoles from explicit pairs of occupied nodes
     (cross correlation of two tracers when gal_b is given)."""
     (idx, x, d), other, A = _densities(gal, ran, ran_nbar, gal_b, ran_b, ran_nbar_b, N, box_lo, box_len,
@@ -211,7 +216,7 @@ def mesh_xi(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, red
     lagmag_grid = mesh.lag_magnitude(N, box_len)
     _, rmean, ncell = mesh.shell_mean(np.zeros_like(lagmag_grid), lagmag_grid, redges,
                                       lagmag_grid == 0.0)
-    ells = list(range(0, ell_max + 1, 2))
+    ells = list(range(0, ell_max + 1, 1 if odd else 2))
     nb = len(redges) - 1
     xi = []
     for ell in ells:
