@@ -89,6 +89,7 @@ def lib():
                                            vp]
         L.bym_pk_xi_cross.argtypes = [vp, cat_p, cat_p, cat_p, cat_p, par_p, bins_p, bins_p, dp, dp, i64p, dp, dp,
                                       i64p, vp]
+        L.bym_pk_xi_cross_odd.argtypes = L.bym_pk_xi_cross.argtypes
         L.bym_jit_check.argtypes = [par_p, ctypes.c_char_p, ctypes.c_size_t]
         L.bym_shot_noise.argtypes = [vp, cat_p, cat_p, par_p, dp]
         L.bym_serve_start.argtypes = [vp, ctypes.c_int, ctypes.c_size_t]
@@ -371,15 +372,16 @@ class Context:
         return self._run("both", gal, ran, params, kedges, redges, gal_nbar, ran_nbar, stream)
 
     def pk_xi_cross(self, gal_a, ran_a, gal_b, ran_b, params, kedges=None, redges=None, ran_nbar_a=None,
-                    ran_nbar_b=None, stream=None):
-        """Cross multipoles of tracer A (gal_a, ran_a) with tracer B (gal_b, ran_b), even ell;
-        P_ell when kedges is given, xi_ell when redges is given."""
+                    ran_nbar_b=None, stream=None, odd=False):
+        """Cross multipoles of tracer A (gal_a, ran_a) with tracer B (gal_b, ran_b): even ell up to
+        params.ell_max, or with odd the odd ell = 1, 3, .., params.ell_max (odd); P_ell when kedges
+        is given, xi_ell when redges is given."""
         if kedges is None and redges is None:
             raise ValueError("kedges or redges is required")
         keep = []
         cats = [_catalog(gal_a, None, keep), _catalog(ran_a, ran_nbar_a, keep), _catalog(gal_b, None, keep),
                 _catalog(ran_b, ran_nbar_b, keep)]
-        nl = params.ell_max // 2 + 1
+        nl = (params.ell_max + 1) // 2 if odd else params.ell_max // 2 + 1
         dp = ctypes.POINTER(ctypes.c_double)
         i64p = ctypes.POINTER(ctypes.c_int64)
         out, ptrs = {}, []
@@ -395,10 +397,11 @@ class Context:
             ptrs += [ctypes.byref(b), out[keys[0]].ctypes.data_as(dp), out[keys[1]].ctypes.data_as(dp),
                      out[keys[2]].ctypes.data_as(i64p)]
         st = ctypes.c_void_p(stream) if stream else None
-        rc = self._L.bym_pk_xi_cross(self._h, *[_ptr(c) for c in cats], ctypes.byref(params), ptrs[0], ptrs[4],
-                                     ptrs[1], ptrs[2], ptrs[3], ptrs[5], ptrs[6], ptrs[7], st)
+        fn = self._L.bym_pk_xi_cross_odd if odd else self._L.bym_pk_xi_cross
+        rc = fn(self._h, *[_ptr(c) for c in cats], ctypes.byref(params), ptrs[0], ptrs[4],
+                ptrs[1], ptrs[2], ptrs[3], ptrs[5], ptrs[6], ptrs[7], st)
         self._check(rc)
-        out["ells"] = list(range(0, params.ell_max + 1, 2))
+        out["ells"] = list(range(1 if odd else 0, params.ell_max + 1, 2))
         return out
 
     def shot_noise(self, gal, ran, params, gal_nbar=None, ran_nbar=None) -> float:

@@ -345,11 +345,11 @@ int midpoint_gfield_index(int ell_max, int alpha, int J, int nu, bool even) {
   return -1;
 }
 
-std::vector<BisTerm> bisector_terms(int ell_max, int K) {
+static std::vector<BisTerm> bisector_terms_parity(int ell_max, int K, int par) {
   const int bmax = K / 2;
   const int Jmax = ell_max + bmax;
   std::map<std::tuple<int, int, int>, double> acc;  // (lm, i, j), i <= j
-  for (int l = 0; l <= ell_max; l += 2)
+  for (int l = par; l <= ell_max; l += 2)
     for (int J1 = 0; J1 <= Jmax; ++J1)
       for (int J2 = 0; J2 <= Jmax; ++J2) {
         if ((l + J1 + J2) % 2) continue;
@@ -363,7 +363,7 @@ std::vector<BisTerm> bisector_terms(int ell_max, int K) {
             [&](int mu, int nu1, int nu2, double v) {
               int i = ylm_index(J1, nu1), j = ylm_index(J2, nu2);
               if (i > j) std::swap(i, j);
-              acc[{even_lm_index(l, mu), i, j}] += v;
+              acc[{par ? odd_lm_index(l, mu) : even_lm_index(l, mu), i, j}] += v;
             });
       }
   std::vector<BisTerm> out;
@@ -374,6 +374,10 @@ std::vector<BisTerm> bisector_terms(int ell_max, int K) {
       out.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), kv.second});
   return out;
 }
+
+std::vector<BisTerm> bisector_terms(int ell_max, int K) { return bisector_terms_parity(ell_max, K, 0); }
+
+std::vector<BisTerm> bisector_terms_odd(int ell_max, int K) { return bisector_terms_parity(ell_max, K, 1); }
 
 std::vector<MidTerm> midpoint_terms(int ell_max, int K, bool even) {
   std::vector<MidTerm> out;

@@ -31,6 +31,9 @@ double bisector_B(int beta, int ell, int m, int J1, int J2, int M);  // eq. B-de
 inline int ylm_index(int l, int nu) { return l * l + l + nu; }          // all l
 inline int even_lm_index(int l, int mu) { return l * (l + 1) / 2 + mu; } // even l only
 inline int n_even_lm(int ell_max) { return (ell_max + 1) * (ell_max + 2) / 2; }
+// odd l only (l = 2q + 1): the (2l + 1) entries of l follow those of 1, 3, .., l - 2
+inline int odd_lm_index(int l, int mu) { const int q = (l - 1) / 2; return 2 * q * q + q + mu + l; }
+inline int n_odd_lm(int ell_max) { const int q = (ell_max + 1) / 2; return 2 * q * q + q; }
 
 // Midpoint convolution fields g^alpha_{J nu}: alpha = 0..K (even alpha only for the
 // parity-even form), J = alpha mod 2, alpha mod 2 + 2, .., <= ell_max + alpha, nu = -J..J.
@@ -42,6 +45,8 @@ int midpoint_gfield_index(int ell_max, int alpha, int J, int nu, bool even = fal
 // summed over beta <= floor(K/2); c already symmetrised over (i, j) <-> (j, i).
 struct BisTerm { int lm, i, j; double c; };
 std::vector<BisTerm> bisector_terms(int ell_max, int K);
+// The same for the odd l <= ell_max (lm = odd_lm_index), fields J <= ell_max + floor(K/2).
+std::vector<BisTerm> bisector_terms_odd(int ell_max, int K);
 
 // Midpoint P: H_{lm}(Delta) = sum c t^alpha Y_{y}(hat Delta) g_{g}(Delta)
 // (t = |Delta| / r0, fields carry (2r/r0)^-alpha), y = ylm_index(J1, nu1).

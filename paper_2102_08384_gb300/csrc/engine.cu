@@ -1049,6 +1049,189 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
 #undef CUDA_TRY
 }
 
+// Odd multipoles l = 1, 3, .., ell_max of a cross spectrum (Yamamoto or bisector; ell_max odd):
+// the relabelled first-galaxy terms keep a factor (-1)^l, so the Yamamoto form is
+// [Q^AB - Q^BA] / 2 with Q^XY = F[Y delta_Y] conj(D_X), and the bisector sum of eq.
+// bisector-pk-fft contributes its part odd in k, sum c_ij Im(conj F^A_i F^B_j); P_l is the
+// imaginary part of the shell mean, xi_l the (real) lag sum.  Tracer A: slot 0 and its fields
+// from slot 1, the bisector X fields (xi) after them, tracer B's delta and fields last.
+template <typename T, typename T2>
+static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
+  const bym_params *p = rq.p;
+  const int N = p->n_mesh;
+  const bool want_pk = rq.kb != nullptr, want_xi = rq.rb != nullptr, bis = p->los == BYM_LOS_BISECTOR;
+  std::string jerr;
+  auto os = get_odd_kernels(JitKey{p->los, p->ell_max, order_key(p), p->precision}, jerr);
+  if (!os) return fail(c, BYM_E_CUDA, jerr);
+  auto ks = get_kernels(JitKey{p->los, p->ell_max - 1, order_key(p), p->precision}, jerr);   // bin geometry
+  if (!ks) return fail(c, BYM_E_CUDA, jerr);
+  const Tune &tn = tune_for(c, N, p->precision, p->los);
+  const int nf = (int)os->fields.size(), nlm = os->n_lm, NL = os->n_ell;
+  const long long slot_reals = (long long)N * N * (N + 2), cslot = slot_reals / 2;
+  const size_t slot_bytes = (size_t)slot_reals * sizeof(T);
+  const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
+  const int nextra = bis && want_xi ? nlm : 0;
+  const int xbase = 1 + nf, cbase = xbase + nextra, nslots = cbase + 1 + nf;
+  const int64_t ncat = rq.gal->n + rq.gal_b->n + (rq.ran ? rq.ran->n : 0) + (rq.ran_b ? rq.ran_b->n : 0);
+  const bool cats_dev = rq.gal->on_device && rq.gal_b->on_device && (!rq.ran || rq.ran->on_device) &&
+                        (!rq.ran_b || rq.ran_b->on_device);
+  if (c->budget && (size_t)nslots * slot_bytes + (cats_dev ? 0 : (size_t)ncat * 20) > c->budget)
+    return fail(c, BYM_E_NOMEM, "request exceeds the context's HBM budget");
+
+  Geom *kg = nullptr, *rg = nullptr;
+  int rc;
+  if (want_pk && (rc = get_geom(c, *ks, N, p->box_len, rq.kb, 'k', st, &kg))) return rc;
+  if (want_xi && (rc = get_geom(c, *ks, N, p->box_len, rq.rb, 'r', st, &rg))) return rc;
+  if (!kg && bis && (rc = get_null_kgeom(c, N, &kg))) return rc;
+
+  DevBufs buf(st);
+  auto alloc = [&](void **ptr, size_t bytes) -> int {
+    if (buf.alloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, BYM_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return BYM_OK;
+  };
+#define TRY(x)                  \
+  do {                          \
+    int rc_ = (x);              \
+    if (rc_) return rc_;        \
+  } while (0)
+#define CUDA_TRY(x)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess) return fail(c, BYM_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+  const bym_catalog *cats[4] = {rq.gal, rq.ran, rq.gal_b, rq.ran_b};
+  const float4 *cat4[4] = {nullptr, nullptr, nullptr, nullptr};
+  const float *catnb[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int w = 0; w < 4; ++w) {
+    const bym_catalog *cat = cats[w];
+    if (!cat || cat->n <= 0) continue;
+    if (cat->on_device) {
+      cat4[w] = (const float4 *)cat->xyzw;
+      catnb[w] = cat->nbar;
+      continue;
+    }
+    void *d4 = nullptr;
+    TRY(alloc(&d4, (size_t)cat->n * 16));
+    CUDA_TRY(cudaMemcpyAsync(d4, cat->xyzw, (size_t)cat->n * 16, cudaMemcpyHostToDevice, st));
+    cat4[w] = (const float4 *)d4;
+    if (cat->nbar) {
+      void *dn = nullptr;
+      TRY(alloc(&dn, (size_t)cat->n * 4));
+      CUDA_TRY(cudaMemcpyAsync(dn, cat->nbar, (size_t)cat->n * 4, cudaMemcpyHostToDevice, st));
+      catnb[w] = (const float *)dn;
+    }
+  }
+  double *stats = nullptr, *ksum = nullptr, *rsum = nullptr, *scale = nullptr;
+  T *invw = nullptr;
+  const int nbk = want_pk ? rq.kb->nbins : 1, nbr = want_xi ? rq.rb->nbins : 1;
+  TRY(alloc((void **)&stats, 16 * sizeof(double)));
+  TRY(alloc((void **)&ksum, sizeof(double) * NL * nbk));
+  TRY(alloc((void **)&rsum, sizeof(double) * NL * nbr));
+  CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(ksum, 0, sizeof(double) * NL * nbk, st));
+  CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * NL * nbr, st));
+  if (p->compensate) {
+    std::vector<T> w(N);
+    for (int i = 0; i < N; ++i) {
+      const double x = M_PI * lab(i, N) / N;
+      const double sn = x == 0.0 ? 1.0 : std::sin(x) / x;
+      w[i] = (T)(1.0 / std::pow(sn, p->assign));
+    }
+    TRY(alloc((void **)&invw, sizeof(T) * N));
+    CUDA_TRY(cudaMemcpyAsync(invw, w.data(), sizeof(T) * N, cudaMemcpyHostToDevice, st));
+  }
+  std::vector<double> sc((size_t)nf, 1.0 / ((double)N * N * N));
+  TRY(alloc((void **)&scale, sizeof(double) * nf));
+  CUDA_TRY(cudaMemcpyAsync(scale, sc.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
+
+  T *slots = nullptr;
+  TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
+  auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
+  auto slot_c = [&](int i) { return (T2 *)(slots + (long long)i * slot_reals); };
+  CUDA_TRY(cudaMemsetAsync(slot_r(0), 0, slot_bytes, st));
+  CUDA_TRY(cudaMemsetAsync(slot_r(cbase), 0, slot_bytes, st));
+  const double esz = (double)sizeof(T), n3 = (double)N * N * N, cplx = 2.0 * esz * N * N * (N / 2 + 1);
+  for (int w = 0; w < 4; ++w)
+    if (cat4[w]) {
+      ProfScope ps(c, st, "norm_reduce", cats[w]->n * ((w & 1) ? 20.0 : 16.0));
+      launch_norm_reduce(cat4[w], catnb[w], cats[w]->n, w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), c->nsm,
+                         st);
+    }
+  for (int w = 0; w < 4; ++w)
+    if (cat4[w]) {
+      ProfScope ps(c, st, "paint", cats[w]->n * 16.0 + n3 * esz);
+      launch_paint<T>(cat4[w], cats[w]->n, w & 1, stats + 8 * (w >> 1), slot_r(w < 2 ? 0 : cbase), N, p->box_lo,
+                      inv_h, p->assign, c->nsm, st);
+    }
+  CUDA_TRY(cudaGetLastError());
+  {
+    const long long ncell = (long long)N * N * N;
+    ProfScope ps(c, st, "gen_fields_odd", 2.0 * (1.0 + nf) * n3 * esz);
+    for (int base : {0, cbase}) {
+      CUDA_TRY(cudaMemsetAsync(slot_r(base + 1), 0, (size_t)nf * slot_bytes, st));
+      CUDA_TRY(launch(os->gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(base),
+                      slot_r(base + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+    }
+  }
+  const int f0 = bis ? 1 : 0, cnt = bis ? nf : 1 + nf;
+  TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn));
+  TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn));
+  const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, tn.per_sm_k);
+  const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
+  const int Lc = want_xi ? (rg->full ? N : 2 * rg->jm + 1) : 0;
+  double pk_scale = 1.0;
+  if (bis) {
+    {
+      ProfScope ps(c, st, "kcontract_bisector_cross_odd", (2.0 * nf + (want_xi ? nlm : 0.0)) * cplx);
+      CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), (const T2 *)slot_c(cbase + 1), cslot,
+                      N, (const int *)kg->lut, nbk, ksum, want_xi ? slot_c(xbase) : (T2 *)nullptr, cslot,
+                      (const T *)invw));
+    }
+    if (want_xi) {
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, xbase, nlm, tn));
+      ProfScope ps(c, st, "xi_lag_odd", (double)Lc * Lc * Lc * nlm * esz);
+      CUDA_TRY(launch(os->xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
+                      (const T *)slot_r(xbase), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
+                      1.0 / ((double)N * N * N)));
+    }
+  } else {
+    if (want_pk) {
+      // [Q^AB - Q^BA], halved on the host: F^B with D_A (+), F^A with D_B (-)
+      pk_scale = 0.5;
+      ProfScope ps(c, st, "kcontract_yamamoto_odd", 2.0 * (nlm + 1.0) * cplx);
+      CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(cbase + 1), cslot, (const T2 *)slot_c(0),
+                      N, (const int *)kg->lut, nbk, ksum, (const T *)invw, (T)1));
+      CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(cbase), N,
+                      (const int *)kg->lut, nbk, ksum, (const T *)invw, (T)-1));
+    }
+    if (want_xi) {
+      {
+        ProfScope ps(c, st, "spec_mul_cross", (3.0 * nf + 2.0) * cplx);
+        launch_spec_mul_cross<T, T2>(slot_c(1), slot_c(cbase + 1), cslot, nf, slot_c(0), slot_c(cbase), N, scale,
+                                     invw, c->nsm * tn.per_sm_spec / 8, st, -1.0);
+      }
+      TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
+      ProfScope ps(c, st, "xi_lag_odd", (double)Lc * Lc * Lc * nf * esz);
+      CUDA_TRY(launch(os->xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
+                      slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0));
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> hstats(16), hk((size_t)NL * nbk), hr((size_t)NL * nbr);
+  CUDA_TRY(cudaMemcpyAsync(hstats.data(), stats, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hk.data(), ksum, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hr.data(), rsum, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  prof_collect(c);
+  return finish_results(c, rq, hstats.data(), hk.data(), hr.data(), kg, rg, NL, nbk, nbr, h, true, pk_scale);
+#undef TRY
+#undef CUDA_TRY
+}
+
 // norm 2 (Sec. 2.2: the Landy-Szalay form of the catalog pair counts): P with the
 // FKP normalisation; xi_ell(r_b) = S_ell[delta](b) / (alpha_r^2 S_0[n_r](b)), both raw
 // bin sums of the same mesh estimator; the random-random sum is the ell = 0 one, where
@@ -1080,6 +1263,30 @@ static int run_rr_normalised(bym_ctx *c, const Request &rq, cudaStream_t st) {
 
 int bym::run_request(bym_ctx *c, const Request &rq, cudaStream_t st) {
   if (!c) return BYM_E_INVAL;
+  if (rq.odd) {   // odd multipoles: ell_max odd; the rest is checked as for ell_max - 1
+    const bym_params *p = rq.p;
+    if (!p || !rq.gal_b) return fail(c, BYM_E_INVAL, "odd multipoles: params and two tracers are required");
+    if (p->ell_max < 1 || p->ell_max > 7 || p->ell_max % 2 == 0)
+      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: ell_max must be odd, 1..7");
+    if (p->los != BYM_LOS_YAMAMOTO && p->los != BYM_LOS_BISECTOR)
+      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: Yamamoto or bisector line of sight");
+    if (p->norm == 2 || p->interlace || (c->field_chunk > 0 && p->los == BYM_LOS_BISECTOR))
+      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: no norm 2, no interlacing, no field blocks");
+    bym_params pe = *p;
+    pe.ell_max = p->ell_max - 1;
+    int rc = validate(c, rq.gal, rq.ran, &pe, rq.kb, rq.rb);
+    if (!rc) rc = validate(c, rq.gal_b, rq.ran_b, &pe, rq.kb, rq.rb);
+    if (rc) return rc;
+    if ((rq.kb && !rq.pk) || (rq.rb && !rq.xi) || (!rq.kb && !rq.rb))
+      return fail(c, BYM_E_INVAL, "missing output array");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
+    if (!st) st = c->stream;
+    try {
+      return p->precision == 64 ? run_odd<double, double2>(c, rq, st) : run_odd<float, float2>(c, rq, st);
+    } catch (const std::exception &e) {
+      return fail(c, BYM_E_CUDA, std::string("internal error: ") + e.what());
+    }
+  }
   int rc = validate(c, rq.gal, rq.ran, rq.p, rq.kb, rq.rb);
   if (rc) return rc;
   if (rq.gal_b && (rc = validate(c, rq.gal_b, rq.ran_b, rq.p, rq.kb, rq.rb))) return rc;
@@ -1201,6 +1408,21 @@ int bym_pk_xi_cross(bym_ctx *c, const bym_catalog *gal_a, const bym_catalog *ran
   Request rq{gal_a, ran_a, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
   rq.gal_b = gal_b;
   rq.ran_b = ran_b;
+  return run_request(c, rq, (cudaStream_t)stream);
+}
+
+int bym_pk_xi_cross_odd(bym_ctx *c, const bym_catalog *gal_a, const bym_catalog *ran_a, const bym_catalog *gal_b,
+                        const bym_catalog *ran_b, const bym_params *p, const bym_bins *kbins, const bym_bins *rbins,
+                        double *pk, double *k_mean, int64_t *n_modes, double *xi, double *r_mean, int64_t *n_cells,
+                        void *stream) {
+  if (!c) return BYM_E_INVAL;
+  if (!gal_b) return fail(c, BYM_E_INVAL, "gal_b is NULL");
+  if (!kbins && !rbins) return fail(c, BYM_E_INVAL, "kbins or rbins is required");
+  std::lock_guard<std::mutex> lock(c->mu);
+  Request rq{gal_a, ran_a, p, kbins, rbins, pk, k_mean, n_modes, xi, r_mean, n_cells};
+  rq.gal_b = gal_b;
+  rq.ran_b = ran_b;
+  rq.odd = true;
   return run_request(c, rq, (cudaStream_t)stream);
 }
 
@@ -1767,6 +1989,15 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len) {
     src.clear();
     try {
       src = generate_chunk_source(JitKey{p->los, p->ell_max, order_key(p), p->precision}, 16, nullptr);
+    } catch (const std::exception &e) {
+      lg = e.what();
+    }
+    ok = !src.empty() && compile_cubin(src, cubin, lg);
+  }
+  if (ok && (p->los == BYM_LOS_YAMAMOTO || p->los == BYM_LOS_BISECTOR) && p->ell_max + 1 <= 7) {
+    src.clear();   // the odd-multipole module for ell_max + 1
+    try {
+      src = generate_odd_source(JitKey{p->los, p->ell_max + 1, order_key(p), p->precision}, nullptr);
     } catch (const std::exception &e) {
       lg = e.what();
     }

@@ -598,6 +598,183 @@ std::string generate_cross_source(const JitKey &key) {
   return o.str();
 }
 
+// ---------------------------------------------------------------------------
+// Odd multipoles (l = 1, 3, .., ell_max, ell_max odd) of cross spectra, in a module of
+// their own.  Outputs are indexed by odd_lm_index (fields / X slots) and (l - 1) / 2
+// (shell sums).  A P_l of odd l is the imaginary part of the shell mean of
+// sum_nu Y_{l nu}(k) X_{l nu}(k); xi_l is real.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::vector<FieldInfo> odd_field_list(const JitKey &key) {
+  std::vector<FieldInfo> list;
+  if (key.los == 0) {                       // Yamamoto: Y_{l nu} delta, odd l
+    for (int l = 1; l <= key.ell_max; l += 2)
+      for (int nu = -l; nu <= l; ++nu) list.push_back({0, l, nu});
+  } else {                                  // bisector: Y_{J nu} delta, J <= ell_max + floor(K/2)
+    const int Jmax = key.ell_max + key.K / 2;
+    for (int J = 0; J <= Jmax; ++J)
+      for (int nu = -J; nu <= J; ++nu) list.push_back({0, J, nu});
+  }
+  return list;
+}
+
+void emit_k_head(std::ostream &o, int NLo) {
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NLo << ");\n  const int H = N / 2 + 1;\n";
+  emit_bin_loop_head(o, "(long long)N * N * H");
+  o << "    int bin = -1; real v[" << NLo << "] = {";
+  for (int l = 0; l < NLo; ++l) o << (l ? ", " : "") << "(real)0";
+  o << "};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+  o << "      const int ix = (int)(row / N), iy = (int)(row % N);\n";
+  o << "      const int nx = bym_lab(ix, N), ny = bym_lab(iy, N), nz = (iz == N / 2) ? -N / 2 : iz;\n";
+  o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
+  o << "      bin = lut[n2];\n";
+}
+
+// shell sums of the odd l from X<odd_lm>: v[(l - 1) / 2] = w sum_nu Y_{l nu}(k) X_{l nu}
+void emit_k_tail(std::ostream &o, int L, bool f32, int NLo) {
+  o << "        if (bin >= 0) {\n";
+  o << "          const real w = (iz == 0 || iz == N / 2) ? (real)1 : (real)2;\n";
+  o << "          const real r2 = (real)n2; const real ir = bym_rsqrt(r2);\n";
+  o << "          const real ux = nx * ir, uy = ny * ir, uz = nz * ir; const real zm = (real)1;\n";
+  {
+    std::ostringstream yy;
+    emit_ylm(yy, L, f32, "yk", "ux", "uy", "uz", "zm");
+    std::istringstream is(yy.str());
+    std::string line;
+    while (std::getline(is, line)) o << "        " << line << "\n";
+  }
+  for (int l = 1; l <= L; l += 2) {
+    o << "          { real T = (real)0;";
+    for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << odd_lm_index(l, mu) << ";";
+    o << " v[" << (l - 1) / 2 << "] = w * T; }\n";
+  }
+  o << "        }\n      }\n    }\n";
+  o << "    bym_bin_flush<" << NLo << ", real>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
+}
+
+}  // namespace
+
+std::string generate_odd_source(const JitKey &key, OddSet *meta) {
+  if (key.ell_max < 1 || key.ell_max % 2 == 0 || (key.los != 0 && key.los != 2))
+    throw std::runtime_error("odd multipoles: odd ell_max, Yamamoto or bisector");
+  const bool f32 = key.prec == 32;
+  const char *real = f32 ? "float" : "double";
+  const int L = key.ell_max, NLo = (L + 1) / 2, n_lm = n_odd_lm(L);
+  const auto list = odd_field_list(key);
+  const int nf = (int)list.size();
+  std::ostringstream o;
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << kPrelude;
+  emit_gen_fields(o, "gen_fields_odd", list, 0, nf);
+
+  if (key.los == 0) {
+    // Yamamoto: X_{l nu} = sgn Im(F_{l nu}(k) conj D(k)) W^-2; two launches (F^B with D_A, sgn 1;
+    // F^A with D_B, sgn -1) add [Q^AB - Q^BA], halved on the host
+    o << "extern \"C\" __global__ void __launch_bounds__(256) kcontract_odd(const real2* __restrict__ F, long long cslot,"
+         " const real2* __restrict__ D, int N, const int* __restrict__ lut, int nbins, double* __restrict__ gsum,"
+         " const real* __restrict__ invw, real sgn) {\n";
+    emit_k_head(o, NLo);
+    o << "      if (bin >= 0) {\n";
+    o << "        real cc = sgn;\n";
+    o << "        if (invw) { const real wv = invw[ix] * invw[iy] * invw[iz]; cc = sgn * wv * wv; }\n";
+    o << "        const real2 d = D[m];\n";
+    for (int i = 0; i < nf; ++i)
+      o << "        real X" << odd_lm_index(list[i].J, list[i].nu) << "; { const real2 f = F[" << i
+        << "LL * cslot + m]; X" << odd_lm_index(list[i].J, list[i].nu) << " = (f.y * d.x - f.x * d.y) * cc; }\n";
+    emit_k_tail(o, L, f32, NLo);
+  } else {
+    // bisector: X_{l nu}(k) = sum over ordered field pairs c_ij Im(conj F^A_i F^B_j) W^-2, the part of
+    // the bilinear sum of eq. bisector-pk-fft that is odd in k; xout (for xi) gets i X
+    o << "extern \"C\" __global__ void __launch_bounds__(256) kcontract_cross_odd(const real2* __restrict__ FA,"
+         " const real2* __restrict__ FB, long long cslot, int N, const int* __restrict__ lut, int nbins,"
+         " double* __restrict__ gsum, real2* __restrict__ xout, long long xslot, const real* __restrict__ invw) {\n";
+    emit_k_head(o, NLo);
+    o << "      if (xout || bin >= 0) {\n";
+    o << "        real cc = (real)1;\n";
+    o << "        if (invw) { cc = invw[ix] * invw[iy] * invw[iz]; cc = cc * cc; }\n";
+    for (int i = 0; i < n_lm; ++i) o << "        real X" << i << " = (real)0;\n";
+    std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> by_pair;
+    for (auto &t : bisector_terms_odd(key.ell_max, key.K)) {
+      if (t.i == t.j) {
+        by_pair[{t.i, t.j}].push_back({t.lm, t.c});
+      } else {
+        by_pair[{t.i, t.j}].push_back({t.lm, 0.5 * t.c});
+        by_pair[{t.j, t.i}].push_back({t.lm, 0.5 * t.c});
+      }
+    }
+    std::set<int> ub;
+    for (auto &kv : by_pair) ub.insert(kv.first.second);
+    for (int j : ub) o << "        const real2 b" << j << " = FB[" << j << "LL * cslot + m];\n";
+    int cur = -1;
+    for (auto &kv : by_pair) {
+      const int i = kv.first.first, j = kv.first.second;
+      if (i != cur) {
+        if (cur >= 0) o << "        }\n";
+        o << "        { const real2 a" << i << " = FA[" << i << "LL * cslot + m];\n";
+        cur = i;
+      }
+      o << "        { const real q = a" << i << ".x * b" << j << ".y - a" << i << ".y * b" << j << ".x;";
+      for (auto &lc : kv.second) o << " X" << lc.first << " += " << lit(lc.second, f32) << " * q;";
+      o << " }\n";
+    }
+    if (cur >= 0) o << "        }\n";
+    for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
+    o << "        if (xout) {\n";
+    for (int i = 0; i < n_lm; ++i)
+      o << "          { real2 xv; xv.x = (real)0; xv.y = X" << i << "; xout[" << i << "LL * xslot + m] = xv; }\n";
+    o << "        }\n";
+    emit_k_tail(o, L, f32, NLo);
+  }
+
+  // xi on the lag cube: T_l(Delta) = sum_nu Y_{l nu}(Delta) Z_{l nu}(Delta), Z in odd_lm order
+  o << "extern \"C\" __global__ void __launch_bounds__(256) xi_lag_odd(const real* __restrict__ Z, long long slot,"
+       " int N, int jm, int full, const int* __restrict__ lut, int nbins, double* __restrict__ gsum,"
+       " double zscale) {\n";
+  o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NLo << ");\n";
+  o << "  const int Lc = full ? N : 2 * jm + 1;\n";
+  emit_bin_loop_head(o, "(long long)Lc * Lc * Lc");
+  o << "    int bin = -1; double v[" << NLo << "] = {";
+  for (int l = 0; l < NLo; ++l) o << (l ? ", " : "") << "0.0";
+  o << "};\n";
+  o << "    if (m < total) {\n";
+  o << "      const int a = (int)(m % Lc); const long long t = m / Lc;\n";
+  o << "      const int b = (int)(t % Lc); const int c = (int)(t / Lc);\n";
+  o << "      const int jx = full ? bym_lab(c, N) : c - jm, jy = full ? bym_lab(b, N) : b - jm,"
+       " jz = full ? bym_lab(a, N) : a - jm;\n";
+  o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
+  o << "      bin = lut[j2];\n";
+  o << "      if (bin >= 0) {\n";
+  o << "        const int ix = jx < 0 ? jx + N : jx, iy = jy < 0 ? jy + N : jy, iz = jz < 0 ? jz + N : jz;\n";
+  o << "        const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "        const double rr = sqrt((double)j2); const double ir = 1.0 / rr;\n";
+  o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
+  {
+    std::ostringstream yy;
+    emit_ylm(yy, L, false, "yl", "ux", "uy", "uz", "zm");
+    std::istringstream is(yy.str());
+    std::string line;
+    while (std::getline(is, line)) o << "      " << line << "\n";
+  }
+  for (int l = 1; l <= L; l += 2) {
+    o << "        { double T = 0.0;";
+    for (int mu = -l; mu <= l; ++mu)
+      o << " T += yl" << ylm_index(l, mu) << " * (double)Z[" << odd_lm_index(l, mu) << "LL * slot + off];";
+    o << " v[" << (l - 1) / 2 << "] = T * zscale; }\n";
+  }
+  o << "      }\n    }\n";
+  o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
+
+  if (meta) {
+    meta->fields = list;
+    meta->n_lm = n_lm;
+    meta->n_ell = NLo;
+  }
+  return o.str();
+}
+
 bool compile_cubin(const std::string &src, std::vector<char> &cubin, std::string &log) {
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "bym_generated.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
@@ -700,6 +877,42 @@ cudaKernel_t get_cross_kernel(const JitKey &key, std::string &err) {
   }
   cache[key] = k;   // the library stays loaded for the life of the process, as the other modules do
   return k;
+}
+
+std::shared_ptr<OddSet> get_odd_kernels(const JitKey &key, std::string &err) {
+  static std::mutex mu;
+  static std::map<JitKey, std::shared_ptr<OddSet>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  auto os = std::make_shared<OddSet>();
+  std::string src;
+  try {
+    src = generate_odd_source(key, os.get());
+  } catch (const std::exception &e) {
+    err = std::string("kernel generation failed: ") + e.what();
+    return nullptr;
+  }
+  std::vector<char> cubin;
+  std::string log;
+  if (!compile_cubin(src, cubin, log)) {
+    err = "NVRTC compile failed: " + log.substr(0, 2000);
+    return nullptr;
+  }
+  if (cudaLibraryLoadData(&os->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+    err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(cudaGetLastError());
+    return nullptr;
+  }
+  const char *kc = key.los == 0 ? "kcontract_odd" : "kcontract_cross_odd";
+  if (cudaLibraryGetKernel(&os->gen_fields, os->lib, "gen_fields_odd") != cudaSuccess ||
+      cudaLibraryGetKernel(&os->kcontract, os->lib, kc) != cudaSuccess ||
+      cudaLibraryGetKernel(&os->xi_lag, os->lib, "xi_lag_odd") != cudaSuccess) {
+    cudaGetLastError();
+    err = "generated odd-multipole module is missing a kernel";
+    return nullptr;
+  }
+  cache[key] = os;
+  return os;
 }
 
 std::shared_ptr<ChunkSet> get_chunk_kernels(const JitKey &key, int max_fields, std::string &err) {

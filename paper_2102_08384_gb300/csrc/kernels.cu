@@ -175,14 +175,15 @@ __global__ void __launch_bounds__(256) bym_spec_mul(T2 *__restrict__ F, long lon
   }
 }
 
-// Two tracers: FA_f <- [FA_f conj(DB) + FB_f conj(DA)] s_f W^-2 / 2 for f = 0..nf-1, with FA / FB
-// the weighted-field spectra of tracer A / B and DA / DB their density spectra.
+// Two tracers: FA_f <- [sa FA_f conj(DB) + FB_f conj(DA)] s_f W^-2 / 2 for f = 0..nf-1, with FA / FB
+// the weighted-field spectra of tracer A / B and DA / DB their density spectra; sa = (-1)^l
+// for the Yamamoto fields of odd l (the line of sight through the first galaxy).
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) bym_spec_mul_cross(T2 *__restrict__ FA, const T2 *__restrict__ FB,
                                                           long long cslot, int nf, const T2 *__restrict__ DA,
                                                           const T2 *__restrict__ DB, int N,
                                                           const double *__restrict__ scale,
-                                                          const T *__restrict__ invw) {
+                                                          const T *__restrict__ invw, T sa) {
   const int H = N / 2 + 1;
   const long long nm = (long long)N * N * H;
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += (long long)gridDim.x * blockDim.x) {
@@ -199,8 +200,8 @@ __global__ void __launch_bounds__(256) bym_spec_mul_cross(T2 *__restrict__ FA, c
       const T2 a = *q, b = FB[(long long)f * cslot + m];
       const T s = (T)scale[f] * cc;
       T2 r;
-      r.x = (a.x * db.x + a.y * db.y + b.x * da.x + b.y * da.y) * s;
-      r.y = (a.y * db.x - a.x * db.y + b.y * da.x - b.x * da.y) * s;
+      r.x = (sa * (a.x * db.x + a.y * db.y) + b.x * da.x + b.y * da.y) * s;
+      r.y = (sa * (a.y * db.x - a.x * db.y) + b.y * da.x - b.x * da.y) * s;
       *q = r;
     }
   }
@@ -267,10 +268,10 @@ void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const d
 
 template <typename T, typename T2>
 void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const T2 *DA, const T2 *DB, int N,
-                           const double *scale, const T *invw, int nsm, cudaStream_t st) {
+                           const double *scale, const T *invw, int nsm, cudaStream_t st, double sa) {
   if (nf <= 0) return;
   const long long nm = (long long)N * N * (N / 2 + 1);
-  bym_spec_mul_cross<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(FA, FB, cslot, nf, DA, DB, N, scale, invw);
+  bym_spec_mul_cross<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(FA, FB, cslot, nf, DA, DB, N, scale, invw, (T)sa);
 }
 
 template <typename T, typename T2>
@@ -294,9 +295,9 @@ template void launch_spec_mul<double, double2>(double2 *, long long, int, const 
                                                const double *, int, cudaStream_t);
 template void launch_spec_mul_cross<float, float2>(float2 *, const float2 *, long long, int, const float2 *,
                                                    const float2 *, int, const double *, const float *, int,
-                                                   cudaStream_t);
+                                                   cudaStream_t, double);
 template void launch_spec_mul_cross<double, double2>(double2 *, const double2 *, long long, int, const double2 *,
                                                      const double2 *, int, const double *, const double *, int,
-                                                     cudaStream_t);
+                                                     cudaStream_t, double);
 
 }  // namespace bym

@@ -16,10 +16,10 @@ template <typename T, typename T2>
 void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const double *scale, const T *invw, int nsm,
                      cudaStream_t st);
 
-// two tracers: FA_f <- [FA_f conj(DB) + FB_f conj(DA)] scale_f W^-2 / 2 (half-spectrum slots)
+// two tracers: FA_f <- [sa FA_f conj(DB) + FB_f conj(DA)] scale_f W^-2 / 2 (half-spectrum slots)
 template <typename T, typename T2>
 void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const T2 *DA, const T2 *DB, int N,
-                           const double *scale, const T *invw, int nsm, cudaStream_t st);
+                           const double *scale, const T *invw, int nsm, cudaStream_t st, double sa = 1.0);
 
 // F_f <- (F_f + P G_f) / 2, P(k) = ph[n_x] ph[n_y] ph[n_z] (half-spectrum slots)
 template <typename T, typename T2>

@@ -190,3 +190,85 @@ def test_polarisation_and_monopole_at_512(pkg, survey_halves):
     for los in ("bisector", "midpoint"):
         check_multipoles(out[los]["pk"][:1], out["yamamoto"]["pk"][:1], "pk", label=f"{los} cross P0: ")
         check_multipoles(out[los]["xi"][:1], out["yamamoto"]["xi"][:1], "xi", label=f"{los} cross xi0: ")
+
+
+# ---------------------------------------------------------------- odd multipoles (ell = 1, 3)
+def _check_odd(got, want, rtol, scale_rows, label):
+    """Odd multipoles: each row to rtol of its own largest value plus rtol of the scale row
+    (the even cross multipole of the same bins) in that bin."""
+    got, want = np.asarray(got), np.asarray(want)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    for i in range(want.shape[0]):
+        tol = rtol * (np.abs(want[i]).max() + np.abs(scale_rows))
+        err = np.abs(got[i] - want[i])
+        assert np.all(err <= tol), f"{label} row {i}: err {err.max():.3e} tol {tol[np.argmax(err - tol)]:.3e}"
+
+
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("bisector", 2), ("bisector", 4)])
+def test_odd_cross_fp64(pkg, ctx, cubes, los, K):
+    a, b = cubes
+    N = 32
+    kedges = np.linspace(0.0, math.pi / (a.box_len / N), 9)
+    redges = np.linspace(0.0, 250.0, 11)
+    p = pkg.make_params(box_lo=a.box_lo, box_len=a.box_len, n_mesh=N, ell_max=3, los=los, order=K, precision=64,
+                        assign=3, compensate=True)
+    got = ctx.pk_xi_cross(a.gal, a.ran, b.gal, b.ran, p, kedges, redges, ran_nbar_a=a.ran_nbar,
+                          ran_nbar_b=b.ran_nbar, odd=True)
+    assert got["ells"] == [1, 3]
+    kw = dict(N=N, box_lo=a.box_lo, box_len=a.box_len, assign=3, ell_max=3, los=los, order=K, compensate=True,
+              odd=True, gal_b=b.gal, ran_b=b.ran, ran_nbar_b=b.ran_nbar)
+    want_p = E.pk_multipoles(a.gal, a.ran, a.ran_nbar, kedges=kedges, **kw)["pk"]
+    want_x = E.xi_multipoles(a.gal, a.ran, a.ran_nbar, redges=redges, **kw)["xi"]
+    _check_odd(got["pk"], want_p[[1, 3]], 1e-10, want_p[0], f"{los} K={K} odd P")
+    _check_odd(got["xi"], want_x[[1, 3]], 1e-10, np.abs(want_x[0]).max(), f"{los} K={K} odd xi")
+    assert np.abs(want_p[1]).max() > 1e-3 * np.abs(want_p[0]).max()      # the dipole is there
+    # A <-> B: odd multipoles change sign; one tracer twice: they vanish
+    ba = ctx.pk_xi_cross(b.gal, b.ran, a.gal, a.ran, p, kedges, redges, ran_nbar_a=b.ran_nbar,
+                         ran_nbar_b=a.ran_nbar, odd=True)
+    _check_odd(-ba["pk"], got["pk"], 1e-12, want_p[0], "swap P")
+    _check_odd(-ba["xi"], got["xi"], 1e-12, np.abs(want_x[0]).max(), "swap xi")
+    aa = ctx.pk_xi_cross(a.gal, a.ran, a.gal, a.ran, p, kedges, redges, ran_nbar_a=a.ran_nbar,
+                         ran_nbar_b=a.ran_nbar, odd=True)
+    assert np.abs(aa["pk"]).max() < 1e-10 * np.abs(want_p[0]).max()
+    assert np.abs(aa["xi"]).max() < 1e-10 * np.abs(want_x[0]).max()
+    only_p = ctx.pk_xi_cross(a.gal, a.ran, b.gal, b.ran, p, kedges=kedges, ran_nbar_a=a.ran_nbar,
+                             ran_nbar_b=b.ran_nbar, odd=True)
+    _check_odd(only_p["pk"], got["pk"], 1e-12, want_p[0], "P only")
+
+
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("bisector", 4)])
+def test_odd_cross_fp32_cap(pkg, ctx, cap_pair, los, K):
+    cap, A, B = cap_pair
+    N = 40
+    kedges = np.linspace(0.0, math.pi / (cap.box_len / N), 11)
+    redges = np.linspace(0.0, 8 * cap.box_len / N, 9)
+    p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=3, los=los, order=K,
+                        precision=32, assign=3, compensate=True)
+    got = ctx.pk_xi_cross(A[0], A[1], B[0], B[1], p, kedges, redges, ran_nbar_a=A[2], ran_nbar_b=B[2], odd=True)
+    kw = dict(N=N, box_lo=cap.box_lo, box_len=cap.box_len, assign=3, ell_max=3, los=los, order=K, compensate=True,
+              odd=True, gal_b=B[0], ran_b=B[1], ran_nbar_b=B[2])
+    want_p = E.pk_multipoles(A[0], A[1], A[2], kedges=kedges, **kw)["pk"]
+    want_x = E.xi_multipoles(A[0], A[1], A[2], redges=redges, **kw)["xi"]
+    # FP32: 1e-4 of each odd multipole's largest value plus 1e-5 of the monopole in the bin
+    tol_p = 1e-4 * np.abs(want_p[[1, 3]]).max(axis=1)[:, None] + 1e-5 * np.abs(want_p[0])[None, :]
+    assert np.all(np.abs(got["pk"] - want_p[[1, 3]]) <= tol_p), np.abs(got["pk"] - want_p[[1, 3]]) / tol_p
+    tol_x = 1e-4 * np.abs(want_x[[1, 3]]).max(axis=1)[:, None] + 1e-5 * np.abs(want_x[0]).max()
+    assert np.all(np.abs(got["xi"] - want_x[[1, 3]]) <= tol_x), np.abs(got["xi"] - want_x[[1, 3]]) / tol_x
+
+
+def test_odd_errors(pkg, ctx, cubes):
+    a, b = cubes
+    kedges = np.linspace(0.0, 0.1, 5)
+
+    def code(**kw):
+        p = pkg.make_params(box_lo=a.box_lo, box_len=a.box_len, n_mesh=16, **kw)
+        with pytest.raises(pkg.BymError) as ei:
+            ctx.pk_xi_cross(a.gal, a.ran, b.gal, b.ran, p, kedges, ran_nbar_a=a.ran_nbar, ran_nbar_b=b.ran_nbar,
+                            odd=True)
+        return ei.value.code
+
+    assert code(ell_max=3, los="midpoint", order=2) == -6
+    assert code(ell_max=2, los="bisector", order=2) == -6
+    assert code(ell_max=9, los="bisector", order=2) == -6
+    assert code(ell_max=3, los="bisector", order=2, norm=2) == -6
+    assert code(ell_max=3, los="yamamoto", interlace=True) == -6
