@@ -345,32 +345,39 @@ def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     halves = [(t[0::2].contiguous(), t[1::2].contiguous()) for t in (gal_d, ran_d, rnb_d)]
-    # label, los, order, norm, field chunk (-1: interlaced), cross
-    cases = [("midpoint_even order 4", "midpoint_even", 4, 1, 0, False),
-             ("midpoint order 4, g fields in ranges of 45", "midpoint", 4, 1, 45, False),
-             ("bisector order 4, fields in blocks of 16", "bisector", 4, 1, 16, False),
-             ("midpoint order 4, xi / RR (norm 2)", "midpoint", 4, 2, 0, False),
-             ("bisector order 4, interlaced", "bisector", 4, 1, -1, False),
-             ("bisector order 4, cross spectra of two tracers", "bisector", 4, 1, 0, True),
-             ("midpoint order 4, cross spectra of two tracers", "midpoint", 4, 1, 0, True)]
+    # label, los, order, norm, field chunk (-1: interlaced), cross (2: its odd multipoles 1, 3)
+    cases = [("midpoint_even order 4", "midpoint_even", 4, 1, 0, 0),
+             ("midpoint order 4, g fields in ranges of 45", "midpoint", 4, 1, 45, 0),
+             ("bisector order 4, fields in blocks of 16", "bisector", 4, 1, 16, 0),
+             ("midpoint order 4, xi / RR (norm 2)", "midpoint", 4, 2, 0, 0),
+             ("bisector order 4, interlaced", "bisector", 4, 1, -1, 0),
+             ("bisector order 4, cross spectra of two tracers", "bisector", 4, 1, 0, 1),
+             ("midpoint order 4, cross spectra of two tracers", "midpoint", 4, 1, 0, 1),
+             ("bisector order 4, odd multipoles (1, 3) of the cross spectra", "bisector", 4, 1, 0, 2),
+             ("yamamoto, odd multipoles (1, 3) of the cross spectra", "yamamoto", 0, 1, 0, 2)]
     out = {}
     for label, los, K, norm, chunk, cross in cases:
         il = chunk < 0                   # -1: interlaced, resident
         chunk = max(chunk, 0)
-        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=n_mesh, assign=3, ell_max=ELL_MAX, los=los,
-                            order=K, compensate=True, precision=32, norm=norm, interlace=il)
+        odd = cross == 2
+        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=n_mesh, assign=3,
+                            ell_max=3 if odd else ELL_MAX, los=los, order=K, compensate=True, precision=32, norm=norm,
+                            interlace=il)
         ctx.set_field_chunk(chunk)
         if cross:
             (ga, gb), (ra, rb), (na, nb) = halves
 
             def run():
-                ctx.pk_xi_cross(ga, ra, gb, rb, p, KEDGES, REDGES, ran_nbar_a=na, ran_nbar_b=nb, stream=sh)
+                ctx.pk_xi_cross(ga, ra, gb, rb, p, KEDGES, REDGES, ran_nbar_a=na, ran_nbar_b=nb, stream=sh,
+                                odd=odd)
         else:
             def run():
                 ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
-        n_f = {"midpoint_even": 88, "midpoint": 145, "bisector": 49}[los]
+        n_f = {"midpoint_even": 88, "midpoint": 145, "bisector": 49, "yamamoto": 15}[los]
         slot = n_mesh * n_mesh * (n_mesh + 2) * 4
-        if chunk and los == "midpoint":
+        if odd:                          # odd fields (bisector J <= 5, Yamamoto l = 1, 3) and 10 X slots
+            slots = 2 + 2 * (36 if los == "bisector" else 10) + (10 if los == "bisector" else 0)
+        elif chunk and los == "midpoint":
             slots = 2 + chunk + 15
         elif chunk:
             slots = 1 + 2 * chunk + 15
@@ -584,15 +591,20 @@ def _roofline(prof, steps):
     return roof, kernels, ours_launches
 
 
+# the source files that define each kernel the roofline may name
+KERNEL_SOURCES = {"fft_native_x_convolve": ["fft512.cu", "fft512.h"]}
+
+
 def _ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current build (profiles/traffic.md lists kernel | bytes | build id)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the kernel's current source (profiles/traffic.md lists kernel | bytes |
+    hash of the kernel's source files, or of all library sources for other kernels)."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
     try:
         import paper_2102_08384_gb300.build as b
-        build_id = b.source_hash()
+        build_id = b.file_hash(KERNEL_SOURCES[kernel]) if kernel in KERNEL_SOURCES else b.source_hash()
     except Exception:
         return None
     for line in open(path):

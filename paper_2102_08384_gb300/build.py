@@ -50,6 +50,17 @@ def source_hash() -> str:
     return h.hexdigest()[:12]
 
 
+def file_hash(names) -> str:
+    """Short content hash of the named files under csrc/ (identifies one kernel's source)."""
+    import hashlib
+    h = hashlib.sha256()
+    for n in sorted(names):
+        with open(os.path.join(CSRC, n), "rb") as fh:
+            h.update(n.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
