@@ -354,6 +354,7 @@ def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
              ("bisector order 4, cross spectra of two tracers", "bisector", 4, 1, 0, 1),
              ("midpoint order 4, cross spectra of two tracers", "midpoint", 4, 1, 0, 1),
              ("bisector order 4, odd multipoles (1, 3) of the cross spectra", "bisector", 4, 1, 0, 2),
+             ("midpoint order 4, odd multipoles (1, 3) of the cross spectra", "midpoint", 4, 1, 0, 2),
              ("yamamoto, odd multipoles (1, 3) of the cross spectra", "yamamoto", 0, 1, 0, 2)]
     out = {}
     for label, los, K, norm, chunk, cross in cases:
@@ -375,8 +376,8 @@ def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
                 ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
         n_f = {"midpoint_even": 88, "midpoint": 145, "bisector": 49, "yamamoto": 15}[los]
         slot = n_mesh * n_mesh * (n_mesh + 2) * 4
-        if odd:                          # odd fields (bisector J <= 5, Yamamoto l = 1, 3) and 10 X slots
-            slots = 2 + 2 * (36 if los == "bisector" else 10) + (10 if los == "bisector" else 0)
+        if odd:   # odd field sets (bisector J <= 5: 36, midpoint J - alpha odd: 110, Yamamoto: 10), 10 X / H slots
+            slots = 2 + 2 * {"bisector": 36, "midpoint": 110, "yamamoto": 10}[los] + (0 if los == "yamamoto" else 10)
         elif chunk and los == "midpoint":
             slots = 2 + chunk + 15
         elif chunk:

@@ -170,16 +170,17 @@ int bym_pk_xi_cross(bym_ctx *ctx, const bym_catalog *gal_a, const bym_catalog *r
                     double *xi, double *r_mean, int64_t *n_cells, void *cuda_stream);
 
 /* Odd multipoles ell = 1, 3, .., p->ell_max (p->ell_max odd, 1..7) of the cross spectra
- * of two tracers, for the Yamamoto and bisector lines of sight.  The relabelling
- * (Delta -> -Delta, k -> -k) that brings the first-galaxy terms to the form of the
- * second-galaxy ones leaves a factor (-1)^ell (Sec. 3.2, before eq. P-ell-k-symm), so
- * the Yamamoto form is [Q^AB - Q^BA] / 2, Q^XY = F[Y delta_Y](k) conj(delta_X(k)), and the
+ * of two tracers, for the Yamamoto, midpoint (all-parity series) and bisector lines of
+ * sight.  The relabelling (Delta -> -Delta, k -> -k) that brings the first-galaxy terms to
+ * the form of the second-galaxy ones leaves a factor (-1)^ell (Sec. 3.2, before eq.
+ * P-ell-k-symm), so the Yamamoto form is [Q^AB - Q^BA] / 2, Q^XY = F[Y delta_Y](k)
+ * conj(delta_X(k)), the midpoint g fields (J - alpha odd) are [-g^AB + g^BA] / 2, and the
  * bisector sum of eq. bisector-pk-fft contributes its part odd in k.  P_ell is the
  * imaginary part of the shell mean (real densities make it imaginary); xi_ell is real.
  * Odd multipoles change sign under A <-> B and vanish for one tracer.  Arguments and
  * outputs as for bym_pk_xi_cross, laid out [(ell - 1) / 2][bin]; the even multipoles are
- * not computed (call bym_pk_xi_cross).  BYM_E_UNSUPPORTED for the midpoint forms, norm
- * = 2, interlacing, or bisector field blocks forced by bym_set_field_chunk. */
+ * not computed (call bym_pk_xi_cross).  BYM_E_UNSUPPORTED for the parity-even midpoint
+ * form, norm = 2, interlacing, or field ranges / blocks forced by bym_set_field_chunk. */
 int bym_pk_xi_cross_odd(bym_ctx *ctx, const bym_catalog *gal_a, const bym_catalog *ran_a,
                         const bym_catalog *gal_b, const bym_catalog *ran_b, const bym_params *p,
                         const bym_bins *kbins, const bym_bins *rbins,
@@ -189,7 +190,7 @@ int bym_pk_xi_cross_odd(bym_ctx *ctx, const bym_catalog *gal_a, const bym_catalo
 /* Compile (without running) the runtime-specialised kernels for these
  * parameters (for the midpoint forms and the bisector also the kernels of
  * field ranges, see bym_set_field_chunk, for the bisector the two-tracer
- * contraction of bym_pk_xi_cross, and for Yamamoto and the bisector the odd-multipole
+ * contraction of bym_pk_xi_cross, and except for the parity-even form the odd-multipole
  * kernels of bym_pk_xi_cross_odd with ell_max + 1); works without a GPU.  Used by build
  * checks. */
 int bym_jit_check(const bym_params *p, char *log, size_t log_len);

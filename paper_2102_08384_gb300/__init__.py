@@ -374,8 +374,8 @@ class Context:
     def pk_xi_cross(self, gal_a, ran_a, gal_b, ran_b, params, kedges=None, redges=None, ran_nbar_a=None,
                     ran_nbar_b=None, stream=None, odd=False):
         """Cross multipoles of tracer A (gal_a, ran_a) with tracer B (gal_b, ran_b): even ell up to
-        params.ell_max, or with odd the odd ell = 1, 3, .., params.ell_max (odd); P_ell when kedges
-        is given, xi_ell when redges is given."""
+        params.ell_max, or with odd the odd ell = 1, 3, .., params.ell_max (odd; not the parity-even
+        midpoint form); P_ell when kedges is given, xi_ell when redges is given."""
         if kedges is None and redges is None:
             raise ValueError("kedges or redges is required")
         keep = []

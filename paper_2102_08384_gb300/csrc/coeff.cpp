@@ -375,6 +375,53 @@ static std::vector<BisTerm> bisector_terms_parity(int ell_max, int K, int par) {
   return out;
 }
 
+std::vector<GField> midpoint_gfields_odd(int ell_max, int K) {
+  std::vector<GField> out;
+  for (int a = 0; a <= K; ++a)
+    for (int J = (a + 1) % 2; J <= ell_max + a; J += 2)
+      for (int nu = -J; nu <= J; ++nu) out.push_back({a, J, nu});
+  return out;
+}
+
+int midpoint_gfield_index_odd(int ell_max, int alpha, int J, int nu) {
+  int idx = 0;
+  for (int a = 0; a <= alpha; ++a)
+    for (int j = (a + 1) % 2; j <= ell_max + a; j += 2) {
+      if (a == alpha && j == J) return idx + nu + J;
+      idx += 2 * j + 1;
+    }
+  return -1;
+}
+
+std::vector<MidTerm> midpoint_terms_odd(int ell_max, int K) {
+  std::vector<MidTerm> out;
+  for (int l = 1; l <= ell_max; l += 2)
+    for (int a = 0; a <= K; ++a)
+      for (int J1 = a % 2; J1 <= a; J1 += 2)
+        for (int J2 = std::max(0, l - a); J2 <= l + a; ++J2) {
+          if ((l + a + J2) % 2) continue;
+          real_coupling(
+              l, J1, J2, [&](int m, int M) { return shift_phi(a, l, m, J1, J2, M); },
+              [&](int mu, int nu1, int nu2, double v) {
+                out.push_back({odd_lm_index(l, mu), a, ylm_index(J1, nu1),
+                               midpoint_gfield_index_odd(ell_max, a, J2, nu2), v});
+              });
+        }
+  return out;
+}
+
+std::vector<XiTerm> midpoint_xi_terms_odd(int ell_max, int K) {
+  std::vector<XiTerm> out;
+  for (int l = 1; l <= ell_max; l += 2)
+    for (int a = 0; a <= K; ++a)
+      for (int J = std::max(0, l - a); J <= l + a; ++J) {
+        if ((a + l + J) % 2) continue;
+        const double f = legendre_shift_f(a, l, J);
+        if (std::fabs(f) > 1e-13) out.push_back({l, a, J, f});
+      }
+  return out;
+}
+
 std::vector<BisTerm> bisector_terms(int ell_max, int K) { return bisector_terms_parity(ell_max, K, 0); }
 
 std::vector<BisTerm> bisector_terms_odd(int ell_max, int K) { return bisector_terms_parity(ell_max, K, 1); }

@@ -40,6 +40,10 @@ inline int n_odd_lm(int ell_max) { const int q = (ell_max + 1) / 2; return 2 * q
 struct GField { int alpha, J, nu; };
 std::vector<GField> midpoint_gfields(int ell_max, int K, bool even = false);
 int midpoint_gfield_index(int ell_max, int alpha, int J, int nu, bool even = false);
+// The g fields of the odd l <= ell_max (ell_max odd): J = alpha + 1, alpha - 1, .. >= 0,
+// J <= ell_max + alpha (J1 = alpha mod 2 and J1 + J2 = l mod 2).
+std::vector<GField> midpoint_gfields_odd(int ell_max, int K);
+int midpoint_gfield_index_odd(int ell_max, int alpha, int J, int nu);
 
 // Bisector P / X: X_{lm}(k) = sum c * Re(conj F_i(k) F_j(k)), i <= j (field i = ylm_index),
 // summed over beta <= floor(K/2); c already symmetrised over (i, j) <-> (j, i).
@@ -52,9 +56,12 @@ std::vector<BisTerm> bisector_terms_odd(int ell_max, int K);
 // (t = |Delta| / r0, fields carry (2r/r0)^-alpha), y = ylm_index(J1, nu1).
 struct MidTerm { int lm, alpha, y, g; double c; };
 std::vector<MidTerm> midpoint_terms(int ell_max, int K, bool even = false);   // even: Phi instead of phi
+// odd l <= ell_max: lm = odd_lm_index, g = midpoint_gfield_index_odd
+std::vector<MidTerm> midpoint_terms_odd(int ell_max, int K);
 
 // Midpoint xi: T_l(Delta) = sum f t^alpha sum_nu Y_{J nu}(hat Delta) g^alpha_{J nu}(Delta).
 struct XiTerm { int l, alpha, J; double f; };
 std::vector<XiTerm> midpoint_xi_terms(int ell_max, int K, bool even = false);  // even: F instead of f
+std::vector<XiTerm> midpoint_xi_terms_odd(int ell_max, int K);                  // odd l <= ell_max
 
 }  // namespace bym

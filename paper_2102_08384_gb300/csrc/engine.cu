@@ -1070,8 +1070,10 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
   const long long slot_reals = (long long)N * N * (N + 2), cslot = slot_reals / 2;
   const size_t slot_bytes = (size_t)slot_reals * sizeof(T);
   const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
-  const int nextra = bis && want_xi ? nlm : 0;
+  const bool mid = p->los == BYM_LOS_MIDPOINT;
+  const int nextra = (bis && want_xi) || (mid && want_pk) ? nlm : 0;   // bisector X (xi) or midpoint H (P)
   const int xbase = 1 + nf, cbase = xbase + nextra, nslots = cbase + 1 + nf;
+  const double tscale = h * inv_r0;
   const int64_t ncat = rq.gal->n + rq.gal_b->n + (rq.ran ? rq.ran->n : 0) + (rq.ran_b ? rq.ran_b->n : 0);
   const bool cats_dev = rq.gal->on_device && rq.gal_b->on_device && (!rq.ran || rq.ran->on_device) &&
                         (!rq.ran_b || rq.ran_b->on_device);
@@ -1144,7 +1146,11 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
     TRY(alloc((void **)&invw, sizeof(T) * N));
     CUDA_TRY(cudaMemcpyAsync(invw, w.data(), sizeof(T) * N, cudaMemcpyHostToDevice, st));
   }
+  // midpoint: g = [-g^AB + g^BA] / 2 with the (-1)^J of eq. g-JM-form, from the product
+  // [-F^A conj(D_B) + F^B conj(D_A)] s / 2 with s = -(-1)^J / N^3
   std::vector<double> sc((size_t)nf, 1.0 / ((double)N * N * N));
+  if (mid)
+    for (int i = 0; i < nf; ++i) sc[(size_t)i] *= (os->fields[(size_t)i].J % 2) ? 1.0 : -1.0;
   TRY(alloc((void **)&scale, sizeof(double) * nf));
   CUDA_TRY(cudaMemcpyAsync(scale, sc.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
 
@@ -1196,7 +1202,30 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
       ProfScope ps(c, st, "xi_lag_odd", (double)Lc * Lc * Lc * nlm * esz);
       CUDA_TRY(launch(os->xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st,
                       (const T *)slot_r(xbase), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
-                      1.0 / ((double)N * N * N)));
+                      1.0 / ((double)N * N * N), tscale));
+    }
+  } else if (mid) {
+    {
+      ProfScope ps(c, st, "spec_mul_cross", (3.0 * nf + 2.0) * cplx);
+      launch_spec_mul_cross<T, T2>(slot_c(1), slot_c(cbase + 1), cslot, nf, slot_c(0), slot_c(cbase), N, scale, invw,
+                                   c->nsm * tn.per_sm_spec / 8, st, -1.0);
+    }
+    TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
+    if (want_xi) {
+      ProfScope ps(c, st, "xi_lag_odd", (double)Lc * Lc * Lc * nf * esz);
+      CUDA_TRY(launch(os->xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
+                      slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
+    }
+    if (want_pk) {
+      {
+        ProfScope ps(c, st, "mid_combine_odd", ((double)nf + nlm) * n3 * esz);
+        CUDA_TRY(launch(os->mid_combine, grid_of((long long)N * N * N, c->nsm, tn.per_sm_comb), 256, 0, st,
+                        (const T *)slot_r(1), slot_reals, slot_r(xbase), N, tscale));
+      }
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, xbase, nlm, tn));
+      ProfScope ps(c, st, "kcontract_midpoint_odd", nlm * cplx);
+      CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(xbase), cslot, N, (const int *)kg->lut, nbk,
+                      ksum));
     }
   } else {
     if (want_pk) {
@@ -1217,7 +1246,7 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
       TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
       ProfScope ps(c, st, "xi_lag_odd", (double)Lc * Lc * Lc * nf * esz);
       CUDA_TRY(launch(os->xi_lag, grid_of((long long)Lc * Lc * Lc, c->nsm, 4), 256, smr, st, (const T *)slot_r(1),
-                      slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0));
+                      slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum, 1.0, tscale));
     }
   }
   CUDA_TRY(cudaGetLastError());
@@ -1268,10 +1297,10 @@ int bym::run_request(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (!p || !rq.gal_b) return fail(c, BYM_E_INVAL, "odd multipoles: params and two tracers are required");
     if (p->ell_max < 1 || p->ell_max > 7 || p->ell_max % 2 == 0)
       return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: ell_max must be odd, 1..7");
-    if (p->los != BYM_LOS_YAMAMOTO && p->los != BYM_LOS_BISECTOR)
-      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: Yamamoto or bisector line of sight");
-    if (p->norm == 2 || p->interlace || (c->field_chunk > 0 && p->los == BYM_LOS_BISECTOR))
-      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: no norm 2, no interlacing, no field blocks");
+    if (p->los == BYM_LOS_MIDPOINT_EVEN)
+      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: the parity-even midpoint form is even-ell only");
+    if (p->norm == 2 || p->interlace || (c->field_chunk > 0 && p->los != BYM_LOS_YAMAMOTO))
+      return fail(c, BYM_E_UNSUPPORTED, "odd multipoles: no norm 2, no interlacing, no field ranges or blocks");
     bym_params pe = *p;
     pe.ell_max = p->ell_max - 1;
     int rc = validate(c, rq.gal, rq.ran, &pe, rq.kb, rq.rb);
@@ -1994,7 +2023,7 @@ int bym_jit_check(const bym_params *p, char *log, size_t log_len) {
     }
     ok = !src.empty() && compile_cubin(src, cubin, lg);
   }
-  if (ok && (p->los == BYM_LOS_YAMAMOTO || p->los == BYM_LOS_BISECTOR) && p->ell_max + 1 <= 7) {
+  if (ok && p->los != BYM_LOS_MIDPOINT_EVEN && p->ell_max + 1 <= 7) {
     src.clear();   // the odd-multipole module for ell_max + 1
     try {
       src = generate_odd_source(JitKey{p->los, p->ell_max + 1, order_key(p), p->precision}, nullptr);

@@ -188,9 +188,9 @@ void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldI
 // mid_combine for the g fields [f0, f1) (read from slots 0 .. f1 - f0 of G): H = (or +=) the
 // terms of H_{l mu} = sum phi Y (|Delta|/r0)^alpha g that involve those fields.
 void emit_mid_combine(std::ostream &o, const char *name, const JitKey &key, const std::vector<MidTerm> &terms,
-                      int f0, int f1, bool accumulate) {
+                      int f0, int f1, bool accumulate, int n_out = -1) {
   const bool f32 = key.prec == 32;
-  const int n_lm = n_even_lm(key.ell_max);
+  const int n_lm = n_out >= 0 ? n_out : n_even_lm(key.ell_max);
   o << "extern \"C\" __global__ void __launch_bounds__(256) " << name << "(const real* __restrict__ G,"
        " long long slot, real* __restrict__ Hout, int N, double tscale) {\n";
   o << "  const long long ncell = (long long)N * N * N;\n";
@@ -608,7 +608,9 @@ namespace {
 
 std::vector<FieldInfo> odd_field_list(const JitKey &key) {
   std::vector<FieldInfo> list;
-  if (key.los == 0) {                       // Yamamoto: Y_{l nu} delta, odd l
+  if (key.los == 1) {                       // midpoint: g^alpha_{J nu} with J - alpha odd
+    for (auto &g : midpoint_gfields_odd(key.ell_max, key.K)) list.push_back({g.alpha, g.J, g.nu});
+  } else if (key.los == 0) {                // Yamamoto: Y_{l nu} delta, odd l
     for (int l = 1; l <= key.ell_max; l += 2)
       for (int nu = -l; nu <= l; ++nu) list.push_back({0, l, nu});
   } else {                                  // bisector: Y_{J nu} delta, J <= ell_max + floor(K/2)
@@ -658,8 +660,8 @@ void emit_k_tail(std::ostream &o, int L, bool f32, int NLo) {
 }  // namespace
 
 std::string generate_odd_source(const JitKey &key, OddSet *meta) {
-  if (key.ell_max < 1 || key.ell_max % 2 == 0 || (key.los != 0 && key.los != 2))
-    throw std::runtime_error("odd multipoles: odd ell_max, Yamamoto or bisector");
+  if (key.ell_max < 1 || key.ell_max % 2 == 0 || key.los < 0 || key.los > 2)
+    throw std::runtime_error("odd multipoles: odd ell_max, Yamamoto, midpoint or bisector");
   const bool f32 = key.prec == 32;
   const char *real = f32 ? "float" : "double";
   const int L = key.ell_max, NLo = (L + 1) / 2, n_lm = n_odd_lm(L);
@@ -670,7 +672,17 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
   o << kPrelude;
   emit_gen_fields(o, "gen_fields_odd", list, 0, nf);
 
-  if (key.los == 0) {
+  if (key.los == 1) {
+    // midpoint: H_{l nu}(Delta) = sum phi Y_{J1}(Delta) t^alpha g^alpha_{J2}(Delta) over the odd-l g fields
+    // (mid_combine_odd), then X_{l nu} = Im F[H_{l nu}](k) (kcontract_mid_odd)
+    emit_mid_combine(o, "mid_combine_odd", key, midpoint_terms_odd(key.ell_max, key.K), 0, nf, false, n_lm);
+    o << "extern \"C\" __global__ void __launch_bounds__(256) kcontract_mid_odd(const real2* __restrict__ F,"
+         " long long cslot, int N, const int* __restrict__ lut, int nbins, double* __restrict__ gsum) {\n";
+    emit_k_head(o, NLo);
+    o << "      if (bin >= 0) {\n";
+    for (int i = 0; i < n_lm; ++i) o << "        const real X" << i << " = F[" << i << "LL * cslot + m].y;\n";
+    emit_k_tail(o, L, f32, NLo);
+  } else if (key.los == 0) {
     // Yamamoto: X_{l nu} = sgn Im(F_{l nu}(k) conj D(k)) W^-2; two launches (F^B with D_A, sgn 1;
     // F^A with D_B, sgn -1) add [Q^AB - Q^BA], halved on the host
     o << "extern \"C\" __global__ void __launch_bounds__(256) kcontract_odd(const real2* __restrict__ F, long long cslot,"
@@ -729,10 +741,17 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
     emit_k_tail(o, L, f32, NLo);
   }
 
-  // xi on the lag cube: T_l(Delta) = sum_nu Y_{l nu}(Delta) Z_{l nu}(Delta), Z in odd_lm order
+  // xi on the lag cube: T_l(Delta) = sum_nu Y_{l nu}(Delta) Z_{l nu}(Delta), Z in odd_lm order; midpoint:
+  // T_l(Delta) = sum f t^alpha sum_nu Y_{J nu}(Delta) g^alpha_{J nu}(Delta) over the odd-l g fields
+  std::vector<XiTerm> xterms;
+  int jlag = L;
+  if (key.los == 1) {
+    xterms = midpoint_xi_terms_odd(key.ell_max, key.K);
+    for (auto &x : xterms) jlag = std::max(jlag, x.J);
+  }
   o << "extern \"C\" __global__ void __launch_bounds__(256) xi_lag_odd(const real* __restrict__ Z, long long slot,"
        " int N, int jm, int full, const int* __restrict__ lut, int nbins, double* __restrict__ gsum,"
-       " double zscale) {\n";
+       " double zscale, double tscale) {\n";
   o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NLo << ");\n";
   o << "  const int Lc = full ? N : 2 * jm + 1;\n";
   emit_bin_loop_head(o, "(long long)Lc * Lc * Lc");
@@ -753,16 +772,35 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
   o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
   {
     std::ostringstream yy;
-    emit_ylm(yy, L, false, "yl", "ux", "uy", "uz", "zm");
+    emit_ylm(yy, jlag, false, "yl", "ux", "uy", "uz", "zm");
     std::istringstream is(yy.str());
     std::string line;
     while (std::getline(is, line)) o << "      " << line << "\n";
   }
-  for (int l = 1; l <= L; l += 2) {
-    o << "        { double T = 0.0;";
-    for (int mu = -l; mu <= l; ++mu)
-      o << " T += yl" << ylm_index(l, mu) << " * (double)Z[" << odd_lm_index(l, mu) << "LL * slot + off];";
-    o << " v[" << (l - 1) / 2 << "] = T * zscale; }\n";
+  if (key.los == 1) {
+    o << "        const double t1 = rr * tscale;\n";
+    for (int a2 = 2; a2 <= key.K; ++a2) o << "        const double t" << a2 << " = t" << a2 - 1 << " * t1;\n";
+    for (int l = 1; l <= L; l += 2) {
+      o << "        { double T = 0.0;\n";
+      for (auto &x : xterms) {
+        if (x.l != l) continue;
+        o << "          { double S = 0.0;";
+        for (int nu = -x.J; nu <= x.J; ++nu)
+          o << " S += yl" << ylm_index(x.J, nu) << " * (double)Z["
+            << midpoint_gfield_index_odd(key.ell_max, x.alpha, x.J, nu) << "LL * slot + off];";
+        o << " T += " << lit(x.f, false);
+        if (x.alpha > 0) o << " * t" << x.alpha;
+        o << " * S; }\n";
+      }
+      o << "          v[" << (l - 1) / 2 << "] = T * zscale; }\n";
+    }
+  } else {
+    for (int l = 1; l <= L; l += 2) {
+      o << "        { double T = 0.0;";
+      for (int mu = -l; mu <= l; ++mu)
+        o << " T += yl" << ylm_index(l, mu) << " * (double)Z[" << odd_lm_index(l, mu) << "LL * slot + off];";
+      o << " v[" << (l - 1) / 2 << "] = T * zscale; }\n";
+    }
   }
   o << "      }\n    }\n";
   o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
@@ -903,10 +941,11 @@ std::shared_ptr<OddSet> get_odd_kernels(const JitKey &key, std::string &err) {
     err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(cudaGetLastError());
     return nullptr;
   }
-  const char *kc = key.los == 0 ? "kcontract_odd" : "kcontract_cross_odd";
+  const char *kc = key.los == 0 ? "kcontract_odd" : key.los == 1 ? "kcontract_mid_odd" : "kcontract_cross_odd";
   if (cudaLibraryGetKernel(&os->gen_fields, os->lib, "gen_fields_odd") != cudaSuccess ||
       cudaLibraryGetKernel(&os->kcontract, os->lib, kc) != cudaSuccess ||
-      cudaLibraryGetKernel(&os->xi_lag, os->lib, "xi_lag_odd") != cudaSuccess) {
+      cudaLibraryGetKernel(&os->xi_lag, os->lib, "xi_lag_odd") != cudaSuccess ||
+      (key.los == 1 && cudaLibraryGetKernel(&os->mid_combine, os->lib, "mid_combine_odd") != cudaSuccess)) {
     cudaGetLastError();
     err = "generated odd-multipole module is missing a kernel";
     return nullptr;

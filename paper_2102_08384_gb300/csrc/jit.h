@@ -58,17 +58,21 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
 std::string generate_cross_source(const JitKey &key);
 cudaKernel_t get_cross_kernel(const JitKey &key, std::string &err);
 
-// Odd multipoles l = 1, 3, .., ell_max (key.ell_max odd) of cross spectra, Yamamoto (los 0) or
-// bisector (los 2): gen_fields_odd (Yamamoto: Y_{l nu} delta for odd l; bisector: Y_{J nu} delta,
-// J <= ell_max + floor(K/2)), the contraction (Yamamoto kcontract_odd(F, cslot, D, N, lut, nbins,
-// gsum, invw, sgn): sgn Im(F conj D) W^-2; bisector kcontract_cross_odd with the arguments of
-// kcontract_cross: sum c_ij Im(conj F^A_i F^B_j) W^-2, xout = i X) and xi_lag_odd(Z, slot, N, jm,
-// full, lut, nbins, gsum, zscale).  Shell sums [bin][(l - 1) / 2]; X and Z slots in odd_lm_index order.
+// Odd multipoles l = 1, 3, .., ell_max (key.ell_max odd) of cross spectra, Yamamoto (los 0),
+// midpoint (los 1, all-parity series) or bisector (los 2): gen_fields_odd (Yamamoto: Y_{l nu} delta
+// for odd l; midpoint: the g fields with J - alpha odd; bisector: Y_{J nu} delta, J <= ell_max +
+// floor(K/2)), the contraction (Yamamoto kcontract_odd(F, cslot, D, N, lut, nbins, gsum, invw, sgn):
+// sgn Im(F conj D) W^-2; midpoint mid_combine_odd and kcontract_mid_odd(F, cslot, N, lut, nbins,
+// gsum): Im F[H]; bisector kcontract_cross_odd with the arguments of kcontract_cross: sum c_ij
+// Im(conj F^A_i F^B_j) W^-2, xout = i X) and xi_lag_odd(Z, slot, N, jm, full, lut, nbins, gsum,
+// zscale, tscale).  Shell sums [bin][(l - 1) / 2]; X, H and Z slots in odd_lm_index order (midpoint
+// Z: the g fields in midpoint_gfield_index_odd order).
 struct OddSet {
   std::vector<FieldInfo> fields;
   int n_lm = 0, n_ell = 0;
   cudaLibrary_t lib = nullptr;
   cudaKernel_t gen_fields = nullptr, kcontract = nullptr, xi_lag = nullptr;
+  cudaKernel_t mid_combine = nullptr;   // midpoint: mid_combine_odd(G, slot, Hout, N, tscale)
 };
 std::string generate_odd_source(const JitKey &key, OddSet *meta);
 std::shared_ptr<OddSet> get_odd_kernels(const JitKey &key, std::string &err);

@@ -204,7 +204,8 @@ def _check_odd(got, want, rtol, scale_rows, label):
         assert np.all(err <= tol), f"{label} row {i}: err {err.max():.3e} tol {tol[np.argmax(err - tol)]:.3e}"
 
 
-@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("bisector", 2), ("bisector", 4)])
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 2), ("midpoint", 3), ("bisector", 2),
+                                   ("bisector", 4)])
 def test_odd_cross_fp64(pkg, ctx, cubes, los, K):
     a, b = cubes
     N = 32
@@ -236,7 +237,7 @@ def test_odd_cross_fp64(pkg, ctx, cubes, los, K):
     _check_odd(only_p["pk"], got["pk"], 1e-12, want_p[0], "P only")
 
 
-@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("bisector", 4)])
+@pytest.mark.parametrize("los,K", [("yamamoto", 0), ("midpoint", 4), ("bisector", 4)])
 def test_odd_cross_fp32_cap(pkg, ctx, cap_pair, los, K):
     cap, A, B = cap_pair
     N = 40
@@ -267,7 +268,7 @@ def test_odd_errors(pkg, ctx, cubes):
                             odd=True)
         return ei.value.code
 
-    assert code(ell_max=3, los="midpoint", order=2) == -6
+    assert code(ell_max=3, los="midpoint_even", order=2) == -6
     assert code(ell_max=2, los="bisector", order=2) == -6
     assert code(ell_max=9, los="bisector", order=2) == -6
     assert code(ell_max=3, los="bisector", order=2, norm=2) == -6
