@@ -289,9 +289,30 @@ static int fft_kind(const bym_ctx *c, int N, int prec, const Tune &tn) {
   }
 }
 
-// cuFFT 2D transforms of the planes of slots [first, first + count), tn.fft_batch slots per call
+// Forward plane transforms of painted or generated fields over the x planes [x0, x0 + np) only
+// (np = 0: all): the other planes of such a field are zero, and so are their transforms.
+struct XRange {
+  int x0 = 0, np = 0;
+};
+
+// cuFFT 2D transforms of the planes of slots [first, first + count), tn.fft_batch slots per call;
+// forward with a plane range: one call per slot over the range's planes
 static int fft_planes(bym_ctx *c, cudaStream_t st, int inverse, int N, void *base, size_t slot_bytes, int first,
-                      int count, const Tune &tn) {
+                      int count, const Tune &tn, const XRange *xr = nullptr) {
+  if (xr && xr->np > 0 && !inverse) {
+    const size_t plane_bytes = slot_bytes / N;
+    for (int i = 0; i < count; ++i) {
+      cufftHandle h;
+      int rc = get_plan(c, st, N, 32, 0, xr->np, &h, 2);
+      if (rc) return rc;
+      cufftSetStream(h, st);
+      cufftSetWorkArea(h, c->fft_work);
+      char *ptr = (char *)base + (size_t)(first + i) * slot_bytes + (size_t)xr->x0 * plane_bytes;
+      if (cufftExecR2C(h, (cufftReal *)ptr, (cufftComplex *)ptr) != CUFFT_SUCCESS)
+        return fail(c, BYM_E_CUDA, "cufftExec (plane range) failed");
+    }
+    return BYM_OK;
+  }
   for (int done = 0; done < count;) {
     const int b = std::min(std::max(tn.fft_batch, 1), count - done);
     cufftHandle h;
@@ -309,7 +330,7 @@ static int fft_planes(bym_ctx *c, cudaStream_t st, int inverse, int N, void *bas
 }
 
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
-                     int first, int count, const Tune &tn) {
+                     int first, int count, const Tune &tn, const XRange *xr = nullptr) {
   const double esz = prec == 64 ? 8.0 : 4.0;
   const int kind = fft_kind(c, N, prec, tn);
   if (kind) {
@@ -319,12 +340,17 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
     const double cplx = 2.0 * esz * (double)N * N * (N / 2 + 1);
     if (kind == 1) {   // cuFFT over the (y, z) planes, the library's x pass
       if (!inverse) {
-        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * (double)N * N * N);
-        TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn));
+        const double np = xr && xr->np > 0 ? xr->np : N;
+        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * np * N * N);
+        TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn, xr));
       }
       {
-        ProfScope ps(c, st, inverse ? "fft_native_x_inv" : "fft_native_x_fwd", count * 2.0 * cplx);
-        e = native_fft_xpass(inverse ? 1 : 0, (float *)base, sr, first, count, nullptr, nullptr, nullptr, st);
+        // forward with a plane range: the rows outside it are zero and are not read
+        const bool rng = !inverse && xr && xr->np > 0;
+        const double rd = rng ? (double)xr->np / N : 1.0;
+        ProfScope ps(c, st, inverse ? "fft_native_x_inv" : "fft_native_x_fwd", count * (1.0 + rd) * cplx);
+        e = native_fft_xpass(inverse ? 1 : 0, (float *)base, sr, first, count, nullptr, nullptr, nullptr, st,
+                             rng ? xr->x0 : 0, rng ? xr->x0 + xr->np : N);
       }
       if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
       if (inverse) {
@@ -369,7 +395,8 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
 // sits between the forward and inverse x passes.
 template <typename T, typename T2>
 static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *slots, size_t slot_bytes, int first,
-                           int count, const double *scale, const T *invw, const Tune &tn) {
+                           int count, const double *scale, const T *invw, const Tune &tn,
+                           const XRange *xr = nullptr) {
   const int kind = fft_kind(c, N, prec, tn);
   const double esz = sizeof(T), n3 = (double)N * N * N, cplx = 2.0 * esz * N * N * (N / 2 + 1);
   const long long slot_reals = (long long)(slot_bytes / sizeof(T));
@@ -378,14 +405,18 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     if (kind == 1) {
       {
-        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * n3);
-        TRY_RC(fft_planes(c, st, 0, N, slots, slot_bytes, first, count, tn));
+        const double np = xr && xr->np > 0 ? xr->np : N;
+        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * n3 * np / N);
+        TRY_RC(fft_planes(c, st, 0, N, slots, slot_bytes, first, count, tn, xr));
       }
       {
-        // read every F once and D once (each D tile serves all fields of the launch), write F
-        ProfScope ps(c, st, "fft_native_x_convolve", (2.0 * count + 1.0) * cplx);
+        // read every F once over its occupied rows and D once (each D tile serves all fields of the
+        // launch), write F
+        const bool rng = xr && xr->np > 0;
+        const double rd = rng ? (double)xr->np / N : 1.0;
+        ProfScope ps(c, st, "fft_native_x_convolve", (count * (1.0 + rd) + 1.0) * cplx);
         e = native_fft_xpass(2, (float *)slots, slot_reals, first, count, (const float *)slots, scale,
-                             (const float *)invw, st);
+                             (const float *)invw, st, rng ? xr->x0 : 0, rng ? xr->x0 + xr->np : N);
       }
       if (e == cudaSuccess) {
         ProfScope ps(c, st, "cufft_planes_c2r", count * 2.0 * esz * n3);
@@ -586,6 +617,36 @@ static int finish_results(bym_ctx *c, const Request &rq, const double *hstats, c
   return BYM_OK;
 }
 
+// The x planes that hold painted values in the delta slots given (their union), rounded out to a
+// multiple of 32 planes (so that few plan sizes arise); waits for the stream.  Leaves *out at
+// "every plane" when nothing was painted or the range spans the mesh.
+template <typename T>
+static int plane_range(bym_ctx *c, cudaStream_t st, DevBufs &buf, const std::vector<const T *> &deltas, int N,
+                       XRange *out) {
+  int *d = nullptr;
+  if (buf.alloc((void **)&d, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "plane range allocation failed");
+  }
+  const int init[2] = {N, -1};
+  int h[2] = {N, -1};
+  cudaError_t e = cudaMemcpyAsync(d, init, sizeof init, cudaMemcpyHostToDevice, st);
+  for (const T *p : deltas)
+    if (e == cudaSuccess) {
+      launch_plane_range<T>(p, N, d, st);
+      e = cudaGetLastError();
+    }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("plane range: ") + cudaGetErrorString(e));
+  if (h[1] < h[0] || h[0] < 0 || h[1] >= N) return BYM_OK;
+  const int np = (h[1] - h[0] + 1 + 31) / 32 * 32;
+  if (np >= N) return BYM_OK;
+  out->x0 = std::min(h[0], N - np);
+  out->np = np;
+  return BYM_OK;
+}
+
 // pd == nullptr: run the request and wait.  pd != nullptr: enqueue it on st (nothing
 // waits; uploads come from pd->stage, results land in pd->host) for finish_results
 // after the stream (or the graph it was captured into) has run; catalogs must then be
@@ -775,6 +836,25 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
         launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(ibase), N, p->box_lo, inv_h, p->assign, c->nsm, st, 0.5);
     }
   CUDA_TRY(cudaGetLastError());
+  // forward plane transforms of painted and generated fields only over their occupied x planes
+  // (library x pass backend; not in enqueued requests, which must not wait)
+  XRange xr;
+  if (!pd && fft_kind(c, N, p->precision, tn) == 1) {
+    std::vector<const T *> ds = {slot_r(0)};
+    if (il) ds.push_back(slot_r(ibase));
+    if (cross) ds.push_back(slot_r(cbase));
+    TRY(plane_range<T>(c, st, buf, ds, N, &xr));
+  }
+  // zero-fill field slots before their generation: only the range's planes when there is one (the
+  // others are neither transformed nor read by the x pass)
+  auto zero_slots = [&](int first, int count) -> cudaError_t {
+    if (xr.np > 0) {
+      const size_t plane = slot_bytes / N;
+      return cudaMemset2DAsync((char *)slot_r(first) + (size_t)xr.x0 * plane, slot_bytes, 0, (size_t)xr.np * plane,
+                               (size_t)count, st);
+    }
+    return cudaMemsetAsync(slot_r(first), 0, (size_t)count * slot_bytes, st);
+  };
   static const char *kLosName[4] = {"yamamoto", "midpoint", "bisector", "midpoint_even"};
   const std::string los_name = kLosName[p->los];
   const std::string n_gen = "gen_fields_" + los_name, n_kc = "kcontract_" + los_name, n_xi = "xi_lag_" + los_name;
@@ -784,16 +864,16 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   if (!chunk) {
     const long long ncell = (long long)N * N * N;
     ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * n3 * esz);
-    CUDA_TRY(cudaMemsetAsync(slot_r(1), 0, (size_t)nf * slot_bytes, st));
+    CUDA_TRY(zero_slots(1, nf));
     CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
                     slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
     if (cross) {   // tracer B's fields from its delta
-      CUDA_TRY(cudaMemsetAsync(slot_r(cbase + 1), 0, (size_t)nf * slot_bytes, st));
+      CUDA_TRY(zero_slots(cbase + 1, nf));
       CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(cbase),
                       slot_r(cbase + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
     }
     if (il) {   // the same fields on the shifted mesh, from its delta and node positions
-      CUDA_TRY(cudaMemsetAsync(slot_r(ibase + 1), 0, (size_t)nf * slot_bytes, st));
+      CUDA_TRY(zero_slots(ibase + 1, nf));
       CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(ibase),
                       slot_r(ibase + 1), slot_reals, N, p->box_lo[0] + 0.5 * h, p->box_lo[1] + 0.5 * h,
                       p->box_lo[2] + 0.5 * h, h, inv_r0));
@@ -801,8 +881,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   }
   if (il) {
     // forward transforms of both sets (delta and the fields), then F <- (F + P G) / 2
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, ibase, 1 + nf, tn));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn, &xr));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, ibase, 1 + nf, tn, &xr));
     std::vector<T2> ph((size_t)N);
     for (int i = 0; i < N; ++i) {
       const int n = lab(i, N);
@@ -832,8 +912,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     // two tracers: A's delta and fields in slots [0, 1 + nf), B's in [cbase, cbase + 1 + nf)
     const bool bis = p->los == BYM_LOS_BISECTOR;
     const int f0 = bis ? 1 : 0, cnt = bis ? nf : 1 + nf;
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn));
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn, &xr));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn, &xr));
     if (bis) {
       {
         ProfScope ps(c, st, "kcontract_bisector_cross", (2.0 * nf + (want_xi ? nlm : 0.0)) * cplx);
@@ -887,7 +967,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
       }
     }
   } else if (p->los == BYM_LOS_YAMAMOTO) {
-    if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn));
+    if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn, &xr));
     if (want_pk) {
       ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * cplx);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
@@ -907,17 +987,17 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   } else if (chunk && is_midpoint(p)) {
     // delta's spectrum in slot 0, its real copy in slot 1 feeds gen_fields of every range
     CUDA_TRY(cudaMemcpyAsync(slot_r(1), slot_r(0), slot_bytes, cudaMemcpyDeviceToDevice, st));
-    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
+    TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn, &xr));
     for (size_t q = 0; q < CK->ranges.size(); ++q) {
       const int f0 = CK->ranges[q].first, nq = CK->ranges[q].second - f0;
       {
         ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * n3 * esz);
-        CUDA_TRY(cudaMemsetAsync(slot_r(2), 0, (size_t)nq * slot_bytes, st));
+        CUDA_TRY(zero_slots(2, nq));
         CUDA_TRY(launch(CK->gen[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_gen), 256, 0, st,
                         (const T *)slot_r(1), slot_r(2), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h,
                         inv_r0));
       }
-      TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 2, nq, scale + f0, invw, tn)));
+      TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 2, nq, scale + f0, invw, tn, &xr)));
       if (want_xi) {
         const int Lc = rg->full ? N : 2 * rg->jm + 1;
         ProfScope ps(c, st, n_xi.c_str(), (double)Lc * Lc * Lc * nq * esz);
@@ -944,8 +1024,8 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
       }
       TRY(fft_slots(c, st, p->precision, 1, N, slots, slot_bytes, 1, nf, tn));
     } else {
-      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn));
-      TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 1, nf, scale, invw, tn)));
+      TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1, tn, &xr));
+      TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 1, nf, scale, invw, tn, &xr)));
     }
     if (want_xi) {
       const int Lc = rg->full ? N : 2 * rg->jm + 1;
@@ -972,12 +1052,12 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
       const int q0 = CK->ranges[q].first, nq = CK->ranges[q].second - q0;
       {
         ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * n3 * esz);
-        CUDA_TRY(cudaMemsetAsync(slot_r(base), 0, (size_t)nq * slot_bytes, st));
+        CUDA_TRY(zero_slots(base, nq));
         CUDA_TRY(launch(CK->gen[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_gen), 256, 0, st,
                         (const T *)slot_r(0), slot_r(base), slot_reals, N, p->box_lo[0], p->box_lo[1],
                         p->box_lo[2], h, inv_r0));
       }
-      return fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, base, nq, tn);
+      return fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, base, nq, tn, &xr);
     };
     T2 *xout = want_xi ? slot_c(xbase) : nullptr;
     int accumulate = 0;
@@ -1003,7 +1083,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
                       1.0 / ((double)N * N * N), tscale));
     }
   } else {
-    if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf, tn));
+    if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1, nf, tn, &xr));
     if (want_xi) {
       {
         ProfScope ps(c, st, "kcontract_bisector_x", ((double)nf + nlm) * cplx);
@@ -1174,18 +1254,26 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
                       inv_h, p->assign, c->nsm, st);
     }
   CUDA_TRY(cudaGetLastError());
+  XRange xr;   // forward plane transforms over the occupied x planes (library x pass backend)
+  if (fft_kind(c, N, p->precision, tn) == 1) TRY(plane_range<T>(c, st, buf, {slot_r(0), slot_r(cbase)}, N, &xr));
   {
     const long long ncell = (long long)N * N * N;
     ProfScope ps(c, st, "gen_fields_odd", 2.0 * (1.0 + nf) * n3 * esz);
     for (int base : {0, cbase}) {
-      CUDA_TRY(cudaMemsetAsync(slot_r(base + 1), 0, (size_t)nf * slot_bytes, st));
+      if (xr.np > 0) {   // only the range's planes: the others are neither transformed nor read
+        const size_t plane = slot_bytes / N;
+        CUDA_TRY(cudaMemset2DAsync((char *)slot_r(base + 1) + (size_t)xr.x0 * plane, slot_bytes, 0,
+                                   (size_t)xr.np * plane, (size_t)nf, st));
+      } else {
+        CUDA_TRY(cudaMemsetAsync(slot_r(base + 1), 0, (size_t)nf * slot_bytes, st));
+      }
       CUDA_TRY(launch(os->gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(base),
                       slot_r(base + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
     }
   }
   const int f0 = bis ? 1 : 0, cnt = bis ? nf : 1 + nf;
-  TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn));
-  TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn));
+  TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn, &xr));
+  TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn, &xr));
   const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, tn.per_sm_k);
   const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
   const int Lc = want_xi ? (rg->full ? N : 2 * rg->jm + 1) : 0;

@@ -492,8 +492,11 @@ __device__ __forceinline__ XTile x_tile(long long t) {
 // asynchronous copy of one tile: T[c][x] = src[x][c], c < nvalid; one commit group.
 // Thread e copies column c = e % TC at rows x = e / TC + (NT / TC) q, q = 0..NM TC / NT - 1,
 // unrolled so that no copy waits for the previous one to release its address registers.
+// Rows outside [xlo, xhi) are known to be zero (planes that hold no painted value): they are
+// written as zeros instead of copied.
 template <int TC>
-__device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid, int cst) {
+__device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid, int cst, int xlo = 0,
+                                             int xhi = NM) {
   constexpr int NT = XShape<TC>::NT, XR = NT / TC, NQ = NM * TC / NT;
   const long long xs = (long long)NM * HZ;
   const int c = threadIdx.x % TC, x0 = threadIdx.x / TC;
@@ -501,7 +504,13 @@ __device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int n
     float2 *t = T + c * XShape<TC>::XS + x0;
     const float2 *g = src + x0 * xs + (long long)c * cst;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) cp_async8(t + q * XR, g + (long long)q * XR * xs);
+    for (int q = 0; q < NQ; ++q) {
+      const int x = x0 + q * XR;
+      if (x >= xlo && x < xhi)
+        cp_async8(t + q * XR, g + (long long)q * XR * xs);
+      else
+        t[q * XR] = make_float2(0.f, 0.f);
+    }
   }
   cp_async_commit();
 }
@@ -509,7 +518,8 @@ __device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int n
 template <int MODE, int TC>
 __global__ void __launch_bounds__(XShape<TC>::NT, 1)
     fft512_x(float2 *__restrict__ data, long long slot_cplx, long long ntiles, const float2 *__restrict__ gtw,
-             const float2 *__restrict__ D, const double *__restrict__ scale, const float *__restrict__ invw) {
+             const float2 *__restrict__ D, const double *__restrict__ scale, const float *__restrict__ invw,
+             int xlo, int xhi) {
   using X = XShape<TC>;
   constexpr int XS_ = X::XS;
   extern __shared__ float4 smem4[];
@@ -529,7 +539,7 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
   long long t = blockIdx.x;
   int f = 0;
   XTile cur = x_tile<TC>(t);
-  x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid, cur.cst);
+  x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid, cur.cst, xlo, xhi);
   if (MODE == 2) x_tile_issue<TC>(buf1, D + cur.off, cur.nvalid, cur.cst);
   for (int i = tid; i < EX; i += X::NT) TW[i] = gtw[i];
   if (MODE == 2 && invw)
@@ -551,7 +561,7 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
     const XTile nxt = has_next ? x_tile<TC>(tn + (long long)fn * npos) : cur;
     float2 *Anext = MODE == 2 ? (A == buf0 ? buf2 : buf0) : (A == buf0 ? buf1 : buf0);
     if (has_next)
-      x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid, nxt.cst);
+      x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid, nxt.cst, xlo, xhi);
     else
       cp_async_commit();
     float2 *col = A + g * XS_;
@@ -719,7 +729,7 @@ int sm_count(int dev) {
 
 template <int MODE>
 cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const float *D, const double *scale,
-                  const float *invw, cudaStream_t st) {
+                  const float *invw, cudaStream_t st, int xlo = 0, int xhi = NM) {
   using X = XShape<XTC>;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -728,7 +738,7 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
   const long long units = MODE == 2 ? X::NPOS : ntiles;
   const long long grid = std::min<long long>(units, (long long)sm_count(dev) * (MODE == 2 ? X::PER_SM2 : X::PER_SM01));
   fft512_x<MODE, XTC><<<(unsigned)grid, X::NT, MODE == 2 ? X::SMEM2 : X::SMEM01, st>>>(
-      (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw);
+      (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw, xlo, xhi);
   return cudaGetLastError();
 }
 
@@ -799,7 +809,7 @@ cudaError_t native_fft_inverse(float *slots, long long slot_reals, int first, in
 }
 
 cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int first, int count, const float *D,
-                             const double *scale, const float *invw, cudaStream_t st) {
+                             const double *scale, const float *invw, cudaStream_t st, int xlo, int xhi) {
   if (mode < 0 || mode > 2 || (mode == 2 && (!D || !scale))) return cudaErrorInvalidValue;
   if (count <= 0) return cudaSuccess;
   int dev = 0;
@@ -810,9 +820,9 @@ cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int f
   for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
     const int n = count - done < 65535 ? count - done : 65535;
     float *b = base + (long long)done * slot_reals;
-    e = mode == 0   ? xpass<0>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)
+    e = mode == 0   ? xpass<0>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st, xlo, xhi)
         : mode == 1 ? xpass<1>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)
-                    : xpass<2>(b, slot_reals, n, tw, D, scale + done, invw, st);
+                    : xpass<2>(b, slot_reals, n, tw, D, scale + done, invw, st, xlo, xhi);
   }
   return e;
 }

@@ -18,8 +18,10 @@ cudaError_t native_fft_convolve(float *slots, long long slot_reals, int first, i
                                 const double *scale, const float *invw, int cluster, cudaStream_t st);
 
 // the x pass alone (C2C along x of half spectra) for slots [first, first + count):
-// mode 0 forward, 1 inverse, 2 forward -> * conj(D) scale[f] W(k)^-2 -> inverse
+// mode 0 forward, 1 inverse, 2 forward -> * conj(D) scale[f] W(k)^-2 -> inverse.  Modes 0 and 2
+// read the input rows x in [xlo, xhi) only and take the others as zero (planes that hold no
+// painted value); the output covers every x.
 cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int first, int count, const float *D,
-                             const double *scale, const float *invw, cudaStream_t st);
+                             const double *scale, const float *invw, cudaStream_t st, int xlo = 0, int xhi = 512);
 
 }  // namespace bym

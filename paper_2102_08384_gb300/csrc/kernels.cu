@@ -207,6 +207,22 @@ __global__ void __launch_bounds__(256) bym_spec_mul_cross(T2 *__restrict__ FA, c
   }
 }
 
+// The x planes of a padded real slot (N x N x (N + 2)) that hold a non-zero value: one block per
+// plane; range[0] <- min, range[1] <- max over them (atomics; the caller sets {N, -1} first).
+template <typename T>
+__global__ void __launch_bounds__(256) bym_plane_range(const T *__restrict__ d, int N, int *__restrict__ range) {
+  const int x = blockIdx.x;
+  const long long plane = (long long)N * (N + 2);
+  const T *p = d + (long long)x * plane;
+  int any = 0;
+  for (long long i = threadIdx.x; i < plane; i += blockDim.x) any |= (p[i] != (T)0);
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0 && any) {
+    atomicMin(range, x);
+    atomicMax(range + 1, x);
+  }
+}
+
 // Interlacing: F_f(k) <- (F_f(k) + P(k) G_f(k)) / 2 for f = 0..nf-1, with G the transform of
 // the same field on the mesh shifted by half a cell along each axis and P(k) = prod over the
 // axes of ph[n_axis] (per-axis phase exp(-i pi n / N) of the shift, 0 at the Nyquist index).
@@ -274,6 +290,11 @@ void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const 
   bym_spec_mul_cross<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(FA, FB, cslot, nf, DA, DB, N, scale, invw, (T)sa);
 }
 
+template <typename T>
+void launch_plane_range(const T *slot, int N, int *range, cudaStream_t st) {
+  bym_plane_range<T><<<N, 256, 0, st>>>(slot, N, range);
+}
+
 template <typename T, typename T2>
 void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st) {
   if (nf <= 0) return;
@@ -285,6 +306,8 @@ template void launch_interlace<float, float2>(float2 *, const float2 *, long lon
                                               cudaStream_t);
 template void launch_interlace<double, double2>(double2 *, const double2 *, long long, int, int, const double2 *, int,
                                                 cudaStream_t);
+template void launch_plane_range<float>(const float *, int, int *, cudaStream_t);
+template void launch_plane_range<double>(const double *, int, int *, cudaStream_t);
 template void launch_paint<float>(const float4 *, long long, int, const double *, float *, int, const double *, double,
                                   int, int, cudaStream_t, double);
 template void launch_paint<double>(const float4 *, long long, int, const double *, double *, int, const double *,

@@ -21,6 +21,11 @@ template <typename T, typename T2>
 void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const T2 *DA, const T2 *DB, int N,
                            const double *scale, const T *invw, int nsm, cudaStream_t st, double sa = 1.0);
 
+// the x planes of a padded real slot holding non-zero values: range[0] = min(range[0], x),
+// range[1] = max(range[1], x) over them (set range to {N, -1} before the first call)
+template <typename T>
+void launch_plane_range(const T *slot, int N, int *range, cudaStream_t st);
+
 // F_f <- (F_f + P G_f) / 2, P(k) = ph[n_x] ph[n_y] ph[n_z] (half-spectrum slots)
 template <typename T, typename T2>
 void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st);
