@@ -124,3 +124,39 @@ def test_xi_only_ranges_of_two(env, cat):
     finally:
         ctx.set_field_chunk(0)
     check_multipoles(out[4]["xi"], out[0]["xi"], "xi", label="xi-only ranges of two: ")
+
+
+def _slab(rng, lo, box, n, x_ranges):
+    """n points uniform in the x slabs given (cell units) of the 512^3 mesh box, the middle half in y, z."""
+    h = box / N
+    xs = np.concatenate([rng.uniform(a, b, n // len(x_ranges)) for a, b in x_ranges]) * h
+    yz = rng.uniform(0.25, 0.75, size=(len(xs), 2)) * box
+    pts = np.column_stack([xs, yz]) + lo[None, :]
+    return np.column_stack([pts, np.ones(len(pts))]).astype(np.float32)
+
+
+@pytest.mark.parametrize("geometry", ["wraps", "top", "middle"])
+def test_occupied_plane_range_edges(env, geometry):
+    # the library x pass backend transforms only the occupied x planes forward: catalogs that wrap
+    # across the periodic x boundary (every plane range), a thin slab at the top of the mesh (the
+    # range shifted down to fit) and one in the middle, against the cuFFT backend
+    torch, pkg, lib, ctx = env
+    lo, box = np.array([1000.0, 1000.0, 1000.0]), 1024.0
+    x_ranges = {"wraps": [(0.2, 2.5), (508.5, 511.8)], "top": [(500.3, 509.7)], "middle": [(200.2, 205.9)]}[geometry]
+    rng = np.random.default_rng(5)
+    gal = _slab(rng, lo, box, 20000, x_ranges)
+    ran = _slab(rng, lo, box, 200000, x_ranges)
+    nbar = np.full(len(ran), len(gal) / (box ** 3 / 4 * 0.01), np.float32)
+    h = box / N
+    kedges = np.linspace(0.0, 0.8 * math.pi / h, 9)
+    redges = np.linspace(0.0, 12 * h, 7)
+    for los, K in (("yamamoto", 0), ("midpoint", 2), ("bisector", 2)):
+        p = pkg.make_params(box_lo=lo, box_len=box, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
+                            compensate=True, precision=32)
+        out = {}
+        for m in (0, 4):
+            assert lib.bym_set_fft_backend(ctx._h, m) == 0
+            out[m] = ctx.pk_xi_multipoles(gal, ran, p, kedges, redges, ran_nbar=nbar)
+        check_multipoles(out[4]["pk"], out[0]["pk"], "pk", label=f"{geometry} {los} P: ")
+        check_multipoles(out[4]["xi"], out[0]["xi"], "xi", label=f"{geometry} {los} xi: ")
+    assert lib.bym_set_fft_backend(ctx._h, 1) == 0
