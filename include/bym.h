@@ -12,8 +12,9 @@
  * expanded to order K in the pair opening angle theta ("order"): the midpoint
  * series keeps alpha <= K (eq. Ylm-shift-theorem, eq. Legendre-shift-theorem-
  * all-parity), the bisector series keeps beta <= floor(K/2) (eq.
- * bisector-ylm-expan, beta <-> theta^(2 beta)).  Only even ell are returned
- * (ell = 0, 2, .., ell_max), as the paper assumes (Sec. 3.2).
+ * bisector-ylm-expan, beta <-> theta^(2 beta)).  The auto-spectrum calls return the even
+ * ell = 0, 2, .., ell_max, as the paper assumes (Sec. 3.2); the cross spectra of two
+ * tracers have even (bym_pk_xi_cross) and odd (bym_pk_xi_cross_odd) multipoles.
  *
  * Conventions shared by every entry point:
  *   - The observer sits at the origin.  Mesh node i (per axis) is at
@@ -60,7 +61,8 @@ enum {
   BYM_E_NOMEM = -3,        /* device allocation failed or the request exceeds the HBM budget */
   BYM_E_CUDA = -4,         /* CUDA runtime / cuFFT / NVRTC failure */
   BYM_E_TIMEOUT = -5,      /* bym_wait deadline passed (the request keeps running) */
-  BYM_E_UNSUPPORTED = -6,  /* odd ell_max, order > 12 (> 4 parity-even), ell_max > 8, n_mesh out of range */
+  BYM_E_UNSUPPORTED = -6,  /* odd ell_max (outside bym_pk_xi_cross_odd), order > 12 (> 4 parity-even),
+                              ell_max > 8, n_mesh out of range, a combination a call does not offer */
   BYM_E_BUSY = -7          /* no free serving slot */
 };
 
@@ -234,9 +236,12 @@ int bym_set_field_chunk(bym_ctx *ctx, int max_fields);
  * two-pass kernels wherever they apply, 8-CTA clusters; 3: the same with
  * 16-CTA clusters (a non-portable cluster size: a launch the device refuses
  * returns BYM_E_CUDA); 4: cuFFT 2D transforms of the (y, z) planes with the
- * library's x pass; 2 (the default): whichever bym_autotune measured fastest
- * for the request's shape, cuFFT 3D if it has not been tuned.  Returns
- * BYM_E_INVAL for other modes. */
+ * library's x pass; 5: cuFFT 2D plane transforms with cuFFT 1D transforms along
+ * x (any n_mesh and precision); 2 (the default): whichever bym_autotune measured
+ * fastest for the request's shape, cuFFT 3D if it has not been tuned.  With
+ * modes 4 and 5 the forward transforms of painted fields skip the x planes that
+ * hold no painted value (zero planes, zero transforms; not in requests enqueued
+ * into CUDA graphs).  Returns BYM_E_INVAL for other modes. */
 int bym_set_fft_backend(bym_ctx *ctx, int mode);
 
 /* Autotuner.  Runs the given request (which must be valid) several times on

@@ -277,52 +277,99 @@ static const Tune &tune_for(bym_ctx *c, int N, int prec, int los) {
 
 // Which FFT path a request takes: 0 cuFFT 3D transforms; 1 cuFFT 2D transforms of the
 // (y, z) planes with the library's x pass (and the convolution product fused into
-// it); 8 / 16 the library's two-pass transforms with 8- / 16-CTA plane clusters.
+// it); 2 cuFFT 2D plane transforms and cuFFT 1D transforms along x (any mesh and
+// precision); 8 / 16 the library's two-pass transforms with 8- / 16-CTA plane clusters.
 static int fft_kind(const bym_ctx *c, int N, int prec, const Tune &tn) {
-  if (!native_fft_supported(N, prec)) return 0;
+  if (c->fft_mode == 5) return 2;
+  if (!native_fft_supported(N, prec)) return (c->fft_mode == 2 && tn.native == 2) ? 2 : 0;
   switch (c->fft_mode) {
     case 0: return 0;
     case 1: return 8;
     case 3: return 16;
     case 4: return 1;
-    default: return (tn.native == 1 || tn.native == 8 || tn.native == 16) ? tn.native : 0;
+    default: return (tn.native == 1 || tn.native == 2 || tn.native == 8 || tn.native == 16) ? tn.native : 0;
   }
+}
+
+// cuFFT 1D C2C transforms along x of every (ky, kz) column of one slot's half spectrum (stride
+// N (N/2 + 1) complex, in place); the sign is chosen at execution
+static int get_xplan(bym_ctx *c, cudaStream_t st, int N, int prec, cufftHandle *out) {
+  auto key = std::make_tuple(N, prec, 6, 1);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    *out = it->second;
+    return BYM_OK;
+  }
+  cufftHandle h;
+  if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftCreate failed");
+  cufftSetAutoAllocation(h, 0);
+  long long n[1] = {N}, emb[1] = {N};
+  const long long H2 = (long long)N * (N / 2 + 1);
+  size_t work = 0;
+  const cufftResult r = cufftMakePlanMany64(h, 1, n, emb, H2, 1, emb, H2, 1, prec == 64 ? CUFFT_Z2Z : CUFFT_C2C, H2,
+                                            &work);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(h);
+    return fail(c, BYM_E_CUDA, "cufftMakePlanMany (x) failed (" + std::to_string((int)r) + ")");
+  }
+  if (work > c->fft_work_size) {   // as in get_plan: grown in the order of the request's stream
+    if (c->fft_work) cudaFreeAsync(c->fft_work, st);
+    c->fft_work = nullptr;
+    c->fft_work_size = 0;
+    if (cudaMallocAsync(&c->fft_work, work, st) != cudaSuccess) {
+      cudaGetLastError();
+      cufftDestroy(h);
+      return fail(c, BYM_E_NOMEM, "cuFFT work area allocation failed");
+    }
+    c->fft_work_size = work;
+  }
+  c->plans[key] = h;
+  *out = h;
+  return BYM_OK;
 }
 
 // Forward plane transforms of painted or generated fields over the x planes [x0, x0 + np) only
 // (np = 0: all): the other planes of such a field are zero, and so are their transforms.
 struct XRange {
   int x0 = 0, np = 0;
+  bool rows = false;   // the x pass reads only the range's rows too (library x pass), so the other
+                       // planes of a field slot need no zero-fill
 };
 
 // cuFFT 2D transforms of the planes of slots [first, first + count), tn.fft_batch slots per call;
 // forward with a plane range: one call per slot over the range's planes
+static cufftResult plane_exec(cufftHandle h, int prec, int inverse, char *ptr) {
+  if (prec == 64)
+    return inverse ? cufftExecZ2D(h, (cufftDoubleComplex *)ptr, (cufftDoubleReal *)ptr)
+                   : cufftExecD2Z(h, (cufftDoubleReal *)ptr, (cufftDoubleComplex *)ptr);
+  return inverse ? cufftExecC2R(h, (cufftComplex *)ptr, (cufftReal *)ptr)
+                 : cufftExecR2C(h, (cufftReal *)ptr, (cufftComplex *)ptr);
+}
+
 static int fft_planes(bym_ctx *c, cudaStream_t st, int inverse, int N, void *base, size_t slot_bytes, int first,
-                      int count, const Tune &tn, const XRange *xr = nullptr) {
+                      int count, const Tune &tn, const XRange *xr = nullptr, int prec = 32) {
   if (xr && xr->np > 0 && !inverse) {
     const size_t plane_bytes = slot_bytes / N;
     for (int i = 0; i < count; ++i) {
       cufftHandle h;
-      int rc = get_plan(c, st, N, 32, 0, xr->np, &h, 2);
+      int rc = get_plan(c, st, N, prec, 0, xr->np, &h, 2);
       if (rc) return rc;
       cufftSetStream(h, st);
       cufftSetWorkArea(h, c->fft_work);
       char *ptr = (char *)base + (size_t)(first + i) * slot_bytes + (size_t)xr->x0 * plane_bytes;
-      if (cufftExecR2C(h, (cufftReal *)ptr, (cufftComplex *)ptr) != CUFFT_SUCCESS)
-        return fail(c, BYM_E_CUDA, "cufftExec (plane range) failed");
+      if (plane_exec(h, prec, 0, ptr) != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftExec (plane range) failed");
     }
     return BYM_OK;
   }
   for (int done = 0; done < count;) {
     const int b = std::min(std::max(tn.fft_batch, 1), count - done);
     cufftHandle h;
-    int rc = get_plan(c, st, N, 32, inverse, b * N, &h, 2);
+    int rc = get_plan(c, st, N, prec, inverse, b * N, &h, 2);
     if (rc) return rc;
     cufftSetStream(h, st);
     cufftSetWorkArea(h, c->fft_work);
     char *ptr = (char *)base + (size_t)(first + done) * slot_bytes;
-    const cufftResult r = inverse ? cufftExecC2R(h, (cufftComplex *)ptr, (cufftReal *)ptr)
-                                  : cufftExecR2C(h, (cufftReal *)ptr, (cufftComplex *)ptr);
+    const cufftResult r = plane_exec(h, prec, inverse, ptr);
     if (r != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftExec (planes) failed (" + std::to_string((int)r) + ")");
     done += b;
   }
@@ -333,6 +380,32 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
                      int first, int count, const Tune &tn, const XRange *xr = nullptr) {
   const double esz = prec == 64 ? 8.0 : 4.0;
   const int kind = fft_kind(c, N, prec, tn);
+  if (kind == 2) {   // cuFFT plane transforms (forward over the occupied planes), cuFFT along x
+    const double np = !inverse && xr && xr->np > 0 ? xr->np : N;
+    if (!inverse) {
+      ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * np * N * N);
+      TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn, xr, prec));
+    }
+    {
+      ProfScope ps(c, st, inverse ? "cufft_x_inv" : "cufft_x_fwd", count * 4.0 * esz * N * N * (N / 2 + 1));
+      cufftHandle h;
+      TRY_RC(get_xplan(c, st, N, prec, &h));
+      cufftSetStream(h, st);
+      cufftSetWorkArea(h, c->fft_work);
+      for (int i = 0; i < count; ++i) {
+        char *ptr = (char *)base + (size_t)(first + i) * slot_bytes;
+        const int dir = inverse ? CUFFT_INVERSE : CUFFT_FORWARD;
+        const cufftResult r = prec == 64 ? cufftExecZ2Z(h, (cufftDoubleComplex *)ptr, (cufftDoubleComplex *)ptr, dir)
+                                         : cufftExecC2C(h, (cufftComplex *)ptr, (cufftComplex *)ptr, dir);
+        if (r != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftExec (x) failed (" + std::to_string((int)r) + ")");
+      }
+    }
+    if (inverse) {
+      ProfScope ps(c, st, "cufft_planes_c2r", count * 2.0 * esz * (double)N * N * N);
+      TRY_RC(fft_planes(c, st, 1, N, base, slot_bytes, first, count, tn, nullptr, prec));
+    }
+    return BYM_OK;
+  }
   if (kind) {
     cudaError_t e = native_fft_prepare();
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
@@ -400,7 +473,7 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
   const int kind = fft_kind(c, N, prec, tn);
   const double esz = sizeof(T), n3 = (double)N * N * N, cplx = 2.0 * esz * N * N * (N / 2 + 1);
   const long long slot_reals = (long long)(slot_bytes / sizeof(T));
-  if (kind) {
+  if (kind && kind != 2) {
     cudaError_t e = native_fft_prepare();
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     if (kind == 1) {
@@ -430,7 +503,7 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     return BYM_OK;
   }
-  TRY_RC(fft_slots(c, st, prec, 0, N, slots, slot_bytes, first, count, tn));
+  TRY_RC(fft_slots(c, st, prec, 0, N, slots, slot_bytes, first, count, tn, xr));
   {
     ProfScope ps(c, st, "spec_mul", (2.0 * count + 1.0) * cplx);
     launch_spec_mul<T, T2>((T2 *)((char *)slots + (size_t)first * slot_bytes), slot_reals / 2, count,
@@ -839,16 +912,18 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   // forward plane transforms of painted and generated fields only over their occupied x planes
   // (library x pass backend; not in enqueued requests, which must not wait)
   XRange xr;
-  if (!pd && fft_kind(c, N, p->precision, tn) == 1) {
+  const int fkind = fft_kind(c, N, p->precision, tn);
+  if (!pd && (fkind == 1 || fkind == 2)) {
     std::vector<const T *> ds = {slot_r(0)};
     if (il) ds.push_back(slot_r(ibase));
     if (cross) ds.push_back(slot_r(cbase));
     TRY(plane_range<T>(c, st, buf, ds, N, &xr));
+    xr.rows = fkind == 1;
   }
   // zero-fill field slots before their generation: only the range's planes when there is one (the
   // others are neither transformed nor read by the x pass)
   auto zero_slots = [&](int first, int count) -> cudaError_t {
-    if (xr.np > 0) {
+    if (xr.np > 0 && xr.rows) {
       const size_t plane = slot_bytes / N;
       return cudaMemset2DAsync((char *)slot_r(first) + (size_t)xr.x0 * plane, slot_bytes, 0, (size_t)xr.np * plane,
                                (size_t)count, st);
@@ -1254,13 +1329,17 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
                       inv_h, p->assign, c->nsm, st);
     }
   CUDA_TRY(cudaGetLastError());
-  XRange xr;   // forward plane transforms over the occupied x planes (library x pass backend)
-  if (fft_kind(c, N, p->precision, tn) == 1) TRY(plane_range<T>(c, st, buf, {slot_r(0), slot_r(cbase)}, N, &xr));
+  XRange xr;   // forward plane transforms over the occupied x planes (plane-transform backends)
+  const int fkind = fft_kind(c, N, p->precision, tn);
+  if (fkind == 1 || fkind == 2) {
+    TRY(plane_range<T>(c, st, buf, {slot_r(0), slot_r(cbase)}, N, &xr));
+    xr.rows = fkind == 1;
+  }
   {
     const long long ncell = (long long)N * N * N;
     ProfScope ps(c, st, "gen_fields_odd", 2.0 * (1.0 + nf) * n3 * esz);
     for (int base : {0, cbase}) {
-      if (xr.np > 0) {   // only the range's planes: the others are neither transformed nor read
+      if (xr.np > 0 && xr.rows) {   // only the range's planes: the others are neither transformed nor read
         const size_t plane = slot_bytes / N;
         CUDA_TRY(cudaMemset2DAsync((char *)slot_r(base + 1) + (size_t)xr.x0 * plane, slot_bytes, 0,
                                    (size_t)xr.np * plane, (size_t)nf, st));
@@ -1544,7 +1623,7 @@ int bym_pk_xi_cross_odd(bym_ctx *c, const bym_catalog *gal_a, const bym_catalog 
 }
 
 int bym_set_fft_backend(bym_ctx *c, int mode) {
-  if (!c || mode < 0 || mode > 4) return BYM_E_INVAL;
+  if (!c || mode < 0 || mode > 5) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
   c->fft_mode = mode;
   c->graph_warm.clear();   // other plans and kernels: warm again before the next captured batch
@@ -2039,6 +2118,13 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
     if ((rc = timed(t, prof))) return rc;
     const double ms = fft_ms(prof);
     if (ms < best_fft) best_fft = ms, best.fft_batch = b, best.native = 0;
+  }
+  if (c->fft_mode == 2) {   // cuFFT planes (forward over the occupied planes) + cuFFT along x
+    Tune t = best;
+    t.native = 2;
+    if ((rc = timed(t, prof))) return rc;
+    const double ms = fft_ms(prof);
+    if (ms < best_fft) best_fft = ms, best.native = 2;
   }
   if (native_fft_supported(p->n_mesh, p->precision) && c->fft_mode == 2) {
     for (int cl : {1, 8, 16}) {  // cuFFT planes + library x pass; library two-pass with 8- / 16-CTA clusters

@@ -154,9 +154,30 @@ def test_occupied_plane_range_edges(env, geometry):
         p = pkg.make_params(box_lo=lo, box_len=box, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
                             compensate=True, precision=32)
         out = {}
-        for m in (0, 4):
+        for m in (0, 4, 5):
             assert lib.bym_set_fft_backend(ctx._h, m) == 0
             out[m] = ctx.pk_xi_multipoles(gal, ran, p, kedges, redges, ran_nbar=nbar)
-        check_multipoles(out[4]["pk"], out[0]["pk"], "pk", label=f"{geometry} {los} P: ")
-        check_multipoles(out[4]["xi"], out[0]["xi"], "xi", label=f"{geometry} {los} xi: ")
+        for m in (4, 5):
+            check_multipoles(out[m]["pk"], out[0]["pk"], "pk", label=f"{geometry} {los} mode {m} P: ")
+            check_multipoles(out[m]["xi"], out[0]["xi"], "xi", label=f"{geometry} {los} mode {m} xi: ")
+    assert lib.bym_set_fft_backend(ctx._h, 1) == 0
+
+
+@pytest.mark.parametrize("n_mesh,prec", [(96, 64), (256, 32), (160, 32)])
+def test_cufft_plane_backend_any_mesh(env, cat, n_mesh, prec):
+    # backend 5: cuFFT 2D plane transforms (forward over the occupied planes of the cap) and cuFFT
+    # 1D transforms along x, for meshes the library's own kernels do not cover, against cuFFT 3D
+    torch, pkg, lib, ctx = env
+    kedges = np.linspace(0.0, 0.8 * math.pi / (cat.box_len / n_mesh), 9)
+    redges = np.arange(10.0, 190.01, 20.0)
+    tol = (1e-10, 1e-10) if prec == 64 else (1e-5, 1e-4)
+    for los, K in (("yamamoto", 0), ("midpoint", 2), ("bisector", 2)):
+        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=n_mesh, assign=3, ell_max=4, los=los,
+                            order=K, compensate=True, precision=prec)
+        out = {}
+        for m in (0, 5):
+            assert lib.bym_set_fft_backend(ctx._h, m) == 0
+            out[m] = ctx.pk_xi_multipoles(cat.gal, cat.ran, p, kedges, redges, ran_nbar=cat.ran_nbar)
+        check_multipoles(out[5]["pk"], out[0]["pk"], "pk", *tol, label=f"N={n_mesh} {los} P: ")
+        check_multipoles(out[5]["xi"], out[0]["xi"], "xi", *tol, label=f"N={n_mesh} {los} xi: ")
     assert lib.bym_set_fft_backend(ctx._h, 1) == 0
