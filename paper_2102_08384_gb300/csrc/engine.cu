@@ -913,7 +913,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   // (library x pass backend; not in enqueued requests, which must not wait)
   XRange xr;
   const int fkind = fft_kind(c, N, p->precision, tn);
-  if (!pd && (fkind == 1 || fkind == 2)) {
+  if (!pd && !rq.full_planes && (fkind == 1 || fkind == 2)) {
     std::vector<const T *> ds = {slot_r(0)};
     if (il) ds.push_back(slot_r(ibase));
     if (cross) ds.push_back(slot_r(cbase));
@@ -1776,6 +1776,7 @@ static int batch_create(bym_ctx *c, int n, const bym_request *reqs, const bym_re
       std::vector<double> a((size_t)NL * nbk + 1), b((size_t)nbk + 1), d((size_t)NL * nbr + 1), f2((size_t)nbr + 1);
       std::vector<int64_t> f((size_t)nbk + 1), g((size_t)nbr + 1);
       Request w{rq->gal, rq->ran, rq->p, rq->kb, rq->rb, a.data(), b.data(), f.data(), d.data(), f2.data(), g.data()};
+      w.full_planes = true;   // the captured run transforms every plane: warm the same cuFFT plans
       const int rc = rq->p->precision == 64 ? run_typed<double, double2>(e, w, e->stream)
                                             : run_typed<float, float2>(e, w, e->stream);
       if (rc) {

@@ -35,6 +35,7 @@ struct Request {
   double *alpha = nullptr;      // optional out: alpha_r = sum w_g / sum w_r of the request
   const bym_catalog *gal_b = nullptr, *ran_b = nullptr;   // second tracer of a cross spectrum (else NULL)
   bool odd = false;             // the odd multipoles of a cross spectrum (p->ell_max odd)
+  bool full_planes = false;     // transform every x plane (as requests captured into graphs do)
 };
 
 struct Server;  // serving loop state (serve.cpp)

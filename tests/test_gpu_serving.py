@@ -197,3 +197,29 @@ def test_batch_plan_relaunch_follows_device_catalogs(pkg, cap):
         torch.cuda.synchronize()
     plan.close()
     ctx.close()
+
+
+def test_batch_plan_with_plane_backends_at_512(pkg, cap):
+    # 512^3 items under the plane-transform backends (4: library x pass, 5: cuFFT along x): the
+    # captured runs transform every plane, their warm-up the same, and results match a plain run
+    N = 512
+    kedges = np.linspace(0.0, 0.2, 6)
+    redges = np.linspace(0.0, 150.0, 6)
+    for mode in (4, 5):
+        ctx = pkg.Context(0)
+        ctx.set_fft_backend(mode)
+        items = []
+        for los, K in (("midpoint", 2), ("bisector", 2)):
+            p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, assign=3, ell_max=2, los=los,
+                                order=K, compensate=True, precision=32)
+            items.append(dict(gal=cap.gal, ran=cap.ran, ran_nbar=cap.ran_nbar, params=p, kedges=kedges,
+                              redges=redges))
+        seq = [ctx.pk_xi_multipoles(it["gal"], it["ran"], it["params"], kedges, redges, ran_nbar=it["ran_nbar"])
+               for it in items]
+        plan = ctx.batch_plan(items)
+        got = plan.launch()
+        plan.close()
+        ctx.close()
+        for a, b in zip(got, seq):
+            check_multipoles(a["pk"], b["pk"], "pk", label=f"mode {mode} graph P: ")
+            check_multipoles(a["xi"], b["xi"], "xi", label=f"mode {mode} graph xi: ")
