@@ -238,7 +238,8 @@ int bym_set_field_chunk(bym_ctx *ctx, int max_fields);
  * returns BYM_E_CUDA); 4: cuFFT 2D transforms of the (y, z) planes with the
  * library's x pass; 5: cuFFT 2D plane transforms with cuFFT 1D transforms along
  * x (any n_mesh and precision); 2 (the default): whichever bym_autotune measured
- * fastest for the request's shape, cuFFT 3D if it has not been tuned.  With
+ * fastest for the request's shape; if it has not been tuned, mode 4 where the
+ * library's kernels apply (n_mesh = 512, FP32), else cuFFT 3D.  With
  * modes 4 and 5 the forward transforms of painted fields skip the x planes that
  * hold no painted value (zero planes, zero transforms; not in requests enqueued
  * into CUDA graphs).  Returns BYM_E_INVAL for other modes. */

@@ -287,7 +287,9 @@ static int fft_kind(const bym_ctx *c, int N, int prec, const Tune &tn) {
     case 1: return 8;
     case 3: return 16;
     case 4: return 1;
-    default: return (tn.native == 1 || tn.native == 2 || tn.native == 8 || tn.native == 16) ? tn.native : 0;
+    default:
+      if (tn.native < 0) return 1;   // untuned: the plane-transform backend with the library's x pass
+      return (tn.native == 1 || tn.native == 2 || tn.native == 8 || tn.native == 16) ? tn.native : 0;
   }
 }
 

@@ -47,7 +47,9 @@ struct Tune {
   int per_sm_k = 4;       // kcontract / kcontract_x
   int per_sm_spec = 8;    // spec_mul
   int fft_batch = 8;      // transforms per cuFFT call
-  int native = 0;         // library FFT kernels where they apply: 0 = cuFFT, else CTAs per plane-pass cluster (8, 16)
+  int native = -1;        // FFT path: 0 cuFFT 3D, 1 cuFFT planes + library x pass, 2 cuFFT planes + cuFFT x,
+                          // 8 / 16 library two-pass (CTAs per plane-pass cluster); -1 untuned: 1 where the
+                          // library's kernels apply (512^3 FP32), else 0
 };
 
 struct ProfEntry {
