@@ -706,11 +706,14 @@ static int plane_range(bym_ctx *c, cudaStream_t st, DevBufs &buf, const std::vec
   const int init[2] = {N, -1};
   int h[2] = {N, -1};
   cudaError_t e = cudaMemcpyAsync(d, init, sizeof init, cudaMemcpyHostToDevice, st);
-  for (const T *p : deltas)
-    if (e == cudaSuccess) {
-      launch_plane_range<T>(p, N, d, st);
-      e = cudaGetLastError();
-    }
+  {
+    ProfScope ps(c, st, "plane_range", (double)deltas.size() * N * N * (N + 2) * sizeof(T));
+    for (const T *p : deltas)
+      if (e == cudaSuccess) {
+        launch_plane_range<T>(p, N, d, st);
+        e = cudaGetLastError();
+      }
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("plane range: ") + cudaGetErrorString(e));
