@@ -12,8 +12,8 @@ numpy / scipy / sympy primitives, and it shares no code with the CUDA path:
                     solid-harmonic coupling A (Appendix A, Appendix B eq.
                     solid-harm-application), complex spherical harmonics.
 * ``coeffs``     -- the series coefficients phi (Appendix B, eq.
-                    shift-coeff-def), f (Appendix F, eq. f-alpha-def) and
-                    B (Appendix G, eq. B-def), in the complex basis.
+                    shift-coeff-def), f (Appendix E, eq. f-alpha-def) and
+                    B (Appendix F, eq. B-def), in the complex basis.
 * ``mesh``       -- CIC/TSC painting, mesh/lag/Fourier grids, FKP
                     normalisation and shell binning (Sec. 2).
 * ``estimators`` -- the FFT series estimators (O3): Yamamoto, midpoint and

@@ -5,9 +5,9 @@ Test infrastructure only (see ``oracle/__init__``).
 * ``phi(alpha, ell, m, J1, J2, M)`` -- spherical-harmonic shift theorem,
   Appendix B, eq. shift-coeff-def (boxed), used by eq. Ylm-shift-theorem:
       Y_ell^m(hat(a+A)) = sum phi^{alpha,ell m}_{J1 J2 M} (a/A)^alpha Y_J1^M(hat a) Y_J2^{m-M}(hat A).
-* ``f_leg(alpha, ell, J)`` -- Legendre shift theorem, Appendix F, eq.
+* ``f_leg(alpha, ell, J)`` -- Legendre shift theorem, Appendix E, eq.
   f-alpha-def (boxed), used by eq. Legendre-shift-theorem-all-parity.
-* ``B(beta, ell, m, J1, J2, M)`` -- bisector expansion, Appendix G, eq. B-def
+* ``B(beta, ell, m, J1, J2, M)`` -- bisector expansion, Appendix F, eq. B-def
   (boxed), used by eq. bisector-ylm-expan.
 
 Each coefficient is the paper's sum taken term by term in its own order and
@@ -18,8 +18,8 @@ Parity pins (tests/test_oracle_coeffs.py):
   * the printed L_2 example to alpha=4 (eq. L2-all), every term;
   * the printed bisector Y_2^1 example at beta=0,1 (Sec. 5.1), every term;
   * closed forms phi^0, phi^{alpha,00} (Appendix B), f^0, f^{alpha,0}
-    (Appendix F), B^0, B^{beta,00} (Appendix G);
-  * selection rules (parities, J ranges) and the sum rule of Appendix F;
+    (Appendix E), B^0, B^{beta,00} (Appendix F);
+  * selection rules (parities, J ranges) and the sum rule of Appendix E;
   * truncation error of each series against the exact function at random
     geometry, falling as eps^(K+1) (midpoint) or theta^(2 beta+2) (bisector);
   * f by an independent route: a direct Taylor expansion (sympy) of
@@ -118,7 +118,7 @@ def shift_series_ylm(ell: int, m: int, a, A, K: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# f: Legendre shift theorem (Appendix F)
+# f: Legendre shift theorem (Appendix E)
 # --------------------------------------------------------------------------
 @lru_cache(maxsize=None)
 def f_leg(alpha: int, ell: int, J: int) -> float:
@@ -133,7 +133,7 @@ def f_leg(alpha: int, ell: int, J: int) -> float:
 
 @lru_cache(maxsize=None)
 def h_leg(beta: int, alpha: int, ell: int, J: int) -> float:
-    """h^{beta, alpha ell}_J of Appendix F.2: f^{beta, ell}_J with C^{ell/2} replaced by C^{(ell+alpha)/2}."""
+    """h^{beta, alpha ell}_J of Appendix E.2: f^{beta, ell}_J with C^{ell/2} replaced by C^{(ell+alpha)/2}."""
     return _f_sum(beta, ell, J, ell + alpha)
 
 
@@ -189,7 +189,7 @@ def shift_series_legendre(ell: int, a, A, K: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# parity-even midpoint coefficients (Appendix C, D, F.2)
+# parity-even midpoint coefficients (Appendix C, D, E.2)
 # --------------------------------------------------------------------------
 @lru_cache(maxsize=None)
 def Omega(beta: int, alpha: int, J1: int, J2: int, m: int, M: int, S1: int, S2: int, T: int) -> float:
@@ -240,9 +240,9 @@ def Phi_table(alpha: int, ell: int, m: int, tol: float = 1e-13) -> dict:
 
 @lru_cache(maxsize=None)
 def F_even(alpha: int, ell: int, J: int) -> float:
-    """F^{alpha, ell}_J of the parity-even Legendre expansion (Appendix F.2, eq. F-coeff-def and the
+    """F^{alpha, ell}_J of the parity-even Legendre expansion (Appendix E.2, eq. F-coeff-def and the
     explicit forms after it): F^0 = delta_{ell J}, F^2 = -f^2, F^4 = -f^4 + sum_S f^{2,ell}_S h^{2,2S}_J.
-    They enter as L_ell = 1/2 sum (2J+1)/(2ell+1) F [...] (the form of the boxed Appendix F.2 equation)."""
+    They enter as L_ell = 1/2 sum (2J+1)/(2ell+1) F [...] (the form of the boxed Appendix E.2 equation)."""
     if alpha == 0:
         return f_leg(0, ell, J)
     if alpha == 2:
@@ -301,7 +301,7 @@ def even_series_legendre(ell: int, r1, r2, K: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# B: bisector expansion (Appendix G)
+# B: bisector expansion (Appendix F)
 # --------------------------------------------------------------------------
 @lru_cache(maxsize=None)
 def B(beta: int, ell: int, m: int, J1: int, J2: int, M: int) -> float:

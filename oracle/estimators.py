@@ -9,7 +9,7 @@ Every estimator follows the paper's boxed equation literally, with full complex
   midpoint  P: eq. FFT-midpoint, g from eq. g-JM-form
             xi: eq. xi-parity-all-estimator (same g functions)
   midpoint_even  the parity-even forms (Sec. 3.3 / Sec. 4.3 boxed): Phi and F
-            coefficients (Appendices D, F.2), even alpha only, same g functions
+            coefficients (Appendices D, E.2), even alpha only, same g functions
   bisector  P: eq. bisector-pk-fft (boxed form)
             xi: Sec. 6 boxed estimator, h summed over the B coefficients
                 before the inverse transform as Sec. 6 suggests

@@ -39,7 +39,7 @@ def binom(n: int, k: int) -> int:
 
 def gen_binom(a: Fraction, k: int) -> Fraction:
     """Generalised binomial coefficient (a choose k) = (a)_k / k! with the
-    falling factorial, as used for binom(-ell/2, beta) in Appendix G."""
+    falling factorial, as used for binom(-ell/2, beta) in Appendix F."""
     out = Fraction(1)
     for i in range(k):
         out *= (a - i)
@@ -155,22 +155,33 @@ def solid_A(ell: int, m: int, lam: int, mu: int) -> float:
 # --------------------------------------------------------------------------
 # complex spherical harmonics (DLMF 14.30 with Condon-Shortley phase)
 # --------------------------------------------------------------------------
-def ylm(ell: int, m: int, v) -> np.ndarray:
-    """Complex Y_ell^m of the direction of the vectors v[..., 3].
-
-    Uses scipy.special.sph_harm_y (DLMF convention, Condon-Shortley phase).
-    The zero vector has no direction; it is assigned Y_ell^m(0) = delta_{ell0}/sqrt(4pi),
-    the only choice under which the series below stay exact at zero separation."""
+def direction_angles(v):
+    """(theta, phi, zero) of the vectors v[..., 3]: polar and azimuthal angles, and a flag
+    for the zero vector (which has no direction; its angles are set to 0)."""
     v = np.asarray(v, dtype=np.float64)
     x, y, z = v[..., 0], v[..., 1], v[..., 2]
     r = np.sqrt(x * x + y * y + z * z)
-    if abs(m) > ell:
-        return np.zeros(r.shape, dtype=np.complex128)
     zero = r == 0.0
     rs = np.where(zero, 1.0, r)
     theta = np.arccos(np.clip(z / rs, -1.0, 1.0))
     phi = np.arctan2(y, x)
+    return theta, phi, zero
+
+
+def ylm_angles(ell: int, m: int, theta, phi, zero) -> np.ndarray:
+    """Complex Y_ell^m at polar angles (theta, phi), scipy.special.sph_harm_y (DLMF
+    convention, Condon-Shortley phase).  Where ``zero`` is set (the zero vector) the value is
+    Y_ell^m(0) = delta_{ell0}/sqrt(4pi), the only choice under which the series below stay
+    exact at zero separation."""
+    if abs(m) > ell:
+        return np.zeros(np.shape(theta), dtype=np.complex128)
     out = sph_harm_y(ell, m, theta, phi).astype(np.complex128)
     if np.any(zero):
         out = np.where(zero, (1.0 / math.sqrt(FOUR_PI)) if ell == 0 else 0.0, out)
     return out
+
+
+def ylm(ell: int, m: int, v) -> np.ndarray:
+    """Complex Y_ell^m of the direction of the vectors v[..., 3] (``ylm_angles`` of
+    ``direction_angles``)."""
+    return ylm_angles(ell, m, *direction_angles(v))

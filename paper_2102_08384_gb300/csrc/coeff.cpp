@@ -2,7 +2,7 @@
 //
 // The complex-basis coefficients follow the paper's boxed definitions term by
 // term (Appendix A building blocks; phi: Appendix B eq. shift-coeff-def;
-// f: Appendix F eq. f-alpha-def; B: Appendix G eq. B-def).  The kernels work
+// f: Appendix E eq. f-alpha-def; B: Appendix F eq. B-def).  The kernels work
 // with real spherical harmonics, so each coupling is then rotated into the
 // real basis with the unitary map U (Y_R = U Y) and emitted as a sparse list.
 #include "coeff.h"
@@ -244,7 +244,7 @@ double parity_even_Phi(int alpha, int ell, int m, int J1, int J2, int M) {
   return total;
 }
 
-// Appendix F.2: F^0 = f^0, F^2 = -f^2, F^4 = -f^4 + sum_S f^{2,ell}_S h^{2,2S}_J.
+// Appendix E.2: F^0 = f^0, F^2 = -f^2, F^4 = -f^4 + sum_S f^{2,ell}_S h^{2,2S}_J.
 double parity_even_F(int alpha, int ell, int J) {
   if (alpha == 0) return legendre_shift_f(0, ell, J);
   if (alpha == 2) return -legendre_shift_f(2, ell, J);

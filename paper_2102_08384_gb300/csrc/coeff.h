@@ -20,9 +20,9 @@ double shift_omega(int beta, int ell, int m, int alpha, int J1, int J2, int M);
 double shift_Omega(int beta, int alpha, int J1, int J2, int m, int M, int S1, int S2, int T);
 double legendre_shift_f(int alpha, int ell, int J);                  // eq. f-alpha-def
 double legendre_shift_sum(int alpha, int ell, int J, int two_gamma);
-double legendre_shift_h(int beta, int alpha, int ell, int J);        // h^{beta, alpha ell}_J (Appendix F.2)
+double legendre_shift_h(int beta, int alpha, int ell, int J);        // h^{beta, alpha ell}_J (Appendix E.2)
 double parity_even_Phi(int alpha, int ell, int m, int J1, int J2, int M);  // Appendix D, alpha <= 4
-double parity_even_F(int alpha, int ell, int J);                     // Appendix F.2, alpha <= 4
+double parity_even_F(int alpha, int ell, int J);                     // Appendix E.2, alpha <= 4
 double bisector_B(int beta, int ell, int m, int J1, int J2, int M);  // eq. B-def
 
 // ---- real-basis indexing ---------------------------------------------------

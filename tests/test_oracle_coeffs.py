@@ -56,7 +56,7 @@ def test_phi_closed_forms(ell):
 
 
 def test_f_closed_forms():
-    # Appendix F: f^{0,ell}_J = delta_{ell J}; f^{alpha,0}_J = delta_{alpha 0} delta_{J 0}
+    # Appendix E: f^{0,ell}_J = delta_{ell J}; f^{alpha,0}_J = delta_{alpha 0} delta_{J 0}
     for ell in range(0, 7):
         for J in range(0, 9):
             assert f_leg(0, ell, J) == pytest.approx(1.0 if J == ell else 0.0, abs=1e-13)
@@ -90,7 +90,7 @@ def test_selection_rules():
                 for (J1, J2, M) in phi_table(alpha, ell, m):
                     assert (alpha + J1) % 2 == 0 and (ell + alpha + J2) % 2 == 0
                     assert J1 <= alpha and max(0, ell - alpha) <= J2 <= ell + alpha
-    # f vanishes unless alpha+ell+J even (Appendix F)
+    # f vanishes unless alpha+ell+J even (Appendix E)
     for alpha in range(0, 6):
         for ell in range(0, 7):
             for J in f_table(alpha, ell):
@@ -104,7 +104,7 @@ def test_selection_rules():
 
 
 def test_f_sum_rule():
-    # Appendix F: putting A parallel to a gives 1 = sum_alpha sum_J (2J+1)/(2ell+1) f k^-alpha,
+    # Appendix E: putting A parallel to a gives 1 = sum_alpha sum_J (2J+1)/(2ell+1) f k^-alpha,
     # so the weighted sum vanishes for every alpha > 0 (the printed eq. L2-all, L24-even
     # coefficients show the same); the (2J+1) weight is the reading of the garbled statement.
     for ell in range(0, 7):
