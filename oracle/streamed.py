@@ -18,6 +18,9 @@ another order:
   2 J1 + 1 factors Y_J1^M(Delta) Delta^alpha are kept for the group; a g function is computed
   once per group that needs it;
 * midpoint xi: the sum of f Y_J^M*(Delta) Delta^alpha g^alpha_JM is taken g by g, each g once;
+* Yamamoto P and xi (eq. Yamamoto-estimator, eq. 2pcf-yama): one field F[Y_ell^m delta] at a
+  time, its product with D*(k) contracted on the binned modes and, inverse-transformed, on the
+  binned lags;
 * bisector P and xi: the bilinear sum runs pair by pair over the (left, right) fields
   F[Y_J1^M delta](-k) and F[Y_J2^(m-M) delta](k), the left fields held in blocks and the right
   ones made one at a time; xi takes the inverse transform of each pair's product, whose sum
@@ -30,8 +33,8 @@ another order:
 Elementwise work on full grids runs slab by slab along the first axis in a thread pool,
 which changes no arithmetic.
 
-Parity pin (tests/test_oracle_streamed.py): equal to ``oracle.estimators`` to 1e-12 for both
-lines of sight, order 2 and 4, ell <= 4, P and xi, CIC and compensated TSC.
+Parity pin (tests/test_oracle_streamed.py): equal to ``oracle.estimators`` to 1e-12 for the
+three lines of sight, orders 2 and 4, ell <= 4, P and xi, CIC and compensated TSC.
 """
 from __future__ import annotations
 
@@ -223,13 +226,13 @@ def bisector_pairs(K, ell_max):
 
 def pk_xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max, los, order, kedges=None,
                      redges=None, compensate=False, norm=1, block=8, threads=None, progress=None):
-    """P_ell(k) and/or xi_ell(r), ell = 0, 2, .., ell_max, for los 'midpoint' or 'bisector' at
-    order K: the values of ``estimators.pk_multipoles`` / ``xi_multipoles`` (one tracer, no
+    """P_ell(k) and/or xi_ell(r), ell = 0, 2, .., ell_max, for los 'yamamoto', 'midpoint' or
+    'bisector' (order K): the values of ``estimators.pk_multipoles`` / ``xi_multipoles`` (one tracer, no
     interlacing, norm 0 or 1).  ``block``: left bisector fields held at once.  ``progress(kind,
     done, total)`` is called after every product / pair ('unit') and may raise ``Stop`` to end
     the run early (the partial sums are then discarded)."""
-    if los not in ("midpoint", "bisector"):
-        raise ValueError("the streamed order covers the midpoint and bisector lines of sight")
+    if los not in ("yamamoto", "midpoint", "bisector"):
+        raise ValueError("the streamed order covers the Yamamoto, midpoint and bisector lines of sight")
     if ell_max < 0 or ell_max % 2:
         raise ValueError("even ell_max")
     if norm not in (0, 1):
@@ -247,7 +250,10 @@ def pk_xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max,
     if want_x:
         Z = {ell: np.zeros(s.lag_mag_c.shape, dtype=np.complex128) for ell in ells}
 
-    if los == "midpoint":
+    if los == "yamamoto":
+        _yamamoto(s, ells, want_p, want_x, T if want_p else None, Z if want_x else None, Yk if want_p else None,
+                  progress)
+    elif los == "midpoint":
         _midpoint(s, order, ell_max, ells, want_p, want_x, T if want_p else None, Z if want_x else None,
                   Yk if want_p else None, progress)
     else:
@@ -259,6 +265,25 @@ def pk_xi_multipoles(gal, ran, ran_nbar, *, N, box_lo, box_len, assign, ell_max,
     if want_x:
         out.update(s.xi_out(ells, Z))
     return out
+
+
+def _yamamoto(s, ells, want_p, want_x, T, Z, Yk, progress):
+    """Sum over m of Y_ell^m*(k) D*(k) F[Y_ell^m delta](k) (P) and of Y_ell^m*(Delta) times the
+    inverse transform of D* F[Y_ell^m delta] (xi), one field at a time."""
+    total = sum(2 * ell + 1 for ell in ells)
+    done = 0
+    for ell in ells:
+        for m in range(-ell, ell + 1):
+            prod = s.transform(ylm_angles(ell, m, *s.ang_occ))
+            _slabs(s.N, lambda lo, hi: prod[lo:hi].__imul__(s.Dc[lo:hi]), s.threads)
+            if want_p:
+                T[ell] += Yk[(ell, m)] * prod.ravel()[s.ball]
+            if want_x:
+                Z[ell] += np.conj(ylm_angles(ell, m, *s.ang_c)) * _ifftn(prod)[s.cube]
+            del prod
+            done += 1
+            if progress:
+                progress("unit", done, total)
 
 
 def _midpoint(s, K, ell_max, ells, want_p, want_x, T, Z, Yk, progress):
@@ -362,6 +387,8 @@ def _bisector(s, K, ell_max, ells, want_p, want_x, T, Z, Yk, block, progress):
 
 
 def work_units(los, K, ell_max):
-    """Number of products (midpoint) or field pairs (bisector) a request visits."""
+    """Number of products (midpoint), field pairs (bisector) or fields (Yamamoto) a request visits."""
+    if los == "yamamoto":
+        return sum(2 * ell + 1 for ell in range(0, ell_max + 1, 2))
     return len(midpoint_products(K, ell_max)) if los == "midpoint" else len(bisector_pairs(K, ell_max))
 

@@ -26,7 +26,8 @@ def _close(a, b, tol=1e-12):
         assert np.max(np.abs(a[l] - b[l])) <= tol * scale, (l, np.max(np.abs(a[l] - b[l])) / scale)
 
 
-@pytest.mark.parametrize("los,K,N,assign,comp", [("midpoint", 2, 20, 2, False), ("midpoint", 4, 16, 3, True),
+@pytest.mark.parametrize("los,K,N,assign,comp", [("yamamoto", 0, 20, 2, False), ("yamamoto", 0, 16, 3, True),
+                                                 ("midpoint", 2, 20, 2, False), ("midpoint", 4, 16, 3, True),
                                                  ("bisector", 2, 20, 2, False), ("bisector", 4, 16, 3, True)])
 def test_streamed_equals_plain(cap, los, K, N, assign, comp):
     h = cap.box_len / N
@@ -64,4 +65,4 @@ def test_streamed_one_statistic_and_stop(cap):
         S.pk_xi_multipoles(cap.gal, cap.ran, cap.ran_nbar, kedges=kedges, progress=stop_after_two, **kw)
     assert seen == [(1, S.work_units("bisector", 2, 2)), (2, S.work_units("bisector", 2, 2))]
     with pytest.raises(ValueError):
-        S.pk_xi_multipoles(cap.gal, cap.ran, cap.ran_nbar, kedges=kedges, **dict(kw, los="yamamoto"))
+        S.pk_xi_multipoles(cap.gal, cap.ran, cap.ran_nbar, kedges=kedges, **dict(kw, los="midpoint_even"))
