@@ -59,7 +59,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--fft-backend", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="force an FFT backend (bym_set_fft_backend) instead of the tuned choice (profiling runs)")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--order", type=int, default=ORDER, help="expansion order (4 is the benchmark; profiling runs)")
+    ap.add_argument("--ell-max", type=int, default=ELL_MAX, help="largest multipole (4 is the benchmark; profiling runs)")
     return ap.parse_args()
 
 
@@ -131,39 +133,66 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle baseline
-def oracle_sample(cat, n_mesh_full):
+def oracle_sample(cat, n_mesh_full, units=3):
     """Time the FP64 oracle on a bounded sample of the same workload and scale it.
 
-    Sample: the same estimators (midpoint and bisector, P_ell and xi_ell, order
-    4, ell <= 4, TSC, compensated) on every 10th object of the catalog, on a
-    32^3 mesh.  Its painting time is measured separately and scaled by 10 (object
-    count); the rest (FFTs and field arithmetic) by the mesh work ratio
-    (512/32)^3 * log(512^3)/log(32^3)."""
-    from oracle import estimators as E
+    The oracle is oracle.streamed (the loop order that holds a few full grids; equal to the
+    plain estimators to 1e-12), on the benchmark's own mesh, catalog, bins and order, for the
+    midpoint and the bisector line of sight, P and xi together.  Sample: painting of every 10th
+    object (scaled by 10: painting is linear in the objects), then for each line of sight the
+    set-up (transform of delta, binned modes and lags) and its first `units` products (midpoint)
+    or field pairs (bisector), scaled by the number of units the request visits.  The first
+    midpoint products each need their own g function, so the linear scaling over-estimates the
+    midpoint cost; the full oracle run that wrote tests/golden/survey512_order4.json is reported
+    beside it (measured on the host that ran it)."""
     from oracle import mesh as M
+    from oracle import streamed as S
     sub = slice(None, None, 10)
-    gal, ran, rn = cat.gal[sub], cat.ran[sub], cat.ran_nbar[sub]
-    Ns = 32
-    kw = dict(N=Ns, box_lo=cat.box_lo, box_len=cat.box_len, assign=3, ell_max=ELL_MAX, order=ORDER,
-              compensate=True)
     t0 = time.perf_counter()
-    M.density_mesh(gal, ran, Ns, cat.box_lo, cat.box_len, 3)
-    t_paint = time.perf_counter() - t0
-    t0 = time.perf_counter()
+    M.density_mesh(cat.gal[sub], cat.ran[sub], n_mesh_full, cat.box_lo, cat.box_len, 3)
+    t_paint = 10.0 * (time.perf_counter() - t0)
+    parts = {}
     for los in ("midpoint", "bisector"):
-        E.pk_multipoles(gal, ran, rn, los=los, kedges=KEDGES, **kw)
-        E.xi_multipoles(gal, ran, rn, los=los, redges=REDGES, **kw)
-    t_sample = time.perf_counter() - t0
-    n_paint = 4
-    t_mesh = max(t_sample - n_paint * t_paint, 0.0)
-    ratio = (n_mesh_full / Ns) ** 3 * math.log(n_mesh_full ** 3) / math.log(Ns ** 3)
-    t_full = n_paint * t_paint * 10.0 + t_mesh * ratio
-    return {"value": 1.0 / t_full, "unit": "catalogs/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"FP64 oracle (numpy/scipy.fft, all {os.cpu_count()} host cores) on every 10th object at "
-                       f"32^3: {t_sample:.1f} s measured (painting {t_paint:.2f} s per call); scaled to the "
-                       f"full catalog at {n_mesh_full}^3 by object count (painting) and by mesh work "
-                       f"(N^3 log N^3, x{ratio:.0f}) -> {t_full:.0f} s per catalog"),
-            "sample_seconds": t_sample}
+        marks = {}
+        t0 = time.perf_counter()
+
+        def progress(kind, done, total):
+            if kind == "setup":
+                marks["setup"] = time.perf_counter() - t0
+            elif kind == "unit":
+                marks["total"] = total
+                if done >= units:
+                    marks["units"] = time.perf_counter() - t0 - marks["setup"]
+                    raise S.Stop
+        try:
+            S.pk_xi_multipoles(cat.gal[sub], cat.ran[sub], cat.ran_nbar[sub], N=n_mesh_full, box_lo=cat.box_lo,
+                               box_len=cat.box_len, assign=3, ell_max=ELL_MAX, los=los, order=ORDER, kedges=KEDGES,
+                               redges=REDGES, compensate=True, norm=1, progress=progress)
+        except S.Stop:
+            pass
+        per_unit = marks["units"] / units
+        parts[los] = {"setup_s": marks["setup"], "per_unit_s": per_unit, "units": marks["total"],
+                      "est_s": marks["setup"] + per_unit * marks["total"]}
+    t_sample = t_paint / 10.0 + sum(v["setup_s"] + units * v["per_unit_s"] for v in parts.values())
+    t_full = 2 * t_paint + sum(v["est_s"] for v in parts.values())
+    out = {"value": 1.0 / t_full, "unit": "catalogs/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"FP64 oracle (oracle.streamed, numpy/scipy.fft, {os.cpu_count()} host cores) on the {n_mesh_full}^3 "
+                      f"workload: painting of every 10th object x10 ({t_paint:.1f} s per catalog painting), then per LOS "
+                      f"its set-up and first {units} units, scaled by the units it visits "
+                      + ", ".join(f"{k}: {v['setup_s']:.1f} s + {v['per_unit_s']:.2f} s x {v['units']}"
+                                  for k, v in parts.items())
+                      + f" -> {t_full:.0f} s per catalog ({t_sample:.0f} s sampled)"),
+           "sample_seconds": t_sample}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "survey512_order4.json")) as fh:
+            g = json.load(fh)
+        wall = sum(v["oracle_wall_s"] for v in g["los"].values())
+        out["full_run_measured"] = {"seconds": wall, "catalogs_per_s": 1.0 / wall, "cores": g["host"]["cores"],
+                                    "machine": g["host"]["machine"],
+                                    "what": "the whole oracle run (both LOS, P and xi) that wrote the golden values"}
+    except (OSError, KeyError, ValueError):
+        pass
+    return out
 
 
 def run_reference(args):
@@ -214,7 +243,8 @@ def run_ours(args):
     if args.fft_backend is not None:
         ctx.set_fft_backend(args.fft_backend)
     params = [pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=args.mesh, assign=3,
-                              ell_max=ELL_MAX, los=los, order=ORDER, compensate=True, precision=32, norm=1)
+                              ell_max=args.ell_max, los=los, order=args.order if los != "yamamoto" else 0,
+                              compensate=True, precision=32, norm=1)
               for los in args.los.split(",")]
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
@@ -274,9 +304,9 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms_e = _max_over_ranks(e0.elapsed_time(e1), ws)
-        nl, nbk, nbr = ELL_MAX // 2 + 1, len(KEDGES) - 1, len(REDGES) - 1
-        h2d = 2 * (g_h.nbytes + r_h.nbytes + rn_h.nbytes)
-        d2h = 2 * (8 * 8 + nl * nbk * 8 + nl * nbr * 8)
+        nl, nbk, nbr = args.ell_max // 2 + 1, len(KEDGES) - 1, len(REDGES) - 1
+        h2d = len(params) * (g_h.nbytes + r_h.nbytes + rn_h.nbytes)
+        d2h = len(params) * (8 * 8 + nl * nbk * 8 + nl * nbr * 8)
         e2e = {"value": ws * args.steps / (ms_e / 1000.0), "unit": "catalogs/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -290,7 +320,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "catalogs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_mesh": args.mesh, "order": ORDER, "ell_max": ELL_MAX,
+            "config": {"workload": WORKLOAD, "n_mesh": args.mesh, "order": args.order, "ell_max": args.ell_max,
                        "n_gal": int(len(cat.gal)), "n_ran": int(len(cat.ran)), "box_len": cat.box_len,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (catalog 176 MB, fields > 30 GB)",
@@ -302,6 +332,7 @@ def run_ours(args):
         permr = torch.randperm(ran_d.shape[0], device=dev)
         ran_p, rnb_p = ran_d[permr].contiguous(), rnb_d[permr].contiguous()
         line["next_rows"] = next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, args.mesh)
+        line["large_meshes"] = large_mesh_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d)
         line["batch"] = batch_leg(pkg, torch, dev, cat, gal_p, ran_p, rnb_p)
         line["serving"] = serving_leg(pkg, torch, dev, cat, gal_p, ran_p, rnb_p, args.serve_requests)
     if ws == 1 and not args.no_cpu_baseline:
@@ -404,6 +435,57 @@ def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
                       "field_memory_gb": slots * slot / 1e9}
     ctx.set_field_chunk(0)
     ctx.close()
+    return out
+
+
+def large_mesh_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d):
+    """The benchmark catalog on 768^3 and 1024^3 meshes, where the resident order-4 field sets do
+    not fit the GPU (midpoint 161 slots of 1.82 / 4.3 GB, bisector 65): the midpoint with its g fields
+    in ranges and the bisector with its fields in blocks, beside the resident Yamamoto request; each
+    timed once after a warm-up run (CUDA events), with its mesh slots and the largest relative
+    difference of its monopole (P_0 and xi_0, which do not depend on the line of sight) from
+    Yamamoto's.  FFTs: cuFFT plane transforms over the occupied planes and cuFFT along x."""
+    out = {}
+    ctx = pkg.Context(dev.index)
+    ctx.set_fft_backend(5)
+    stream = torch.cuda.current_stream(dev)
+    try:
+        for N, mchunk, bchunk in ((768, 24, 16), (1024, 16, 8)):
+            slot = N * N * (N + 2) * 4
+            res = {}
+            for label, los, K, chunk, slots in (("yamamoto", "yamamoto", 0, 0, 16),
+                                                (f"midpoint order 4, g fields in ranges of {mchunk}", "midpoint", 4,
+                                                 mchunk, 2 + mchunk + 15),
+                                                (f"bisector order 4, fields in blocks of {bchunk}", "bisector", 4,
+                                                 bchunk, 1 + 2 * bchunk + 15)):
+                ctx.set_field_chunk(chunk)
+                p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=ELL_MAX,
+                                    los=los, order=K, compensate=True, precision=32, norm=1)
+                try:
+                    ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d)
+                    torch.cuda.synchronize(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                except pkg.BymError as e:
+                    res[label] = {"error": str(e), "mesh_slots": slots, "field_memory_gb": slots * slot / 1e9}
+                    continue
+                res[label] = {"ms_per_catalog": e0.elapsed_time(e1), "mesh_slots": slots,
+                              "field_memory_gb": slots * slot / 1e9, "_r": r}
+            ref = res.get("yamamoto", {}).get("_r")
+            for v in res.values():
+                r = v.pop("_r", None)
+                if r is not None and ref is not None:
+                    v["monopole_max_rel_diff_vs_yamamoto"] = float(max(
+                        np.max(np.abs(r["pk"][0] - ref["pk"][0]) / np.abs(ref["pk"][0])),
+                        np.max(np.abs(r["xi"][0] - ref["xi"][0])) / np.max(np.abs(ref["xi"][0]))))
+            out[f"{N}^3"] = res
+    finally:
+        ctx.set_field_chunk(0)
+        ctx.close()
     return out
 
 

@@ -591,6 +591,19 @@ static int get_geom(bym_ctx *c, const KernelSet &ks, int N, double L, const bym_
     g.count[i] = (int64_t)std::llround(hs[2 * i]);
     g.mean[i] = g.count[i] > 0 ? hs[2 * i + 1] / hs[2 * i] : 0.0;
   }
+  if (kind == 'k') {
+    // count = sum over the binned half-spectrum modes of their weight (1 on the kz = 0 and
+    // kz = N/2 planes, 2 elsewhere): half modes = (count + weight-1 modes) / 2
+    long long total = 0, w1 = 0;
+    for (int i = 0; i < b->nbins; ++i) total += g.count[i];
+    for (int iz : {0, N / 2})
+      for (int ix = 0; ix < N; ++ix)
+        for (int iy = 0; iy < N; ++iy) {
+          const long long nx = ix < N / 2 ? ix : ix - N, ny = iy < N / 2 ? iy : iy - N, nz = iz;
+          if (lut[(size_t)(nx * nx + ny * ny + nz * nz)] >= 0) ++w1;
+        }
+    g.half_binned = (total + w1) / 2;
+  }
   auto res = cache.emplace(key, std::move(g));
   *out = &res.first->second;
   return BYM_OK;
@@ -658,6 +671,8 @@ static int finish_results(bym_ctx *c, const Request &rq, const double *hstats, c
                           const Geom *kg, const Geom *rg, int NL, int nbk, int nbr, double h, bool cross = false,
                           double pk_scale = 1.0) {
   const bym_params *p = rq.p;
+  if (native_fft_fault(c->device))
+    return fail(c, BYM_E_CUDA, "a 512^3 x pass gave up waiting for a tile copy on this device; results are invalid");
   const double bad = hstats[3] + (cross ? hstats[11] : 0.0);
   if (bad > 0.0)
     return fail(c, BYM_E_OUT_OF_BOX, std::to_string((long long)bad) + " objects lie outside the box or are not finite");
@@ -718,9 +733,10 @@ static int plane_range(bym_ctx *c, cudaStream_t st, DevBufs &buf, const std::vec
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("plane range: ") + cudaGetErrorString(e));
   if (h[1] < h[0] || h[0] < 0 || h[1] >= N) return BYM_OK;
-  const int np = (h[1] - h[0] + 1 + 31) / 32 * 32;
+  // whole blocks of 32 planes (the x pass moves tiles in boxes of 32 rows)
+  const int x0 = h[0] / 32 * 32, x1 = std::min(N, (h[1] + 32) / 32 * 32), np = x1 - x0;
   if (np >= N) return BYM_OK;
-  out->x0 = std::min(h[0], N - np);
+  out->x0 = x0;
   out->np = np;
   return BYM_OK;
 }
@@ -894,25 +910,34 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
   auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
   auto slot_c = [&](int i) { return (T2 *)(slots + (long long)i * slot_reals); };
-  CUDA_TRY(cudaMemsetAsync(slots, 0, slot_bytes, st));
-  if (il) CUDA_TRY(cudaMemsetAsync(slot_r(ibase), 0, slot_bytes, st));
-  if (cross) CUDA_TRY(cudaMemsetAsync(slot_r(cbase), 0, slot_bytes, st));
+  // painted slots (delta, the interlaced and the second tracer's delta) need no zero-fill: the
+  // painter writes every cell
 
   // norms and painting
   const double esz = (double)sizeof(T), n3 = (double)N * N * N, nhalf = (double)N * N * (N / 2 + 1);
+  double *npart = nullptr;
+  TRY(alloc((void **)&npart, norm_scratch_bytes(c->nsm)));
   for (int w = 0; w < 4; ++w)
     if (cat4[w]) {
       ProfScope ps(c, st, "norm_reduce", catn[w] * ((w & 1) ? 20.0 : 16.0));
-      launch_norm_reduce(cat4[w], catnb[w], catn[w], w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), c->nsm, st);
+      launch_norm_reduce(cat4[w], catnb[w], catn[w], w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), npart, c->nsm,
+                         st);
     }
-  for (int w = 0; w < 4; ++w)
-    if (cat4[w]) {
-      ProfScope ps(c, st, "paint", catn[w] * 16.0 + n3 * esz);
-      launch_paint<T>(cat4[w], catn[w], w & 1, stats + 8 * (w >> 1), slot_r(w < 2 ? 0 : cbase), N, p->box_lo, inv_h,
-                      p->assign, c->nsm, st);
-      if (il)
-        launch_paint<T>(cat4[w], catn[w], w, stats, slot_r(ibase), N, p->box_lo, inv_h, p->assign, c->nsm, st, 0.5);
+  {
+    void *pscr = nullptr;
+    TRY(alloc(&pscr, paint_scratch_bytes(N, std::max(catn[0] + catn[1], catn[2] + catn[3]))));
+    for (int t = 0; t < (cross ? 2 : 1); ++t) {
+      const int w = 2 * t;
+      ProfScope ps(c, st, "paint", (catn[w] + catn[w + 1]) * 16.0 + n3 * esz);
+      CUDA_TRY(launch_paint<T>(cat4[w], catn[w], cat4[w + 1], catn[w + 1], stats + 8 * t, slot_r(t ? cbase : 0), N,
+                               p->box_lo, inv_h, p->assign, pscr, c->nsm, st));
     }
+    if (il) {
+      ProfScope ps(c, st, "paint", (catn[0] + catn[1]) * 16.0 + n3 * esz);
+      CUDA_TRY(launch_paint<T>(cat4[0], catn[0], cat4[1], catn[1], stats, slot_r(ibase), N, p->box_lo, inv_h,
+                               p->assign, pscr, c->nsm, st, 0.5));
+    }
+  }
   CUDA_TRY(cudaGetLastError());
   // forward plane transforms of painted and generated fields only over their occupied x planes
   // (library x pass backend; not in enqueued requests, which must not wait)
@@ -925,16 +950,11 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     TRY(plane_range<T>(c, st, buf, ds, N, &xr));
     xr.rows = fkind == 1;
   }
-  // zero-fill field slots before their generation: only the range's planes when there is one (the
-  // others are neither transformed nor read by the x pass)
-  auto zero_slots = [&](int first, int count) -> cudaError_t {
-    if (xr.np > 0 && xr.rows) {
-      const size_t plane = slot_bytes / N;
-      return cudaMemset2DAsync((char *)slot_r(first) + (size_t)xr.x0 * plane, slot_bytes, 0, (size_t)xr.np * plane,
-                               (size_t)count, st);
-    }
-    return cudaMemsetAsync(slot_r(first), 0, (size_t)count * slot_bytes, st);
-  };
+  // field generation writes every value of the x planes [gx0, gx0 + gnp): the occupied range when
+  // the x pass reads only the range's rows (the other planes are neither transformed nor read),
+  // else every plane
+  const int gx0 = (xr.np > 0 && xr.rows) ? xr.x0 : 0, gnp = (xr.np > 0 && xr.rows) ? xr.np : N;
+  const long long gvals = (long long)gnp * N * (N + 2);
   static const char *kLosName[4] = {"yamamoto", "midpoint", "bisector", "midpoint_even"};
   const std::string los_name = kLosName[p->los];
   const std::string n_gen = "gen_fields_" + los_name, n_kc = "kcontract_" + los_name, n_xi = "xi_lag_" + los_name;
@@ -942,21 +962,18 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
 
   // field generation (streamed ranges generate their own fields below)
   if (!chunk) {
-    const long long ncell = (long long)N * N * N;
-    ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * n3 * esz);
-    CUDA_TRY(zero_slots(1, nf));
-    CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
-                    slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+    ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * gvals * esz * ((cross || il) ? 2.0 : 1.0));
+    CUDA_TRY(launch(K.gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
+                    slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp));
     if (cross) {   // tracer B's fields from its delta
-      CUDA_TRY(zero_slots(cbase + 1, nf));
-      CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(cbase),
-                      slot_r(cbase + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
+      CUDA_TRY(launch(K.gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(cbase),
+                      slot_r(cbase + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0,
+                      gnp));
     }
     if (il) {   // the same fields on the shifted mesh, from its delta and node positions
-      CUDA_TRY(zero_slots(ibase + 1, nf));
-      CUDA_TRY(launch(K.gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(ibase),
+      CUDA_TRY(launch(K.gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(ibase),
                       slot_r(ibase + 1), slot_reals, N, p->box_lo[0] + 0.5 * h, p->box_lo[1] + 0.5 * h,
-                      p->box_lo[2] + 0.5 * h, h, inv_r0));
+                      p->box_lo[2] + 0.5 * h, h, inv_r0, gx0, gnp));
     }
   }
   if (il) {
@@ -1013,7 +1030,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
       if (p->los == BYM_LOS_YAMAMOTO && want_pk) {
         // the two endpoint lines of sight: F[Y delta_A] conj(D_B) + F[Y delta_B] conj(D_A), halved on the host
         pk_scale = 0.5;
-        ProfScope ps(c, st, n_kc.c_str(), 2.0 * (nlm + 1.0) * cplx);
+        ProfScope ps(c, st, n_kc.c_str(), 2.0 * (nlm + 1.0) * 2.0 * esz * (double)kg->half_binned);
         CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(cbase), N,
                         (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
         CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(cbase + 1), cslot, (const T2 *)slot_c(0),
@@ -1041,7 +1058,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
                           (const T *)slot_r(1), slot_reals, slot_r(1 + nf), N, tscale));
         }
         TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm, tn));
-        ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
+        ProfScope ps(c, st, n_kc.c_str(), nlm * 2.0 * esz * (double)kg->half_binned);
         CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
                         (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
       }
@@ -1049,7 +1066,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   } else if (p->los == BYM_LOS_YAMAMOTO) {
     if (!il) TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 0, 1 + nf, tn, &xr));
     if (want_pk) {
-      ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * cplx);
+      ProfScope ps(c, st, n_kc.c_str(), (nlm + 1.0) * 2.0 * esz * (double)kg->half_binned);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
     }
@@ -1071,11 +1088,9 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     for (size_t q = 0; q < CK->ranges.size(); ++q) {
       const int f0 = CK->ranges[q].first, nq = CK->ranges[q].second - f0;
       {
-        ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * n3 * esz);
-        CUDA_TRY(zero_slots(2, nq));
-        CUDA_TRY(launch(CK->gen[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_gen), 256, 0, st,
-                        (const T *)slot_r(1), slot_r(2), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h,
-                        inv_r0));
+        ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * gvals * esz);
+        CUDA_TRY(launch(CK->gen[q], grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(1),
+                        slot_r(2), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp));
       }
       TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 2, nq, scale + f0, invw, tn, &xr)));
       if (want_xi) {
@@ -1092,7 +1107,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     }
     if (want_pk) {
       TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, xbase, nlm, tn));
-      ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
+      ProfScope ps(c, st, n_kc.c_str(), nlm * 2.0 * esz * (double)kg->half_binned);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(xbase), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
     }
@@ -1120,7 +1135,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
                         (const T *)slot_r(1), slot_reals, slot_r(1 + nf), N, tscale));
       }
       TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, 1 + nf, nlm, tn));
-      ProfScope ps(c, st, n_kc.c_str(), nlm * cplx);
+      ProfScope ps(c, st, n_kc.c_str(), nlm * 2.0 * esz * (double)kg->half_binned);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1 + nf), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)nullptr));
     }
@@ -1131,11 +1146,9 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     auto make_block = [&](int q, int base) -> int {
       const int q0 = CK->ranges[q].first, nq = CK->ranges[q].second - q0;
       {
-        ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * n3 * esz);
-        CUDA_TRY(zero_slots(base, nq));
-        CUDA_TRY(launch(CK->gen[q], grid_of((long long)N * N * N, c->nsm, tn.per_sm_gen), 256, 0, st,
-                        (const T *)slot_r(0), slot_r(base), slot_reals, N, p->box_lo[0], p->box_lo[1],
-                        p->box_lo[2], h, inv_r0));
+        ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * gvals * esz);
+        CUDA_TRY(launch(CK->gen[q], grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0),
+                        slot_r(base), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp));
       }
       return fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, base, nq, tn, &xr);
     };
@@ -1177,7 +1190,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
                       (const T *)slot_r(1 + nf), slot_reals, N, rg->jm, rg->full, (const int *)rg->lut, nbr, rsum,
                       1.0 / ((double)N * N * N), tscale));
     } else {
-      ProfScope ps(c, st, n_kc.c_str(), (double)nf * cplx);
+      ProfScope ps(c, st, n_kc.c_str(), (double)nf * 2.0 * esz * (double)kg->half_binned);
       CUDA_TRY(launch(K.kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(0), N,
                       (const int *)kg->lut, nbk, ksum, (T2 *)nullptr, 0LL, (const T *)invw));
     }
@@ -1318,21 +1331,27 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
   TRY(alloc((void **)&slots, (size_t)nslots * slot_bytes));
   auto slot_r = [&](int i) { return slots + (long long)i * slot_reals; };
   auto slot_c = [&](int i) { return (T2 *)(slots + (long long)i * slot_reals); };
-  CUDA_TRY(cudaMemsetAsync(slot_r(0), 0, slot_bytes, st));
-  CUDA_TRY(cudaMemsetAsync(slot_r(cbase), 0, slot_bytes, st));
   const double esz = (double)sizeof(T), n3 = (double)N * N * N, cplx = 2.0 * esz * N * N * (N / 2 + 1);
+  double *npart = nullptr;
+  TRY(alloc((void **)&npart, norm_scratch_bytes(c->nsm)));
+  long long catn[4];
+  for (int w = 0; w < 4; ++w) catn[w] = cat4[w] ? cats[w]->n : 0;
   for (int w = 0; w < 4; ++w)
     if (cat4[w]) {
-      ProfScope ps(c, st, "norm_reduce", cats[w]->n * ((w & 1) ? 20.0 : 16.0));
-      launch_norm_reduce(cat4[w], catnb[w], cats[w]->n, w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), c->nsm,
+      ProfScope ps(c, st, "norm_reduce", catn[w] * ((w & 1) ? 20.0 : 16.0));
+      launch_norm_reduce(cat4[w], catnb[w], catn[w], w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), npart, c->nsm,
                          st);
     }
-  for (int w = 0; w < 4; ++w)
-    if (cat4[w]) {
-      ProfScope ps(c, st, "paint", cats[w]->n * 16.0 + n3 * esz);
-      launch_paint<T>(cat4[w], cats[w]->n, w & 1, stats + 8 * (w >> 1), slot_r(w < 2 ? 0 : cbase), N, p->box_lo,
-                      inv_h, p->assign, c->nsm, st);
+  {
+    void *pscr = nullptr;
+    TRY(alloc(&pscr, paint_scratch_bytes(N, std::max(catn[0] + catn[1], catn[2] + catn[3]))));
+    for (int t = 0; t < 2; ++t) {
+      const int w = 2 * t;
+      ProfScope ps(c, st, "paint", (catn[w] + catn[w + 1]) * 16.0 + n3 * esz);
+      CUDA_TRY(launch_paint<T>(cat4[w], catn[w], cat4[w + 1], catn[w + 1], stats + 8 * t, slot_r(t ? cbase : 0), N,
+                               p->box_lo, inv_h, p->assign, pscr, c->nsm, st));
     }
+  }
   CUDA_TRY(cudaGetLastError());
   XRange xr;   // forward plane transforms over the occupied x planes (plane-transform backends)
   const int fkind = fft_kind(c, N, p->precision, tn);
@@ -1341,19 +1360,14 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
     xr.rows = fkind == 1;
   }
   {
-    const long long ncell = (long long)N * N * N;
-    ProfScope ps(c, st, "gen_fields_odd", 2.0 * (1.0 + nf) * n3 * esz);
-    for (int base : {0, cbase}) {
-      if (xr.np > 0 && xr.rows) {   // only the range's planes: the others are neither transformed nor read
-        const size_t plane = slot_bytes / N;
-        CUDA_TRY(cudaMemset2DAsync((char *)slot_r(base + 1) + (size_t)xr.x0 * plane, slot_bytes, 0,
-                                   (size_t)xr.np * plane, (size_t)nf, st));
-      } else {
-        CUDA_TRY(cudaMemsetAsync(slot_r(base + 1), 0, (size_t)nf * slot_bytes, st));
-      }
-      CUDA_TRY(launch(os->gen_fields, grid_of(ncell, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(base),
-                      slot_r(base + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0));
-    }
+    // every value of the planes [gx0, gx0 + gnp) of every field (see run_typed)
+    const int gx0 = (xr.np > 0 && xr.rows) ? xr.x0 : 0, gnp = (xr.np > 0 && xr.rows) ? xr.np : N;
+    const long long gvals = (long long)gnp * N * (N + 2);
+    ProfScope ps(c, st, "gen_fields_odd", 2.0 * (1.0 + nf) * gvals * esz);
+    for (int base : {0, cbase})
+      CUDA_TRY(launch(os->gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(base),
+                      slot_r(base + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0,
+                      gnp));
   }
   const int f0 = bis ? 1 : 0, cnt = bis ? nf : 1 + nf;
   TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn, &xr));
@@ -1395,7 +1409,7 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
                         (const T *)slot_r(1), slot_reals, slot_r(xbase), N, tscale));
       }
       TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, xbase, nlm, tn));
-      ProfScope ps(c, st, "kcontract_midpoint_odd", nlm * cplx);
+      ProfScope ps(c, st, "kcontract_midpoint_odd", nlm * 2.0 * esz * (double)kg->half_binned);
       CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(xbase), cslot, N, (const int *)kg->lut, nbk,
                       ksum));
     }
@@ -1403,7 +1417,7 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (want_pk) {
       // [Q^AB - Q^BA], halved on the host: F^B with D_A (+), F^A with D_B (-)
       pk_scale = 0.5;
-      ProfScope ps(c, st, "kcontract_yamamoto_odd", 2.0 * (nlm + 1.0) * cplx);
+      ProfScope ps(c, st, "kcontract_yamamoto_odd", 2.0 * (nlm + 1.0) * 2.0 * esz * (double)kg->half_binned);
       CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(cbase + 1), cslot, (const T2 *)slot_c(0),
                       N, (const int *)kg->lut, nbk, ksum, (const T *)invw, (T)1));
       CUDA_TRY(launch(os->kcontract, gk, 256, smk, st, (const T2 *)slot_c(1), cslot, (const T2 *)slot_c(cbase), N,
@@ -1975,6 +1989,11 @@ int bym_shot_noise(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, c
   }
   cudaMemsetAsync(stats, 0, 8 * sizeof(double), st);
   const double inv_h = p->n_mesh / p->box_len;
+  double *npart = nullptr;
+  if (buf.alloc((void **)&npart, norm_scratch_bytes(c->nsm)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BYM_E_NOMEM, "device allocation failed");
+  }
   for (int w = 0; w < 2; ++w) {
     const bym_catalog *cat = cats[w];
     if (!cat || cat->n <= 0) continue;
@@ -1992,7 +2011,7 @@ int bym_shot_noise(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, c
       d4 = (const float4 *)a;
       dn = (const float *)b;
     }
-    launch_norm_reduce(d4, dn, cat->n, w, p->box_lo, inv_h, p->n_mesh, stats, c->nsm, st);
+    launch_norm_reduce(d4, dn, cat->n, w, p->box_lo, inv_h, p->n_mesh, stats, npart, c->nsm, st);
   }
   double hs[8];
   cudaError_t e = cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st);
@@ -2108,11 +2127,14 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
       if (n == "spec_mul" && ms < bspec) bspec = ms, best.per_sm_spec = f;
     }
   }
-  // transforms: library kernels against cuFFT, then cuFFT's batch size
+  // transforms: library kernels against cuFFT, then cuFFT's batch size.  Every kernel whose work
+  // depends on the choice is counted: the transforms, the spectral product, the occupied-plane scan
+  // and the field generation (which writes only the occupied planes when the x pass reads only those)
   auto fft_ms = [](const std::map<std::string, ProfEntry> &m) {
     double s = 0.0;
     for (auto &kv : m)
-      if (kv.first.rfind("cufft", 0) == 0 || kv.first.rfind("fft_native", 0) == 0 || kv.first == "spec_mul")
+      if (kv.first.rfind("cufft", 0) == 0 || kv.first.rfind("fft_native", 0) == 0 || kv.first == "spec_mul" ||
+          kv.first == "plane_range" || kv.first.rfind("gen_fields", 0) == 0)
         s += kv.second.ms;
     return s;
   };

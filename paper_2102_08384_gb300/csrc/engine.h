@@ -22,6 +22,7 @@ struct Geom {
   int jm = 0, full = 0;         // lag cube half-width (r bins only)
   std::vector<int64_t> count;   // modes / lag cells per bin (full grid)
   std::vector<double> mean;     // mean |k| or |Delta| per bin
+  long long half_binned = 0;    // k bins: half-spectrum modes in some bin (the modes a contraction reads)
 };
 
 struct Request {

@@ -26,6 +26,8 @@
 // column transform.  Transforms are unnormalised, with the e^{-i k.x} sign for
 // the forward direction, like cuFFT's.
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -123,13 +125,20 @@ __device__ __forceinline__ void idft(float2 (&v)[L]) {  // e^{+i} direction, unn
 
 __device__ __forceinline__ int col_b(int j) { return j ? 32 - j : 16; }
 
+// Exchange storage of a 16-thread group, 32 x 16 complex slots (a, b): a padded row-major
+// buffer (row stride ES, bank-conflict free).
+struct PadEx {
+  float2 *E;
+  __device__ __forceinline__ float2 &operator()(int a, int b) const { return E[a * ES + b]; }
+};
+
 // Forward 512-point DFT by a 16-thread group.  In: v[m] = x[16 m + j].
 // Out: A[k2] = X[ka + 32 k2], B[k2] = X[kb + 32 k2].  TW[k1 * ES + j] = W512^(k1 j);
-// E: this group's exchange buffer, EX float2, or EX / 2 with HALF (the exchange then
-// runs in two rounds, k1 < 16 then k1 >= 16); gm: this group's lane mask.
-template <bool HALF = false>
+// ex: this group's exchange storage, slots (a, b) with a < 32, b < 16 (a < 16 with HALF: the
+// exchange then runs in two rounds, k1 < 16 then k1 >= 16); gm: this group's lane mask.
+template <bool HALF = false, class EXS>
 __device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
-                                       const float2 *__restrict__ TW, float2 *E) {
+                                       const float2 *__restrict__ TW, const EXS &ex) {
   dft<32, 5>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], TW[k1 * ES + j]);
@@ -137,35 +146,41 @@ __device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 
   __syncwarp(gm);
   if (HALF) {
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) E[k1 * ES + j] = v[k1];
+    for (int k1 = 0; k1 < 16; ++k1) ex(k1, j) = v[k1];
     __syncwarp(gm);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) A[i] = E[ka * ES + i];
+    for (int i = 0; i < 16; ++i) A[i] = ex(ka, i);
     __syncwarp(gm);
 #pragma unroll
-    for (int k1 = 16; k1 < 32; ++k1) E[(k1 - 16) * ES + j] = v[k1];
+    for (int k1 = 16; k1 < 32; ++k1) ex(k1 - 16, j) = v[k1];
     __syncwarp(gm);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) B[i] = E[(kb - 16) * ES + i];
+    for (int i = 0; i < 16; ++i) B[i] = ex(kb - 16, i);
   } else {
 #pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) E[k1 * ES + j] = v[k1];
+    for (int k1 = 0; k1 < 32; ++k1) ex(k1, j) = v[k1];
     __syncwarp(gm);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      A[i] = E[ka * ES + i];
-      B[i] = E[kb * ES + i];
+      A[i] = ex(ka, i);
+      B[i] = ex(kb, i);
     }
   }
   dft<16, 4>(A);
   dft<16, 4>(B);
 }
 
+template <bool HALF = false>
+__device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
+                                       const float2 *__restrict__ TW, float2 *E) {
+  fwd512<HALF>(v, A, B, j, gm, TW, PadEx{E});
+}
+
 // Inverse (e^{+i}, unnormalised) 512-point DFT by a 16-thread group, from the
 // layout fwd512 produces to v[m] = x[16 m + j].
-template <bool HALF = false>
+template <bool HALF = false, class EXS>
 __device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
-                                       const float2 *__restrict__ TW, float2 *E) {
+                                       const float2 *__restrict__ TW, const EXS &ex) {
   idft<16, 4>(A);
   idft<16, 4>(B);
   const int ka = j, kb = col_b(j);
@@ -177,27 +192,33 @@ __device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 
   __syncwarp(gm);
   if (HALF) {
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) E[ka * ES + n1] = A[n1];
+    for (int n1 = 0; n1 < 16; ++n1) ex(ka, n1) = A[n1];
     __syncwarp(gm);
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) v[k1] = E[k1 * ES + j];
+    for (int k1 = 0; k1 < 16; ++k1) v[k1] = ex(k1, j);
     __syncwarp(gm);
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) E[(kb - 16) * ES + n1] = B[n1];
+    for (int n1 = 0; n1 < 16; ++n1) ex(kb - 16, n1) = B[n1];
     __syncwarp(gm);
 #pragma unroll
-    for (int k1 = 16; k1 < 32; ++k1) v[k1] = E[(k1 - 16) * ES + j];
+    for (int k1 = 16; k1 < 32; ++k1) v[k1] = ex(k1 - 16, j);
   } else {
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) {
-      E[ka * ES + n1] = A[n1];
-      E[kb * ES + n1] = B[n1];
+      ex(ka, n1) = A[n1];
+      ex(kb, n1) = B[n1];
     }
     __syncwarp(gm);
 #pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) v[k1] = E[k1 * ES + j];
+    for (int k1 = 0; k1 < 32; ++k1) v[k1] = ex(k1, j);
   }
   idft<32, 5>(v);
+}
+
+template <bool HALF = false>
+__device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
+                                       const float2 *__restrict__ TW, float2 *E) {
+  inv512<HALF>(A, B, v, j, gm, TW, PadEx{E});
 }
 
 // Two spectra from the transform of z = a + i b (a, b real sequences):
@@ -648,6 +669,273 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// x pass through the tensor memory accelerator (the x pass every caller uses).
+// The columns of a half-spectrum slot are taken in the flattened order f = ky HZ + kz (x stride
+// NM HZ complex values).  A tile is XC = 16 consecutive columns -- 128 contiguous bytes per
+// row, every tile starting on a 128-byte boundary whatever its ky -- and all 512 rows; a slot
+// has 131584 / 16 = 8224 tiles.  Tiles are loaded and stored by TMA in boxes of 32 rows with the
+// 128-byte swizzle (16-byte chunk index XOR row % 8), so the threads issue no copy or store
+// instructions of their own.  A 16-thread group transforms one column; the exchange of the
+// 512-point engine runs in place in that column's own storage (slot (a, b) at row
+// 16 a + (b ^ (a % 16))), which keeps every shared access of a warp at two wavefronts.
+// Persistent: one 256-thread CTA per SM.  Modes 0 and 1 keep three tile buffers (load of the
+// next tile, transform of this one, store of the previous one in flight); mode 2 keeps two data
+// buffers and the tile of D, walks the tile positions and, at each one, every field of the launch,
+// so D is read once per launch.  Waits on the tile barriers give up after about two seconds,
+// record a fault in *fault and end the kernel once the copies in flight have landed.
+// ---------------------------------------------------------------------------
+constexpr int XC = 16;                              // columns per tile
+constexpr int XBR = 32;                             // rows per TMA box
+constexpr long long XNCOL = (long long)NM * HZ;     // columns per slot
+constexpr long long XNT = XNCOL / XC;               // tiles per slot
+constexpr int XTILE = NM * XC * 8;                  // bytes per tile buffer
+static_assert(XNCOL % XC == 0, "a slot is a whole number of tiles");
+
+struct XtLayout {                                   // dynamic shared memory, from a 1024-byte aligned base
+  static constexpr int NBUF = 3;                    // modes 0, 1: three tiles; mode 2: two tiles + the D tile
+  static constexpr size_t TW_OFF = (size_t)NBUF * XTILE;
+  static constexpr size_t W1_OFF = TW_OFF + sizeof(float2) * EX;
+  static constexpr size_t BAR_OFF = W1_OFF + sizeof(float) * NM;
+  static constexpr size_t BYTES = BAR_OFF + 8 * NBUF + 1024;
+};
+
+// byte offset of element (row x, column c) of a tile written with the 128-byte swizzle
+__device__ __forceinline__ unsigned xt_off(int x, int c) {
+  return (unsigned)(x * 128 + ((((c >> 1) ^ x) & 7) << 4) + ((c & 1) << 3));
+}
+
+struct XtCol {                                      // one column of a swizzled tile
+  unsigned char *tile;
+  int c;
+  __device__ __forceinline__ float2 &at(int x) const { return *(float2 *)(tile + xt_off(x, c)); }
+  __device__ __forceinline__ float2 &operator()(int a, int b) const { return at(16 * a + (b ^ (a & 15))); }
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase of the given parity to complete; false after about two seconds
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 2000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load(unsigned char *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store(const CUtensorMap *map, int c0, int c1, int c2, const unsigned char *src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+               ::"l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1)
+    fft512_xt(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmd, int nslots,
+              const float2 *__restrict__ gtw, const double *__restrict__ scale, const float *__restrict__ invw,
+              int xlo, int xhi, unsigned *__restrict__ fault) {
+  using L = XtLayout;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // 1024-byte aligned base (the 128-byte swizzle repeats every 8 rows); pointer arithmetic on the
+  // shared array keeps every access below a shared-memory instruction
+  unsigned char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+  float2 *TW = (float2 *)(sm + L::TW_OFF);
+  float *W1 = (float *)(sm + L::W1_OFF);
+  unsigned long long *bar = (unsigned long long *)(sm + L::BAR_OFF);
+  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
+  const unsigned gm = 0xFFFFu << (tid & 16);
+  const int ka = j, kb = col_b(j);
+  const int lo = MODE == 1 ? 0 : xlo, hi = MODE == 1 ? NM : xhi;   // rows read from HBM
+  const bool part = lo > 0 || hi < NM;
+  const long long nunits = MODE == 2 ? XNT : (long long)nslots * XNT;
+  const int nf = MODE == 2 ? nslots : 1;
+  constexpr int NDB = MODE == 2 ? 2 : 3;            // data buffers
+
+  if (tid == 0) {
+    for (int b = 0; b < L::NBUF; ++b) mbar_init(bar + b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < EX; i += blockDim.x) TW[i] = gtw[i];
+  if (MODE == 2 && invw)
+    for (int i = tid; i < NM; i += blockDim.x) W1[i] = invw[i];
+  __syncthreads();
+
+  // item i = (unit u, field f): modes 0, 1 take the tiles of every slot (f = 0), mode 2 the
+  // positions with every field; data buffer i % NDB, whose barrier completes once per use
+  auto issue_data = [&](long long u, int f, int b) {
+    const int slot = MODE == 2 ? f : (int)(u / XNT);
+    const int c0 = (int)((MODE == 2 ? u : u % XNT) * (2 * XC));
+    mbar_expect_tx(bar + b, (unsigned)(hi - lo) * 128u);
+    for (int x0 = lo; x0 < hi; x0 += XBR) tma_load(sm + (size_t)b * XTILE + (size_t)x0 * 128, &tm, c0, x0, slot, bar + b);
+  };
+  auto issue_d = [&](long long u) {
+    mbar_expect_tx(bar + 2, (unsigned)NM * 128u);
+    for (int x0 = 0; x0 < NM; x0 += XBR)
+      tma_load(sm + (size_t)2 * XTILE + (size_t)x0 * 128, &tmd, (int)(u * (2 * XC)), x0, 0, bar + 2);
+  };
+  // pending loads (bit b: buffer b), and the parity each one completes with, for a clean exit
+  unsigned pend = 0, ppar = 0;
+  long long u = blockIdx.x;
+  if (tid == 0 && u < nunits) {
+    issue_data(u, 0, 0);
+    pend |= 1u;
+    if (MODE == 2) {
+      issue_d(u);
+      pend |= 4u;
+    }
+  }
+  bool ok = true;
+  long long i = 0;
+  for (long long k = 0; u < nunits && ok; u += gridDim.x, ++k) {
+    for (int f = 0; f < nf && ok; ++f, ++i) {
+      const int b = (int)(i % NDB);
+      const unsigned par = (unsigned)((i / NDB) & 1);
+      bool w = mbar_wait(bar + b, par);
+      if (MODE == 2 && f == 0) w = w && mbar_wait(bar + 2, (unsigned)(k & 1));
+      ok = __syncthreads_and(w);
+      if (!ok) break;
+      if (tid == 0) {
+        pend &= ~(1u << b);
+        if (MODE == 2 && f == 0) pend &= ~4u;
+      }
+      unsigned char *tile = sm + (size_t)b * XTILE;
+      if (MODE != 1 && part) {                       // rows outside [lo, hi) hold no painted value
+        for (int r = tid; r < NM - (hi - lo); r += blockDim.x) {
+          const int x = r < lo ? r : r + (hi - lo);
+          float4 *row = (float4 *)(tile + (size_t)x * 128);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {                                // prefetch the next item
+        long long un = u;
+        int fn = f + 1;
+        if (fn >= nf) {
+          un = u + gridDim.x;
+          fn = 0;
+        }
+        if (un < nunits) {
+          const int bn = (int)((i + 1) % NDB);
+          if (MODE == 2)
+            bulk_wait_read<0>();                     // the store of item i - 1 (buffer bn) has read its tile
+          else
+            bulk_wait_read<1>();                     // the store of item i - 2 (buffer bn) has read its tile
+          issue_data(un, fn, bn);
+          pend |= 1u << bn;
+          ppar = (ppar & ~(1u << bn)) | ((unsigned)(((i + 1) / NDB) & 1) << bn);
+        }
+      }
+      const int slot = MODE == 2 ? f : (int)(u / XNT);
+      const long long tl = MODE == 2 ? u : u % XNT;
+      const XtCol col{tile, g};
+      float2 v[32], As[16], Bs[16];
+      const float s = MODE == 2 ? (float)scale[f] : 1.f;
+      if (MODE == 1) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          As[k2] = col.at(ka + 32 * k2);
+          Bs[k2] = col.at(kb + 32 * k2);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) v[m] = col.at(16 * m + j);
+        fwd512(v, As, Bs, j, gm, TW, col);
+      }
+      if (MODE == 2) {
+        const XtCol dcol{sm + (size_t)2 * XTILE, g};
+        if (f == 0) {
+          // D <- conj(D) W^-2 in place, once per position: every thread rewrites exactly the
+          // entries kx = ka + 32 k2, kb + 32 k2 of its column that it reads below
+          const long long fc = tl * XC + g;
+          const int ky = (int)(fc / HZ), kz = (int)(fc % HZ);
+          const float cyz = invw ? W1[ky] * W1[kz] : 1.f;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const int kxa = ka + 32 * k2, kxb = kb + 32 * k2;
+            float wa = 1.f, wb = 1.f;
+            if (invw) {
+              wa = W1[kxa] * cyz;
+              wb = W1[kxb] * cyz;
+            }
+            dcol.at(kxa) = cscale(cconj(dcol.at(kxa)), wa * wa);
+            dcol.at(kxb) = cscale(cconj(dcol.at(kxb)), wb * wb);
+          }
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          As[k2] = cscale(cmul(As[k2], dcol.at(ka + 32 * k2)), s);
+          Bs[k2] = cscale(cmul(Bs[k2], dcol.at(kb + 32 * k2)), s);
+        }
+      }
+      if (MODE == 0) {
+        __syncwarp(gm);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          col.at(ka + 32 * k2) = As[k2];
+          col.at(kb + 32 * k2) = Bs[k2];
+        }
+      } else {
+        inv512(As, Bs, v, j, gm, TW, col);
+        __syncwarp(gm);
+#pragma unroll
+        for (int m = 0; m < 32; ++m) col.at(16 * m + j) = v[m];
+      }
+      fence_async_smem();                            // these writes (and D's rewrite) before async-proxy use
+      __syncthreads();
+      if (tid == 0) {
+        for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, (int)(tl * (2 * XC)), x0, slot, tile + (size_t)x0 * 128);
+        bulk_commit();
+        if (MODE == 2 && f == nf - 1 && u + gridDim.x < nunits) {   // D of the next position
+          issue_d(u + gridDim.x);
+          pend |= 4u;
+          ppar = (ppar & ~4u) | ((unsigned)((k + 1) & 1) << 2);
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    if (!ok) {
+      *(volatile unsigned *)fault = 1u;
+      for (int b = 0; b < L::NBUF; ++b)              // let the loads in flight land before leaving
+        if (pend & (1u << b)) mbar_wait(bar + b, (ppar >> b) & 1u);
+    }
+    bulk_wait_all();
+  }
+}
+
 float2 *g_twiddles[64] = {nullptr};
 std::mutex g_tw_mu;
 
@@ -727,18 +1015,54 @@ int sm_count(int dev) {
   return n[dev];
 }
 
+// per device: a word of mapped host memory that an x pass sets when a tile wait gives up
+// (device view g_xfault, host view g_xfault_host: the host reads it without a CUDA call)
+unsigned *g_xfault[64] = {nullptr};
+volatile unsigned *g_xfault_host[64] = {nullptr};
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// TMA map of n half-spectrum slots from base b: dims (2 NM HZ floats of an x-plane, NM planes, n slots),
+// boxes of 32 floats (16 complex columns, 128 bytes) x 32 planes x 1 slot, 128-byte swizzle
+cudaError_t slot_map(CUtensorMap *m, float *b, long long slot_reals, int n) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * XNCOL), (cuuint64_t)NM, (cuuint64_t)n};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * XNCOL * sizeof(float)), (cuuint64_t)(slot_reals * sizeof(float))};
+  const cuuint32_t box[3] = {2 * XC, XBR, 1}, estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, b, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int MODE>
 cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const float *D, const double *scale,
                   const float *invw, cudaStream_t st, int xlo = 0, int xhi = NM) {
-  using X = XShape<XTC>;
+  if (xlo < 0 || xhi > NM || xlo >= xhi || xlo % XBR || xhi % XBR) return cudaErrorInvalidValue;
+  if (((unsigned long long)b & 15ull) || (MODE == 2 && ((unsigned long long)D & 15ull)) ||
+      (slot_reals * sizeof(float)) % 16)
+    return cudaErrorInvalidValue;
   int dev = 0;
   cudaGetDevice(&dev);
-  const long long ntiles = X::NPOS * n;
-  // mode 2 distributes tile positions (each with all n fields), modes 0 and 1 tiles
-  const long long units = MODE == 2 ? X::NPOS : ntiles;
-  const long long grid = std::min<long long>(units, (long long)sm_count(dev) * (MODE == 2 ? X::PER_SM2 : X::PER_SM01));
-  fft512_x<MODE, XTC><<<(unsigned)grid, X::NT, MODE == 2 ? X::SMEM2 : X::SMEM01, st>>>(
-      (float2 *)b, slot_reals / 2, ntiles, tw, (const float2 *)D, scale, invw, xlo, xhi);
+  CUtensorMap tm, tmd;
+  cudaError_t e = slot_map(&tm, b, slot_reals, n);
+  if (e == cudaSuccess) e = slot_map(&tmd, MODE == 2 ? (float *)D : b, slot_reals, 1);
+  if (e != cudaSuccess) return e;
+  const long long units = MODE == 2 ? XNT : XNT * n;
+  const long long grid = std::min<long long>(units, (long long)sm_count(dev));
+  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmd, n, tw, scale, invw, xlo, xhi,
+                                                                g_xfault[dev]);
   return cudaGetLastError();
 }
 
@@ -757,16 +1081,19 @@ cudaError_t native_fft_prepare() {
   if (!attrs[dev]) {
     if ((e = plane_attrs<8>()) != cudaSuccess) return e;
     if ((e = plane_attrs<16>()) != cudaSuccess) return e;
-    using X = XShape<XTC>;
-    if ((e = cudaFuncSetAttribute(fft512_x<0, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM01)) !=
-        cudaSuccess)
+    const int xs = (int)XtLayout::BYTES;
+    if ((e = cudaFuncSetAttribute(fft512_xt<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, xs)) != cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<1, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM01)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(fft512_xt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, xs)) != cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(fft512_x<2, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM2)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(fft512_xt<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, xs)) != cudaSuccess)
       return e;
+    if (!tensor_map_encoder()) return cudaErrorNotSupported;
+    unsigned *hf = nullptr;
+    if ((e = cudaHostAlloc((void **)&hf, sizeof(unsigned), cudaHostAllocMapped)) != cudaSuccess) return e;
+    *hf = 0;
+    if ((e = cudaHostGetDevicePointer((void **)&g_xfault[dev], hf, 0)) != cudaSuccess) return e;
+    g_xfault_host[dev] = hf;
     attrs[dev] = true;
   }
   return cudaSuccess;
@@ -826,6 +1153,8 @@ cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int f
   }
   return e;
 }
+
+bool native_fft_fault(int dev) { return dev >= 0 && dev < 64 && g_xfault_host[dev] && *g_xfault_host[dev] != 0u; }
 
 cudaError_t native_fft_convolve(float *slots, long long slot_reals, int first, int count, const float *D,
                                 const double *scale, const float *invw, int cluster, cudaStream_t st) {

@@ -159,17 +159,35 @@ void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldI
     Jmax = std::max(Jmax, list[i].J);
     amax = std::max(amax, list[i].alpha);
   }
+  // one thread per value of the padded rows of the x planes [x0, x0 + np): every value of those
+  // planes of every field is written (zero where delta is zero and in the row padding), so the
+  // field slots need no zero-fill; a warp stores 32 consecutive values of a row per field
   o << "extern \"C\" __global__ void __launch_bounds__(256, 2) " << name << "(const real* __restrict__ delta,"
        " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
-       " double inv_r0) {\n";
-  o << "  const long long ncell = (long long)N * N * N;\n";
-  o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;"
-       " c += (long long)gridDim.x * blockDim.x) {\n";
-  o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
-  o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
-  o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
-  o << "    const real d = delta[off];\n";
-  o << "    if (d == (real)0) continue;   // field slots are zero-filled before the launch\n";
+       " double inv_r0, int x0, int np) {\n";
+  // a warp takes 32 consecutive values; when all of them are zero (most warps: the survey fills a
+  // fraction of each occupied plane) its lanes write the zeros of every field as 16-byte stores
+  // (the 32 values start on a 128-byte boundary: N(N+2) and the slot stride are multiples of 8)
+  const int nf = f1 - f0;
+  o << "  const long long row = N + 2, plane = (long long)N * row, base = (long long)x0 * plane;\n";
+  o << "  const long long nval = (long long)np * plane;\n";
+  o << "  const int lane = threadIdx.x & 31;\n";
+  o << "  for (long long w0 = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < nval;"
+       " w0 += (long long)gridDim.x * blockDim.x) {\n";
+  o << "    const long long c = w0 + lane;\n";
+  o << "    const long long off = base + c;\n";
+  o << "    const int iz = (int)(c % row); const long long t = c / row;\n";
+  o << "    const int iy = (int)(t % N); const int ix = x0 + (int)(t / N);\n";
+  o << "    const real d = (c < nval && iz < N) ? delta[off] : (real)0;\n";
+  o << "    if (__all_sync(0xffffffffu, d == (real)0) && w0 + 32 <= nval) {\n";
+  o << "      constexpr int VPW = 32 * (int)sizeof(real) / 16;   // 16-byte vectors per field\n";
+  o << "      for (int q = lane; q < " << nf << " * VPW; q += 32)\n";
+  o << "        ((real4z*)(out + (long long)(q / VPW) * slot + base + w0))[q % VPW] = real4z{};\n";
+  o << "      continue;\n    }\n";
+  o << "    if (c >= nval) continue;\n";
+  o << "    if (d == (real)0) {\n";
+  for (int i = f0; i < f1; ++i) o << "      out[" << i - f0 << "LL * slot + off] = (real)0;\n";
+  o << "      continue;\n    }\n";
   o << "    const double x = lo0 + ix * h, y = lo1 + iy * h, z = lo2 + iz * h;\n";
   o << "    const double r2 = x * x + y * y + z * z;\n";
   o << "    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;\n";
@@ -340,8 +358,8 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
        " long long xslot, const real* __restrict__ invw, int accumulate) {\n";
   o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n  const int H = N / 2 + 1;\n";
   emit_bin_loop_head(o, "(long long)N * N * H");
-  o << "    int bin = -1; real v[" << NL << "] = {";
-  for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "(real)0";
+  o << "    int bin = -1; double v[" << NL << "] = {";
+  for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
   o << "};\n";
   o << "    if (m < total) {\n";
   o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
@@ -400,23 +418,23 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
       << " xv.y = (real)0; xout[" << i << "LL * xslot + m] = xv; }\n";
   o << "        }\n";
   o << "        if (bin >= 0) {\n";
-  o << "          const real w = (iz == 0 || iz == N / 2) ? (real)1 : (real)2;\n";
-  o << "          const real r2 = (real)n2; const real ir = bym_rsqrt(r2);\n";
-  o << "          const real ux = nx * ir, uy = ny * ir, uz = nz * ir; const real zm = (real)1;\n";
+  o << "          const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;\n";
+  o << "          const double r2 = (double)n2; const double ir = bym_rsqrt(r2);\n";
+  o << "          const double ux = nx * ir, uy = ny * ir, uz = nz * ir; const double zm = 1.0;\n";
   {
     std::ostringstream yy;
-    emit_ylm(yy, L, f32, "yk", "ux", "uy", "uz", "zm");
+    emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm");
     std::istringstream is(yy.str());
     std::string line;
     while (std::getline(is, line)) o << "        " << line << "\n";
   }
   for (int l = 0; l <= L; l += 2) {
-    o << "          { real T = (real)0;";
-    for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << even_lm_index(l, mu) << ";";
+    o << "          { double T = 0.0;";
+    for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * (double)X" << even_lm_index(l, mu) << ";";
     o << " v[" << l / 2 << "] = w * T; }\n";
   }
   o << "        }\n      }\n    }\n";
-  o << "    bym_bin_flush<" << NL << ", real>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
 }
 
 }  // namespace
@@ -431,7 +449,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   const int nf = (int)F.list.size();
   const bool midpoint = key.los == 1 || key.los == 3, even = key.los == 3;
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
   o << kPrelude;
 
   // ------------------------------------------------------------------ gen_fields
@@ -477,8 +495,8 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
          " long long xslot, const real* __restrict__ invw) {\n";
     o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NL << ");\n  const int H = N / 2 + 1;\n";
     emit_bin_loop_head(o, "(long long)N * N * H");
-    o << "    int bin = -1; real v[" << NL << "] = {";
-    for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "(real)0";
+    o << "    int bin = -1; double v[" << NL << "] = {";
+    for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
     o << "};\n";
     o << "    if (m < total) {\n";
     o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
@@ -516,24 +534,24 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
         }
     }
     o << "        if (bin >= 0) {\n";
-    o << "          const real w = (iz == 0 || iz == N / 2) ? (real)1 : (real)2;\n";
-    o << "          const real r2 = (real)n2; const real ir = bym_rsqrt(r2);\n";
-    o << "          const real ux = nx * ir, uy = ny * ir, uz = nz * ir; const real zm = (real)1;\n";
+    o << "          const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;\n";
+    o << "          const double r2 = (double)n2; const double ir = bym_rsqrt(r2);\n";
+    o << "          const double ux = nx * ir, uy = ny * ir, uz = nz * ir; const double zm = 1.0;\n";
     {
       std::ostringstream yy;
-      emit_ylm(yy, L, f32, "yk", "ux", "uy", "uz", "zm");
+      emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm");
       std::string s = yy.str();
       std::istringstream is(s);
       std::string line;
       while (std::getline(is, line)) o << "        " << line << "\n";
     }
     for (int l = 0; l <= L; l += 2) {
-      o << "          { real T = (real)0;";
-      for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << even_lm_index(l, mu) << ";";
+      o << "          { double T = 0.0;";
+      for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * (double)X" << even_lm_index(l, mu) << ";";
       o << " v[" << l / 2 << "] = w * T; }\n";
     }
     o << "        }\n      }\n    }\n";
-    o << "    bym_bin_flush<" << NL << ", real>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+    o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
   };
   emit_kcontract("kcontract", false);
   if (key.los == 2) emit_kcontract("kcontract_x", true);
@@ -563,7 +581,7 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
   std::vector<std::pair<int, int>> ranges;
   for (int f0 = 0; f0 < nf; f0 += max_fields) ranges.push_back({f0, std::min(nf, f0 + max_fields)});
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
   o << kPrelude;
   if (key.los == 2) {   // bisector: field blocks and one contraction per block pair a <= b
     const int nb = (int)ranges.size();
@@ -592,7 +610,7 @@ std::string generate_cross_source(const JitKey &key) {
   const char *real = f32 ? "float" : "double";
   const int nf = (int)field_set(key).list.size();
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
   o << kPrelude;
   emit_kcontract_pair(o, "kcontract_cross", key, 0, nf, 0, nf, true);
   return o.str();
@@ -624,8 +642,8 @@ std::vector<FieldInfo> odd_field_list(const JitKey &key) {
 void emit_k_head(std::ostream &o, int NLo) {
   o << "  extern __shared__ double s[];\n  bym_bins_init(s, nbins * " << NLo << ");\n  const int H = N / 2 + 1;\n";
   emit_bin_loop_head(o, "(long long)N * N * H");
-  o << "    int bin = -1; real v[" << NLo << "] = {";
-  for (int l = 0; l < NLo; ++l) o << (l ? ", " : "") << "(real)0";
+  o << "    int bin = -1; double v[" << NLo << "] = {";
+  for (int l = 0; l < NLo; ++l) o << (l ? ", " : "") << "0.0";
   o << "};\n";
   o << "    if (m < total) {\n";
   o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
@@ -638,23 +656,23 @@ void emit_k_head(std::ostream &o, int NLo) {
 // shell sums of the odd l from X<odd_lm>: v[(l - 1) / 2] = w sum_nu Y_{l nu}(k) X_{l nu}
 void emit_k_tail(std::ostream &o, int L, bool f32, int NLo) {
   o << "        if (bin >= 0) {\n";
-  o << "          const real w = (iz == 0 || iz == N / 2) ? (real)1 : (real)2;\n";
-  o << "          const real r2 = (real)n2; const real ir = bym_rsqrt(r2);\n";
-  o << "          const real ux = nx * ir, uy = ny * ir, uz = nz * ir; const real zm = (real)1;\n";
+  o << "          const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;\n";
+  o << "          const double r2 = (double)n2; const double ir = bym_rsqrt(r2);\n";
+  o << "          const double ux = nx * ir, uy = ny * ir, uz = nz * ir; const double zm = 1.0;\n";
   {
     std::ostringstream yy;
-    emit_ylm(yy, L, f32, "yk", "ux", "uy", "uz", "zm");
+    emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm");
     std::istringstream is(yy.str());
     std::string line;
     while (std::getline(is, line)) o << "        " << line << "\n";
   }
   for (int l = 1; l <= L; l += 2) {
-    o << "          { real T = (real)0;";
-    for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * X" << odd_lm_index(l, mu) << ";";
+    o << "          { double T = 0.0;";
+    for (int mu = -l; mu <= l; ++mu) o << " T += yk" << ylm_index(l, mu) << " * (double)X" << odd_lm_index(l, mu) << ";";
     o << " v[" << (l - 1) / 2 << "] = w * T; }\n";
   }
   o << "        }\n      }\n    }\n";
-  o << "    bym_bin_flush<" << NLo << ", real>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
+  o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
 }
 
 }  // namespace
@@ -668,7 +686,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
   const auto list = odd_field_list(key);
   const int nf = (int)list.size();
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
   o << kPrelude;
   emit_gen_fields(o, "gen_fields_odd", list, 0, nf);
 

@@ -4,13 +4,23 @@
 
 namespace bym {
 
+// Catalog sums into stats (see bym_norm_reduce), deterministic: per-block partials in part
+// (norm_scratch_bytes(nsm) bytes of device scratch), added up in block order.
+size_t norm_scratch_bytes(int nsm);
 void launch_norm_reduce(const float4 *p, const float *nbar, long long n, int which, const double lo[3], double inv_h,
-                        int N, double *stats, int nsm, cudaStream_t st);
+                        int N, double *stats, double *part, int nsm, cudaStream_t st);
 
-// shift (cells): paint onto the nodes box_lo + (i + shift) h (interlacing uses 1/2)
+// Device scratch of launch_paint for a mesh of N^3 and n_objects galaxies plus randoms.
+size_t paint_scratch_bytes(int N, long long n_objects);
+
+// delta = paint(gal, +w) + paint(ran, -alpha_r w), alpha_r = stats[0] / stats[1]; every cell of the
+// padded slot is written (no zero-fill needed), deterministically.  stats[6], stats[7] hold
+// the largest |w| of the galaxies and of the randoms (the scale of the fixed-point sums).  shift (cells): paint
+// onto the nodes box_lo + (i + shift) h (interlacing uses 1/2).  ng + nr < 2^32.
 template <typename T>
-void launch_paint(const float4 *p, long long n, int is_ran, const double *stats, T *delta, int N, const double lo[3],
-                  double inv_h, int assign, int nsm, cudaStream_t st, double shift = 0.0);
+cudaError_t launch_paint(const float4 *gal, long long ng, const float4 *ran, long long nr, const double *stats,
+                         T *delta, int N, const double lo[3], double inv_h, int assign, void *scratch, int nsm,
+                         cudaStream_t st, double shift = 0.0);
 
 template <typename T, typename T2>
 void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const double *scale, const T *invw, int nsm,

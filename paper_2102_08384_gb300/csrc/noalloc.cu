@@ -38,18 +38,23 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {nullptr};
+int g_nsm[kMaxDevices] = {0};
 
-// Device address of the scratch array, looked up once per device with that
-// device current (in host code the symbol itself is only a host-side handle).
-cudaError_t scratch_address(int dev, unsigned char **out) {
+// Device address of the scratch array and the device's SM count, looked up once per device
+// with that device current (in host code the symbol itself is only a host-side handle).
+cudaError_t scratch_address(int dev, unsigned char **out, int *nsm) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    int n = 0;
+    if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    g_nsm[dev] = n > 0 ? n : 1;
     g_addr[dev] = p;
   }
   *out = (unsigned char *)g_addr[dev];
+  *nsm = g_nsm[dev];
   return cudaSuccess;
 }
 
@@ -222,7 +227,8 @@ extern "C" int bym_pk_yamamoto_from_spectra_noalloc(const void *F, const void *D
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BYM_E_CUDA;
   unsigned char *scratch = nullptr;
-  if (scratch_address(dev, &scratch) != cudaSuccess) return BYM_E_CUDA;
+  int nsm = 1;
+  if (scratch_address(dev, &scratch, &nsm) != cudaSuccess) return BYM_E_CUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int N = n_mesh, nb = kbins->nbins, NL = ell_max / 2 + 1;
   if (cudaMemcpyAsync(scratch + kOffEdges, kbins->edges, sizeof(double) * (nb + 1), cudaMemcpyHostToDevice, st) !=
@@ -231,7 +237,7 @@ extern "C" int bym_pk_yamamoto_from_spectra_noalloc(const void *F, const void *D
   const double kf = 2.0 * M_PI / box_len;
   noalloc_setup<<<256, 256, 0, st>>>(N, nb, kf, scratch);
   const long long nm = (long long)N * N * (N / 2 + 1);
-  const unsigned grid = (unsigned)std::min<long long>((nm + 255) / 256, 152LL * 8);
+  const unsigned grid = (unsigned)std::min<long long>((nm + 255) / 256, (long long)nsm * 8);
   const float2 *Fp = (const float2 *)F, *Dp = (const float2 *)D;
   if (NL == 1)
     noalloc_contract<1><<<grid, 256, 0, st>>>(Fp, Dp, N, nb, scratch);

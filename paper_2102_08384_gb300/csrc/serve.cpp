@@ -165,6 +165,14 @@ int bym_serve_start(bym_ctx *c, int n_slots, size_t budget) {
       delete s;
       return serve_fail(c, BYM_E_CUDA, "could not create a serving slot");
     }
+    // a slot runs requests exactly as the parent context would: its FFT backend, field ranges
+    // and measured launch shapes
+    e->fft_mode = c->fft_mode;
+    e->field_chunk = c->field_chunk;
+    {
+      std::lock_guard<std::mutex> lock(c->mu);
+      e->tune = c->tune;
+    }
     s->engines.push_back(e);
   }
   c->server = s;
