@@ -489,22 +489,90 @@ def large_mesh_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d):
     return out
 
 
+def torch_lognormal_cap(torch, dev, seed, n_gal, half_angle_deg, r_min=800.0, r_max=1600.0, ran_factor=10.0,
+                        pk_amp=2e4, pk_slope=-1.5, k0=0.1, f_growth=0.7, bias=2.0, P0=1e4, gen_mesh=128):
+    """A survey-like mock on the device, by the recipe of synth.lognormal_cap_catalog (lognormal
+    density from a power-law Gaussian field, Poisson counts in a spherical cap, Kaiser
+    displacements along each galaxy's own line of sight, uniform-in-volume randoms, FKP weights,
+    pole (1,1,1)/sqrt(3)); drawn with torch's generator, so the same recipe but other numbers.
+    Returns device float32 (n, 4) galaxies and randoms, random nbar, box_lo and box_len."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    cos_max = math.cos(math.radians(half_angle_deg))
+    sin_max = math.sin(math.radians(half_angle_deg))
+    v_cap = 2 * math.pi * (1 - cos_max) * (r_max ** 3 - r_min ** 3) / 3.0
+    nbar = n_gal / v_cap
+    zlo = r_min * cos_max
+    side = max(r_max - zlo, 2 * r_max * sin_max) * 1.02
+    g_lo = torch.tensor([-side / 2, -side / 2, 0.5 * (zlo + r_max) - side / 2], dtype=torch.float64, device=dev)
+    Ng, hg, kf = gen_mesh, side / gen_mesh, 2 * math.pi / side
+    n1 = torch.fft.fftfreq(Ng, d=1.0 / Ng, device=dev, dtype=torch.float64)
+    nz = torch.fft.rfftfreq(Ng, d=1.0 / Ng, device=dev, dtype=torch.float64)
+    kx, ky, kz = (n1 * kf)[:, None, None], (n1 * kf)[None, :, None], (nz * kf)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    kk = torch.sqrt(k2)
+    pk = torch.where(kk > 0, pk_amp * (torch.clamp(kk, min=1e-30) / k0) ** pk_slope, torch.zeros_like(kk))
+    white = torch.randn((Ng, Ng, Ng), generator=g, device=dev, dtype=torch.float64)
+    Gk = torch.fft.rfftn(white) * torch.sqrt(pk / hg ** 3)
+    G = torch.fft.irfftn(Gk, s=(Ng, Ng, Ng))
+    dln = torch.exp(G - G.var() / 2.0)
+    counts = torch.poisson(nbar * hg ** 3 * dln, generator=g).to(torch.int64).ravel()
+    cells = torch.repeat_interleave(torch.arange(Ng ** 3, device=dev), counts)
+    ci = torch.stack([cells // (Ng * Ng), (cells // Ng) % Ng, cells % Ng], dim=1)
+    pos = g_lo[None, :] + (ci + torch.rand(ci.shape, generator=g, device=dev, dtype=torch.float64)) * hg
+    rr = torch.linalg.norm(pos, dim=1)
+    keep = (rr >= r_min) & (rr <= r_max) & (pos[:, 2] >= rr * cos_max)
+    pos, ci = pos[keep], ci[keep]
+    inv_k2 = torch.where(k2 > 0, 1.0 / torch.clamp(k2, min=1e-30), torch.zeros_like(k2))
+    dm_k = Gk / bias
+    psi = torch.stack([torch.fft.irfftn(1j * kc * dm_k * inv_k2, s=(Ng, Ng, Ng))[ci[:, 0], ci[:, 1], ci[:, 2]]
+                       for kc in (kx, ky, kz)], dim=1)
+    rhat = pos / torch.linalg.norm(pos, dim=1, keepdim=True)
+    pos = pos + f_growth * torch.sum(psi * rhat, dim=1, keepdim=True) * rhat
+    n_ran = int(round(ran_factor * len(pos)))
+    u = torch.rand(n_ran, generator=g, device=dev, dtype=torch.float64)
+    rad = (r_min ** 3 + u * (r_max ** 3 - r_min ** 3)) ** (1.0 / 3.0)
+    mu = cos_max + (1 - cos_max) * torch.rand(n_ran, generator=g, device=dev, dtype=torch.float64)
+    ph = 2 * math.pi * torch.rand(n_ran, generator=g, device=dev, dtype=torch.float64)
+    st = torch.sqrt(torch.clamp(1 - mu * mu, min=0.0))
+    ran = torch.stack([st * torch.cos(ph), st * torch.sin(ph), mu], dim=1) * rad[:, None]
+    pole = torch.tensor([1.0, 1.0, 1.0], dtype=torch.float64, device=dev) / math.sqrt(3.0)
+    z = torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64, device=dev)
+    v = torch.linalg.cross(z, pole)
+    s_, c_ = torch.linalg.norm(v), torch.dot(z, pole)
+    vx = torch.tensor([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]], dtype=torch.float64, device=dev)
+    R = torch.eye(3, dtype=torch.float64, device=dev) + vx + vx @ vx * ((1 - c_) / s_ ** 2)
+    pos, ran = pos @ R.T, ran @ R.T
+    w = 1.0 / (1.0 + nbar * P0)
+    gal = torch.cat([pos, torch.full((len(pos), 1), w, dtype=torch.float64, device=dev)], dim=1).float()
+    rand = torch.cat([ran, torch.full((n_ran, 1), w, dtype=torch.float64, device=dev)], dim=1).float()
+    lo = torch.minimum(rand[:, :3].min(0).values, gal[:, :3].min(0).values).double()
+    hi = torch.maximum(rand[:, :3].max(0).values, gal[:, :3].max(0).values).double()
+    extent = float((hi - lo).max())
+    box_lo = (0.5 * (lo + hi) - extent).cpu().numpy()
+    return gal.contiguous(), rand.contiguous(), torch.full((n_ran,), nbar, dtype=torch.float32, device=dev), \
+        box_lo, 2.0 * extent
+
+
 def batch_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mocks=64, slots=4):
-    """Many uneven mocks: meshes 128, 192, 256, 384^3 in turn, LOS midpoint for four mocks then
-    bisector for four, order 4, ell <= 4, P and xi; each mock a random 20-100 % of the benchmark's
-    galaxies and randoms in a cap of half-angle 10-30 degrees.  Run (a) one at a time,
-    (b) as one batch through the 4-slot serving loop, (c) as one captured CUDA graph with 4
-    branches (captured once, then relaunched)."""
+    """The batched workload: 64 independent lognormal mocks, seeds 100 + i, N_gal log-uniform in
+    [2e5, 2e6], cap half-angles uniform in [10, 60] degrees over 800-1600 Mpc/h, 10x randoms, meshes
+    128, 192, 256, 384^3 in turn, midpoint for four mocks then bisector for four, order 4, ell <= 4,
+    P and xi, FP32.  Run (a) one at a time, (b) as one batch through the 4-slot serving loop,
+    (c) as one captured CUDA graph with 4 branches (captured once, then relaunched)."""
     rng = np.random.default_rng(100)
     items = []
+    t0 = time.perf_counter()
     for i in range(n_mocks):
         N = (128, 192, 256, 384)[i % 4]
         los = ("midpoint", "bisector")[(i // 4) % 2]     # every mesh with both LOS within 8 mocks
-        frac = float(rng.uniform(0.2, 1.0))
-        g, r, rn = _mock_subsets(torch, cat, gal_d, ran_d, rnb_d, rng, frac, float(rng.uniform(10.0, 30.0)))
-        p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=ELL_MAX, los=los,
+        n_gal = int(10 ** rng.uniform(math.log10(2e5), math.log10(2e6)))
+        g, r, rn, box_lo, box_len = torch_lognormal_cap(torch, dev, 100 + i, n_gal, float(rng.uniform(10.0, 60.0)))
+        p = pkg.make_params(box_lo=box_lo, box_len=box_len, n_mesh=N, assign=3, ell_max=ELL_MAX, los=los,
                             order=ORDER, compensate=True, precision=32, norm=1)
         items.append(dict(gal=g, ran=r, ran_nbar=rn, params=p, kedges=KEDGES, redges=REDGES))
+    torch.cuda.synchronize(dev)
+    t_gen = time.perf_counter() - t0
     ctx = pkg.Context(dev.index)
 
     def alone(it):
@@ -542,9 +610,10 @@ def batch_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mocks=64, slots=4):
     ctx.close()
     n_gal = [int(it["gal"].shape[0]) for it in items]
     return {"mocks": len(items),
-            "mix": "meshes 128/192/256/384^3 in turn, midpoint/bisector alternating, order 4, ell<=4, P_ell+xi_ell, "
-                   "FP32; each a random 20-100 % of the galaxies and randoms in a 10-30 deg cap "
-                   f"({min(n_gal)}-{max(n_gal)} galaxies)",
+            "mix": "64 independent lognormal mocks (seeds 100+i, generated on the device), 2e5-2e6 galaxies "
+                   "log-uniform, 10-60 deg caps, 10x randoms; meshes 128/192/256/384^3 in turn, midpoint/bisector "
+                   f"alternating, order 4, ell<=4, P_ell+xi_ell, FP32 ({min(n_gal)}-{max(n_gal)} galaxies)",
+            "mock_generation_s": t_gen,
             "sequential_catalogs_per_s": len(items) / t_seq,
             "served_batch_catalogs_per_s": len(items) / t_batch,
             "graph_batch_catalogs_per_s": len(items) / t_graph,

@@ -633,7 +633,7 @@ static int get_null_kgeom(bym_ctx *c, int N, Geom **out) {
 
 // Device bytes a request may still take: free memory plus what the stream-ordered
 // pool holds unused, less the given headroom (FFT work areas and small buffers).
-static size_t device_available(bym_ctx *c, size_t headroom) {
+size_t bym::device_available(bym_ctx *c, size_t headroom) {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     cudaGetLastError();
@@ -921,7 +921,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
     if (cat4[w]) {
       ProfScope ps(c, st, "norm_reduce", catn[w] * ((w & 1) ? 20.0 : 16.0));
       launch_norm_reduce(cat4[w], catnb[w], catn[w], w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), npart, c->nsm,
-                         st);
+                         st, p->precision);
     }
   {
     void *pscr = nullptr;
@@ -1340,7 +1340,7 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
     if (cat4[w]) {
       ProfScope ps(c, st, "norm_reduce", catn[w] * ((w & 1) ? 20.0 : 16.0));
       launch_norm_reduce(cat4[w], catnb[w], catn[w], w & 1, p->box_lo, inv_h, N, stats + 8 * (w >> 1), npart, c->nsm,
-                         st);
+                         st, p->precision);
     }
   {
     void *pscr = nullptr;
@@ -2011,7 +2011,7 @@ int bym_shot_noise(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, c
       d4 = (const float4 *)a;
       dn = (const float *)b;
     }
-    launch_norm_reduce(d4, dn, cat->n, w, p->box_lo, inv_h, p->n_mesh, stats, npart, c->nsm, st);
+    launch_norm_reduce(d4, dn, cat->n, w, p->box_lo, inv_h, p->n_mesh, stats, npart, c->nsm, st, p->precision);
   }
   double hs[8];
   cudaError_t e = cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st);

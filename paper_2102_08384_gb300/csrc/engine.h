@@ -98,6 +98,9 @@ int validate(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, const b
 size_t footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, bool want_pk, bool want_xi,
                        bool cats_on_device, int chunk = 0, bool cross = false);
 int run_request(bym_ctx *c, const Request &rq, cudaStream_t st);
+// device bytes still available to requests: free memory plus what the stream-ordered pool holds
+// unused (it keeps freed memory between requests), less headroom
+size_t device_available(bym_ctx *c, size_t headroom);
 void shutdown_serving(bym_ctx *c);
 
 }  // namespace bym

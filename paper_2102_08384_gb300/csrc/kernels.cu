@@ -23,6 +23,68 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+constexpr int kPaintTile = 16;
+constexpr int kPaintStripes = 16;   // copies of each tile's counter (spreads the atomics of a busy tile)
+
+struct PaintGeom {
+  double lo[3], inv_h, shift;         // FP64 geometry (FP64 meshes)
+  float lo_h[3], lo_l[3], ih_h, ih_l; // lo and 1/h as float pairs (FP32 meshes)
+  float fshift;
+  int N, assign, nt;                  // nt = tiles per axis
+};
+
+// a + b = s + e exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// u = (x - lo) inv_h as uh + ul with |ul| <= ulp(uh) / 2
+__device__ __forceinline__ void cell_coord(float x, float lo_h, float lo_l, float ih_h, float ih_l, float &uh,
+                                           float &ul) {
+  float s, e;
+  two_sum(x, -lo_h, s, e);                 // x - lo_h = s + e exactly
+  const float el = e - lo_l;               // x - lo = s + el (to the rounding of el)
+  const float p = s * ih_h;
+  const float pe = fmaf(s, ih_h, -p);      // s ih_h = p + pe exactly
+  const float q = pe + fmaf(s, ih_l, el * ih_h);
+  uh = p + q;                              // renormalise
+  ul = q - (uh - p);
+}
+
+__device__ __forceinline__ bool in_box(float uh, float ul, int N) {
+  return (uh > 0.f || (uh == 0.f && ul >= 0.f)) && (uh < (float)N || (uh == (float)N && ul < 0.f));
+}
+
+// an object inside [lo, lo + N h) along every axis, decided as the painter decides it
+template <typename T>
+__device__ __forceinline__ bool inside_box(const float4 q, const PaintGeom &g) {
+  if (sizeof(T) == 4) {
+    float uh, ul;
+    cell_coord(q.x, g.lo_h[0], g.lo_l[0], g.ih_h, g.ih_l, uh, ul);
+    if (!in_box(uh, ul, g.N)) return false;
+    cell_coord(q.y, g.lo_h[1], g.lo_l[1], g.ih_h, g.ih_l, uh, ul);
+    if (!in_box(uh, ul, g.N)) return false;
+    cell_coord(q.z, g.lo_h[2], g.lo_l[2], g.ih_h, g.ih_l, uh, ul);
+    return in_box(uh, ul, g.N);
+  }
+  const double u[3] = {((double)q.x - g.lo[0]) * g.inv_h, ((double)q.y - g.lo[1]) * g.inv_h,
+                       ((double)q.z - g.lo[2]) * g.inv_h};
+  return u[0] >= 0.0 && u[0] < g.N && u[1] >= 0.0 && u[1] < g.N && u[2] >= 0.0 && u[2] < g.N;
+}
+
+struct FF {   // an unevaluated sum of two floats
+  float h, l;
+};
+__device__ __forceinline__ FF ff_add(FF a, float bh, float bl) {
+  float s, e;
+  two_sum(a.h, bh, s, e);
+  e += a.l + bl;
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+
 }  // namespace
 
 // Per-block sums of one catalog (galaxies, which = 0, or randoms, which = 1), written to
@@ -32,21 +94,29 @@ __device__ __forceinline__ double warp_sum(double v) {
 // bym_norm_finish adds them up in block order (so the totals are the same on every run):
 // stats[which] += sum w, stats[2] += sum nbar w^2 (randoms), stats[3] += bad,
 // stats[4 + which] += sum w^2, stats[6 + which] = max(stats[6 + which], largest |w|).
+template <typename T>
 __global__ void __launch_bounds__(256) bym_norm_reduce(const float4 *__restrict__ p, const float *__restrict__ nbar,
-                                                       long long n, int which, double lo0, double lo1, double lo2,
-                                                       double inv_h, int N, double *__restrict__ part) {
-  double sw = 0.0, snw2 = 0.0, bad = 0.0, sw2 = 0.0, swa = 0.0;
+                                                       long long n, int which, PaintGeom g,
+                                                       double *__restrict__ part) {
+  // per thread: float-pair sums (w^2 and nbar w^2 from exact float products), exact counts
+  FF fw{0.f, 0.f}, fw2{0.f, 0.f}, fnw2{0.f, 0.f};
+  int nbad = 0;
+  float wa = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float4 q = p[i];
-    const double ux = ((double)q.x - lo0) * inv_h, uy = ((double)q.y - lo1) * inv_h, uz = ((double)q.z - lo2) * inv_h;
-    const bool ok = (ux >= 0.0) && (ux < N) && (uy >= 0.0) && (uy < N) && (uz >= 0.0) && (uz < N) &&
-                    isfinite((double)q.w);
-    if (!ok) bad += 1.0;
-    sw += (double)q.w;
-    sw2 += (double)q.w * (double)q.w;
-    swa = fmax(swa, fabs((double)q.w));
-    if (which == 1 && nbar) snw2 += (double)nbar[i] * (double)q.w * (double)q.w;
+    if (!(inside_box<T>(q, g) && isfinite(q.w))) ++nbad;
+    const float w = q.w;
+    fw = ff_add(fw, w, 0.f);
+    const float w2 = w * w, w2e = fmaf(w, w, -w2);
+    fw2 = ff_add(fw2, w2, w2e);
+    wa = fmaxf(wa, fabsf(w));
+    if (which == 1 && nbar) {
+      const float nb = nbar[i], t = w2 * nb;
+      fnw2 = ff_add(fnw2, t, fmaf(w2, nb, -t) + w2e * nb);
+    }
   }
+  double sw = (double)fw.h + (double)fw.l, sw2 = (double)fw2.h + (double)fw2.l;
+  double snw2 = (double)fnw2.h + (double)fnw2.l, bad = (double)nbad, swa = (double)wa;
   __shared__ double red[5][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   sw = warp_sum(sw);
@@ -120,16 +190,6 @@ __global__ void bym_norm_finish(const double *__restrict__ part, int nblk, int w
 // u = (x - lo) / h is formed as an unevaluated pair of floats (about 44 bits) on the FP32 pipes.
 namespace {
 
-constexpr int kPaintTile = 16;
-constexpr int kPaintStripes = 16;   // copies of each tile's counter (spreads the atomics of a busy tile)
-
-struct PaintGeom {
-  double lo[3], inv_h, shift;         // FP64 geometry (FP64 meshes)
-  float lo_h[3], lo_l[3], ih_h, ih_l; // lo and 1/h as float pairs (FP32 meshes)
-  float fshift;
-  int N, assign, nt;                  // nt = tiles per axis
-};
-
 struct alignas(16) PaintD4 {          // FP64 record: offsets and signed weight
   double x, y, z, w;
 };
@@ -143,26 +203,6 @@ template <>
 struct PaintRec<double> {
   using type = PaintD4;
 };
-
-// a + b = s + e exactly (Knuth's two-sum)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// u = (x - lo) inv_h as uh + ul with |ul| <= ulp(uh) / 2
-__device__ __forceinline__ void cell_coord(float x, float lo_h, float lo_l, float ih_h, float ih_l, float &uh,
-                                           float &ul) {
-  float s, e;
-  two_sum(x, -lo_h, s, e);                 // x - lo_h = s + e exactly
-  const float el = e - lo_l;               // x - lo = s + el (to the rounding of el)
-  const float p = s * ih_h;
-  const float pe = fmaf(s, ih_h, -p);      // s ih_h = p + pe exactly
-  const float q = pe + fmaf(s, ih_l, el * ih_h);
-  uh = p + q;                              // renormalise
-  ul = q - (uh - p);
-}
 
 // Stencil origin b and offset d of one axis from u = uh + ul (u in [0, N)), FP32 meshes:
 // v = u - shift (+ 1/2 for TSC), b = floor(v), d = v - b in [0, 1) (TSC: minus 1/2).
@@ -187,10 +227,6 @@ __device__ __forceinline__ void axis_origin(float uh, float ul, float fshift, in
   }
   b = (int)fl;
   d = kA == 3 ? r - 0.5f : r;
-}
-
-__device__ __forceinline__ bool in_box(float uh, float ul, int N) {
-  return (uh > 0.f || (uh == 0.f && ul >= 0.f)) && (uh < (float)N || (uh == (float)N && ul < 0.f));
 }
 
 template <typename T, int kA>
@@ -559,12 +595,34 @@ static unsigned grid_for(long long work, int nsm) {
 
 size_t norm_scratch_bytes(int nsm) { return sizeof(double) * 5 * (size_t)nsm * 8; }
 
+static PaintGeom make_geom(const double lo[3], double inv_h, int N, int assign, double shift) {
+  PaintGeom g;
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = lo[a];
+    g.lo_h[a] = (float)lo[a];
+    g.lo_l[a] = (float)(lo[a] - (double)g.lo_h[a]);
+  }
+  g.inv_h = inv_h;
+  g.ih_h = (float)inv_h;
+  g.ih_l = (float)(inv_h - (double)g.ih_h);
+  g.shift = shift;
+  g.fshift = (float)shift;
+  g.N = N;
+  g.assign = assign;
+  g.nt = (N + kPaintTile - 1) / kPaintTile;
+  return g;
+}
+
 void launch_norm_reduce(const float4 *p, const float *nbar, long long n, int which, const double lo[3], double inv_h,
-                        int N, double *stats, double *part, int nsm, cudaStream_t st) {
+                        int N, double *stats, double *part, int nsm, cudaStream_t st, int precision) {
   if (n <= 0) return;
-  const unsigned g = grid_for(n, nsm);
-  bym_norm_reduce<<<g, 256, 0, st>>>(p, nbar, n, which, lo[0], lo[1], lo[2], inv_h, N, part);
-  bym_norm_finish<<<1, 32, 0, st>>>(part, (int)g, which, stats);
+  const unsigned blocks = grid_for(n, nsm);
+  const PaintGeom g = make_geom(lo, inv_h, N, 3, 0.0);
+  if (precision == 64)
+    bym_norm_reduce<double><<<blocks, 256, 0, st>>>(p, nbar, n, which, g, part);
+  else
+    bym_norm_reduce<float><<<blocks, 256, 0, st>>>(p, nbar, n, which, g, part);
+  bym_norm_finish<<<1, 32, 0, st>>>(part, (int)blocks, which, stats);
 }
 
 static long long paint_counters(int N) {
@@ -583,20 +641,7 @@ cudaError_t launch_paint(const float4 *gal, long long ng, const float4 *ran, lon
                          T *delta, int N, const double lo[3], double inv_h, int assign, void *scratch, int nsm,
                          cudaStream_t st, double shift) {
   if (ng < 0 || nr < 0 || ng + nr > 0xffffffffll || (assign != 2 && assign != 3)) return cudaErrorInvalidValue;
-  PaintGeom g;
-  for (int a = 0; a < 3; ++a) {
-    g.lo[a] = lo[a];
-    g.lo_h[a] = (float)lo[a];
-    g.lo_l[a] = (float)(lo[a] - (double)g.lo_h[a]);
-  }
-  g.inv_h = inv_h;
-  g.ih_h = (float)inv_h;
-  g.ih_l = (float)(inv_h - (double)g.ih_h);
-  g.shift = shift;
-  g.fshift = (float)shift;
-  g.N = N;
-  g.assign = assign;
-  g.nt = (N + kPaintTile - 1) / kPaintTile;
+  const PaintGeom g = make_geom(lo, inv_h, N, assign, shift);
   const long long ntiles = (long long)g.nt * g.nt * g.nt, ncnt = paint_counters(N), nblk = (ncnt + 1023) / 1024;
   const long long n = ng + nr;
   // scratch: cursor[ncnt] | start[ncnt + 1] | bsum[nblk] | records (PaintD4 / float4) | short4 | bucket

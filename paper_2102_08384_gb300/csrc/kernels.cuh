@@ -7,8 +7,9 @@ namespace bym {
 // Catalog sums into stats (see bym_norm_reduce), deterministic: per-block partials in part
 // (norm_scratch_bytes(nsm) bytes of device scratch), added up in block order.
 size_t norm_scratch_bytes(int nsm);
+// precision 32: the in-box test runs as the FP32 painter's (float pairs), 64: in FP64.
 void launch_norm_reduce(const float4 *p, const float *nbar, long long n, int which, const double lo[3], double inv_h,
-                        int N, double *stats, double *part, int nsm, cudaStream_t st);
+                        int N, double *stats, double *part, int nsm, cudaStream_t st, int precision);
 
 // Device scratch of launch_paint for a mesh of N^3 and n_objects galaxies plus randoms.
 size_t paint_scratch_bytes(int N, long long n_objects);

@@ -150,10 +150,9 @@ int bym_serve_start(bym_ctx *c, int n_slots, size_t budget) {
   if (n_slots < 1 || n_slots > 16) return serve_fail(c, BYM_E_INVAL, "n_slots must be in 1..16");
   if (c->server) return serve_fail(c, BYM_E_BUSY, "a serving loop is already running");
   if (cudaSetDevice(c->device) != cudaSuccess) return serve_fail(c, BYM_E_CUDA, "cudaSetDevice failed");
-  if (!budget) {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return serve_fail(c, BYM_E_CUDA, "cudaMemGetInfo failed");
-    budget = (size_t)(0.9 * (double)fr);
+  if (!budget) {   // 90 % of what requests can take: free memory and what the memory pool holds unused
+    budget = (size_t)(0.9 * (double)device_available(c, 0));
+    if (!budget) return serve_fail(c, BYM_E_CUDA, "no device memory available for serving");
   }
   auto *s = new Server();
   s->parent = c;
