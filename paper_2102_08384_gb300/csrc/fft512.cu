@@ -682,7 +682,8 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
 // Persistent: one 256-thread CTA per SM.  Modes 0 and 1 keep three tile buffers (load of the
 // next tile, transform of this one, store of the previous one in flight); mode 2 keeps two data
 // buffers and the tile of D, walks the tile positions and, at each one, every field of the launch,
-// so D is read once per launch.  Waits on the tile barriers give up after about two seconds,
+// so D is read once per launch; each thread keeps its conj(D) W^-2 entries in registers for the
+// fields of a position, and the next position's D tile loads as soon as the first field is done.  Waits on the tile barriers give up after about two seconds,
 // record a fault in *fault and end the kernel once the copies in flight have landed.
 // ---------------------------------------------------------------------------
 constexpr int XC = 16;                              // columns per tile
@@ -818,6 +819,7 @@ __global__ void __launch_bounds__(256, 1)
   }
   bool ok = true;
   long long i = 0;
+  float2 dr[32];                                     // mode 2: conj(D) W^-2 of this thread's entries
   for (long long k = 0; u < nunits && ok; u += gridDim.x, ++k) {
     for (int f = 0; f < nf && ok; ++f, ++i) {
       const int b = (int)(i % NDB);
@@ -875,10 +877,10 @@ __global__ void __launch_bounds__(256, 1)
         fwd512(v, As, Bs, j, gm, TW, col);
       }
       if (MODE == 2) {
-        const XtCol dcol{sm + (size_t)2 * XTILE, g};
         if (f == 0) {
-          // D <- conj(D) W^-2 in place, once per position: every thread rewrites exactly the
-          // entries kx = ka + 32 k2, kb + 32 k2 of its column that it reads below
+          // conj(D) W^-2 at this thread's entries kx = ka + 32 k2 (dr[k2]) and kb + 32 k2
+          // (dr[16 + k2]), kept in registers for every field of the position
+          const XtCol dcol{sm + (size_t)2 * XTILE, g};
           const long long fc = tl * XC + g;
           const int ky = (int)(fc / HZ), kz = (int)(fc % HZ);
           const float cyz = invw ? W1[ky] * W1[kz] : 1.f;
@@ -890,14 +892,14 @@ __global__ void __launch_bounds__(256, 1)
               wa = W1[kxa] * cyz;
               wb = W1[kxb] * cyz;
             }
-            dcol.at(kxa) = cscale(cconj(dcol.at(kxa)), wa * wa);
-            dcol.at(kxb) = cscale(cconj(dcol.at(kxb)), wb * wb);
+            dr[k2] = cscale(cconj(dcol.at(kxa)), wa * wa);
+            dr[16 + k2] = cscale(cconj(dcol.at(kxb)), wb * wb);
           }
         }
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
-          As[k2] = cscale(cmul(As[k2], dcol.at(ka + 32 * k2)), s);
-          Bs[k2] = cscale(cmul(Bs[k2], dcol.at(kb + 32 * k2)), s);
+          As[k2] = cscale(cmul(As[k2], dr[k2]), s);
+          Bs[k2] = cscale(cmul(Bs[k2], dr[16 + k2]), s);
         }
       }
       if (MODE == 0) {
@@ -918,7 +920,7 @@ __global__ void __launch_bounds__(256, 1)
       if (tid == 0) {
         for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, (int)(tl * (2 * XC)), x0, slot, tile + (size_t)x0 * 128);
         bulk_commit();
-        if (MODE == 2 && f == nf - 1 && u + gridDim.x < nunits) {   // D of the next position
+        if (MODE == 2 && f == 0 && u + gridDim.x < nunits) {   // D of the next position: this one is in registers
           issue_d(u + gridDim.x);
           pend |= 4u;
           ppar = (ppar & ~4u) | ((unsigned)((k + 1) & 1) << 2);

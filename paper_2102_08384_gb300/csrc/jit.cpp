@@ -165,26 +165,14 @@ void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldI
   o << "extern \"C\" __global__ void __launch_bounds__(256, 2) " << name << "(const real* __restrict__ delta,"
        " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
        " double inv_r0, int x0, int np) {\n";
-  // a warp takes 32 consecutive values; when all of them are zero (most warps: the survey fills a
-  // fraction of each occupied plane) its lanes write the zeros of every field as 16-byte stores
-  // (the 32 values start on a 128-byte boundary: N(N+2) and the slot stride are multiples of 8)
-  const int nf = f1 - f0;
   o << "  const long long row = N + 2, plane = (long long)N * row, base = (long long)x0 * plane;\n";
   o << "  const long long nval = (long long)np * plane;\n";
-  o << "  const int lane = threadIdx.x & 31;\n";
-  o << "  for (long long w0 = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < nval;"
-       " w0 += (long long)gridDim.x * blockDim.x) {\n";
-  o << "    const long long c = w0 + lane;\n";
+  o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nval;"
+       " c += (long long)gridDim.x * blockDim.x) {\n";
   o << "    const long long off = base + c;\n";
   o << "    const int iz = (int)(c % row); const long long t = c / row;\n";
   o << "    const int iy = (int)(t % N); const int ix = x0 + (int)(t / N);\n";
-  o << "    const real d = (c < nval && iz < N) ? delta[off] : (real)0;\n";
-  o << "    if (__all_sync(0xffffffffu, d == (real)0) && w0 + 32 <= nval) {\n";
-  o << "      constexpr int VPW = 32 * (int)sizeof(real) / 16;   // 16-byte vectors per field\n";
-  o << "      for (int q = lane; q < " << nf << " * VPW; q += 32)\n";
-  o << "        ((real4z*)(out + (long long)(q / VPW) * slot + base + w0))[q % VPW] = real4z{};\n";
-  o << "      continue;\n    }\n";
-  o << "    if (c >= nval) continue;\n";
+  o << "    const real d = iz < N ? delta[off] : (real)0;\n";
   o << "    if (d == (real)0) {\n";
   for (int i = f0; i < f1; ++i) o << "      out[" << i - f0 << "LL * slot + off] = (real)0;\n";
   o << "      continue;\n    }\n";
@@ -449,7 +437,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   const int nf = (int)F.list.size();
   const bool midpoint = key.los == 1 || key.los == 3, even = key.los == 3;
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
 
   // ------------------------------------------------------------------ gen_fields
@@ -581,7 +569,7 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
   std::vector<std::pair<int, int>> ranges;
   for (int f0 = 0; f0 < nf; f0 += max_fields) ranges.push_back({f0, std::min(nf, f0 + max_fields)});
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
   if (key.los == 2) {   // bisector: field blocks and one contraction per block pair a <= b
     const int nb = (int)ranges.size();
@@ -610,7 +598,7 @@ std::string generate_cross_source(const JitKey &key) {
   const char *real = f32 ? "float" : "double";
   const int nf = (int)field_set(key).list.size();
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
   emit_kcontract_pair(o, "kcontract_cross", key, 0, nf, 0, nf, true);
   return o.str();
@@ -686,7 +674,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
   const auto list = odd_field_list(key);
   const int nf = (int)list.size();
   std::ostringstream o;
-  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\ntypedef " << (std::string(real) == "float" ? "float4" : "double2") << " real4z;\n";
+  o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
   emit_gen_fields(o, "gen_fields_odd", list, 0, nf);
 

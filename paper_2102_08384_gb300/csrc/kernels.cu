@@ -150,20 +150,23 @@ __global__ void __launch_bounds__(256) bym_norm_reduce(const float4 *__restrict_
   }
 }
 
-__global__ void bym_norm_finish(const double *__restrict__ part, int nblk, int which, double *__restrict__ stats) {
-  const int j = threadIdx.x;
-  if (j >= 5) return;
+// One warp per total: lane l adds the partials of blocks l, l + 32, .. in order, then a fixed
+// butterfly; the order of the additions, hence the total, is the same on every run.
+__global__ void __launch_bounds__(160) bym_norm_finish(const double *__restrict__ part, int nblk, int which,
+                                                       double *__restrict__ stats) {
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[5 * b + j];
+  for (int b = lane; b < nblk; b += 32) s = j == 4 ? fmax(s, part[5 * b + j]) : s + part[5 * b + j];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, s, o);
+    s = j == 4 ? fmax(s, t) : s + t;
+  }
+  if (lane) return;
   if (j == 0) stats[which] += s;
   if (j == 1 && which == 1) stats[2] += s;
   if (j == 2) stats[3] += s;
   if (j == 3) stats[4 + which] += s;
-  if (j == 4) {   // the largest |w|: a maximum, not a sum
-    double m = 0.0;
-    for (int b = 0; b < nblk; ++b) m = fmax(m, part[5 * b + 4]);
-    stats[6 + which] = fmax(stats[6 + which], m);
-  }
+  if (j == 4) stats[6 + which] = fmax(stats[6 + which], s);   // the largest |w|: a maximum, not a sum
 }
 
 // ---------------------------------------------------------------- painting
@@ -622,7 +625,7 @@ void launch_norm_reduce(const float4 *p, const float *nbar, long long n, int whi
     bym_norm_reduce<double><<<blocks, 256, 0, st>>>(p, nbar, n, which, g, part);
   else
     bym_norm_reduce<float><<<blocks, 256, 0, st>>>(p, nbar, n, which, g, part);
-  bym_norm_finish<<<1, 32, 0, st>>>(part, (int)blocks, which, stats);
+  bym_norm_finish<<<1, 160, 0, st>>>(part, (int)blocks, which, stats);
 }
 
 static long long paint_counters(int N) {
