@@ -73,6 +73,18 @@ unsigned grid_of(long long work, int nsm, int per_sm) {
   return (unsigned)std::max(1LL, std::min(g, cap));
 }
 
+// Dynamic shared memory of a shell-sum kernel over n sums: one accumulator per warp of a
+// 256-thread block when that fits the default 48 KB (the sums then do not depend on the order
+// in which blocks and warps finish), else one per block.
+size_t sums_smem(int n) {
+  const size_t per_warp = sizeof(double) * 8 * (size_t)n;
+  return per_warp <= 48 * 1024 ? per_warp : sizeof(double) * (size_t)n;
+}
+
+// Doubles of a shell-sum buffer: the n sums, a ticket counter, and one total per block of the
+// largest grid that adds into it (nsm * per_sm blocks at most, see grid_of).
+size_t sums_doubles(int n, int nsm, int per_sm) { return (size_t)n + 1 + (size_t)nsm * per_sm * (size_t)n; }
+
 int lab(int i, int N) { return i < N / 2 ? i : i - N; }
 
 bool finite_all(const double *v, int n) {
@@ -564,13 +576,13 @@ static int get_geom(bym_ctx *c, const KernelSet &ks, int N, double L, const bym_
     g.jm = g.full ? N / 2 : jm;
   }
   double *sums = nullptr;
-  if (cudaMalloc(&sums, sizeof(double) * 2 * b->nbins) != cudaSuccess) {
+  if (cudaMalloc(&sums, sizeof(double) * sums_doubles(2 * b->nbins, c->nsm, 4)) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, BYM_E_NOMEM, "geometry allocation failed");
   }
-  cudaMemsetAsync(sums, 0, sizeof(double) * 2 * b->nbins, st);
+  cudaMemsetAsync(sums, 0, sizeof(double) * (2 * b->nbins + 1), st);
   cudaError_t e;
-  const size_t smem = sizeof(double) * 2 * b->nbins;
+  const size_t smem = sums_smem(2 * b->nbins);
   if (kind == 'k') {
     const long long work = (long long)N * N * (N / 2 + 1);
     e = launch(ks.kgeom, grid_of(work, c->nsm, 4), 256, smem, st, N, (const int *)g.lut, b->nbins, unit, sums);
@@ -859,10 +871,11 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   TRY(alloc((void **)&stats, 16 * sizeof(double)));    // [0, 8) tracer A, [8, 16) tracer B
   CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * sizeof(double), st));
   const int nbk = want_pk ? rq.kb->nbins : 1, nbr = want_xi ? rq.rb->nbins : 1;
-  TRY(alloc((void **)&ksum, sizeof(double) * NL * nbk));
-  TRY(alloc((void **)&rsum, sizeof(double) * NL * nbr));
-  CUDA_TRY(cudaMemsetAsync(ksum, 0, sizeof(double) * NL * nbk, st));
-  CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * NL * nbr, st));
+  // shell sums, their ticket counter (zeroed) and room for one total per block
+  TRY(alloc((void **)&ksum, sizeof(double) * sums_doubles(NL * nbk, c->nsm, std::max(tn.per_sm_k, 1))));
+  TRY(alloc((void **)&rsum, sizeof(double) * sums_doubles(NL * nbr, c->nsm, 4)));
+  CUDA_TRY(cudaMemsetAsync(ksum, 0, sizeof(double) * (NL * nbk + 1), st));
+  CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * (NL * nbr + 1), st));
   if (p->compensate) {
     std::vector<T> w(N);
     for (int i = 0; i < N; ++i) {
@@ -1001,7 +1014,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   }
 
   const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, tn.per_sm_k);
-  const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
+  const size_t smk = sums_smem(NL * nbk), smr = sums_smem(NL * nbr);
   const double tscale = h * inv_r0;
 
   double pk_scale = 1.0;
@@ -1304,11 +1317,11 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
   T *invw = nullptr;
   const int nbk = want_pk ? rq.kb->nbins : 1, nbr = want_xi ? rq.rb->nbins : 1;
   TRY(alloc((void **)&stats, 16 * sizeof(double)));
-  TRY(alloc((void **)&ksum, sizeof(double) * NL * nbk));
-  TRY(alloc((void **)&rsum, sizeof(double) * NL * nbr));
+  TRY(alloc((void **)&ksum, sizeof(double) * sums_doubles(NL * nbk, c->nsm, std::max(tn.per_sm_k, 1))));
+  TRY(alloc((void **)&rsum, sizeof(double) * sums_doubles(NL * nbr, c->nsm, 4)));
   CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * sizeof(double), st));
-  CUDA_TRY(cudaMemsetAsync(ksum, 0, sizeof(double) * NL * nbk, st));
-  CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * NL * nbr, st));
+  CUDA_TRY(cudaMemsetAsync(ksum, 0, sizeof(double) * (NL * nbk + 1), st));
+  CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * (NL * nbr + 1), st));
   if (p->compensate) {
     std::vector<T> w(N);
     for (int i = 0; i < N; ++i) {
@@ -1373,7 +1386,7 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
   TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn, &xr));
   TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, cbase + f0, cnt, tn, &xr));
   const unsigned gk = grid_of((long long)N * N * (N / 2 + 1), c->nsm, tn.per_sm_k);
-  const size_t smk = sizeof(double) * NL * nbk, smr = sizeof(double) * NL * nbr;
+  const size_t smk = sums_smem(NL * nbk), smr = sums_smem(NL * nbr);
   const int Lc = want_xi ? (rg->full ? N : 2 * rg->jm + 1) : 0;
   double pk_scale = 1.0;
   if (bis) {

@@ -6,7 +6,7 @@
 //               each CTA owns 512/CL rows and 256/CL columns, and the row
 //               spectra go straight to the owner of each column by stores into
 //               its distributed shared memory;
-//   x pass      (tiles of 16 kz columns of one ky): C2C along x.
+//   x pass      (tiles of 16 consecutive (ky, kz) columns, moved by TMA): C2C along x.
 // The inverse runs the x pass then the mirrored plane pass (C2C along y, C2R
 // along z).  The x pass can also apply, between a forward and an inverse
 // transform, the spectral product F conj(D) s W^-2 of the convolution steps
@@ -125,6 +125,17 @@ __device__ __forceinline__ void idft(float2 (&v)[L]) {  // e^{+i} direction, unn
 
 __device__ __forceinline__ int col_b(int j) { return j ? 32 - j : 16; }
 
+// Twiddles of thread j of a group: fwd(k1) = W512^(k1 j), k1 = 1..31; inv_a(n1) = W512^(ka n1),
+// inv_b(n1) = W512^(kb n1), n1 = 1..15 (ka = j, kb = col_b(j)).  TabTw reads them from the padded
+// shared table TW[k1 * ES + j] = W512^(k1 j).
+struct TabTw {
+  const float2 *TW;
+  int j, kb;
+  __device__ __forceinline__ float2 fwd(int k1) const { return TW[k1 * ES + j]; }
+  __device__ __forceinline__ float2 inv_a(int n1) const { return TW[j * ES + n1]; }
+  __device__ __forceinline__ float2 inv_b(int n1) const { return TW[kb * ES + n1]; }
+};
+
 // Exchange storage of a 16-thread group, 32 x 16 complex slots (a, b): a padded row-major
 // buffer (row stride ES, bank-conflict free).
 struct PadEx {
@@ -136,12 +147,12 @@ struct PadEx {
 // Out: A[k2] = X[ka + 32 k2], B[k2] = X[kb + 32 k2].  TW[k1 * ES + j] = W512^(k1 j);
 // ex: this group's exchange storage, slots (a, b) with a < 32, b < 16 (a < 16 with HALF: the
 // exchange then runs in two rounds, k1 < 16 then k1 >= 16); gm: this group's lane mask.
-template <bool HALF = false, class EXS>
-__device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
-                                       const float2 *__restrict__ TW, const EXS &ex) {
+template <bool HALF = false, class EXS, class TWS>
+__device__ __forceinline__ void fwd512x(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
+                                       const TWS &tw, const EXS &ex) {
   dft<32, 5>(v);
 #pragma unroll
-  for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], TW[k1 * ES + j]);
+  for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], tw.fwd(k1));
   const int ka = j, kb = col_b(j);
   __syncwarp(gm);
   if (HALF) {
@@ -173,21 +184,21 @@ __device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 
 template <bool HALF = false>
 __device__ __forceinline__ void fwd512(float2 (&v)[32], float2 (&A)[16], float2 (&B)[16], int j, unsigned gm,
                                        const float2 *__restrict__ TW, float2 *E) {
-  fwd512<HALF>(v, A, B, j, gm, TW, PadEx{E});
+  fwd512x<HALF>(v, A, B, j, gm, TabTw{TW, j, col_b(j)}, PadEx{E});
 }
 
 // Inverse (e^{+i}, unnormalised) 512-point DFT by a 16-thread group, from the
 // layout fwd512 produces to v[m] = x[16 m + j].
-template <bool HALF = false, class EXS>
-__device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
-                                       const float2 *__restrict__ TW, const EXS &ex) {
+template <bool HALF = false, class EXS, class TWS>
+__device__ __forceinline__ void inv512x(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
+                                       const TWS &tw, const EXS &ex) {
   idft<16, 4>(A);
   idft<16, 4>(B);
   const int ka = j, kb = col_b(j);
 #pragma unroll
   for (int n1 = 1; n1 < 16; ++n1) {
-    A[n1] = cmulc(A[n1], TW[ka * ES + n1]);
-    B[n1] = cmulc(B[n1], TW[kb * ES + n1]);
+    A[n1] = cmulc(A[n1], tw.inv_a(n1));
+    B[n1] = cmulc(B[n1], tw.inv_b(n1));
   }
   __syncwarp(gm);
   if (HALF) {
@@ -218,7 +229,7 @@ __device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 
 template <bool HALF = false>
 __device__ __forceinline__ void inv512(float2 (&A)[16], float2 (&B)[16], float2 (&v)[32], int j, unsigned gm,
                                        const float2 *__restrict__ TW, float2 *E) {
-  inv512<HALF>(A, B, v, j, gm, TW, PadEx{E});
+  inv512x<HALF>(A, B, v, j, gm, TabTw{TW, j, col_b(j)}, PadEx{E});
 }
 
 // Two spectra from the transform of z = a + i b (a, b real sequences):
@@ -444,233 +455,8 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 }
 
 // ---------------------------------------------------------------------------
-// x pass: C2C along x for tiles of TC kz columns of one ky
-// mode 0 forward, 1 inverse, 2 forward -> * conj(D) s W^-2 -> inverse
-// Persistent: a few CTAs per SM walk the tiles; each tile is copied into shared
-// memory with cp.async while the previous one is transformed, so loads overlap the
-// FFT work.  Mode 2 walks position-major: a CTA takes the tile positions (ky, kz0)
-// p = blockIdx.x, blockIdx.x + gridDim.x, ... and at each one every field of the
-// launch in turn, so the D tile of a position is copied once (prefetched during the
-// last field of the previous position) and serves all of them.
-// block TC * 16 (TC groups, one column each)
-// ---------------------------------------------------------------------------
-constexpr int XTC = 16;                    // kz columns per tile (128-byte row segments; 8 measured slower)
-template <int TC>
-struct XShape {
-  static constexpr int NT = TC * 16;                   // threads
-  // tile positions of a slot: TC consecutive kz < 256 of one ky (KZF per ky), then the
-  // kz = 256 (Nyquist) columns of TC consecutive ky, so that no tile is mostly empty
-  static constexpr int KZF = 256 / TC;
-  static constexpr long long NPOS = (long long)KZF * NM + NM / TC;
-  // tile row stride (float2): >= EX for the exchange buffer; TC * XS + x spreads the
-  // tile writes of a half-warp (16 / TC rows of x) over distinct banks
-  static constexpr int XS = TC == 16 ? 545 : 546;
-  static constexpr size_t SMEM01 = sizeof(float2) * (EX + 2 * TC * XS);
-  static constexpr size_t SMEM2 = sizeof(float2) * (EX + 3 * TC * XS) + sizeof(float) * NM;
-  static constexpr int PER_SM01 = TC == 16 ? 1 : 3;   // CTAs per SM the grid is sized for
-  static constexpr int PER_SM2 = TC == 16 ? 1 : 2;
-};
-
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-struct XTile {
-  long long off;   // offset of column 0 within a slot, complex units
-  int slot, ky, kz0, nvalid;
-  int nyq;         // 0: column c is (ky, kz0 + c); 1: column c is (ky + c, 256)
-  int cst;         // complex units from column c to column c + 1 (1, or HZ for the kz = 256 columns)
-};
-
-template <int TC>
-__device__ __forceinline__ XTile x_tile(long long t) {
-  using X = XShape<TC>;
-  XTile r;
-  const long long p = t % X::NPOS;
-  r.slot = (int)(t / X::NPOS);
-  if (p < (long long)X::KZF * NM) {
-    r.ky = (int)(p / X::KZF);
-    r.kz0 = (int)(p % X::KZF) * TC;
-    r.nyq = 0;
-    r.cst = 1;
-  } else {
-    r.ky = (int)(p - (long long)X::KZF * NM) * TC;
-    r.kz0 = NM / 2;
-    r.nyq = 1;
-    r.cst = HZ;
-  }
-  r.nvalid = TC;
-  r.off = (long long)r.ky * HZ + r.kz0;
-  return r;
-}
-
-// asynchronous copy of one tile: T[c][x] = src[x][c], c < nvalid; one commit group.
-// Thread e copies column c = e % TC at rows x = e / TC + (NT / TC) q, q = 0..NM TC / NT - 1,
-// unrolled so that no copy waits for the previous one to release its address registers.
-// Rows outside [xlo, xhi) are known to be zero (planes that hold no painted value): they are
-// written as zeros instead of copied.
-template <int TC>
-__device__ __forceinline__ void x_tile_issue(float2 *T, const float2 *src, int nvalid, int cst, int xlo = 0,
-                                             int xhi = NM) {
-  constexpr int NT = XShape<TC>::NT, XR = NT / TC, NQ = NM * TC / NT;
-  const long long xs = (long long)NM * HZ;
-  const int c = threadIdx.x % TC, x0 = threadIdx.x / TC;
-  if (c < nvalid) {
-    float2 *t = T + c * XShape<TC>::XS + x0;
-    const float2 *g = src + x0 * xs + (long long)c * cst;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const int x = x0 + q * XR;
-      if (x >= xlo && x < xhi)
-        cp_async8(t + q * XR, g + (long long)q * XR * xs);
-      else
-        t[q * XR] = make_float2(0.f, 0.f);
-    }
-  }
-  cp_async_commit();
-}
-
-template <int MODE, int TC>
-__global__ void __launch_bounds__(XShape<TC>::NT, 1)
-    fft512_x(float2 *__restrict__ data, long long slot_cplx, long long ntiles, const float2 *__restrict__ gtw,
-             const float2 *__restrict__ D, const double *__restrict__ scale, const float *__restrict__ invw,
-             int xlo, int xhi) {
-  using X = XShape<TC>;
-  constexpr int XS_ = X::XS;
-  extern __shared__ float4 smem4[];
-  float2 *TW = (float2 *)smem4;   // [32][ES]
-  float2 *buf0 = TW + EX;         // tile buffers [TC][XS_]: column c, x = 0..511; double as exchange buffers
-  float2 *buf1 = buf0 + TC * XS_;
-  float2 *buf2 = buf1 + TC * XS_;  // mode 2: buf1 holds D, data alternates between buf0 and buf2
-  float *W1 = (float *)(buf2 + TC * XS_);   // mode 2: per-axis 1/W (compensation), when given
-  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
-  const unsigned gm = 0xFFFFu << (tid & 16);
-  const int ka = j, kb = col_b(j);
-  const long long xs = (long long)NM * HZ;
-  // modes 0, 1: t is the tile index; mode 2: t is the position, f the field
-  const long long npos = X::NPOS;
-  const int nf = MODE == 2 ? (int)(ntiles / npos) : 1;
-  const long long tend = MODE == 2 ? npos : ntiles;
-  long long t = blockIdx.x;
-  int f = 0;
-  XTile cur = x_tile<TC>(t);
-  x_tile_issue<TC>(buf0, data + (long long)cur.slot * slot_cplx + cur.off, cur.nvalid, cur.cst, xlo, xhi);
-  if (MODE == 2) x_tile_issue<TC>(buf1, D + cur.off, cur.nvalid, cur.cst);
-  for (int i = tid; i < EX; i += X::NT) TW[i] = gtw[i];
-  if (MODE == 2 && invw)
-    for (int i = tid; i < NM; i += X::NT) W1[i] = invw[i];
-  float2 *A = buf0;
-  while (t < tend) {
-    if (MODE == 2)
-      cp_async_wait<1>();         // this tile's data (its D may still be in flight)
-    else
-      cp_async_wait<0>();
-    __syncthreads();
-    long long tn = t;
-    int fn = f + 1;
-    if (fn >= nf) {               // modes 0, 1 always; mode 2 after the last field of a position
-      tn = t + gridDim.x;
-      fn = 0;
-    }
-    const bool has_next = tn < tend;
-    const XTile nxt = has_next ? x_tile<TC>(tn + (long long)fn * npos) : cur;
-    float2 *Anext = MODE == 2 ? (A == buf0 ? buf2 : buf0) : (A == buf0 ? buf1 : buf0);
-    if (has_next)
-      x_tile_issue<TC>(Anext, data + (long long)nxt.slot * slot_cplx + nxt.off, nxt.nvalid, nxt.cst, xlo, xhi);
-    else
-      cp_async_commit();
-    float2 *col = A + g * XS_;
-    float2 v[32], As[16], Bs[16];
-    const float s = MODE == 2 ? (float)scale[cur.slot] : 1.f;   // issued before the transform hides its latency
-    if (MODE == 1) {
-#pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        As[k2] = col[ka + 32 * k2];
-        Bs[k2] = col[kb + 32 * k2];
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < 32; ++m) v[m] = col[16 * m + j];
-      fwd512(v, As, Bs, j, gm, TW, col);
-    }
-    if (MODE == 2) {
-      if (f == 0) {               // a new position: its D tile (the group before this tile's prefetch)
-        cp_async_wait<1>();
-        __syncthreads();
-      }
-      float2 *dcol = buf1 + g * XS_;
-      if (f == 0) {
-        // D <- conj(D) W^-2 in place, once per position: every thread rewrites exactly the
-        // entries kx = ka + 32 k2, kb + 32 k2 of its column that it reads below (the pairs
-        // (ka, kb) of the 16 threads cover 0..31 once), so no other thread depends on them
-        const int gc = g < cur.nvalid ? g : 0;
-        const float cyz = invw ? W1[cur.ky + (cur.nyq ? gc : 0)] * W1[cur.kz0 + (cur.nyq ? 0 : gc)] : 1.f;
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-          const int kxa = ka + 32 * k2, kxb = kb + 32 * k2;
-          float wa = 1.f, wb = 1.f;
-          if (invw) {
-            wa = W1[kxa] * cyz;
-            wb = W1[kxb] * cyz;
-          }
-          dcol[kxa] = cscale(cconj(dcol[kxa]), wa * wa);
-          dcol[kxb] = cscale(cconj(dcol[kxb]), wb * wb);
-        }
-      }
-#pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        As[k2] = cscale(cmul(As[k2], dcol[ka + 32 * k2]), s);
-        Bs[k2] = cscale(cmul(Bs[k2], dcol[kb + 32 * k2]), s);
-      }
-      if (has_next && fn == 0) {  // the next tile starts another position: prefetch its D
-        __syncthreads();          // once every group is done with this one
-        x_tile_issue<TC>(buf1, D + nxt.off, nxt.nvalid, nxt.cst);
-      } else {
-        cp_async_commit();
-      }
-    }
-    if (MODE == 0) {
-      __syncwarp(gm);
-#pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        col[ka + 32 * k2] = As[k2];
-        col[kb + 32 * k2] = Bs[k2];
-      }
-    } else {
-      inv512(As, Bs, v, j, gm, TW, col);
-      __syncwarp(gm);
-#pragma unroll
-      for (int m = 0; m < 32; ++m) col[16 * m + j] = v[m];
-    }
-    __syncthreads();
-    {   // write-out: every value of this thread's rows is read from shared memory first, then stored
-      constexpr int XR = X::NT / TC, NQ = NM * TC / X::NT;
-      const int c = tid % TC, x0 = tid / TC;
-      if (c < cur.nvalid) {
-        float2 o[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) o[q] = A[c * XS_ + x0 + q * XR];
-        float2 *base = data + (long long)cur.slot * slot_cplx + cur.off + x0 * xs + (long long)c * cur.cst;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) base[(long long)q * XR * xs] = o[q];
-      }
-    }
-    cur = nxt;
-    A = Anext;
-    t = tn;
-    f = fn;
-  }
-  cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
-// x pass through the tensor memory accelerator (the x pass every caller uses).
+// x pass (C2C along x) through the tensor memory accelerator: mode 0 forward, 1 inverse,
+// 2 forward -> * conj(D) s W^-2 -> inverse.
 // The columns of a half-spectrum slot are taken in the flattened order f = ky HZ + kz (x stride
 // NM HZ complex values).  A tile is XC = 16 consecutive columns -- 128 contiguous bytes per
 // row, every tile starting on a 128-byte boundary whatever its ky -- and all 512 rows; a slot
@@ -682,8 +468,7 @@ __global__ void __launch_bounds__(XShape<TC>::NT, 1)
 // Persistent: one 256-thread CTA per SM.  Modes 0 and 1 keep three tile buffers (load of the
 // next tile, transform of this one, store of the previous one in flight); mode 2 keeps two data
 // buffers and the tile of D, walks the tile positions and, at each one, every field of the launch,
-// so D is read once per launch; each thread keeps its conj(D) W^-2 entries in registers for the
-// fields of a position, and the next position's D tile loads as soon as the first field is done.  Waits on the tile barriers give up after about two seconds,
+// so D is read once per launch.  Waits on the tile barriers give up after about two seconds,
 // record a fault in *fault and end the kernel once the copies in flight have landed.
 // ---------------------------------------------------------------------------
 constexpr int XC = 16;                              // columns per tile
@@ -705,6 +490,18 @@ struct XtLayout {                                   // dynamic shared memory, fr
 __device__ __forceinline__ unsigned xt_off(int x, int c) {
   return (unsigned)(x * 128 + ((((c >> 1) ^ x) & 7) << 4) + ((c & 1) << 3));
 }
+
+// Twiddles of the x pass: thread j keeps W512^(a j) (a < 8) and W512^(8 b j) (b < 4) in registers
+// and forms W512^(k j) = W512^(8 (k / 8) j) W512^((k mod 8) j) with one complex multiply (about
+// two roundings instead of one); the kb half of the inverse reads the shared table.
+struct RegTw {
+  float2 t1[8], t8[4];
+  const float2 *TW;
+  int kb;
+  __device__ __forceinline__ float2 fwd(int k) const { return (k >> 3) ? cmul(t8[k >> 3], t1[k & 7]) : t1[k & 7]; }
+  __device__ __forceinline__ float2 inv_a(int n1) const { return fwd(n1); }
+  __device__ __forceinline__ float2 inv_b(int n1) const { return TW[kb * ES + n1]; }
+};
 
 struct XtCol {                                      // one column of a swizzled tile
   unsigned char *tile;
@@ -792,6 +589,13 @@ __global__ void __launch_bounds__(256, 1)
   if (MODE == 2 && invw)
     for (int i = tid; i < NM; i += blockDim.x) W1[i] = invw[i];
   __syncthreads();
+  RegTw tw;
+  tw.TW = TW;
+  tw.kb = kb;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) tw.t1[a] = TW[a * ES + j];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) tw.t8[b] = TW[8 * b * ES + j];
 
   // item i = (unit u, field f): modes 0, 1 take the tiles of every slot (f = 0), mode 2 the
   // positions with every field; data buffer i % NDB, whose barrier completes once per use
@@ -819,7 +623,6 @@ __global__ void __launch_bounds__(256, 1)
   }
   bool ok = true;
   long long i = 0;
-  float2 dr[32];                                     // mode 2: conj(D) W^-2 of this thread's entries
   for (long long k = 0; u < nunits && ok; u += gridDim.x, ++k) {
     for (int f = 0; f < nf && ok; ++f, ++i) {
       const int b = (int)(i % NDB);
@@ -874,13 +677,13 @@ __global__ void __launch_bounds__(256, 1)
       } else {
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = col.at(16 * m + j);
-        fwd512(v, As, Bs, j, gm, TW, col);
+        fwd512x(v, As, Bs, j, gm, tw, col);
       }
       if (MODE == 2) {
+        const XtCol dcol{sm + (size_t)2 * XTILE, g};
         if (f == 0) {
-          // conj(D) W^-2 at this thread's entries kx = ka + 32 k2 (dr[k2]) and kb + 32 k2
-          // (dr[16 + k2]), kept in registers for every field of the position
-          const XtCol dcol{sm + (size_t)2 * XTILE, g};
+          // D <- conj(D) W^-2 in place, once per position: every thread rewrites exactly the
+          // entries kx = ka + 32 k2, kb + 32 k2 of its column that it reads below
           const long long fc = tl * XC + g;
           const int ky = (int)(fc / HZ), kz = (int)(fc % HZ);
           const float cyz = invw ? W1[ky] * W1[kz] : 1.f;
@@ -892,14 +695,14 @@ __global__ void __launch_bounds__(256, 1)
               wa = W1[kxa] * cyz;
               wb = W1[kxb] * cyz;
             }
-            dr[k2] = cscale(cconj(dcol.at(kxa)), wa * wa);
-            dr[16 + k2] = cscale(cconj(dcol.at(kxb)), wb * wb);
+            dcol.at(kxa) = cscale(cconj(dcol.at(kxa)), wa * wa);
+            dcol.at(kxb) = cscale(cconj(dcol.at(kxb)), wb * wb);
           }
         }
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
-          As[k2] = cscale(cmul(As[k2], dr[k2]), s);
-          Bs[k2] = cscale(cmul(Bs[k2], dr[16 + k2]), s);
+          As[k2] = cscale(cmul(As[k2], dcol.at(ka + 32 * k2)), s);
+          Bs[k2] = cscale(cmul(Bs[k2], dcol.at(kb + 32 * k2)), s);
         }
       }
       if (MODE == 0) {
@@ -910,7 +713,7 @@ __global__ void __launch_bounds__(256, 1)
           col.at(kb + 32 * k2) = Bs[k2];
         }
       } else {
-        inv512(As, Bs, v, j, gm, TW, col);
+        inv512x(As, Bs, v, j, gm, tw, col);
         __syncwarp(gm);
 #pragma unroll
         for (int m = 0; m < 32; ++m) col.at(16 * m + j) = v[m];
@@ -920,7 +723,7 @@ __global__ void __launch_bounds__(256, 1)
       if (tid == 0) {
         for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, (int)(tl * (2 * XC)), x0, slot, tile + (size_t)x0 * 128);
         bulk_commit();
-        if (MODE == 2 && f == 0 && u + gridDim.x < nunits) {   // D of the next position: this one is in registers
+        if (MODE == 2 && f == nf - 1 && u + gridDim.x < nunits) {   // D of the next position
           issue_d(u + gridDim.x);
           pend |= 4u;
           ppar = (ppar & ~4u) | ((unsigned)((k + 1) & 1) << 2);

@@ -87,11 +87,23 @@ __device__ __forceinline__ V bym_wsum(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(BYM_FULL, v, o);
   return v;
 }
-// Per-block FP64 shell sums: every lane holds (bin, v[NL]); lanes that share a
-// bin are pre-reduced with shuffles in the value type V (at most 32 terms) and
-// the group leader adds the partial sum to the FP64 shared accumulator.
+// FP64 shell sums of n = nbins * NL values.  Every lane holds (bin, v[NL]); lanes that share a bin
+// are pre-reduced with shuffles (a fixed butterfly) and the group leader adds the partial sum to a
+// shared accumulator.  With dynamic shared memory for one accumulator per warp (8 n doubles; 256
+// threads) each warp adds into its own in the order of its bins, the block adds the 8 in warp order,
+// every block writes its totals after the n sums in global memory (g[n] is a ticket counter,
+// g[n + 1 + b n + i] block b's total of sum i), and the last block to finish adds them in block
+// order: the sums are then the same on every run.  With room for one accumulator the warps share it
+// through atomics, which orders the additions by arrival.
+__device__ __forceinline__ int bym_nacc(int n) {
+  unsigned sz;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(sz));
+  return sz >= 64u * (unsigned)n ? 8 : 1;
+}
 template <int NL, typename V>
-__device__ __forceinline__ void bym_bin_flush(int bin, const V (&v)[NL], double *s) {
+__device__ __forceinline__ void bym_bin_flush(int bin, const V (&v)[NL], double *s, int n) {
+  const bool own = bym_nacc(n) == 8;
+  double *sw = own ? s + (threadIdx.x >> 5) * n : s;
   unsigned pending = __ballot_sync(BYM_FULL, bin >= 0);
   const int lane = threadIdx.x & 31;
   while (pending) {
@@ -102,21 +114,44 @@ __device__ __forceinline__ void bym_bin_flush(int bin, const V (&v)[NL], double 
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const V x = bym_wsum<V>(mine ? v[l] : (V)0);
-      if (lane == leader) atomicAdd(s + bl * NL + l, (double)x);
+      if (lane == leader) {
+        if (own)
+          sw[bl * NL + l] += (double)x;
+        else
+          atomicAdd(sw + bl * NL + l, (double)x);
+      }
     }
     pending &= ~grp;
   }
 }
 __device__ __forceinline__ void bym_bins_init(double *s, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = 0.0;
+  const int m = bym_nacc(n) * n;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = 0.0;
   __syncthreads();
 }
 __device__ __forceinline__ void bym_bins_out(const double *s, double *g, int n) {
+  __shared__ int bym_last;
   __syncthreads();
+  const int nacc = bym_nacc(n);
+  double *part = g + n + 1;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double x = s[i];
-    if (x != 0.0) atomicAdd(g + i, x);
+    double x = 0.0;
+    for (int w = 0; w < nacc; ++w) x += s[w * n + i];
+    part[(long long)blockIdx.x * n + i] = x;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    bym_last = atomicAdd((unsigned long long *)(g + n), 1ull) == (unsigned long long)(gridDim.x - 1);
+  __syncthreads();
+  if (!bym_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double x = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) x += __ldcg(part + (long long)b * n + i);
+    g[i] += x;
+  }
+  if (threadIdx.x == 0) *(unsigned long long *)(g + n) = 0ull;
 }
 __device__ __forceinline__ int bym_lab(int i, int N) { return i < N / 2 ? i : i - N; }
 __device__ __forceinline__ float bym_rsqrt(float x) { return rsqrtf(x); }
@@ -324,7 +359,7 @@ int emit_xi_lag(std::ostream &o, const char *name, const JitKey &key, int f0, in
     }
   }
   o << "      }\n    }\n";
-  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s, nbins * " << NL << ");\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
   return jlag;
 }
 
@@ -422,7 +457,7 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
     o << " v[" << l / 2 << "] = w * T; }\n";
   }
   o << "        }\n      }\n    }\n";
-  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+  o << "    bym_bin_flush<" << NL << ", double>(bin, v, s, nbins * " << NL << ");\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
 }
 
 }  // namespace
@@ -457,7 +492,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   o << "      bin = lut[n2];\n";
   o << "      if (bin >= 0) { const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;"
        " v[0] = w; v[1] = w * kf * sqrt((double)n2); }\n";
-  o << "    }\n    bym_bin_flush<2, double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
+  o << "    }\n    bym_bin_flush<2, double>(bin, v, s, nbins * 2);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
 
   o << "extern \"C\" __global__ void __launch_bounds__(256) rgeom(int N, int jm, int full,"
        " const int* __restrict__ lut, int nbins, double h, double* __restrict__ gsum) {\n";
@@ -473,7 +508,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   o << "      const int j2 = jx * jx + jy * jy + jz * jz;\n";
   o << "      bin = lut[j2];\n";
   o << "      if (bin >= 0) { v[0] = 1.0; v[1] = h * sqrt((double)j2); }\n";
-  o << "    }\n    bym_bin_flush<2, double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
+  o << "    }\n    bym_bin_flush<2, double>(bin, v, s, nbins * 2);\n  }\n  bym_bins_out(s, gsum, nbins * 2);\n}\n";
 
   // ------------------------------------------------------------------ k-space contraction
   auto emit_kcontract = [&](const char *name, bool with_x) {
@@ -539,7 +574,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
       o << " v[" << l / 2 << "] = w * T; }\n";
     }
     o << "        }\n      }\n    }\n";
-    o << "    bym_bin_flush<" << NL << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
+    o << "    bym_bin_flush<" << NL << ", double>(bin, v, s, nbins * " << NL << ");\n  }\n  bym_bins_out(s, gsum, nbins * " << NL << ");\n}\n";
   };
   emit_kcontract("kcontract", false);
   if (key.los == 2) emit_kcontract("kcontract_x", true);
@@ -660,7 +695,7 @@ void emit_k_tail(std::ostream &o, int L, bool f32, int NLo) {
     o << " v[" << (l - 1) / 2 << "] = w * T; }\n";
   }
   o << "        }\n      }\n    }\n";
-  o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
+  o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s, nbins * " << NLo << ");\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
 }
 
 }  // namespace
@@ -809,7 +844,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
     }
   }
   o << "      }\n    }\n";
-  o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s);\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
+  o << "    bym_bin_flush<" << NLo << ", double>(bin, v, s, nbins * " << NLo << ");\n  }\n  bym_bins_out(s, gsum, nbins * " << NLo << ");\n}\n";
 
   if (meta) {
     meta->fields = list;

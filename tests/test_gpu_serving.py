@@ -58,11 +58,9 @@ def test_results_same_alone_and_in_the_mix(pkg, cap):
     assert stats["count"] == len(items)
     assert stats["p99_s"] >= stats["p50_s"] > 0
     for it, a, m in zip(items, alone, mixed):
-        # the painted mesh is the same bit for bit alone and in the mix; the FP64 shell sums differ
-        # only in the order of their atomic adds
-        check_multipoles(m["pk"], a["pk"], "pk", 1e-12, 1e-12)
-        check_multipoles(m["xi"], a["xi"], "xi", 1e-12, 1e-12)
-        np.testing.assert_array_equal(m["n_modes"], a["n_modes"])
+        # painting and shell sums do not depend on what else runs: the same bits alone and in the mix
+        for key in ("pk", "xi", "k_mean", "r_mean", "n_modes", "n_cells"):
+            np.testing.assert_array_equal(m[key], a[key], err_msg=f"{key} of {it['params'].los}")
 
 
 def test_batch_run_matches_sequential(pkg, cap):
