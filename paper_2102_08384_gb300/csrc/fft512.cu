@@ -462,9 +462,10 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 // row, every tile starting on a 128-byte boundary whatever its ky -- and all 512 rows; a slot
 // has 131584 / 16 = 8224 tiles.  Tiles are loaded and stored by TMA in boxes of 32 rows with the
 // 128-byte swizzle (16-byte chunk index XOR row % 8), so the threads issue no copy or store
-// instructions of their own.  A 16-thread group transforms one column; the exchange of the
-// 512-point engine runs in place in that column's own storage (slot (a, b) at row
-// 16 a + (b ^ (a % 16))), which keeps every shared access of a warp at two wavefronts.
+// instructions of their own.  A 16-thread group (alternate lanes of a warp) transforms one
+// column; the exchange of the 512-point engine runs in place in that column's own storage (slot
+// (a, b) at row 16 a + (b ^ (a % 16))), which keeps every shared access of a warp at two
+// wavefronts, one per half-warp.
 // Persistent: one 256-thread CTA per SM.  Modes 0 and 1 keep three tile buffers (load of the
 // next tile, transform of this one, store of the previous one in flight); mode 2 keeps two data
 // buffers and the tile of D, walks the tile positions and, at each one, every field of the launch,
@@ -482,7 +483,9 @@ struct XtLayout {                                   // dynamic shared memory, fr
   static constexpr int NBUF = 3;                    // modes 0, 1: three tiles; mode 2: two tiles + the D tile
   static constexpr size_t TW_OFF = (size_t)NBUF * XTILE;
   static constexpr size_t W1_OFF = TW_OFF + sizeof(float2) * EX;
-  static constexpr size_t BAR_OFF = W1_OFF + sizeof(float) * NM;
+  static constexpr int NSC = 512;                   // mode 2: fields per launch (their scales s)
+  static constexpr size_t SC_OFF = W1_OFF + sizeof(float) * NM;
+  static constexpr size_t BAR_OFF = SC_OFF + sizeof(float) * NSC;
   static constexpr size_t BYTES = BAR_OFF + 8 * NBUF + 1024;
 };
 
@@ -571,12 +574,16 @@ __global__ void __launch_bounds__(256, 1)
   unsigned char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   float2 *TW = (float2 *)(sm + L::TW_OFF);
   float *W1 = (float *)(sm + L::W1_OFF);
+  float *SC = (float *)(sm + L::SC_OFF);
   unsigned long long *bar = (unsigned long long *)(sm + L::BAR_OFF);
-  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
-  const unsigned gm = 0xFFFFu << (tid & 16);
+  // the two groups of a warp take alternate lanes: a column of a tile uses one 8-byte half of each
+  // 16-byte chunk, so each half-warp (which the 8-byte accesses are served by) then covers both
+  // halves of 8 chunks -- 16 different bank pairs, one wavefront -- where a whole group in one
+  // half-warp would meet each bank pair twice
+  const int tid = threadIdx.x, lane = tid & 31, g = 2 * (tid >> 5) + (lane & 1), j = lane >> 1;
+  const unsigned gm = 0x55555555u << (lane & 1);
   const int ka = j, kb = col_b(j);
   const int lo = MODE == 1 ? 0 : xlo, hi = MODE == 1 ? NM : xhi;   // rows read from HBM
-  const bool part = lo > 0 || hi < NM;
   const long long nunits = MODE == 2 ? XNT : (long long)nslots * XNT;
   const int nf = MODE == 2 ? nslots : 1;
   constexpr int NDB = MODE == 2 ? 2 : 3;            // data buffers
@@ -588,6 +595,8 @@ __global__ void __launch_bounds__(256, 1)
   for (int i = tid; i < EX; i += blockDim.x) TW[i] = gtw[i];
   if (MODE == 2 && invw)
     for (int i = tid; i < NM; i += blockDim.x) W1[i] = invw[i];
+  if (MODE == 2)
+    for (int i = tid; i < nf; i += blockDim.x) SC[i] = (float)scale[i];
   __syncthreads();
   RegTw tw;
   tw.TW = TW;
@@ -636,15 +645,6 @@ __global__ void __launch_bounds__(256, 1)
         if (MODE == 2 && f == 0) pend &= ~4u;
       }
       unsigned char *tile = sm + (size_t)b * XTILE;
-      if (MODE != 1 && part) {                       // rows outside [lo, hi) hold no painted value
-        for (int r = tid; r < NM - (hi - lo); r += blockDim.x) {
-          const int x = r < lo ? r : r + (hi - lo);
-          float4 *row = (float4 *)(tile + (size_t)x * 128);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        __syncthreads();
-      }
       if (tid == 0) {                                // prefetch the next item
         long long un = u;
         int fn = f + 1;
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(256, 1)
       const long long tl = MODE == 2 ? u : u % XNT;
       const XtCol col{tile, g};
       float2 v[32], As[16], Bs[16];
-      const float s = MODE == 2 ? (float)scale[f] : 1.f;
+      const float s = MODE == 2 ? SC[f] : 1.f;
       if (MODE == 1) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
@@ -675,8 +675,11 @@ __global__ void __launch_bounds__(256, 1)
           Bs[k2] = col.at(kb + 32 * k2);
         }
       } else {
+        // rows outside [lo, hi) hold no painted value and were not loaded: lo and hi are multiples
+        // of 32, so row 16 m + j lies in the range exactly when m does in [lo / 16, hi / 16)
+        const int mlo = lo >> 4, mhi = hi >> 4;
 #pragma unroll
-        for (int m = 0; m < 32; ++m) v[m] = col.at(16 * m + j);
+        for (int m = 0; m < 32; ++m) v[m] = (m >= mlo && m < mhi) ? col.at(16 * m + j) : make_float2(0.f, 0.f);
         fwd512x(v, As, Bs, j, gm, tw, col);
       }
       if (MODE == 2) {
@@ -864,6 +867,7 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
   cudaError_t e = slot_map(&tm, b, slot_reals, n);
   if (e == cudaSuccess) e = slot_map(&tmd, MODE == 2 ? (float *)D : b, slot_reals, 1);
   if (e != cudaSuccess) return e;
+  if (MODE == 2 && n > XtLayout::NSC) return cudaErrorInvalidValue;
   const long long units = MODE == 2 ? XNT : XNT * n;
   const long long grid = std::min<long long>(units, (long long)sm_count(dev));
   fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmd, n, tw, scale, invw, xlo, xhi,
@@ -949,8 +953,9 @@ cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int f
   const float2 *tw = twiddles(dev);
   float *base = slots + (long long)first * slot_reals;
   cudaError_t e = cudaSuccess;
-  for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
-    const int n = count - done < 65535 ? count - done : 65535;
+  const int step = mode == 2 ? XtLayout::NSC : 65535;
+  for (int done = 0; done < count && e == cudaSuccess; done += step) {
+    const int n = count - done < step ? count - done : step;
     float *b = base + (long long)done * slot_reals;
     e = mode == 0   ? xpass<0>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st, xlo, xhi)
         : mode == 1 ? xpass<1>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)
@@ -970,8 +975,8 @@ cudaError_t native_fft_convolve(float *slots, long long slot_reals, int first, i
   const float2 *tw = twiddles(dev);
   float *base = slots + (long long)first * slot_reals;
   cudaError_t e = cudaSuccess;
-  for (int done = 0; done < count && e == cudaSuccess; done += 65535) {
-    const int n = count - done < 65535 ? count - done : 65535;
+  for (int done = 0; done < count && e == cudaSuccess; done += XtLayout::NSC) {
+    const int n = count - done < XtLayout::NSC ? count - done : XtLayout::NSC;
     float *b = base + (long long)done * slot_reals;
     if ((e = plane(cluster, false, b, slot_reals, n, tw, st)) != cudaSuccess) break;
     if ((e = xpass<2>(b, slot_reals, n, tw, D, scale + done, invw, st)) != cudaSuccess) break;
