@@ -410,7 +410,7 @@ def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
             def run():
                 ctx.pk_xi_multipoles(gal_d, ran_d, p, KEDGES, REDGES, ran_nbar=rnb_d, stream=sh)
         n_f = {"midpoint_even": 88, "midpoint": 145, "bisector": 49, "yamamoto": 15}[los]
-        slot = n_mesh * n_mesh * (n_mesh + 2) * 4
+        slot = n_mesh * n_mesh * (n_mesh + 4) * 4
         if odd:   # odd field sets (bisector J <= 5: 36, midpoint J - alpha odd: 110, Yamamoto: 10), 10 X / H slots
             slots = 2 + 2 * {"bisector": 36, "midpoint": 110, "yamamoto": 10}[los] + (0 if los == "yamamoto" else 10)
         elif chunk and los == "midpoint":
@@ -455,7 +455,7 @@ def large_mesh_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d):
     stream = torch.cuda.current_stream(dev)
     try:
         for N, mchunk, bchunk in ((768, 24, 16), (1024, 16, 8)):
-            slot = N * N * (N + 2) * 4
+            slot = N * N * (N + 4) * 4
             res = {}
             for label, los, K, chunk, slots in (("yamamoto", "yamamoto", 0, 0, 16),
                                                 (f"midpoint order 4, g fields in ranges of {mchunk}", "midpoint", 4,
@@ -747,8 +747,10 @@ def _roofline(prof, steps):
     return roof, kernels, ours_launches
 
 
-# the source files that define each kernel the roofline may name
-KERNEL_SOURCES = {"fft_native_x_convolve": ["fft512.cu", "fft512.h"]}
+# the source files that define each kernel the roofline may name (the library's FFT passes)
+KERNEL_SOURCES = {k: ["fft512.cu", "fft512.h"] for k in
+                  ("fft_native_x_convolve", "fft_native_x_fwd", "fft_native_x_inv", "fft_native_y_fwd",
+                   "fft_native_y_inv", "fft_native_z_fwd", "fft_native_z_inv")}
 
 
 def _ncu_traffic(kernel):

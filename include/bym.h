@@ -228,21 +228,25 @@ int bym_shot_noise(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran,
 int bym_set_field_chunk(bym_ctx *ctx, int max_fields);
 
 /* FFT backend of ctx.  The library has its own FP32 3D FFT kernels for
- * n_mesh = 512: a plane pass (R2C along z and C2C along y of one x-plane per
- * thread-block cluster of 8 or 16 CTAs) and an x pass (C2C along x), two
- * passes over HBM per transform; in the midpoint convolution steps the
- * product with conj(delta) sits inside the x pass, between its forward and
- * inverse transforms.  mode 0: cuFFT 3D transforms always; 1: the library's
- * two-pass kernels wherever they apply, 8-CTA clusters; 3: the same with
- * 16-CTA clusters (a non-portable cluster size: a launch the device refuses
- * returns BYM_E_CUDA); 4: cuFFT 2D transforms of the (y, z) planes with the
- * library's x pass; 5: cuFFT 2D plane transforms with cuFFT 1D transforms along
- * x (any n_mesh and precision); 2 (the default): whichever bym_autotune measured
- * fastest for the request's shape; if it has not been tuned, mode 4 where the
- * library's kernels apply (n_mesh = 512, FP32), else cuFFT 3D.  With
- * modes 4 and 5 the forward transforms of painted fields skip the x planes that
- * hold no painted value (zero planes, zero transforms; not in requests enqueued
- * into CUDA graphs).  Returns BYM_E_INVAL for other modes. */
+ * n_mesh = 512: an x pass (C2C along x of tiles of 16 columns moved by the
+ * tensor memory accelerator), a y pass (the same along y) and a z pass (R2C /
+ * C2R along z of blocks of 32 rows moved by bulk copies), and a plane pass
+ * (R2C along z and C2C along y of one x-plane per thread-block cluster of 8
+ * or 16 CTAs); in the midpoint convolution steps the product with conj(delta)
+ * sits inside the x pass, between its forward and inverse transforms.
+ * mode 0: cuFFT 3D transforms always; 1: the library's plane pass and x pass
+ * wherever they apply, 8-CTA clusters; 3: the same with 16-CTA clusters (a
+ * non-portable cluster size: a launch the device refuses returns
+ * BYM_E_CUDA); 4: cuFFT 2D transforms of the (y, z) planes with the library's
+ * x pass; 5: cuFFT 2D plane transforms with cuFFT 1D transforms along x (any
+ * n_mesh and precision); 6: the library's z, y and x passes; 2 (the default):
+ * whichever bym_autotune measured fastest for the request's shape; if it has
+ * not been tuned, mode 6 where the library's kernels apply (n_mesh = 512,
+ * FP32), else cuFFT 3D.  With modes 4, 5 and 6 the forward transforms of
+ * painted fields skip the x planes that hold no painted value (zero planes,
+ * zero transforms), and with mode 6 also the rows y that hold none in any
+ * plane (not in requests enqueued into CUDA graphs).  Returns BYM_E_INVAL for
+ * other modes. */
 int bym_set_fft_backend(bym_ctx *ctx, int mode);
 
 /* Autotuner.  Runs the given request (which must be valid) several times on
@@ -258,9 +262,11 @@ int bym_autotune(bym_ctx *ctx, const bym_catalog *gal, const bym_catalog *ran, c
                  size_t report_len);
 
 /* In-place batched FP32 3D FFTs of `count` meshes at `data` (device), each
- * n_mesh * n_mesh * (n_mesh + 2) floats: forward R2C (inverse = 0) gives the
- * half-spectrum n_mesh * n_mesh * (n_mesh/2 + 1) complex in the same memory;
- * inverse C2R (inverse = 1) is unnormalised.  Sign e^{-i k.x} forward. */
+ * n_mesh * n_mesh * (n_mesh + 4) floats (rows of n_mesh values and 4 of
+ * padding): forward R2C (inverse = 0) gives the half-spectrum in the same
+ * memory, rows of n_mesh/2 + 2 complex values of which kz = 0..n_mesh/2 are
+ * the transform (the last is padding); inverse C2R (inverse = 1) is
+ * unnormalised.  Sign e^{-i k.x} forward (Sec. 2 Fourier convention). */
 int bym_fft3d(bym_ctx *ctx, void *data, int n_mesh, int count, int inverse, void *cuda_stream);
 
 /* Kernel tracing.  While enabled, every launch of the library's own kernels

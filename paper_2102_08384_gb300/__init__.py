@@ -263,8 +263,9 @@ class Context:
         self._check(self._L.bym_set_field_chunk(self._h, int(max_fields)))
 
     def set_fft_backend(self, mode: int):
-        """0: cuFFT, 1: the library's FFT kernels where they apply (8-CTA clusters), 2: as tuned (default),
-        3: the library's kernels with 16-CTA clusters, 4: cuFFT plane transforms + the library's x pass."""
+        """0: cuFFT, 1: the library's cluster plane pass + x pass where they apply (8-CTA clusters), 2: as
+        tuned (default), 3: the same with 16-CTA clusters, 4: cuFFT plane transforms + the library's x pass,
+        5: cuFFT plane transforms + cuFFT along x, 6: the library's z, y and x passes (bym_set_fft_backend)."""
         self._check(self._L.bym_set_fft_backend(self._h, int(mode)))
 
     # ------------------------------------------------------------ serving

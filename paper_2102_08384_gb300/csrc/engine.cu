@@ -216,7 +216,7 @@ size_t bym::footprint_bytes(const bym_params *p, int64_t n_gal, int64_t n_ran, b
                             bool cats_on_device, int chunk, bool cross) {
   const size_t N = (size_t)p->n_mesh;
   const size_t esz = p->precision == 64 ? 8 : 4;
-  const size_t slot = N * N * (N + 2) * esz;
+  const size_t slot = N * N * (N + kRowPad) * esz;
   const size_t nf = (size_t)n_fields(p);
   size_t fslots = 1 + nf;                                   // delta + every field
   if (chunk > 0 && is_midpoint(p)) fslots = 2 + std::min(nf, (size_t)chunk);          // two deltas, a range
@@ -245,12 +245,12 @@ static int get_plan(bym_ctx *c, cudaStream_t st, int N, int prec, int inverse, i
   if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftCreate failed");
   cufftSetAutoAllocation(h, 0);
   long long n3[3] = {N, N, N};
-  long long real_emb3[3] = {N, N, 2 * (N / 2 + 1)};
-  long long cplx_emb3[3] = {N, N, N / 2 + 1};
+  long long real_emb3[3] = {N, N, N + kRowPad};          // the padded layout (kernels.cuh)
+  long long cplx_emb3[3] = {N, N, (N + kRowPad) / 2};
   long long *n = rank == 2 ? n3 + 1 : n3, *real_emb = rank == 2 ? real_emb3 + 1 : real_emb3,
             *cplx_emb = rank == 2 ? cplx_emb3 + 1 : cplx_emb3;
-  const long long rdist = (long long)(rank == 2 ? 1 : N) * N * 2 * (N / 2 + 1);
-  const long long cdist = (long long)(rank == 2 ? 1 : N) * N * (N / 2 + 1);
+  const long long rdist = (long long)(rank == 2 ? 1 : N) * N * (N + kRowPad);
+  const long long cdist = (long long)(rank == 2 ? 1 : N) * N * ((N + kRowPad) / 2);
   cufftType type = prec == 64 ? (inverse ? CUFFT_Z2D : CUFFT_D2Z) : (inverse ? CUFFT_C2R : CUFFT_R2C);
   size_t work = 0;
   cufftResult r;
@@ -291,6 +291,8 @@ static const Tune &tune_for(bym_ctx *c, int N, int prec, int los) {
 // (y, z) planes with the library's x pass (and the convolution product fused into
 // it); 2 cuFFT 2D plane transforms and cuFFT 1D transforms along x (any mesh and
 // precision); 8 / 16 the library's two-pass transforms with 8- / 16-CTA plane clusters.
+// FFT path of a request: 0 cuFFT 3D, 1 cuFFT planes + library x pass, 2 cuFFT planes + cuFFT x,
+// 3 library z, y and x passes, 8 / 16 library two-pass (cluster plane pass + x pass)
 static int fft_kind(const bym_ctx *c, int N, int prec, const Tune &tn) {
   if (c->fft_mode == 5) return 2;
   if (!native_fft_supported(N, prec)) return (c->fft_mode == 2 && tn.native == 2) ? 2 : 0;
@@ -299,14 +301,17 @@ static int fft_kind(const bym_ctx *c, int N, int prec, const Tune &tn) {
     case 1: return 8;
     case 3: return 16;
     case 4: return 1;
+    case 6: return 3;
     default:
-      if (tn.native < 0) return 1;   // untuned: the plane-transform backend with the library's x pass
-      return (tn.native == 1 || tn.native == 2 || tn.native == 8 || tn.native == 16) ? tn.native : 0;
+      if (tn.native < 0) return 3;   // untuned: the library's z, y and x passes
+      return (tn.native == 1 || tn.native == 2 || tn.native == 3 || tn.native == 8 || tn.native == 16) ? tn.native
+                                                                                                       : 0;
   }
 }
 
-// cuFFT 1D C2C transforms along x of every (ky, kz) column of one slot's half spectrum (stride
-// N (N/2 + 1) complex, in place); the sign is chosen at execution
+// cuFFT 1D C2C transforms along x of every (ky, kz) column of one slot's half spectrum, the
+// padding column included (stride N (N + kRowPad) / 2 complex, in place); the sign is chosen at
+// execution
 static int get_xplan(bym_ctx *c, cudaStream_t st, int N, int prec, cufftHandle *out) {
   auto key = std::make_tuple(N, prec, 6, 1);
   auto it = c->plans.find(key);
@@ -318,7 +323,7 @@ static int get_xplan(bym_ctx *c, cudaStream_t st, int N, int prec, cufftHandle *
   if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(c, BYM_E_CUDA, "cufftCreate failed");
   cufftSetAutoAllocation(h, 0);
   long long n[1] = {N}, emb[1] = {N};
-  const long long H2 = (long long)N * (N / 2 + 1);
+  const long long H2 = (long long)N * ((N + kRowPad) / 2);
   size_t work = 0;
   const cufftResult r = cufftMakePlanMany64(h, 1, n, emb, H2, 1, emb, H2, 1, prec == 64 ? CUFFT_Z2Z : CUFFT_C2C, H2,
                                             &work);
@@ -346,6 +351,7 @@ static int get_xplan(bym_ctx *c, cudaStream_t st, int N, int prec, cufftHandle *
 // (np = 0: all): the other planes of such a field are zero, and so are their transforms.
 struct XRange {
   int x0 = 0, np = 0;
+  int y0 = 0, ny = 0;  // the rows y in [y0, y0 + ny) of every plane (ny = 0: all) hold the painted values
   bool rows = false;   // the x pass reads only the range's rows too (library x pass), so the other
                        // planes of a field slot need no zero-fill
 };
@@ -390,6 +396,40 @@ static int fft_planes(bym_ctx *c, cudaStream_t st, int inverse, int N, void *bas
   return BYM_OK;
 }
 
+// The (y, z) plane transforms of FP32 512^3 slots for the library's x pass: cuFFT 2D transforms
+// (kind 1) or the library's z and y passes (kind 3); forward over the plane range (and, kind 3,
+// the row range) of xr when given
+static int plane_transforms(bym_ctx *c, cudaStream_t st, int kind, int inverse, int N, void *base, size_t slot_bytes,
+                            int first, int count, const Tune &tn, const XRange *xr) {
+  const bool rng = !inverse && xr && xr->np > 0, yr = !inverse && xr && xr->ny > 0;
+  const int x0 = rng ? xr->x0 : 0, x1 = rng ? xr->x0 + xr->np : N;
+  const int y0 = yr ? xr->y0 : 0, y1 = yr ? xr->y0 + xr->ny : N;
+  if (kind == 1) {
+    ProfScope ps(c, st, inverse ? "cufft_planes_c2r" : "cufft_planes_r2c", count * 2.0 * 4.0 * (double)(x1 - x0) * N * N);
+    return fft_planes(c, st, inverse, N, base, slot_bytes, first, count, tn, inverse ? nullptr : xr);
+  }
+  // z pass: the rows it transforms, read and written; y pass: the rows it reads, every row written
+  const double ny = y1 - y0, np = x1 - x0, row = 2.0 * 4.0 * (N / 2 + 1);
+  const long long sr = (long long)(slot_bytes / 4);
+  cudaError_t e = cudaSuccess;
+  auto zp = [&]() {
+    ProfScope ps(c, st, inverse ? "fft_native_z_inv" : "fft_native_z_fwd", count * 2.0 * np * ny * row);
+    e = native_fft_zpass(inverse, (float *)base, sr, first, count, st, x0, x1, y0, y1);
+  };
+  auto yp = [&]() {
+    ProfScope ps(c, st, inverse ? "fft_native_y_inv" : "fft_native_y_fwd", count * np * (ny + N) * row);
+    e = native_fft_ypass(inverse, (float *)base, sr, first, count, st, x0, x1, y0, y1);
+  };
+  if (!inverse) {
+    zp();
+    if (e == cudaSuccess) yp();
+  } else {
+    yp();
+    if (e == cudaSuccess) zp();
+  }
+  return e == cudaSuccess ? BYM_OK : fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
+}
+
 static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, void *base, size_t slot_bytes,
                      int first, int count, const Tune &tn, const XRange *xr = nullptr) {
   const double esz = prec == 64 ? 8.0 : 4.0;
@@ -425,12 +465,8 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
     const long long sr = (long long)(slot_bytes / 4);
     const double cplx = 2.0 * esz * (double)N * N * (N / 2 + 1);
-    if (kind == 1) {   // cuFFT over the (y, z) planes, the library's x pass
-      if (!inverse) {
-        const double np = xr && xr->np > 0 ? xr->np : N;
-        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * np * N * N);
-        TRY_RC(fft_planes(c, st, 0, N, base, slot_bytes, first, count, tn, xr));
-      }
+    if (kind == 1 || kind == 3) {   // cuFFT or the library's passes over the (y, z) planes, the library's x pass
+      if (!inverse) TRY_RC(plane_transforms(c, st, kind, 0, N, base, slot_bytes, first, count, tn, xr));
       {
         // forward with a plane range: the rows outside it are zero and are not read
         const bool rng = !inverse && xr && xr->np > 0;
@@ -440,10 +476,7 @@ static int fft_slots(bym_ctx *c, cudaStream_t st, int prec, int inverse, int N, 
                              rng ? xr->x0 : 0, rng ? xr->x0 + xr->np : N);
       }
       if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
-      if (inverse) {
-        ProfScope ps(c, st, "cufft_planes_c2r", count * 2.0 * esz * (double)N * N * N);
-        TRY_RC(fft_planes(c, st, 1, N, base, slot_bytes, first, count, tn));
-      }
+      if (inverse) TRY_RC(plane_transforms(c, st, kind, 1, N, base, slot_bytes, first, count, tn, nullptr));
       return BYM_OK;
     }
     {
@@ -490,12 +523,8 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
   if (kind && kind != 2) {
     cudaError_t e = native_fft_prepare();
     if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("native FFT: ") + cudaGetErrorString(e));
-    if (kind == 1) {
-      {
-        const double np = xr && xr->np > 0 ? xr->np : N;
-        ProfScope ps(c, st, "cufft_planes_r2c", count * 2.0 * esz * n3 * np / N);
-        TRY_RC(fft_planes(c, st, 0, N, slots, slot_bytes, first, count, tn, xr));
-      }
+    if (kind == 1 || kind == 3) {
+      TRY_RC(plane_transforms(c, st, kind, 0, N, slots, slot_bytes, first, count, tn, xr));
       {
         // read every F once over its occupied rows and D once (each D tile serves all fields of the
         // launch), write F
@@ -505,10 +534,7 @@ static int convolve_fields(bym_ctx *c, cudaStream_t st, int prec, int N, void *s
         e = native_fft_xpass(2, (float *)slots, slot_reals, first, count, (const float *)slots, scale,
                              (const float *)invw, st, rng ? xr->x0 : 0, rng ? xr->x0 + xr->np : N);
       }
-      if (e == cudaSuccess) {
-        ProfScope ps(c, st, "cufft_planes_c2r", count * 2.0 * esz * n3);
-        TRY_RC(fft_planes(c, st, 1, N, slots, slot_bytes, first, count, tn));
-      }
+      if (e == cudaSuccess) TRY_RC(plane_transforms(c, st, kind, 1, N, slots, slot_bytes, first, count, tn, nullptr));
     } else {
       ProfScope ps(c, st, "fft_native_convolve", count * (2.0 * n3 * esz + cplx));
       e = native_fft_convolve((float *)slots, slot_reals, first, count, (const float *)slots, scale,
@@ -719,22 +745,23 @@ static int finish_results(bym_ctx *c, const Request &rq, const double *hstats, c
   return BYM_OK;
 }
 
-// The x planes that hold painted values in the delta slots given (their union), rounded out to a
-// multiple of 32 planes (so that few plan sizes arise); waits for the stream.  Leaves *out at
-// "every plane" when nothing was painted or the range spans the mesh.
+// The x planes that hold painted values in the delta slots given (their union), and the rows y
+// that do, each rounded out to a multiple of 32 (so that few plan sizes arise, and the tiles of
+// the library's passes line up); waits for the stream.  Leaves *out at "every plane" / "every
+// row" when nothing was painted or a range spans the mesh.
 template <typename T>
 static int plane_range(bym_ctx *c, cudaStream_t st, DevBufs &buf, const std::vector<const T *> &deltas, int N,
                        XRange *out) {
   int *d = nullptr;
-  if (buf.alloc((void **)&d, 2 * sizeof(int)) != cudaSuccess) {
+  if (buf.alloc((void **)&d, 4 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, BYM_E_NOMEM, "plane range allocation failed");
   }
-  const int init[2] = {N, -1};
-  int h[2] = {N, -1};
+  const int init[4] = {N, -1, N, -1};
+  int h[4] = {N, -1, N, -1};
   cudaError_t e = cudaMemcpyAsync(d, init, sizeof init, cudaMemcpyHostToDevice, st);
   {
-    ProfScope ps(c, st, "plane_range", (double)deltas.size() * N * N * (N + 2) * sizeof(T));
+    ProfScope ps(c, st, "plane_range", (double)deltas.size() * N * N * (N + kRowPad) * sizeof(T));
     for (const T *p : deltas)
       if (e == cudaSuccess) {
         launch_plane_range<T>(p, N, d, st);
@@ -744,9 +771,14 @@ static int plane_range(bym_ctx *c, cudaStream_t st, DevBufs &buf, const std::vec
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(c, BYM_E_CUDA, std::string("plane range: ") + cudaGetErrorString(e));
-  if (h[1] < h[0] || h[0] < 0 || h[1] >= N) return BYM_OK;
-  // whole blocks of 32 planes (the x pass moves tiles in boxes of 32 rows)
+  if (h[1] < h[0] || h[0] < 0 || h[1] >= N || h[3] < h[2] || h[2] < 0 || h[3] >= N) return BYM_OK;
+  // whole blocks of 32 planes and rows (the passes move tiles in boxes of 32 rows)
   const int x0 = h[0] / 32 * 32, x1 = std::min(N, (h[1] + 32) / 32 * 32), np = x1 - x0;
+  const int y0 = h[2] / 32 * 32, y1 = std::min(N, (h[3] + 32) / 32 * 32), ny = y1 - y0;
+  if (ny < N) {
+    out->y0 = y0;
+    out->ny = ny;
+  }
   if (np >= N) return BYM_OK;
   out->x0 = x0;
   out->np = np;
@@ -771,7 +803,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   const int nf = (int)K.fields.size();
   const int nlm = K.n_lm, NL = K.n_ell;
   const int nextra = n_extra_slots(p, want_pk, want_xi);
-  const long long slot_reals = (long long)N * N * (N + 2);
+  const long long slot_reals = (long long)N * N * (N + kRowPad);
   const long long cslot = slot_reals / 2;
   const size_t slot_bytes = (size_t)slot_reals * sizeof(T);
   const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
@@ -956,18 +988,20 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   // (library x pass backend; not in enqueued requests, which must not wait)
   XRange xr;
   const int fkind = fft_kind(c, N, p->precision, tn);
-  if (!pd && !rq.full_planes && (fkind == 1 || fkind == 2)) {
+  if (!pd && !rq.full_planes && (fkind == 1 || fkind == 2 || fkind == 3)) {
     std::vector<const T *> ds = {slot_r(0)};
     if (il) ds.push_back(slot_r(ibase));
     if (cross) ds.push_back(slot_r(cbase));
     TRY(plane_range<T>(c, st, buf, ds, N, &xr));
-    xr.rows = fkind == 1;
+    xr.rows = fkind == 1 || fkind == 3;
   }
   // field generation writes every value of the x planes [gx0, gx0 + gnp): the occupied range when
   // the x pass reads only the range's rows (the other planes are neither transformed nor read),
-  // else every plane
+  // else every plane; and of those, the rows y in [gy0, gy0 + gny): the occupied rows when the
+  // library's plane passes transform and read only those, else every row
   const int gx0 = (xr.np > 0 && xr.rows) ? xr.x0 : 0, gnp = (xr.np > 0 && xr.rows) ? xr.np : N;
-  const long long gvals = (long long)gnp * N * (N + 2);
+  const int gy0 = (xr.ny > 0 && fkind == 3) ? xr.y0 : 0, gny = (xr.ny > 0 && fkind == 3) ? xr.ny : N;
+  const long long gvals = (long long)gnp * gny * (N + kRowPad);
   static const char *kLosName[4] = {"yamamoto", "midpoint", "bisector", "midpoint_even"};
   const std::string los_name = kLosName[p->los];
   const std::string n_gen = "gen_fields_" + los_name, n_kc = "kcontract_" + los_name, n_xi = "xi_lag_" + los_name;
@@ -977,16 +1011,16 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
   if (!chunk) {
     ProfScope ps(c, st, n_gen.c_str(), (1.0 + nf) * gvals * esz * ((cross || il) ? 2.0 : 1.0));
     CUDA_TRY(launch(K.gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0), slot_r(1),
-                    slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp));
+                    slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp, gy0, gny));
     if (cross) {   // tracer B's fields from its delta
       CUDA_TRY(launch(K.gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(cbase),
                       slot_r(cbase + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0,
-                      gnp));
+                      gnp, gy0, gny));
     }
     if (il) {   // the same fields on the shifted mesh, from its delta and node positions
       CUDA_TRY(launch(K.gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(ibase),
                       slot_r(ibase + 1), slot_reals, N, p->box_lo[0] + 0.5 * h, p->box_lo[1] + 0.5 * h,
-                      p->box_lo[2] + 0.5 * h, h, inv_r0, gx0, gnp));
+                      p->box_lo[2] + 0.5 * h, h, inv_r0, gx0, gnp, gy0, gny));
     }
   }
   if (il) {
@@ -1103,7 +1137,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
       {
         ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * gvals * esz);
         CUDA_TRY(launch(CK->gen[q], grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(1),
-                        slot_r(2), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp));
+                        slot_r(2), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp, gy0, gny));
       }
       TRY((convolve_fields<T, T2>(c, st, p->precision, N, slots, slot_bytes, 2, nq, scale + f0, invw, tn, &xr)));
       if (want_xi) {
@@ -1161,7 +1195,7 @@ static int run_typed(bym_ctx *c, const Request &rq, cudaStream_t st, Pending *pd
       {
         ProfScope ps(c, st, n_gen.c_str(), (1.0 + nq) * gvals * esz);
         CUDA_TRY(launch(CK->gen[q], grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(0),
-                        slot_r(base), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp));
+                        slot_r(base), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0, gnp, gy0, gny));
       }
       return fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, base, nq, tn, &xr);
     };
@@ -1253,7 +1287,7 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
   if (!ks) return fail(c, BYM_E_CUDA, jerr);
   const Tune &tn = tune_for(c, N, p->precision, p->los);
   const int nf = (int)os->fields.size(), nlm = os->n_lm, NL = os->n_ell;
-  const long long slot_reals = (long long)N * N * (N + 2), cslot = slot_reals / 2;
+  const long long slot_reals = (long long)N * N * (N + kRowPad), cslot = slot_reals / 2;
   const size_t slot_bytes = (size_t)slot_reals * sizeof(T);
   const double h = p->box_len / N, inv_h = N / p->box_len, inv_r0 = 1.0 / p->box_len;
   const bool mid = p->los == BYM_LOS_MIDPOINT;
@@ -1368,19 +1402,20 @@ static int run_odd(bym_ctx *c, const Request &rq, cudaStream_t st) {
   CUDA_TRY(cudaGetLastError());
   XRange xr;   // forward plane transforms over the occupied x planes (plane-transform backends)
   const int fkind = fft_kind(c, N, p->precision, tn);
-  if (fkind == 1 || fkind == 2) {
+  if (fkind == 1 || fkind == 2 || fkind == 3) {
     TRY(plane_range<T>(c, st, buf, {slot_r(0), slot_r(cbase)}, N, &xr));
-    xr.rows = fkind == 1;
+    xr.rows = fkind == 1 || fkind == 3;
   }
   {
-    // every value of the planes [gx0, gx0 + gnp) of every field (see run_typed)
+    // every value of the rows [gy0, gy0 + gny) of the planes [gx0, gx0 + gnp) of every field (see run_typed)
     const int gx0 = (xr.np > 0 && xr.rows) ? xr.x0 : 0, gnp = (xr.np > 0 && xr.rows) ? xr.np : N;
-    const long long gvals = (long long)gnp * N * (N + 2);
+    const int gy0 = (xr.ny > 0 && fkind == 3) ? xr.y0 : 0, gny = (xr.ny > 0 && fkind == 3) ? xr.ny : N;
+    const long long gvals = (long long)gnp * gny * (N + kRowPad);
     ProfScope ps(c, st, "gen_fields_odd", 2.0 * (1.0 + nf) * gvals * esz);
     for (int base : {0, cbase})
       CUDA_TRY(launch(os->gen_fields, grid_of(gvals, c->nsm, tn.per_sm_gen), 256, 0, st, (const T *)slot_r(base),
                       slot_r(base + 1), slot_reals, N, p->box_lo[0], p->box_lo[1], p->box_lo[2], h, inv_r0, gx0,
-                      gnp));
+                      gnp, gy0, gny));
   }
   const int f0 = bis ? 1 : 0, cnt = bis ? nf : 1 + nf;
   TRY(fft_slots(c, st, p->precision, 0, N, slots, slot_bytes, f0, cnt, tn, &xr));
@@ -1655,7 +1690,7 @@ int bym_pk_xi_cross_odd(bym_ctx *c, const bym_catalog *gal_a, const bym_catalog 
 }
 
 int bym_set_fft_backend(bym_ctx *c, int mode) {
-  if (!c || mode < 0 || mode > 5) return BYM_E_INVAL;
+  if (!c || mode < 0 || mode > 6) return BYM_E_INVAL;
   std::lock_guard<std::mutex> lock(c->mu);
   c->fft_mode = mode;
   c->graph_warm.clear();   // other plans and kernels: warm again before the next captured batch
@@ -2056,7 +2091,7 @@ int bym_fft3d(bym_ctx *c, void *data, int n_mesh, int count, int inverse, void *
   std::lock_guard<std::mutex> lock(c->mu);
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, BYM_E_CUDA, "cudaSetDevice failed");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
-  const size_t slot_bytes = (size_t)n_mesh * n_mesh * (n_mesh + 2) * sizeof(float);
+  const size_t slot_bytes = (size_t)n_mesh * n_mesh * (n_mesh + kRowPad) * sizeof(float);
   int rc = fft_slots(c, st, 32, inverse ? 1 : 0, n_mesh, data, slot_bytes, 0, count, Tune());
   if (rc) return rc;
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, BYM_E_CUDA, "FFT failed");
@@ -2168,7 +2203,8 @@ int bym_autotune(bym_ctx *c, const bym_catalog *gal, const bym_catalog *ran, con
     if (ms < best_fft) best_fft = ms, best.native = 2;
   }
   if (native_fft_supported(p->n_mesh, p->precision) && c->fft_mode == 2) {
-    for (int cl : {1, 8, 16}) {  // cuFFT planes + library x pass; library two-pass with 8- / 16-CTA clusters
+    // cuFFT planes + library x pass; library z, y and x passes; library two-pass with 8- / 16-CTA clusters
+    for (int cl : {1, 3, 8, 16}) {
       Tune t = best;
       t.native = cl;
       if ((rc = timed(t, prof))) return rc;

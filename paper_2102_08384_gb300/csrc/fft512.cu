@@ -42,8 +42,8 @@ namespace bym {
 namespace {
 
 constexpr int NM = 512;                  // mesh size handled natively
-constexpr int HZ = NM / 2 + 1;           // 257 kz values
-constexpr long long ROWF = NM + 2;       // padded real row (floats)
+constexpr int HP = NM / 2 + 2;           // complex pitch of a row: 258 (the last value is padding)
+constexpr long long ROWF = 2 * HP;       // padded real row (floats): 2064 bytes, 16-byte aligned
 constexpr int CS = 514;                  // column stride (float2) of the column buffer; even for float4 pairs
 constexpr int ES = 17;                   // row stride (float2) of the exchange buffer and twiddle table
 constexpr int EX = 32 * ES;              // exchange buffer of one group (float2)
@@ -350,11 +350,11 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
   for (int e = tid; e < 256 * S::CPR; e += S::NT) {
     const int c = e % S::CPR, ky = 2 * (e / S::CPR);
     const float4 val = *(const float4 *)(C + c * CS + ky);
-    pc[(long long)ky * HZ + r * S::CPR + c] = make_float2(val.x, val.y);
-    pc[(long long)(ky + 1) * HZ + r * S::CPR + c] = make_float2(val.z, val.w);
+    pc[(long long)ky * HP + r * S::CPR + c] = make_float2(val.x, val.y);
+    pc[(long long)(ky + 1) * HP + r * S::CPR + c] = make_float2(val.z, val.w);
   }
   if (r == 0)
-    for (int ky = tid; ky < NM; ky += S::NT) pc[(long long)ky * HZ + 256] = C[S::CPR * CS + ky];
+    for (int ky = tid; ky < NM; ky += S::NT) pc[(long long)ky * HP + 256] = C[S::CPR * CS + ky];
 }
 
 // ---------------------------------------------------------------------------
@@ -380,12 +380,12 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
   // coalesced read of this CTA's kz range
   for (int e = tid; e < 256 * S::CPR; e += S::NT) {
     const int c = e % S::CPR, ky = 2 * (e / S::CPR);
-    const float2 a = pc[(long long)ky * HZ + r * S::CPR + c];
-    const float2 b = pc[(long long)(ky + 1) * HZ + r * S::CPR + c];
+    const float2 a = pc[(long long)ky * HP + r * S::CPR + c];
+    const float2 b = pc[(long long)(ky + 1) * HP + r * S::CPR + c];
     *(float4 *)(C + c * CS + ky) = make_float4(a.x, a.y, b.x, b.y);
   }
   if (r == 0)
-    for (int ky = tid; ky < NM; ky += S::NT) C[S::CPR * CS + ky] = pc[(long long)ky * HZ + 256];
+    for (int ky = tid; ky < NM; ky += S::NT) C[S::CPR * CS + ky] = pc[(long long)ky * HP + 256];
   __syncthreads();
   // inverse C2C along y; rank 0 transforms kz = 0 + i kz = 256 (both real along y after it)
 #pragma unroll 1
@@ -457,10 +457,10 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 // ---------------------------------------------------------------------------
 // x pass (C2C along x) through the tensor memory accelerator: mode 0 forward, 1 inverse,
 // 2 forward -> * conj(D) s W^-2 -> inverse.
-// The columns of a half-spectrum slot are taken in the flattened order f = ky HZ + kz (x stride
-// NM HZ complex values).  A tile is XC = 16 consecutive columns -- 128 contiguous bytes per
-// row, every tile starting on a 128-byte boundary whatever its ky -- and all 512 rows; a slot
-// has 131584 / 16 = 8224 tiles.  Tiles are loaded and stored by TMA in boxes of 32 rows with the
+// The columns of a half-spectrum slot are taken in the flattened order f = ky HP + kz (x stride
+// NM HP complex values; the padding column kz = 257 of every ky is transformed too, on its own).
+// A tile is XC = 16 consecutive columns -- 128 contiguous bytes per row, every tile starting on
+// a 128-byte boundary whatever its ky -- and all 512 rows; a slot has 132096 / 16 = 8256 tiles.  Tiles are loaded and stored by TMA in boxes of 32 rows with the
 // 128-byte swizzle (16-byte chunk index XOR row % 8), so the threads issue no copy or store
 // instructions of their own.  A 16-thread group (alternate lanes of a warp) transforms one
 // column; the exchange of the 512-point engine runs in place in that column's own storage (slot
@@ -474,8 +474,9 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 // ---------------------------------------------------------------------------
 constexpr int XC = 16;                              // columns per tile
 constexpr int XBR = 32;                             // rows per TMA box
-constexpr long long XNCOL = (long long)NM * HZ;     // columns per slot
+constexpr long long XNCOL = (long long)NM * HP;     // columns per slot
 constexpr long long XNT = XNCOL / XC;               // tiles per slot
+constexpr int YNT = (2 * HP + 2 * XC - 1) / (2 * XC);  // y pass: tiles of an x plane (16 full, 1 of kz 256, 257)
 constexpr int XTILE = NM * XC * 8;                  // bytes per tile buffer
 static_assert(XNCOL % XC == 0, "a slot is a whole number of tiles");
 
@@ -562,11 +563,20 @@ __device__ __forceinline__ void bulk_wait_read() {
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// The tiles of a launch of modes 0 and 1: nslab slabs of ntile tiles, slab q at the third
+// tensor-map coordinate (q / np) sstride + s0 + q % np.  x pass: one slab per slot (ntile = XNT,
+// np = sstride = 1, s0 = 0); y pass: the x planes [s0, s0 + np) of every slot (sstride = NM,
+// ntile = YNT tiles of 16 kz columns, the rows being ky).
+struct XtUnits {
+  long long nslab;
+  int ntile, np, sstride, s0;
+};
+
 template <int MODE>
 __global__ void __launch_bounds__(256, 1)
     fft512_xt(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmd, int nslots,
-              const float2 *__restrict__ gtw, const double *__restrict__ scale, const float *__restrict__ invw,
-              int xlo, int xhi, unsigned *__restrict__ fault) {
+              XtUnits un, const float2 *__restrict__ gtw, const double *__restrict__ scale,
+              const float *__restrict__ invw, int xlo, int xhi, unsigned *__restrict__ fault) {
   using L = XtLayout;
   extern __shared__ __align__(16) unsigned char smraw[];
   // 1024-byte aligned base (the 128-byte swizzle repeats every 8 rows); pointer arithmetic on the
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(256, 1)
   const unsigned gm = 0x55555555u << (lane & 1);
   const int ka = j, kb = col_b(j);
   const int lo = MODE == 1 ? 0 : xlo, hi = MODE == 1 ? NM : xhi;   // rows read from HBM
-  const long long nunits = MODE == 2 ? XNT : (long long)nslots * XNT;
+  const long long nunits = MODE == 2 ? XNT : un.nslab * un.ntile;
   const int nf = MODE == 2 ? nslots : 1;
   constexpr int NDB = MODE == 2 ? 2 : 3;            // data buffers
 
@@ -608,11 +618,22 @@ __global__ void __launch_bounds__(256, 1)
 
   // item i = (unit u, field f): modes 0, 1 take the tiles of every slot (f = 0), mode 2 the
   // positions with every field; data buffer i % NDB, whose barrier completes once per use
+  // tensor-map coordinates of item (u, f): c0 (floats along a row of tiles) and c2 (slot or plane)
+  auto coords = [&](long long u, int f, int &c0, int &c2) {
+    if (MODE == 2) {
+      c0 = (int)(u * (2 * XC));
+      c2 = f;
+    } else {
+      const long long q = u / un.ntile;
+      c0 = (int)(u % un.ntile) * (2 * XC);
+      c2 = (int)(q / un.np) * un.sstride + un.s0 + (int)(q % un.np);
+    }
+  };
   auto issue_data = [&](long long u, int f, int b) {
-    const int slot = MODE == 2 ? f : (int)(u / XNT);
-    const int c0 = (int)((MODE == 2 ? u : u % XNT) * (2 * XC));
+    int c0, c2;
+    coords(u, f, c0, c2);
     mbar_expect_tx(bar + b, (unsigned)(hi - lo) * 128u);
-    for (int x0 = lo; x0 < hi; x0 += XBR) tma_load(sm + (size_t)b * XTILE + (size_t)x0 * 128, &tm, c0, x0, slot, bar + b);
+    for (int x0 = lo; x0 < hi; x0 += XBR) tma_load(sm + (size_t)b * XTILE + (size_t)x0 * 128, &tm, c0, x0, c2, bar + b);
   };
   auto issue_d = [&](long long u) {
     mbar_expect_tx(bar + 2, (unsigned)NM * 128u);
@@ -663,8 +684,7 @@ __global__ void __launch_bounds__(256, 1)
           ppar = (ppar & ~(1u << bn)) | ((unsigned)(((i + 1) / NDB) & 1) << bn);
         }
       }
-      const int slot = MODE == 2 ? f : (int)(u / XNT);
-      const long long tl = MODE == 2 ? u : u % XNT;
+      const long long tl = u;                        // mode 2: the tile position
       const XtCol col{tile, g};
       float2 v[32], As[16], Bs[16];
       const float s = MODE == 2 ? SC[f] : 1.f;
@@ -688,7 +708,7 @@ __global__ void __launch_bounds__(256, 1)
           // D <- conj(D) W^-2 in place, once per position: every thread rewrites exactly the
           // entries kx = ka + 32 k2, kb + 32 k2 of its column that it reads below
           const long long fc = tl * XC + g;
-          const int ky = (int)(fc / HZ), kz = (int)(fc % HZ);
+          const int ky = (int)(fc / HP), kz = (int)(fc % HP);
           const float cyz = invw ? W1[ky] * W1[kz] : 1.f;
 #pragma unroll
           for (int k2 = 0; k2 < 16; ++k2) {
@@ -724,7 +744,9 @@ __global__ void __launch_bounds__(256, 1)
       fence_async_smem();                            // these writes (and D's rewrite) before async-proxy use
       __syncthreads();
       if (tid == 0) {
-        for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, (int)(tl * (2 * XC)), x0, slot, tile + (size_t)x0 * 128);
+        int c0, c2;
+        coords(u, f, c0, c2);
+        for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, c0, x0, c2, tile + (size_t)x0 * 128);
         bulk_commit();
         if (MODE == 2 && f == nf - 1 && u + gridDim.x < nunits) {   // D of the next position
           issue_d(u + gridDim.x);
@@ -738,6 +760,178 @@ __global__ void __launch_bounds__(256, 1)
     if (!ok) {
       *(volatile unsigned *)fault = 1u;
       for (int b = 0; b < L::NBUF; ++b)              // let the loads in flight land before leaving
+        if (pend & (1u << b)) mbar_wait(bar + b, (ppar >> b) & 1u);
+    }
+    bulk_wait_all();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z pass (R2C / C2R along z of whole rows).  A unit is a block of ZR = 32 consecutive rows of
+// one x plane: 66048 contiguous bytes (the 2064-byte rows start on 16-byte boundaries), moved by
+// one bulk copy each way.  A 16-thread group (16 consecutive lanes) transforms the row pair
+// (2 g, 2 g + 1) of the block as the complex sequence a + i b; the engine's exchange runs in
+// place in the pair's own 4128 bytes (slot (a, b) at float2 16 a + (b ^ (a % 16)), one
+// wavefront per half-warp with this row pitch).  Forward: the two half spectra are separated in
+// registers (X[k] and X[512 - k] sit in the same thread) and written over the rows, kz = 0..256;
+// inverse: the rows' half spectra are joined into one sequence, completed by Hermitian symmetry
+// in registers, and transformed back.  Persistent, one 256-thread CTA per SM, three block
+// buffers (load of the next block, transform of this one, store of the previous one in flight);
+// waits give up after about two seconds like the x pass's.
+// ---------------------------------------------------------------------------
+constexpr int ZR = 32;                                   // rows per unit
+constexpr unsigned ZBLK = (unsigned)(ZR * ROWF * 4);     // 66048 bytes per block
+
+struct ZtLayout {
+  static constexpr int NBUF = 3;
+  static constexpr size_t TW_OFF = (size_t)NBUF * ZBLK;
+  static constexpr size_t BAR_OFF = TW_OFF + sizeof(float2) * EX;
+  static constexpr size_t BYTES = BAR_OFF + 8 * NBUF + 128;
+};
+
+struct RowEx {                                           // exchange slots of one row pair, in place
+  float2 *p;
+  __device__ __forceinline__ float2 &operator()(int a, int b) const { return p[16 * a + (b ^ (a & 15))]; }
+};
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+
+// units: the row blocks [ylo / ZR, ylo / ZR + nyb) of the x planes [xlo, xlo + np) of nslots slots
+template <int INV>
+__global__ void __launch_bounds__(256, 1)
+    fft512_zt(float *__restrict__ data, long long slot_reals, int nslots, int xlo, int np, int ylo, int nyb,
+              const float2 *__restrict__ gtw, unsigned *__restrict__ fault) {
+  using L = ZtLayout;
+  extern __shared__ __align__(16) unsigned char smz[];
+  unsigned char *sm = smz + ((128u - (smem_u32(smz) & 127u)) & 127u);
+  float2 *TW = (float2 *)(sm + L::TW_OFF);
+  unsigned long long *bar = (unsigned long long *)(sm + L::BAR_OFF);
+  const int tid = threadIdx.x, g = tid >> 4, j = tid & 15;
+  const unsigned gm = 0xFFFFu << (tid & 16);
+  const int ka = j, kb = col_b(j);
+  const long long nunits = (long long)nslots * np * nyb;
+
+  if (tid == 0) {
+    for (int b = 0; b < L::NBUF; ++b) mbar_init(bar + b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < EX; i += blockDim.x) TW[i] = gtw[i];
+  __syncthreads();
+  RegTw tw;
+  tw.TW = TW;
+  tw.kb = kb;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) tw.t1[a] = TW[a * ES + j];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) tw.t8[b] = TW[8 * b * ES + j];
+
+  auto block = [&](long long u) -> float * {
+    const long long q = u / nyb;
+    const int s = (int)(q / np), x = xlo + (int)(q % np), y0 = ylo + (int)(u % nyb) * ZR;
+    return data + (long long)s * slot_reals + ((long long)x * NM + y0) * ROWF;
+  };
+  auto issue = [&](long long u, int b) {
+    mbar_expect_tx(bar + b, ZBLK);
+    bulk_load(sm + (size_t)b * ZBLK, block(u), ZBLK, bar + b);
+  };
+  unsigned pend = 0, ppar = 0;
+  long long u = blockIdx.x;
+  if (tid == 0 && u < nunits) {
+    issue(u, 0);
+    pend |= 1u;
+  }
+  bool ok = true;
+  for (long long k = 0; u < nunits; u += gridDim.x, ++k) {
+    const int b = (int)(k % L::NBUF);
+    const unsigned par = (unsigned)((k / L::NBUF) & 1);
+    ok = __syncthreads_and(mbar_wait(bar + b, par));
+    if (!ok) break;
+    if (tid == 0) {
+      pend &= ~(1u << b);
+      const long long un = u + gridDim.x;
+      if (un < nunits) {                             // prefetch the next block
+        const int bn = (int)((k + 1) % L::NBUF);
+        bulk_wait_read<1>();                         // the store of block k - 2 (buffer bn) has read it
+        issue(un, bn);
+        pend |= 1u << bn;
+        ppar = (ppar & ~(1u << bn)) | ((unsigned)(((k + 1) / L::NBUF) & 1) << bn);
+      }
+    }
+    float *blk = (float *)(sm + (size_t)b * ZBLK);
+    float *ra = blk + (size_t)(2 * g) * ROWF, *rb = ra + ROWF;
+    float2 *pa = (float2 *)ra, *pb = (float2 *)rb;
+    const RowEx ex{pa};
+    float2 v[32], A[16], B[16];
+    if (!INV) {
+#pragma unroll
+      for (int m = 0; m < 32; ++m) v[m] = make_float2(ra[16 * m + j], rb[16 * m + j]);
+      fwd512x(v, A, B, j, gm, tw, ex);
+      __syncwarp(gm);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {               // kz = ka + 32 k2, kb + 32 k2: 0..255
+        const float4 va = unpack2(A[k2], j ? cconj(B[15 - k2]) : cconj(A[(16 - k2) & 15]));
+        const float4 vb = unpack2(B[k2], j ? cconj(A[15 - k2]) : cconj(B[15 - k2]));
+        pa[ka + 32 * k2] = make_float2(va.x, va.y);
+        pb[ka + 32 * k2] = make_float2(va.z, va.w);
+        pa[kb + 32 * k2] = make_float2(vb.x, vb.y);
+        pb[kb + 32 * k2] = make_float2(vb.z, vb.w);
+      }
+      if (j == 0) {                                  // kz = 256
+        const float4 vn = unpack2(A[8], cconj(A[8]));
+        pa[256] = make_float2(vn.x, vn.y);
+        pb[256] = make_float2(vn.z, vn.w);
+      }
+    } else {
+      float4 ca[8], cb[8];                           // (row a, row b) at kz = ka + 32 k2, kb + 32 k2
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        const float2 a0 = pa[ka + 32 * k2], b0 = pb[ka + 32 * k2], a1 = pa[kb + 32 * k2], b1 = pb[kb + 32 * k2];
+        ca[k2] = make_float4(a0.x, a0.y, b0.x, b0.y);
+        cb[k2] = make_float4(a1.x, a1.y, b1.x, b1.y);
+      }
+      const float2 a256 = pa[256], b256 = pb[256];
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        A[k2] = pack2(make_float2(ca[k2].x, ca[k2].y), make_float2(ca[k2].z, ca[k2].w));
+        B[k2] = pack2(make_float2(cb[k2].x, cb[k2].y), make_float2(cb[k2].z, cb[k2].w));
+      }
+#pragma unroll
+      for (int k2 = 8; k2 < 16; ++k2) {              // kz > 256 from the conjugate at 512 - kz
+        const float4 sa = j ? cb[15 - k2] : ca[(16 - k2) & 7];
+        const float4 sb = j ? ca[15 - k2] : cb[15 - k2];
+        A[k2] = pack2(make_float2(sa.x, -sa.y), make_float2(sa.z, -sa.w));
+        B[k2] = pack2(make_float2(sb.x, -sb.y), make_float2(sb.z, -sb.w));
+      }
+      if (j == 0) A[8] = pack2(a256, b256);          // kz = 256 (its own conjugate partner)
+      __syncwarp(gm);                                // every spectrum read before the exchange
+      inv512x(A, B, v, j, gm, tw, ex);
+      __syncwarp(gm);
+#pragma unroll
+      for (int m = 0; m < 32; ++m) {
+        ra[16 * m + j] = v[m].x;
+        rb[16 * m + j] = v[m].y;
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_store(block(u), blk, ZBLK);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) {
+    if (!ok) {
+      *(volatile unsigned *)fault = 1u;
+      for (int b = 0; b < L::NBUF; ++b)
         if (pend & (1u << b)) mbar_wait(bar + b, (ppar >> b) & 1u);
     }
     bulk_wait_all();
@@ -841,7 +1035,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// TMA map of n half-spectrum slots from base b: dims (2 NM HZ floats of an x-plane, NM planes, n slots),
+// TMA map of n half-spectrum slots from base b: dims (2 NM HP floats of an x-plane, NM planes, n slots),
 // boxes of 32 floats (16 complex columns, 128 bytes) x 32 planes x 1 slot, 128-byte swizzle
 cudaError_t slot_map(CUtensorMap *m, float *b, long long slot_reals, int n) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -870,8 +1064,63 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
   if (MODE == 2 && n > XtLayout::NSC) return cudaErrorInvalidValue;
   const long long units = MODE == 2 ? XNT : XNT * n;
   const long long grid = std::min<long long>(units, (long long)sm_count(dev));
-  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmd, n, tw, scale, invw, xlo, xhi,
+  const XtUnits un{(long long)n, (int)XNT, 1, 1, 0};
+  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmd, n, un, tw, scale, invw, xlo, xhi,
                                                                 g_xfault[dev]);
+  return cudaGetLastError();
+}
+
+// TMA map of the x planes of n slots from base b for the y pass: dims (2 HP floats of a row, NM
+// rows ky, NM n planes), the row stride 2064 bytes (a multiple of 16, which the padded layout
+// exists for) and the plane stride NM rows; boxes of 32 floats x 32 rows x 1 plane, 128-byte
+// swizzle.  The last tile of a row (kz 256 and the padding) lies partly outside dimension 0:
+// its loads read zeros there and its stores skip it.
+cudaError_t plane_map(CUtensorMap *m, float *b, int n) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)ROWF, (cuuint64_t)NM, (cuuint64_t)NM * (cuuint64_t)n};
+  const cuuint64_t strides[2] = {(cuuint64_t)(ROWF * sizeof(float)), (cuuint64_t)(NM * ROWF * sizeof(float))};
+  const cuuint32_t box[3] = {2 * XC, XBR, 1}, estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, b, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// y pass (C2C along y) of the x planes [xlo, xhi) of n slots; mode 0 (forward) reads the rows
+// y in [ylo, yhi) only, mode 1 (inverse) every row
+template <int MODE>
+cudaError_t ypass(float *b, long long slot_reals, int n, const float2 *tw, cudaStream_t st, int xlo, int xhi, int ylo,
+                  int yhi) {
+  static_assert(MODE == 0 || MODE == 1, "forward or inverse");
+  if (xlo < 0 || xhi > NM || xlo >= xhi || ylo < 0 || yhi > NM || ylo >= yhi || ylo % XBR || yhi % XBR)
+    return cudaErrorInvalidValue;
+  if (((unsigned long long)b & 15ull) || slot_reals != (long long)NM * NM * ROWF) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  CUtensorMap tm;
+  cudaError_t e = plane_map(&tm, b, n);
+  if (e != cudaSuccess) return e;
+  const XtUnits un{(long long)n * (xhi - xlo), YNT, xhi - xlo, NM, xlo};
+  const long long grid = std::min<long long>(un.nslab * YNT, (long long)sm_count(dev));
+  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tm, n, un, tw, nullptr, nullptr, ylo, yhi,
+                                                                g_xfault[dev]);
+  return cudaGetLastError();
+}
+
+// z pass of the rows y in [ylo, yhi) of the x planes [xlo, xhi) of n slots
+template <int INV>
+cudaError_t zpass(float *b, long long slot_reals, int n, const float2 *tw, cudaStream_t st, int xlo, int xhi, int ylo,
+                  int yhi) {
+  if (xlo < 0 || xhi > NM || xlo >= xhi || ylo < 0 || yhi > NM || ylo >= yhi || ylo % ZR || yhi % ZR)
+    return cudaErrorInvalidValue;
+  if (((unsigned long long)b & 15ull) || slot_reals != (long long)NM * NM * ROWF) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int np = xhi - xlo, nyb = (yhi - ylo) / ZR;
+  const long long units = (long long)n * np * nyb;
+  const long long grid = std::min<long long>(units, (long long)sm_count(dev));
+  fft512_zt<INV><<<(unsigned)grid, 256, ZtLayout::BYTES, st>>>(b, slot_reals, n, xlo, np, ylo, nyb, tw,
+                                                               g_xfault[dev]);
   return cudaGetLastError();
 }
 
@@ -896,6 +1145,11 @@ cudaError_t native_fft_prepare() {
     if ((e = cudaFuncSetAttribute(fft512_xt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, xs)) != cudaSuccess)
       return e;
     if ((e = cudaFuncSetAttribute(fft512_xt<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, xs)) != cudaSuccess)
+      return e;
+    const int zs = (int)ZtLayout::BYTES;
+    if ((e = cudaFuncSetAttribute(fft512_zt<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(fft512_zt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, zs)) != cudaSuccess)
       return e;
     if (!tensor_map_encoder()) return cudaErrorNotSupported;
     unsigned *hf = nullptr;
@@ -960,6 +1214,34 @@ cudaError_t native_fft_xpass(int mode, float *slots, long long slot_reals, int f
     e = mode == 0   ? xpass<0>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st, xlo, xhi)
         : mode == 1 ? xpass<1>(b, slot_reals, n, tw, nullptr, nullptr, nullptr, st)
                     : xpass<2>(b, slot_reals, n, tw, D, scale + done, invw, st, xlo, xhi);
+  }
+  return e;
+}
+
+cudaError_t native_fft_zpass(int inverse, float *slots, long long slot_reals, int first, int count, cudaStream_t st,
+                             int xlo, int xhi, int ylo, int yhi) {
+  if (count <= 0) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const float2 *tw = twiddles(dev);
+  return inverse ? zpass<1>(slots + (long long)first * slot_reals, slot_reals, count, tw, st, xlo, xhi, ylo, yhi)
+                 : zpass<0>(slots + (long long)first * slot_reals, slot_reals, count, tw, st, xlo, xhi, ylo, yhi);
+}
+
+cudaError_t native_fft_ypass(int inverse, float *slots, long long slot_reals, int first, int count, cudaStream_t st,
+                             int xlo, int xhi, int ylo, int yhi) {
+  if (count <= 0) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const float2 *tw = twiddles(dev);
+  float *base = slots + (long long)first * slot_reals;
+  cudaError_t e = cudaSuccess;
+  const int step = 65535 / NM;                       // planes of a launch fit a 16-bit count
+  for (int done = 0; done < count && e == cudaSuccess; done += step) {
+    const int n = count - done < step ? count - done : step;
+    float *b = base + (long long)done * slot_reals;
+    e = inverse ? ypass<1>(b, slot_reals, n, tw, st, xlo, xhi, ylo, yhi)
+                : ypass<0>(b, slot_reals, n, tw, st, xlo, xhi, ylo, yhi);
   }
   return e;
 }

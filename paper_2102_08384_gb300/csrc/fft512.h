@@ -22,6 +22,18 @@ cudaError_t native_fft_convolve(float *slots, long long slot_reals, int first, i
 // the flag stays set for the device's lifetime
 bool native_fft_fault(int dev);
 
+// The library's own (y, z) plane transforms of slots [first, first + count), in two passes:
+// the z pass (R2C / C2R along z of blocks of 32 whole rows, moved by bulk copies) and the y pass
+// (C2C along y of tiles of 16 kz columns, moved by TMA like the x pass's).  A forward transform
+// runs the z pass then the y pass, an inverse one the y pass then the z pass.  Both cover the x
+// planes [xlo, xhi); the forward z pass transforms the rows y in [ylo, yhi) of them only and the
+// forward y pass reads only those rows (the others hold zeros, whose transforms are zeros in the
+// same bytes); mode-1 (inverse) calls read every row.  xlo, xhi, ylo, yhi are multiples of 32.
+cudaError_t native_fft_zpass(int inverse, float *slots, long long slot_reals, int first, int count, cudaStream_t st,
+                             int xlo = 0, int xhi = 512, int ylo = 0, int yhi = 512);
+cudaError_t native_fft_ypass(int inverse, float *slots, long long slot_reals, int first, int count, cudaStream_t st,
+                             int xlo = 0, int xhi = 512, int ylo = 0, int yhi = 512);
+
 // the x pass alone (C2C along x of half spectra) for slots [first, first + count):
 // mode 0 forward, 1 inverse, 2 forward -> * conj(D) scale[f] W(k)^-2 -> inverse.  Modes 0 and 2
 // read the input rows x in [xlo, xhi) only and take the others as zero (planes that hold no

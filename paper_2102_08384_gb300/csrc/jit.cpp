@@ -194,19 +194,20 @@ void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldI
     Jmax = std::max(Jmax, list[i].J);
     amax = std::max(amax, list[i].alpha);
   }
-  // one thread per value of the padded rows of the x planes [x0, x0 + np): every value of those
-  // planes of every field is written (zero where delta is zero and in the row padding), so the
-  // field slots need no zero-fill; a warp stores 32 consecutive values of a row per field
+  // one thread per value of the padded rows y in [y0, y0 + ny) of the x planes [x0, x0 + np):
+  // every value of those rows of every field is written (zero where delta is zero and in the row
+  // padding), so the field slots need no zero-fill; a warp stores 32 consecutive values of a row
+  // per field
   o << "extern \"C\" __global__ void __launch_bounds__(256, 2) " << name << "(const real* __restrict__ delta,"
        " real* __restrict__ out, long long slot, int N, double lo0, double lo1, double lo2, double h,"
-       " double inv_r0, int x0, int np) {\n";
-  o << "  const long long row = N + 2, plane = (long long)N * row, base = (long long)x0 * plane;\n";
-  o << "  const long long nval = (long long)np * plane;\n";
+       " double inv_r0, int x0, int np, int y0, int ny) {\n";
+  o << "  const long long row = N + 4;\n";
+  o << "  const long long nval = (long long)np * ny * row;\n";
   o << "  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nval;"
        " c += (long long)gridDim.x * blockDim.x) {\n";
-  o << "    const long long off = base + c;\n";
   o << "    const int iz = (int)(c % row); const long long t = c / row;\n";
-  o << "    const int iy = (int)(t % N); const int ix = x0 + (int)(t / N);\n";
+  o << "    const int iy = y0 + (int)(t % ny); const int ix = x0 + (int)(t / ny);\n";
+  o << "    const long long off = ((long long)ix * N + iy) * row + iz;\n";
   o << "    const real d = iz < N ? delta[off] : (real)0;\n";
   o << "    if (d == (real)0) {\n";
   for (int i = f0; i < f1; ++i) o << "      out[" << i - f0 << "LL * slot + off] = (real)0;\n";
@@ -239,7 +240,7 @@ void emit_mid_combine(std::ostream &o, const char *name, const JitKey &key, cons
        " c += (long long)gridDim.x * blockDim.x) {\n";
   o << "    const int iz = (int)(c % N); const long long t = c / N;\n";
   o << "    const int iy = (int)(t % N); const int ix = (int)(t / N);\n";
-  o << "    const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "    const long long off = ((long long)ix * N + iy) * (N + 4) + iz;\n";
   o << "    const int jx = bym_lab(ix, N), jy = bym_lab(iy, N), jz = bym_lab(iz, N);\n";
   o << "    const int j2 = jx * jx + jy * jy + jz * jz;\n";
   o << "    const real rr = bym_sqrt((real)j2);\n";
@@ -318,7 +319,7 @@ int emit_xi_lag(std::ostream &o, const char *name, const JitKey &key, int f0, in
   o << "      bin = lut[j2];\n";
   o << "      if (bin >= 0) {\n";
   o << "        const int ix = jx < 0 ? jx + N : jx, iy = jy < 0 ? jy + N : jy, iz = jz < 0 ? jz + N : jz;\n";
-  o << "        const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "        const long long off = ((long long)ix * N + iy) * (N + 4) + iz;\n";
   o << "        const double rr = sqrt((double)j2); const double ir = 1.0 / rr;\n";
   o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
   {
@@ -385,7 +386,7 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
   for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
   o << "};\n";
   o << "    if (m < total) {\n";
-  o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+  o << "      const int iz = (int)(m % H); const long long row = m / H, mo = row * (H + 1) + iz;\n";
   o << "      const int ix = (int)(row / N), iy = (int)(row % N);\n";
   o << "      const int nx = bym_lab(ix, N), ny = bym_lab(iy, N), nz = (iz == N / 2) ? -N / 2 : iz;\n";
   o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
@@ -416,16 +417,16 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
   const char *na = cross ? "a" : "f", *nb = cross ? "b" : "f";
   // cross: B's fields first, then each A field just before the terms that use it
   if (!cross)
-    for (int i : ua) o << "        const real2 f" << i << " = FA[" << i - a0 << "LL * cslot + m];\n";
+    for (int i : ua) o << "        const real2 f" << i << " = FA[" << i - a0 << "LL * cslot + mo];\n";
   for (int j : ub)
     if (!(same && ua.count(j)))
-      o << "        const real2 " << nb << j << " = " << (same ? "FA[" : "FB[") << j - b0 << "LL * cslot + m];\n";
+      o << "        const real2 " << nb << j << " = " << (same ? "FA[" : "FB[") << j - b0 << "LL * cslot + mo];\n";
   int cur = -1;
   for (auto &kv : by_pair) {
     const int i = kv.first.first, j = kv.first.second;
     if (cross && i != cur) {
       if (cur >= 0) o << "        }\n";
-      o << "        { const real2 a" << i << " = FA[" << i - a0 << "LL * cslot + m];\n";
+      o << "        { const real2 a" << i << " = FA[" << i - a0 << "LL * cslot + mo];\n";
       cur = i;
     }
     o << "        { const real q = " << na << i << ".x * " << nb << j << ".x + " << na << i << ".y * " << nb << j
@@ -437,8 +438,8 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
   for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
   o << "        if (xout) {\n";
   for (int i = 0; i < n_lm; ++i)
-    o << "          { real2 xv; xv.x = X" << i << " + (accumulate ? xout[" << i << "LL * xslot + m].x : (real)0);"
-      << " xv.y = (real)0; xout[" << i << "LL * xslot + m] = xv; }\n";
+    o << "          { real2 xv; xv.x = X" << i << " + (accumulate ? xout[" << i << "LL * xslot + mo].x : (real)0);"
+      << " xv.y = (real)0; xout[" << i << "LL * xslot + mo] = xv; }\n";
   o << "        }\n";
   o << "        if (bin >= 0) {\n";
   o << "          const double w = (iz == 0 || iz == N / 2) ? 1.0 : 2.0;\n";
@@ -485,7 +486,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   emit_bin_loop_head(o, "(long long)N * N * H");
   o << "    int bin = -1; double v[2] = {0.0, 0.0};\n";
   o << "    if (m < total) {\n";
-  o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+  o << "      const int iz = (int)(m % H); const long long row = m / H, mo = row * (H + 1) + iz;\n";
   o << "      const int nx = bym_lab((int)(row / N), N), ny = bym_lab((int)(row % N), N);\n";
   o << "      const int nz = (iz == N / 2) ? -N / 2 : iz;\n";
   o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
@@ -522,7 +523,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     for (int l = 0; l < NL; ++l) o << (l ? ", " : "") << "0.0";
     o << "};\n";
     o << "    if (m < total) {\n";
-    o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+    o << "      const int iz = (int)(m % H); const long long row = m / H, mo = row * (H + 1) + iz;\n";
     o << "      const int ix = (int)(row / N), iy = (int)(row % N);\n";
     o << "      const int nx = bym_lab(ix, N), ny = bym_lab(iy, N), nz = (iz == N / 2) ? -N / 2 : iz;\n";
     o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
@@ -534,13 +535,13 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     // X_{lm}
     for (int i = 0; i < n_lm; ++i) o << "        real X" << i << " = (real)0;\n";
     if (key.los == 0) {
-      o << "        const real2 d = D[m];\n";
+      o << "        const real2 d = D[mo];\n";
       for (int i = 0; i < n_lm; ++i)
-        o << "        { const real2 f = F[" << i << "LL * cslot + m]; X" << i << " = (f.x * d.x + f.y * d.y) * cc; }\n";
+        o << "        { const real2 f = F[" << i << "LL * cslot + mo]; X" << i << " = (f.x * d.x + f.y * d.y) * cc; }\n";
     } else if (midpoint) {
-      for (int i = 0; i < n_lm; ++i) o << "        X" << i << " = F[" << i << "LL * cslot + m].x;\n";
+      for (int i = 0; i < n_lm; ++i) o << "        X" << i << " = F[" << i << "LL * cslot + mo].x;\n";
     } else {
-      for (int i = 0; i < nf; ++i) o << "        const real2 f" << i << " = F[" << i << "LL * cslot + m];\n";
+      for (int i = 0; i < nf; ++i) o << "        const real2 f" << i << " = F[" << i << "LL * cslot + mo];\n";
       auto terms = bisector_terms(key.ell_max, key.K);
       std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> by_pair;
       for (auto &t : terms) by_pair[{t.i, t.j}].push_back({t.lm, t.c});
@@ -553,7 +554,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
       for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
       if (with_x)
         for (int i = 0; i < n_lm; ++i) {
-          o << "        { real2 xv; xv.x = X" << i << "; xv.y = (real)0; xout[" << i << "LL * xslot + m] = xv; }\n";
+          o << "        { real2 xv; xv.x = X" << i << "; xv.y = (real)0; xout[" << i << "LL * xslot + mo] = xv; }\n";
         }
     }
     o << "        if (bin >= 0) {\n";
@@ -669,7 +670,7 @@ void emit_k_head(std::ostream &o, int NLo) {
   for (int l = 0; l < NLo; ++l) o << (l ? ", " : "") << "0.0";
   o << "};\n";
   o << "    if (m < total) {\n";
-  o << "      const int iz = (int)(m % H); const long long row = m / H;\n";
+  o << "      const int iz = (int)(m % H); const long long row = m / H, mo = row * (H + 1) + iz;\n";
   o << "      const int ix = (int)(row / N), iy = (int)(row % N);\n";
   o << "      const int nx = bym_lab(ix, N), ny = bym_lab(iy, N), nz = (iz == N / 2) ? -N / 2 : iz;\n";
   o << "      const int n2 = nx * nx + ny * ny + nz * nz;\n";
@@ -721,7 +722,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
          " long long cslot, int N, const int* __restrict__ lut, int nbins, double* __restrict__ gsum) {\n";
     emit_k_head(o, NLo);
     o << "      if (bin >= 0) {\n";
-    for (int i = 0; i < n_lm; ++i) o << "        const real X" << i << " = F[" << i << "LL * cslot + m].y;\n";
+    for (int i = 0; i < n_lm; ++i) o << "        const real X" << i << " = F[" << i << "LL * cslot + mo].y;\n";
     emit_k_tail(o, L, f32, NLo);
   } else if (key.los == 0) {
     // Yamamoto: X_{l nu} = sgn Im(F_{l nu}(k) conj D(k)) W^-2; two launches (F^B with D_A, sgn 1;
@@ -733,10 +734,10 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
     o << "      if (bin >= 0) {\n";
     o << "        real cc = sgn;\n";
     o << "        if (invw) { const real wv = invw[ix] * invw[iy] * invw[iz]; cc = sgn * wv * wv; }\n";
-    o << "        const real2 d = D[m];\n";
+    o << "        const real2 d = D[mo];\n";
     for (int i = 0; i < nf; ++i)
       o << "        real X" << odd_lm_index(list[i].J, list[i].nu) << "; { const real2 f = F[" << i
-        << "LL * cslot + m]; X" << odd_lm_index(list[i].J, list[i].nu) << " = (f.y * d.x - f.x * d.y) * cc; }\n";
+        << "LL * cslot + mo]; X" << odd_lm_index(list[i].J, list[i].nu) << " = (f.y * d.x - f.x * d.y) * cc; }\n";
     emit_k_tail(o, L, f32, NLo);
   } else {
     // bisector: X_{l nu}(k) = sum over ordered field pairs c_ij Im(conj F^A_i F^B_j) W^-2, the part of
@@ -760,13 +761,13 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
     }
     std::set<int> ub;
     for (auto &kv : by_pair) ub.insert(kv.first.second);
-    for (int j : ub) o << "        const real2 b" << j << " = FB[" << j << "LL * cslot + m];\n";
+    for (int j : ub) o << "        const real2 b" << j << " = FB[" << j << "LL * cslot + mo];\n";
     int cur = -1;
     for (auto &kv : by_pair) {
       const int i = kv.first.first, j = kv.first.second;
       if (i != cur) {
         if (cur >= 0) o << "        }\n";
-        o << "        { const real2 a" << i << " = FA[" << i << "LL * cslot + m];\n";
+        o << "        { const real2 a" << i << " = FA[" << i << "LL * cslot + mo];\n";
         cur = i;
       }
       o << "        { const real q = a" << i << ".x * b" << j << ".y - a" << i << ".y * b" << j << ".x;";
@@ -777,7 +778,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
     for (int i = 0; i < n_lm; ++i) o << "        X" << i << " *= cc;\n";
     o << "        if (xout) {\n";
     for (int i = 0; i < n_lm; ++i)
-      o << "          { real2 xv; xv.x = (real)0; xv.y = X" << i << "; xout[" << i << "LL * xslot + m] = xv; }\n";
+      o << "          { real2 xv; xv.x = (real)0; xv.y = X" << i << "; xout[" << i << "LL * xslot + mo] = xv; }\n";
     o << "        }\n";
     emit_k_tail(o, L, f32, NLo);
   }
@@ -808,7 +809,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
   o << "      bin = lut[j2];\n";
   o << "      if (bin >= 0) {\n";
   o << "        const int ix = jx < 0 ? jx + N : jx, iy = jy < 0 ? jy + N : jy, iz = jz < 0 ? jz + N : jz;\n";
-  o << "        const long long off = ((long long)ix * N + iy) * (N + 2) + iz;\n";
+  o << "        const long long off = ((long long)ix * N + iy) * (N + 4) + iz;\n";
   o << "        const double rr = sqrt((double)j2); const double ir = 1.0 / rr;\n";
   o << "        const double ux = jx * ir, uy = jy * ir, uz = jz * ir, zm = 1.0;\n";
   {

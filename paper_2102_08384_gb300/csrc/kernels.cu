@@ -468,9 +468,9 @@ __global__ void __launch_bounds__(256) bym_paint_tile(const short4 *__restrict__
   }
   __syncthreads();
   const T down = scl[1];
-  const long long row = (long long)(g.N + 2);
-  const bool pad = z0 + wz == g.N;   // the last z tile also clears the two padding values of its rows
-  const int rw = pad ? wz + 2 : wz;
+  const long long row = (long long)(g.N + kRowPad);
+  const bool pad = z0 + wz == g.N;   // the last z tile also clears the padding values of its rows
+  const int rw = pad ? wz + kRowPad : wz;
   for (int i = threadIdx.x; i < wx * wy * rw; i += blockDim.x) {
     const int lz = i % rw, ly = (i / rw) % wy, lx = i / (rw * wy);
     T v = (T)0;
@@ -483,12 +483,13 @@ __global__ void __launch_bounds__(256) bym_paint_tile(const short4 *__restrict__
 }
 
 // F_f(k) <- F_f(k) conj(D(k)) scale[f] c(k), f = 0..nf-1 (slots of cslot complex
-// values each), c = prod_axis invw^2 (compensation, null: 1).
+// values each), c = prod_axis invw^2 (compensation, null: 1).  Like the other elementwise
+// spectral kernels it runs over the whole padded layout, padding included (harmless there).
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) bym_spec_mul(T2 *__restrict__ F, long long cslot, int nf,
                                                     const T2 *__restrict__ D, int N, const double *__restrict__ scale,
                                                     const T *__restrict__ invw) {
-  const int H = N / 2 + 1;
+  const int H = (N + kRowPad) / 2;   // complex pitch of a row
   const long long nm = (long long)N * N * H;
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += (long long)gridDim.x * blockDim.x) {
     const T2 d = D[m];
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(256) bym_spec_mul_cross(T2 *__restrict__ FA, c
                                                           const T2 *__restrict__ DB, int N,
                                                           const double *__restrict__ scale,
                                                           const T *__restrict__ invw, T sa) {
-  const int H = N / 2 + 1;
+  const int H = (N + kRowPad) / 2;   // complex pitch of a row
   const long long nm = (long long)N * N * H;
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += (long long)gridDim.x * blockDim.x) {
     const T2 da = DA[m], db = DB[m];
@@ -543,19 +544,42 @@ __global__ void __launch_bounds__(256) bym_spec_mul_cross(T2 *__restrict__ FA, c
   }
 }
 
-// The x planes of a padded real slot (N x N x (N + 2)) that hold a non-zero value: one block per
-// plane; range[0] <- min, range[1] <- max over them (atomics; the caller sets {N, -1} first).
+// The x planes of a padded real slot (N x N x (N + kRowPad)) that hold a non-zero value, and the
+// rows y that do in any plane: one block per plane; range[0] <- min, range[1] <- max of x,
+// range[2] <- min, range[3] <- max of y over them (atomics; the caller sets {N, -1, N, -1} first).
 template <typename T>
 __global__ void __launch_bounds__(256) bym_plane_range(const T *__restrict__ d, int N, int *__restrict__ range) {
+  __shared__ int ylo, yhi;
+  if (threadIdx.x == 0) {
+    ylo = N;
+    yhi = -1;
+  }
+  __syncthreads();
   const int x = blockIdx.x;
-  const long long plane = (long long)N * (N + 2);
-  const T *p = d + (long long)x * plane;
-  int any = 0;
-  for (long long i = threadIdx.x; i < plane; i += blockDim.x) any |= (p[i] != (T)0);
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0 && any) {
+  const int row = N + kRowPad;
+  const T *p = d + (long long)x * N * row;
+  int lo = N, hi = -1;
+  // a warp per row at a time: coalesced reads, the row's index known without a division
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int y = threadIdx.x >> 5; y < N; y += nw) {
+    const T *r = p + (long long)y * row;
+    int any = 0;
+    for (int z = lane; z < row; z += 32) any |= (r[z] != (T)0);
+    if (__any_sync(0xffffffffu, any)) {
+      lo = min(lo, y);
+      hi = max(hi, y);
+    }
+  }
+  if (hi >= 0) {
+    atomicMin(&ylo, lo);
+    atomicMax(&yhi, hi);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && yhi >= 0) {
     atomicMin(range, x);
     atomicMax(range + 1, x);
+    atomicMin(range + 2, ylo);
+    atomicMax(range + 3, yhi);
   }
 }
 
@@ -565,7 +589,7 @@ __global__ void __launch_bounds__(256) bym_plane_range(const T *__restrict__ d, 
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) bym_interlace(T2 *__restrict__ F, const T2 *__restrict__ G, long long cslot,
                                                      int nf, int N, const T2 *__restrict__ ph) {
-  const int H = N / 2 + 1;
+  const int H = (N + kRowPad) / 2;   // complex pitch of a row
   const long long nm = (long long)N * N * H;
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += (long long)gridDim.x * blockDim.x) {
     const int iz = (int)(m % H);
@@ -683,7 +707,7 @@ template <typename T, typename T2>
 void launch_spec_mul(T2 *F, long long cslot, int nf, const T2 *D, int N, const double *scale, const T *invw, int nsm,
                      cudaStream_t st) {
   if (nf <= 0) return;
-  const long long nm = (long long)N * N * (N / 2 + 1);
+  const long long nm = (long long)N * N * ((N + kRowPad) / 2);
   bym_spec_mul<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(F, cslot, nf, D, N, scale, invw);
 }
 
@@ -691,7 +715,7 @@ template <typename T, typename T2>
 void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const T2 *DA, const T2 *DB, int N,
                            const double *scale, const T *invw, int nsm, cudaStream_t st, double sa) {
   if (nf <= 0) return;
-  const long long nm = (long long)N * N * (N / 2 + 1);
+  const long long nm = (long long)N * N * ((N + kRowPad) / 2);
   bym_spec_mul_cross<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(FA, FB, cslot, nf, DA, DB, N, scale, invw, (T)sa);
 }
 
@@ -703,7 +727,7 @@ void launch_plane_range(const T *slot, int N, int *range, cudaStream_t st) {
 template <typename T, typename T2>
 void launch_interlace(T2 *F, const T2 *G, long long cslot, int nf, int N, const T2 *ph, int nsm, cudaStream_t st) {
   if (nf <= 0) return;
-  const long long nm = (long long)N * N * (N / 2 + 1);
+  const long long nm = (long long)N * N * ((N + kRowPad) / 2);
   bym_interlace<T, T2><<<grid_for(nm, nsm), 256, 0, st>>>(F, G, cslot, nf, N, ph);
 }
 

@@ -4,6 +4,12 @@
 
 namespace bym {
 
+// Padded in-place layout of a mesh slot: N x N rows of N + kRowPad reals, or N / 2 + 2 complex
+// values of which kz = 0..N/2 hold the half spectrum and the last is padding.  Four padding reals
+// (not the two an in-place transform needs) put every row on a 16-byte boundary (2064 bytes at
+// N = 512 in FP32), which lets the tensor memory accelerator move tiles along y.
+constexpr int kRowPad = 4;
+
 // Catalog sums into stats (see bym_norm_reduce), deterministic: per-block partials in part
 // (norm_scratch_bytes(nsm) bytes of device scratch), added up in block order.
 size_t norm_scratch_bytes(int nsm);
@@ -33,7 +39,8 @@ void launch_spec_mul_cross(T2 *FA, const T2 *FB, long long cslot, int nf, const 
                            const double *scale, const T *invw, int nsm, cudaStream_t st, double sa = 1.0);
 
 // the x planes of a padded real slot holding non-zero values: range[0] = min(range[0], x),
-// range[1] = max(range[1], x) over them (set range to {N, -1} before the first call)
+// range[1] = max(range[1], x) over them, and range[2], range[3] likewise for the rows y that hold
+// one in any plane (set range to {N, -1, N, -1} before the first call)
 template <typename T>
 void launch_plane_range(const T *slot, int N, int *range, cudaStream_t st);
 

@@ -29,13 +29,13 @@ def env():
 
 
 def _slots(torch, x):
-    """(count, N, N, N) real -> padded slots (count, N, N, N + 2)."""
-    s = torch.zeros(x.shape[0], N, N, N + 2, dtype=torch.float32, device=x.device)
+    """(count, N, N, N) real -> padded slots (count, N, N, N + 4)."""
+    s = torch.zeros(x.shape[0], N, N, N + 4, dtype=torch.float32, device=x.device)
     s[..., :N] = x
     return s
 
 
-@pytest.mark.parametrize("mode", [1, 3, 4])
+@pytest.mark.parametrize("mode", [1, 3, 4, 6])
 def test_forward_and_inverse_match_cufft(env, mode):
     torch, pkg, lib, ctx = env
     assert lib.bym_set_fft_backend(ctx._h, mode) == 0
@@ -44,7 +44,7 @@ def test_forward_and_inverse_match_cufft(env, mode):
     buf = _slots(torch, x)
     torch.cuda.synchronize()
     assert lib.bym_fft3d(ctx._h, buf.data_ptr(), N, 2, 0, None) == 0
-    got = torch.view_as_complex(buf.view(2, N, N, N // 2 + 1, 2))
+    got = torch.view_as_complex(buf.view(2, N, N, N // 2 + 2, 2))[..., :N // 2 + 1]
     want = torch.fft.rfftn(x, dim=(1, 2, 3))
     err = (got - want).abs().max().item() / want.abs().max().item()
     rms = ((got - want).abs().pow(2).mean().sqrt() / want.abs().pow(2).mean().sqrt()).item()
@@ -57,7 +57,9 @@ def test_forward_and_inverse_match_cufft(env, mode):
     # inverse of a cuFFT spectrum against cuFFT's inverse
     spec = torch.fft.rfftn(x[:1], dim=(1, 2, 3))
     want_r = torch.fft.irfftn(spec, s=(N, N, N), dim=(1, 2, 3), norm="forward")
-    buf2 = torch.view_as_real(spec).clone().view(1, N, N, N + 2)
+    buf2 = torch.zeros(1, N, N, N // 2 + 2, 2, device=spec.device)
+    buf2[..., :N // 2 + 1, :] = torch.view_as_real(spec)
+    buf2 = buf2.view(1, N, N, N + 4)
     torch.cuda.synchronize()
     assert lib.bym_fft3d(ctx._h, buf2.data_ptr(), N, 1, 1, None) == 0
     err = (buf2[..., :N] - want_r).abs().max().item() / want_r.abs().max().item()
@@ -73,7 +75,9 @@ def cat():
 @pytest.mark.parametrize("los,K,mode,il", [("yamamoto", 0, 1, 0), ("midpoint", 4, 1, 0), ("bisector", 4, 1, 0),
                                            ("midpoint_even", 2, 1, 0), ("midpoint", 2, 3, 0), ("bisector", 2, 3, 0),
                                            ("midpoint", 4, 4, 0), ("bisector", 4, 4, 0), ("yamamoto", 0, 4, 0),
-                                           ("midpoint", 2, 4, 1), ("bisector", 2, 1, 1)])
+                                           ("midpoint", 2, 4, 1), ("bisector", 2, 1, 1),
+                                           ("yamamoto", 0, 6, 0), ("midpoint", 4, 6, 0), ("bisector", 4, 6, 0),
+                                           ("midpoint_even", 2, 6, 0), ("midpoint", 2, 6, 1)])
 def test_requests_native_vs_cufft(env, cat, los, K, mode, il):
     torch, pkg, lib, ctx = env
     p = pkg.make_params(box_lo=cat.box_lo, box_len=cat.box_len, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
@@ -88,7 +92,7 @@ def test_requests_native_vs_cufft(env, cat, los, K, mode, il):
     check_multipoles(out[mode]["xi"], out[0]["xi"], "xi", label=f"{los} xi: ")
 
 
-@pytest.mark.parametrize("mode", [1, 4])
+@pytest.mark.parametrize("mode", [1, 4, 6])
 def test_streamed_ranges_with_library_kernels(env, cat, mode):
     # midpoint g fields in ranges of 9 (slots 2.. of the request) through the library's kernels
     torch, pkg, lib, ctx = env
@@ -118,34 +122,45 @@ def test_xi_only_ranges_of_two(env, cat):
     out = {}
     ctx.set_field_chunk(2)
     try:
-        for mode in (0, 4):
+        for mode in (0, 4, 6):
             assert lib.bym_set_fft_backend(ctx._h, mode) == 0
             out[mode] = ctx.xi_multipoles(cat.gal, cat.ran, p, redges, ran_nbar=cat.ran_nbar)
     finally:
         ctx.set_field_chunk(0)
-    check_multipoles(out[4]["xi"], out[0]["xi"], "xi", label="xi-only ranges of two: ")
+    for mode in (4, 6):
+        check_multipoles(out[mode]["xi"], out[0]["xi"], "xi", label=f"xi-only ranges of two, mode {mode}: ")
 
 
-def _slab(rng, lo, box, n, x_ranges):
-    """n points uniform in the x slabs given (cell units) of the 512^3 mesh box, the middle half in y, z."""
+def _slab(rng, lo, box, n, x_ranges, y_ranges=None):
+    """n points uniform in the x slabs given (cell units) of the 512^3 mesh box, in y in the y slabs
+    given (cell units; default the middle half), the middle half in z."""
     h = box / N
     xs = np.concatenate([rng.uniform(a, b, n // len(x_ranges)) for a, b in x_ranges]) * h
-    yz = rng.uniform(0.25, 0.75, size=(len(xs), 2)) * box
-    pts = np.column_stack([xs, yz]) + lo[None, :]
+    if y_ranges is None:
+        ys = rng.uniform(0.25, 0.75, size=len(xs)) * box
+    else:
+        ys = np.concatenate([rng.uniform(a, b, n // len(y_ranges)) for a, b in y_ranges]) * h
+        ys = rng.permutation(ys)
+    zs = rng.uniform(0.25, 0.75, size=len(xs)) * box
+    pts = np.column_stack([xs, ys, zs]) + lo[None, :]
     return np.column_stack([pts, np.ones(len(pts))]).astype(np.float32)
 
 
-@pytest.mark.parametrize("geometry", ["wraps", "top", "middle"])
+@pytest.mark.parametrize("geometry", ["wraps", "top", "middle", "y wraps", "y top"])
 def test_occupied_plane_range_edges(env, geometry):
-    # the library x pass backend transforms only the occupied x planes forward: catalogs that wrap
-    # across the periodic x boundary (every plane range), a thin slab at the top of the mesh (the
-    # range shifted down to fit) and one in the middle, against the cuFFT backend
+    # the library x pass backends transform only the occupied x planes forward (and the library's
+    # own plane passes only the occupied rows y of them): catalogs that wrap across the periodic
+    # x boundary (every plane range), a thin slab at the top of the mesh (the range shifted down to
+    # fit) and one in the middle; then a slab wrapping in y and one at the top in y; against the
+    # cuFFT backend
     torch, pkg, lib, ctx = env
     lo, box = np.array([1000.0, 1000.0, 1000.0]), 1024.0
-    x_ranges = {"wraps": [(0.2, 2.5), (508.5, 511.8)], "top": [(500.3, 509.7)], "middle": [(200.2, 205.9)]}[geometry]
+    x_ranges = {"wraps": [(0.2, 2.5), (508.5, 511.8)], "top": [(500.3, 509.7)], "middle": [(200.2, 205.9)],
+                "y wraps": [(100.5, 140.5)], "y top": [(300.1, 330.9)]}[geometry]
+    y_ranges = {"y wraps": [(0.3, 3.5), (507.5, 511.6)], "y top": [(480.2, 511.4)]}.get(geometry)
     rng = np.random.default_rng(5)
-    gal = _slab(rng, lo, box, 20000, x_ranges)
-    ran = _slab(rng, lo, box, 200000, x_ranges)
+    gal = _slab(rng, lo, box, 20000, x_ranges, y_ranges)
+    ran = _slab(rng, lo, box, 200000, x_ranges, y_ranges)
     nbar = np.full(len(ran), len(gal) / (box ** 3 / 4 * 0.01), np.float32)
     h = box / N
     kedges = np.linspace(0.0, 0.8 * math.pi / h, 9)
@@ -154,10 +169,10 @@ def test_occupied_plane_range_edges(env, geometry):
         p = pkg.make_params(box_lo=lo, box_len=box, n_mesh=N, assign=3, ell_max=4, los=los, order=K,
                             compensate=True, precision=32)
         out = {}
-        for m in (0, 4, 5):
+        for m in (0, 4, 5, 6):
             assert lib.bym_set_fft_backend(ctx._h, m) == 0
             out[m] = ctx.pk_xi_multipoles(gal, ran, p, kedges, redges, ran_nbar=nbar)
-        for m in (4, 5):
+        for m in (4, 5, 6):
             check_multipoles(out[m]["pk"], out[0]["pk"], "pk", label=f"{geometry} {los} mode {m} P: ")
             check_multipoles(out[m]["xi"], out[0]["xi"], "xi", label=f"{geometry} {los} mode {m} xi: ")
     assert lib.bym_set_fft_backend(ctx._h, 1) == 0

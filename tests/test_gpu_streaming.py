@@ -78,7 +78,7 @@ def test_budget_turns_on_ranges(pkg, cap):
     p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=4, los="midpoint", order=4,
                         precision=32)
     full = pkg.footprint(p, len(cap.gal), len(cap.ran))
-    slot = N * N * (N + 2) * 4
+    slot = N * N * (N + 4) * 4
     ctx = pkg.Context(0)
     whole = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
     ctx.close()
@@ -139,7 +139,7 @@ def test_budget_turns_on_bisector_blocks(pkg, cap):
     p = pkg.make_params(box_lo=cap.box_lo, box_len=cap.box_len, n_mesh=N, ell_max=4, los="bisector", order=4,
                         precision=32)
     full = pkg.footprint(p, len(cap.gal), len(cap.ran))      # 1 + 49 + 15 slots
-    slot = N * N * (N + 2) * 4
+    slot = N * N * (N + 4) * 4
     ctx = pkg.Context(0)
     whole = ctx.pk_xi_multipoles(cap.gal, cap.ran, p, kedges, redges, ran_nbar=cap.ran_nbar)
     ctx.close()
