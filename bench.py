@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--los", default="midpoint,bisector", help="comma-separated LOS list (profiling runs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving / batching leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
-    ap.add_argument("--fft-backend", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--fft-backend", type=int, default=None, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="force an FFT backend (bym_set_fft_backend) instead of the tuned choice (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--order", type=int, default=ORDER, help="expansion order (4 is the benchmark; profiling runs)")
@@ -371,12 +371,12 @@ def _mock_subsets(torch, cat, gal_d, ran_d, rnb_d, rng, frac, half_angle_deg):
 
 def next_rows_leg(pkg, torch, dev, cat, gal_d, ran_d, rnb_d, n_mesh, reps=2):
     """The benchmark catalog at the benchmark mesh through the extensions beyond the paper's
-    boxed estimators (hybrid FFT backend), each timed (CUDA events, after one warm-up run)
+    boxed estimators (the library's FFT passes), each timed (CUDA events, after one warm-up run)
     beside its device footprint: the parity-even midpoint form; the midpoint g fields streamed in ranges of 45;
     the bisector fields in blocks of 16; xi normalised by the random-random count; interlacing; the
     cross spectra of two tracers (the catalog's even- and odd-numbered galaxies and randoms)."""
     ctx = pkg.Context(dev.index)
-    ctx.set_fft_backend(4)        # the FFT path the autotuner picks for the benchmark step
+    ctx.set_fft_backend(6)        # the library's FFT passes: the path the autotuner picks for the step
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     halves = [(t[0::2].contiguous(), t[1::2].contiguous()) for t in (gal_d, ran_d, rnb_d)]
