@@ -41,15 +41,20 @@ std::string lit(double v, bool f32) {
 
 // Declares variables P<l*l+l+nu> = Y_{l nu}(u) for l <= L from the unit vector
 // (ux, uy, uz); zm (0 or 1) zeroes every l > 0 term (the zero vector carries
-// Y = delta_{l0} / sqrt(4 pi)).
+// Y = delta_{l0} / sqrt(4 pi)).  Y_{l, +-m} = sqrt2 p_l^m(uz) Re / Im (ux + i uy)^m with p_l^m the
+// normalised associated-Legendre polynomial without its sin^m factor.  az32 (FP64 build of the
+// recurrence only): the recurrence over l runs in FP64, the azimuthal factor (ux + i uy)^m and
+// the products in FP32, and P<..> are floats.
 void emit_ylm(std::ostream &o, int L, bool f32, const std::string &P, const std::string &ux,
-              const std::string &uy, const std::string &uz, const std::string &zm) {
+              const std::string &uy, const std::string &uz, const std::string &zm, bool az32 = false) {
   const char *TY = f32 ? "float" : "double";
-  o << "  " << TY << " " << P << "c0 = 1, " << P << "s0 = 0;\n";
+  const char *TA = f32 || az32 ? "float" : "double";   // the azimuthal factor and the products
+  const std::string ax = az32 ? "(float)" + ux : ux, ay = az32 ? "(float)" + uy : uy;
+  o << "  " << TA << " " << P << "c0 = 1, " << P << "s0 = 0;\n";
   for (int m = 1; m <= L; ++m)
-    o << "  " << TY << " " << P << "c" << m << " = " << P << "c" << m - 1 << " * " << ux << " - " << P << "s"
-      << m - 1 << " * " << uy << ", " << P << "s" << m << " = " << P << "s" << m - 1 << " * " << ux << " + " << P
-      << "c" << m - 1 << " * " << uy << ";\n";
+    o << "  " << TA << " " << P << "c" << m << " = " << P << "c" << m - 1 << " * " << ax << " - " << P << "s"
+      << m - 1 << " * " << ay << ", " << P << "s" << m << " = " << P << "s" << m - 1 << " * " << ax << " + " << P
+      << "c" << m - 1 << " * " << ay << ";\n";
   for (int m = 0; m <= L; ++m) {
     if (m == 0)
       o << "  " << TY << " " << P << "p0_0 = " << lit(1.0 / std::sqrt(4.0 * M_PI), f32) << ";\n";
@@ -67,14 +72,17 @@ void emit_ylm(std::ostream &o, int L, bool f32, const std::string &P, const std:
     }
     for (int l = m; l <= L; ++l) {
       if (m == 0) {
-        o << "  " << TY << " " << P << l * l + l << " = " << P << "p" << l << "_0";
+        o << "  " << TA << " " << P << l * l + l << " = " << (az32 ? "(float)(" : "(") << P << "p" << l << "_0";
         if (l > 0) o << " * " << zm;
-        o << ";\n";
+        o << ");\n";
       } else {
-        o << "  " << TY << " " << P << l * l + l + m << " = " << lit(std::sqrt(2.0), f32) << " * " << P << "p" << l
-          << "_" << m << " * " << P << "c" << m << ";\n";
-        o << "  " << TY << " " << P << l * l + l - m << " = " << lit(std::sqrt(2.0), f32) << " * " << P << "p" << l
-          << "_" << m << " * " << P << "s" << m << ";\n";
+        // sqrt2 p_l^m once (in the recurrence's precision), then the azimuthal products
+        const std::string q = az32 ? "(float)(" + lit(std::sqrt(2.0), false) + " * " + P + "p" + std::to_string(l) +
+                                         "_" + std::to_string(m) + ")"
+                                   : lit(std::sqrt(2.0), f32) + " * " + P + "p" + std::to_string(l) + "_" +
+                                         std::to_string(m);
+        o << "  " << TA << " " << P << l * l + l + m << " = " << q << " * " << P << "c" << m << ";\n";
+        o << "  " << TA << " " << P << l * l + l - m << " = " << q << " * " << P << "s" << m << ";\n";
       }
     }
   }
@@ -188,7 +196,9 @@ void emit_bin_loop_head(std::ostream &o, const std::string &count_expr) {
 }
 
 // gen_fields kernel for fields [f0, f1) of the list, written to slots 0 .. f1 - f0 of out.
-void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldInfo> &list, int f0, int f1) {
+// f32: FP32 build (the azimuthal factor and the products in FP32, the Legendre recurrence in FP64).
+void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldInfo> &list, int f0, int f1,
+                     bool f32) {
   int Jmax = 0, amax = 0;
   for (int i = f0; i < f1; ++i) {
     Jmax = std::max(Jmax, list[i].J);
@@ -220,7 +230,7 @@ void emit_gen_fields(std::ostream &o, const char *name, const std::vector<FieldI
   if (amax > 0) o << "    const double q = r2 > 0.0 ? 1.0 / (2.0 * sqrt(r2) * inv_r0) : 0.0;\n";
   for (int a = 1; a <= amax; ++a) o << "    const double rad" << a << " = rad" << a - 1 << " * q;\n";
   for (int a = 0; a <= amax; ++a) o << "    const real rr" << a << " = (real)rad" << a << ";\n";
-  emit_ylm(o, Jmax, false, "y", "ux", "uy", "uz", "zm");
+  emit_ylm(o, Jmax, false, "y", "ux", "uy", "uz", "zm", f32);
   for (int i = f0; i < f1; ++i)
     o << "    out[" << i - f0 << "LL * slot + off] = (real)y" << ylm_index(list[i].J, list[i].nu) << " * rr"
       << list[i].alpha << ";\n";
@@ -477,7 +487,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
   o << kPrelude;
 
   // ------------------------------------------------------------------ gen_fields
-  emit_gen_fields(o, "gen_fields", F.list, 0, nf);
+  emit_gen_fields(o, "gen_fields", F.list, 0, nf, key.prec == 32);
 
   // ------------------------------------------------------------------ geometry
   o << "extern \"C\" __global__ void __launch_bounds__(256) kgeom(int N, const int* __restrict__ lut, int nbins,"
@@ -610,7 +620,8 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
   if (key.los == 2) {   // bisector: field blocks and one contraction per block pair a <= b
     const int nb = (int)ranges.size();
     for (int a = 0; a < nb; ++a) {
-      emit_gen_fields(o, ("gen_fields_c" + std::to_string(a)).c_str(), F.list, ranges[a].first, ranges[a].second);
+      emit_gen_fields(o, ("gen_fields_c" + std::to_string(a)).c_str(), F.list, ranges[a].first, ranges[a].second,
+                      key.prec == 32);
       for (int b = a; b < nb; ++b)
         emit_kcontract_pair(o, ("kcontract_p" + std::to_string(a) + "_" + std::to_string(b)).c_str(), key,
                             ranges[a].first, ranges[a].second, ranges[b].first, ranges[b].second);
@@ -621,7 +632,7 @@ std::string generate_chunk_source(const JitKey &key, int max_fields, ChunkSet *m
   const auto terms = midpoint_terms(key.ell_max, key.K, even);
   for (size_t q = 0; q < ranges.size(); ++q) {
     const std::string sfx = "_c" + std::to_string(q);
-    emit_gen_fields(o, ("gen_fields" + sfx).c_str(), F.list, ranges[q].first, ranges[q].second);
+    emit_gen_fields(o, ("gen_fields" + sfx).c_str(), F.list, ranges[q].first, ranges[q].second, key.prec == 32);
     emit_mid_combine(o, ("mid_combine" + sfx).c_str(), key, terms, ranges[q].first, ranges[q].second, q > 0);
     emit_xi_lag(o, ("xi_lag" + sfx).c_str(), key, ranges[q].first, ranges[q].second);
   }
@@ -712,7 +723,7 @@ std::string generate_odd_source(const JitKey &key, OddSet *meta) {
   std::ostringstream o;
   o << "typedef " << real << " real;\ntypedef " << real << "2 real2;\n";
   o << kPrelude;
-  emit_gen_fields(o, "gen_fields_odd", list, 0, nf);
+  emit_gen_fields(o, "gen_fields_odd", list, 0, nf, key.prec == 32);
 
   if (key.los == 1) {
     // midpoint: H_{l nu}(Delta) = sum phi Y_{J1}(Delta) t^alpha g^alpha_{J2}(Delta) over the odd-l g fields

@@ -2,11 +2,15 @@
 over 600-2000 Mpc/h, 512^3 TSC, bisector line of sight at order 6 (the
 memory-heaviest field set: 64 transforms), ell <= 4, FP32.
 
-At full size the oracle computes the monopole exactly (ell = 0 does not depend
-on the line of sight), so the order-6 bisector monopole is checked against the
-Yamamoto one; every multipole is then checked, and its error reported, against
-the FP64 oracle on a 1-in-50 subsample of the same catalog at 96^3."""
+Every multipole at full size is compared bin by bin with the FP64 oracle values in
+tests/golden/large512_bisector6.json (written by tests/golden/make_large512.py from
+oracle.streamed), with the error stated per multipole; the order-6 bisector monopole is also
+checked against the Yamamoto one (ell = 0 does not depend on the line of sight), and every
+multipole against the plain oracle on a 1-in-50 subsample of the same catalog at 96^3."""
+import hashlib
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -73,3 +77,35 @@ def test_per_multipole_error_against_oracle(pkg, big):
           "P", max_rel(got["pk"], want_p, "pk"), "xi", max_rel(got["xi"], want_x, "xi"))
     check_multipoles(got["pk"], want_p, "pk", label="P: ")
     check_multipoles(got["xi"], want_x, "xi", label="xi: ")
+
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large512_bisector6.json")
+
+
+def test_every_multipole_against_oracle_at_512(pkg, big):
+    torch = pytest.importorskip("torch")
+    with open(GOLD) as fh:
+        gold = json.load(fh)
+    fp = gold["catalog"]
+    for k, a in (("gal_sha256", big.gal), ("ran_sha256", big.ran), ("ran_nbar_sha256", big.ran_nbar)):
+        assert hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest() == fp[k], \
+            f"the catalog generator changed ({k}): regenerate the golden file"
+    kedges, redges = np.array(gold["kedges"]), np.array(gold["redges"])
+    g, r, rn = (torch.from_numpy(a).cuda() for a in (big.gal, big.ran, big.ran_nbar))
+    ctx = pkg.Context(0)
+    try:
+        p = pkg.make_params(box_lo=big.box_lo, box_len=big.box_len, n_mesh=gold["n_mesh"], assign=3,
+                            ell_max=gold["ell_max"], los="bisector", order=gold["order"], compensate=True,
+                            precision=32, norm=1)
+        got = ctx.pk_xi_multipoles(g, r, p, kedges, redges, ran_nbar=rn)
+    finally:
+        ctx.close()
+    want = gold["los"]["bisector"]
+    print("large workload, FP32 bisector order 6 at 512^3 vs FP64 oracle, max relative error per multipole "
+          "(ell = 0, 2, 4): P", max_rel(got["pk"], want["pk"], "pk"), "xi", max_rel(got["xi"], want["xi"], "xi"))
+    check_multipoles(got["pk"], want["pk"], "pk", label="P: ")
+    check_multipoles(got["xi"], want["xi"], "xi", label="xi: ")
+    np.testing.assert_array_equal(got["n_modes"], want["n_modes"])
+    np.testing.assert_array_equal(got["n_cells"], want["n_cells"])
+    np.testing.assert_allclose(got["k_mean"], want["k_mean"], rtol=1e-12)
+    np.testing.assert_allclose(got["r_mean"], want["r_mean"], rtol=1e-12)
