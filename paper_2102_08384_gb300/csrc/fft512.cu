@@ -473,7 +473,8 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 // record a fault in *fault and end the kernel once the copies in flight have landed.
 // ---------------------------------------------------------------------------
 constexpr int XC = 16;                              // columns per tile
-constexpr int XBR = 32;                             // rows per TMA box
+constexpr int XBR = 32;                             // rows per TMA box of a partial row range
+constexpr int XBW = 256;                            // rows per TMA box otherwise (the largest box)
 constexpr long long XNCOL = (long long)NM * HP;     // columns per slot
 constexpr long long XNT = XNCOL / XC;               // tiles per slot
 constexpr int YNT = (2 * HP + 2 * XC - 1) / (2 * XC);  // y pass: tiles of an x plane (16 full, 1 of kz 256, 257)
@@ -574,7 +575,8 @@ struct XtUnits {
 
 template <int MODE>
 __global__ void __launch_bounds__(256, 1)
-    fft512_xt(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmd, int nslots,
+    fft512_xt(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmw,
+              const __grid_constant__ CUtensorMap tmd, int nslots,
               XtUnits un, const float2 *__restrict__ gtw, const double *__restrict__ scale,
               const float *__restrict__ invw, int xlo, int xhi, unsigned *__restrict__ fault) {
   using L = XtLayout;
@@ -633,7 +635,11 @@ __global__ void __launch_bounds__(256, 1)
     int c0, c2;
     coords(u, f, c0, c2);
     mbar_expect_tx(bar + b, (unsigned)(hi - lo) * 128u);
-    for (int x0 = lo; x0 < hi; x0 += XBR) tma_load(sm + (size_t)b * XTILE + (size_t)x0 * 128, &tm, c0, x0, c2, bar + b);
+    for (int x0 = lo; x0 < hi;) {                   // boxes of XBW rows where they fit, else XBR
+      const bool wide = MODE != 2 && (x0 % XBW) == 0 && x0 + XBW <= hi;
+      tma_load(sm + (size_t)b * XTILE + (size_t)x0 * 128, wide ? &tmw : &tm, c0, x0, c2, bar + b);
+      x0 += wide ? XBW : XBR;
+    }
   };
   auto issue_d = [&](long long u) {
     mbar_expect_tx(bar + 2, (unsigned)NM * 128u);
@@ -746,7 +752,11 @@ __global__ void __launch_bounds__(256, 1)
       if (tid == 0) {
         int c0, c2;
         coords(u, f, c0, c2);
-        for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, c0, x0, c2, tile + (size_t)x0 * 128);
+        // wide boxes in modes 0 and 1; the convolution pass measured faster with narrow ones
+        if (MODE == 2)
+          for (int x0 = 0; x0 < NM; x0 += XBR) tma_store(&tm, c0, x0, c2, tile + (size_t)x0 * 128);
+        else
+          for (int x0 = 0; x0 < NM; x0 += XBW) tma_store(&tmw, c0, x0, c2, tile + (size_t)x0 * 128);
         bulk_commit();
         if (MODE == 2 && f == nf - 1 && u + gridDim.x < nunits) {   // D of the next position
           issue_d(u + gridDim.x);
@@ -1036,13 +1046,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // TMA map of n half-spectrum slots from base b: dims (2 NM HP floats of an x-plane, NM planes, n slots),
-// boxes of 32 floats (16 complex columns, 128 bytes) x 32 planes x 1 slot, 128-byte swizzle
-cudaError_t slot_map(CUtensorMap *m, float *b, long long slot_reals, int n) {
+// boxes of 32 floats (16 complex columns, 128 bytes) x `rows` planes x 1 slot, 128-byte swizzle
+cudaError_t slot_map(CUtensorMap *m, float *b, long long slot_reals, int n, int rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {(cuuint64_t)(2 * XNCOL), (cuuint64_t)NM, (cuuint64_t)n};
   const cuuint64_t strides[2] = {(cuuint64_t)(2 * XNCOL * sizeof(float)), (cuuint64_t)(slot_reals * sizeof(float))};
-  const cuuint32_t box[3] = {2 * XC, XBR, 1}, estr[3] = {1, 1, 1};
+  const cuuint32_t box[3] = {2 * XC, (cuuint32_t)rows, 1}, estr[3] = {1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, b, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -1057,30 +1067,31 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
     return cudaErrorInvalidValue;
   int dev = 0;
   cudaGetDevice(&dev);
-  CUtensorMap tm, tmd;
-  cudaError_t e = slot_map(&tm, b, slot_reals, n);
-  if (e == cudaSuccess) e = slot_map(&tmd, MODE == 2 ? (float *)D : b, slot_reals, 1);
+  CUtensorMap tm, tmw, tmd;
+  cudaError_t e = slot_map(&tm, b, slot_reals, n, XBR);
+  if (e == cudaSuccess) e = slot_map(&tmw, b, slot_reals, n, XBW);
+  if (e == cudaSuccess) e = slot_map(&tmd, MODE == 2 ? (float *)D : b, slot_reals, 1, XBR);
   if (e != cudaSuccess) return e;
   if (MODE == 2 && n > XtLayout::NSC) return cudaErrorInvalidValue;
   const long long units = MODE == 2 ? XNT : XNT * n;
   const long long grid = std::min<long long>(units, (long long)sm_count(dev));
   const XtUnits un{(long long)n, (int)XNT, 1, 1, 0};
-  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmd, n, un, tw, scale, invw, xlo, xhi,
+  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmw, tmd, n, un, tw, scale, invw, xlo, xhi,
                                                                 g_xfault[dev]);
   return cudaGetLastError();
 }
 
 // TMA map of the x planes of n slots from base b for the y pass: dims (2 HP floats of a row, NM
 // rows ky, NM n planes), the row stride 2064 bytes (a multiple of 16, which the padded layout
-// exists for) and the plane stride NM rows; boxes of 32 floats x 32 rows x 1 plane, 128-byte
+// exists for) and the plane stride NM rows; boxes of 32 floats x `rows` rows x 1 plane, 128-byte
 // swizzle.  The last tile of a row (kz 256 and the padding) lies partly outside dimension 0:
 // its loads read zeros there and its stores skip it.
-cudaError_t plane_map(CUtensorMap *m, float *b, int n) {
+cudaError_t plane_map(CUtensorMap *m, float *b, int n, int rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {(cuuint64_t)ROWF, (cuuint64_t)NM, (cuuint64_t)NM * (cuuint64_t)n};
   const cuuint64_t strides[2] = {(cuuint64_t)(ROWF * sizeof(float)), (cuuint64_t)(NM * ROWF * sizeof(float))};
-  const cuuint32_t box[3] = {2 * XC, XBR, 1}, estr[3] = {1, 1, 1};
+  const cuuint32_t box[3] = {2 * XC, (cuuint32_t)rows, 1}, estr[3] = {1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, b, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -1097,12 +1108,13 @@ cudaError_t ypass(float *b, long long slot_reals, int n, const float2 *tw, cudaS
   if (((unsigned long long)b & 15ull) || slot_reals != (long long)NM * NM * ROWF) return cudaErrorInvalidValue;
   int dev = 0;
   cudaGetDevice(&dev);
-  CUtensorMap tm;
-  cudaError_t e = plane_map(&tm, b, n);
+  CUtensorMap tm, tmw;
+  cudaError_t e = plane_map(&tm, b, n, XBR);
+  if (e == cudaSuccess) e = plane_map(&tmw, b, n, XBW);
   if (e != cudaSuccess) return e;
   const XtUnits un{(long long)n * (xhi - xlo), YNT, xhi - xlo, NM, xlo};
   const long long grid = std::min<long long>(un.nslab * YNT, (long long)sm_count(dev));
-  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tm, n, un, tw, nullptr, nullptr, ylo, yhi,
+  fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmw, tmw, n, un, tw, nullptr, nullptr, ylo, yhi,
                                                                 g_xfault[dev]);
   return cudaGetLastError();
 }
