@@ -617,6 +617,7 @@ __global__ void __launch_bounds__(256, 1)
   for (int a = 0; a < 8; ++a) tw.t1[a] = TW[a * ES + j];
 #pragma unroll
   for (int b = 0; b < 4; ++b) tw.t8[b] = TW[8 * b * ES + j];
+  const TabTw ttw{TW, j, kb};   // mode 2: every twiddle read from the shared table
 
   // item i = (unit u, field f): modes 0, 1 take the tiles of every slot (f = 0), mode 2 the
   // positions with every field; data buffer i % NDB, whose barrier completes once per use
@@ -706,7 +707,10 @@ __global__ void __launch_bounds__(256, 1)
         const int mlo = lo >> 4, mhi = hi >> 4;
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = (m >= mlo && m < mhi) ? col.at(16 * m + j) : make_float2(0.f, 0.f);
-        fwd512x(v, As, Bs, j, gm, tw, col);
+        if (MODE == 2)
+          fwd512x(v, As, Bs, j, gm, ttw, col);
+        else
+          fwd512x(v, As, Bs, j, gm, tw, col);
       }
       if (MODE == 2) {
         const XtCol dcol{sm + (size_t)2 * XTILE, g};
@@ -742,7 +746,10 @@ __global__ void __launch_bounds__(256, 1)
           col.at(kb + 32 * k2) = Bs[k2];
         }
       } else {
-        inv512x(As, Bs, v, j, gm, tw, col);
+        if (MODE == 2)
+          inv512x(As, Bs, v, j, gm, ttw, col);
+        else
+          inv512x(As, Bs, v, j, gm, tw, col);
         __syncwarp(gm);
 #pragma unroll
         for (int m = 0; m < 32; ++m) col.at(16 * m + j) = v[m];
