@@ -496,18 +496,6 @@ __device__ __forceinline__ unsigned xt_off(int x, int c) {
   return (unsigned)(x * 128 + ((((c >> 1) ^ x) & 7) << 4) + ((c & 1) << 3));
 }
 
-// Twiddles of the x pass: thread j keeps W512^(a j) (a < 8) and W512^(8 b j) (b < 4) in registers
-// and forms W512^(k j) = W512^(8 (k / 8) j) W512^((k mod 8) j) with one complex multiply (about
-// two roundings instead of one); the kb half of the inverse reads the shared table.
-struct RegTw {
-  float2 t1[8], t8[4];
-  const float2 *TW;
-  int kb;
-  __device__ __forceinline__ float2 fwd(int k) const { return (k >> 3) ? cmul(t8[k >> 3], t1[k & 7]) : t1[k & 7]; }
-  __device__ __forceinline__ float2 inv_a(int n1) const { return fwd(n1); }
-  __device__ __forceinline__ float2 inv_b(int n1) const { return TW[kb * ES + n1]; }
-};
-
 struct XtCol {                                      // one column of a swizzled tile
   unsigned char *tile;
   int c;
@@ -610,14 +598,7 @@ __global__ void __launch_bounds__(256, 1)
   if (MODE == 2)
     for (int i = tid; i < nf; i += blockDim.x) SC[i] = (float)scale[i];
   __syncthreads();
-  RegTw tw;
-  tw.TW = TW;
-  tw.kb = kb;
-#pragma unroll
-  for (int a = 0; a < 8; ++a) tw.t1[a] = TW[a * ES + j];
-#pragma unroll
-  for (int b = 0; b < 4; ++b) tw.t8[b] = TW[8 * b * ES + j];
-  const TabTw ttw{TW, j, kb};   // mode 2: every twiddle read from the shared table
+  const TabTw ttw{TW, j, kb};   // twiddles read from the shared table (no registers held for them)
 
   // item i = (unit u, field f): modes 0, 1 take the tiles of every slot (f = 0), mode 2 the
   // positions with every field; data buffer i % NDB, whose barrier completes once per use
@@ -707,10 +688,7 @@ __global__ void __launch_bounds__(256, 1)
         const int mlo = lo >> 4, mhi = hi >> 4;
 #pragma unroll
         for (int m = 0; m < 32; ++m) v[m] = (m >= mlo && m < mhi) ? col.at(16 * m + j) : make_float2(0.f, 0.f);
-        if (MODE == 2)
-          fwd512x(v, As, Bs, j, gm, ttw, col);
-        else
-          fwd512x(v, As, Bs, j, gm, tw, col);
+        fwd512x(v, As, Bs, j, gm, ttw, col);
       }
       if (MODE == 2) {
         const XtCol dcol{sm + (size_t)2 * XTILE, g};
@@ -746,10 +724,7 @@ __global__ void __launch_bounds__(256, 1)
           col.at(kb + 32 * k2) = Bs[k2];
         }
       } else {
-        if (MODE == 2)
-          inv512x(As, Bs, v, j, gm, ttw, col);
-        else
-          inv512x(As, Bs, v, j, gm, tw, col);
+        inv512x(As, Bs, v, j, gm, ttw, col);
         __syncwarp(gm);
 #pragma unroll
         for (int m = 0; m < 32; ++m) col.at(16 * m + j) = v[m];
@@ -843,13 +818,7 @@ __global__ void __launch_bounds__(256, 1)
   }
   for (int i = tid; i < EX; i += blockDim.x) TW[i] = gtw[i];
   __syncthreads();
-  RegTw tw;
-  tw.TW = TW;
-  tw.kb = kb;
-#pragma unroll
-  for (int a = 0; a < 8; ++a) tw.t1[a] = TW[a * ES + j];
-#pragma unroll
-  for (int b = 0; b < 4; ++b) tw.t8[b] = TW[8 * b * ES + j];
+  const TabTw tw{TW, j, kb};    // twiddles read from the shared table
 
   auto block = [&](long long u) -> float * {
     const long long q = u / nyb;
