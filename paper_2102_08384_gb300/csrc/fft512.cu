@@ -466,8 +466,11 @@ __global__ void __launch_bounds__(PlaneShape<CL>::NT, PlaneShape<CL>::MINB)
 // column; the exchange of the 512-point engine runs in place in that column's own storage (slot
 // (a, b) at row 16 a + (b ^ (a % 16))), which keeps every shared access of a warp at two
 // wavefronts, one per half-warp.
-// Persistent: one 256-thread CTA per SM.  Modes 0 and 1 keep three tile buffers (load of the
-// next tile, transform of this one, store of the previous one in flight); mode 2 keeps two data
+// Persistent: one 256-thread CTA per SM.  Modes 0 and 1 keep three tile buffers.  In the x pass,
+// once a tile's store is issued the load of the tile two items ahead goes into the buffer the
+// previous store has left, so two loads are in flight while the CTA waits for the next tile; the
+// y pass (whose tiles share DRAM rows with their neighbours) measured faster with one: its next
+// tile loads while this one is transformed.  Mode 2 keeps two data
 // buffers and the tile of D, walks the tile positions and, at each one, every field of the launch,
 // so D is read once per launch.  Waits on the tile barriers give up after about two seconds,
 // record a fault in *fault and end the kernel once the copies in flight have landed.
@@ -559,6 +562,7 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 struct XtUnits {
   long long nslab;
   int ntile, np, sstride, s0;
+  int ahead;       // modes 0, 1: tiles loading ahead of the one transformed (2: x pass, 1: y pass)
 };
 
 template <int MODE>
@@ -637,6 +641,9 @@ __global__ void __launch_bounds__(256, 1)
     if (MODE == 2) {
       issue_d(u);
       pend |= 4u;
+    } else if (un.ahead == 2 && u + gridDim.x < nunits) {   // two tiles ahead from the start
+      issue_data(u + gridDim.x, 0, 1);
+      pend |= 2u;
     }
   }
   bool ok = true;
@@ -654,7 +661,7 @@ __global__ void __launch_bounds__(256, 1)
         if (MODE == 2 && f == 0) pend &= ~4u;
       }
       unsigned char *tile = sm + (size_t)b * XTILE;
-      if (tid == 0) {                                // prefetch the next item
+      if ((MODE == 2 || un.ahead == 1) && tid == 0) {   // prefetch the next item
         long long un = u;
         int fn = f + 1;
         if (fn >= nf) {
@@ -740,6 +747,13 @@ __global__ void __launch_bounds__(256, 1)
         else
           for (int x0 = 0; x0 < NM; x0 += XBW) tma_store(&tmw, c0, x0, c2, tile + (size_t)x0 * 128);
         bulk_commit();
+        if (MODE != 2 && un.ahead == 2 && u + 2 * gridDim.x < nunits) {   // the tile two items ahead
+          const int b2 = (int)((i + 2) % NDB);
+          bulk_wait_read<1>();                       // the store of item i - 1 (buffer b2) has read its tile
+          issue_data(u + 2 * gridDim.x, 0, b2);
+          pend |= 1u << b2;
+          ppar = (ppar & ~(1u << b2)) | ((unsigned)(((i + 2) / NDB) & 1) << b2);
+        }
         if (MODE == 2 && f == nf - 1 && u + gridDim.x < nunits) {   // D of the next position
           issue_d(u + gridDim.x);
           pend |= 4u;
@@ -1051,7 +1065,7 @@ cudaError_t xpass(float *b, long long slot_reals, int n, const float2 *tw, const
   if (MODE == 2 && n > XtLayout::NSC) return cudaErrorInvalidValue;
   const long long units = MODE == 2 ? XNT : XNT * n;
   const long long grid = std::min<long long>(units, (long long)sm_count(dev));
-  const XtUnits un{(long long)n, (int)XNT, 1, 1, 0};
+  const XtUnits un{(long long)n, (int)XNT, 1, 1, 0, 2};
   fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmw, tmd, n, un, tw, scale, invw, xlo, xhi,
                                                                 g_xfault[dev]);
   return cudaGetLastError();
@@ -1088,7 +1102,7 @@ cudaError_t ypass(float *b, long long slot_reals, int n, const float2 *tw, cudaS
   cudaError_t e = plane_map(&tm, b, n, XBR);
   if (e == cudaSuccess) e = plane_map(&tmw, b, n, XBW);
   if (e != cudaSuccess) return e;
-  const XtUnits un{(long long)n * (xhi - xlo), YNT, xhi - xlo, NM, xlo};
+  const XtUnits un{(long long)n * (xhi - xlo), YNT, xhi - xlo, NM, xlo, 1};
   const long long grid = std::min<long long>(un.nslab * YNT, (long long)sm_count(dev));
   fft512_xt<MODE><<<(unsigned)grid, 256, XtLayout::BYTES, st>>>(tm, tmw, tmw, n, un, tw, nullptr, nullptr, ylo, yhi,
                                                                 g_xfault[dev]);
