@@ -11,7 +11,7 @@ library's cluster plane pass, cuFFT plane transforms with the library's x pass, 
 plus cuFFT transforms along x; and the memory-bounded forms: midpoint g fields in ranges of 45
 and bisector fields in blocks of 16.
 
-Tolerances (the benchmark spec): 1e-5 relative on P_0 and xi_0; 1e-4 relative on ell = 2, 4 where
+Tolerances: 1e-5 relative on P_0 and xi_0; 1e-4 relative on ell = 2, 4 where
 |X_ell| exceeds 1 % of the monopole scale, 1e-4 of that scale elsewhere."""
 import hashlib
 import json
