@@ -523,7 +523,8 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
 
   // ------------------------------------------------------------------ k-space contraction
   auto emit_kcontract = [&](const char *name, bool with_x) {
-    o << "extern \"C\" __global__ void __launch_bounds__(256) " << name
+    // the bisector form with X written holds ~140 registers unbounded: two blocks per SM (16 warps)
+    o << "extern \"C\" __global__ void __launch_bounds__(256" << (with_x ? ", 2" : "") << ") " << name
       << "(const real2* __restrict__ F, long long cslot, const real2* __restrict__ D, int N,"
          " const int* __restrict__ lut, int nbins, double* __restrict__ gsum, real2* __restrict__ xout,"
          " long long xslot, const real* __restrict__ invw) {\n";
