@@ -457,7 +457,7 @@ void emit_kcontract_pair(std::ostream &o, const char *name, const JitKey &key, i
   o << "          const double ux = nx * ir, uy = ny * ir, uz = nz * ir; const double zm = 1.0;\n";
   {
     std::ostringstream yy;
-    emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm");
+    emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm", f32);
     std::istringstream is(yy.str());
     std::string line;
     while (std::getline(is, line)) o << "        " << line << "\n";
@@ -574,7 +574,7 @@ std::string generate_source(const JitKey &key, KernelSet *meta) {
     o << "          const double ux = nx * ir, uy = ny * ir, uz = nz * ir; const double zm = 1.0;\n";
     {
       std::ostringstream yy;
-      emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm");
+      emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm", f32);
       std::string s = yy.str();
       std::istringstream is(s);
       std::string line;
@@ -697,7 +697,7 @@ void emit_k_tail(std::ostream &o, int L, bool f32, int NLo) {
   o << "          const double ux = nx * ir, uy = ny * ir, uz = nz * ir; const double zm = 1.0;\n";
   {
     std::ostringstream yy;
-    emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm");
+    emit_ylm(yy, L, false, "yk", "ux", "uy", "uz", "zm", f32);
     std::istringstream is(yy.str());
     std::string line;
     while (std::getline(is, line)) o << "        " << line << "\n";
